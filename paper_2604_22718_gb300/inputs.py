@@ -1,0 +1,159 @@
+"""Seeded synthetic inputs for the RTT sampler.
+
+This module only *generates data*: lattice orderings, bond lists, RTT tensors
+and initial spin configurations.  It contains none of the method's arithmetic
+(no amplitude, ratio, energy or acceptance computation), so both the CUDA path
+and the FP64 oracle may consume what it produces.
+
+Workloads (2D transverse-field Ising model on open Lx x Ly lattices, Sec. 4,
+Eq. ising-model; RTT path = a lattice ordering repeated R times, the path sum
+of Sec. 2.2.1):
+
+* ``tiny_fp64``   3x3, R=2, chi=8,   h=3.0,   iid N(0,1)/sqrt(chi) tensors
+* ``plain_6x6``   6x6, R=2, chi=64,  h=3.0,   Gaussian/sqrt(chi) x Haar Q_k
+* ``prec_10x10``  10x10, R=3, chi=128, h=3.04, same generator
+* ``learned_16x16`` 16x16, R=2, chi=128, h=3.044, same generator
+* ``batched64``   64 instances, Lx in {4,6,8,12}, R in {2,3,4},
+                  chi in {32,64,128,256}, h ~ U[2.5,3.5]
+
+All randomness comes from ``numpy.random.Generator(PCG64(seed))``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+__all__ = [
+    "RTTInstance", "snake_order", "open_bonds", "periodic_path",
+    "gaussian_tensors", "mixed_tensors", "make_instance", "initial_spins",
+    "WORKLOADS", "workload", "batched_instances",
+]
+
+
+@dataclasses.dataclass
+class RTTInstance:
+    """Plain container for one RTT state and its TFIM Hamiltonian."""
+    n_spins: int
+    path: np.ndarray        # int32 [L], path[k] = spin tied to train site k
+    tensors: np.ndarray     # float64 [L][2][chi][chi], A_k[s][a][b]
+    b_left: np.ndarray      # float64 [chi]
+    b_right: np.ndarray     # float64 [chi]
+    bonds: np.ndarray       # int32 [n_bonds][2]
+    J: float
+    h: float
+    name: str = ""
+    lx: int = 0
+    ly: int = 0
+    R: int = 0
+
+    @property
+    def length(self) -> int:
+        return int(self.path.shape[0])
+
+    @property
+    def chi(self) -> int:
+        return int(self.tensors.shape[2])
+
+
+def snake_order(lx: int, ly: int) -> np.ndarray:
+    """Boustrophedon ordering of an lx x ly lattice, site index i = y*lx + x.
+
+    Row y is walked left-to-right for even y and right-to-left for odd y."""
+    out = []
+    for y in range(ly):
+        xs = range(lx) if y % 2 == 0 else range(lx - 1, -1, -1)
+        out.extend(y * lx + x for x in xs)
+    return np.asarray(out, dtype=np.int32)
+
+
+def open_bonds(lx: int, ly: int) -> np.ndarray:
+    """Nearest-neighbour bonds of an open lx x ly square lattice."""
+    b = []
+    for y in range(ly):
+        for x in range(lx):
+            i = y * lx + x
+            if x + 1 < lx:
+                b.append((i, i + 1))
+            if y + 1 < ly:
+                b.append((i, i + lx))
+    return np.asarray(b, dtype=np.int32).reshape(-1, 2)
+
+
+def periodic_path(order: np.ndarray, R: int) -> np.ndarray:
+    """The ordering repeated R times (path sum of R copies)."""
+    return np.tile(np.asarray(order, dtype=np.int32), R)
+
+
+def gaussian_tensors(rng: np.random.Generator, L: int, chi: int) -> np.ndarray:
+    """A_k[s][a][b] i.i.d. N(0,1)/sqrt(chi)."""
+    return rng.standard_normal((L, 2, chi, chi)) / np.sqrt(chi)
+
+
+def _haar_orthogonal(rng: np.random.Generator, chi: int) -> np.ndarray:
+    g = rng.standard_normal((chi, chi))
+    q, r = np.linalg.qr(g)
+    d = np.sign(np.diag(r))
+    d[d == 0] = 1.0
+    return q * d[None, :]
+
+
+def mixed_tensors(rng: np.random.Generator, L: int, chi: int) -> np.ndarray:
+    """A_k[s] = (G_k[s]/sqrt(chi)) Q_k with one Haar-random orthogonal Q_k per site."""
+    g = rng.standard_normal((L, 2, chi, chi)) / np.sqrt(chi)
+    out = np.empty_like(g)
+    for k in range(L):
+        q = _haar_orthogonal(rng, chi)
+        out[k, 0] = g[k, 0] @ q
+        out[k, 1] = g[k, 1] @ q
+    return out
+
+
+def make_instance(lx: int, ly: int, R: int, chi: int, h: float, seed: int,
+                  mixing: bool = True, J: float = 1.0, name: str = "") -> RTTInstance:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    order = snake_order(lx, ly)
+    path = periodic_path(order, R)
+    L = path.shape[0]
+    t = mixed_tensors(rng, L, chi) if mixing else gaussian_tensors(rng, L, chi)
+    ones = np.ones(chi, dtype=np.float64)
+    return RTTInstance(n_spins=lx * ly, path=path, tensors=np.ascontiguousarray(t),
+                       b_left=ones.copy(), b_right=ones.copy(),
+                       bonds=open_bonds(lx, ly), J=float(J), h=float(h), name=name,
+                       lx=lx, ly=ly, R=R)
+
+
+def initial_spins(seed: int, n_chains: int, n_spins: int) -> np.ndarray:
+    """uint8 [n_chains][n_spins], uniform random bits (seed stream separate from tensors)."""
+    rng = np.random.Generator(np.random.PCG64([seed, 0x5350494e]))
+    return rng.integers(0, 2, size=(n_chains, n_spins), dtype=np.uint8)
+
+
+# name -> (lx, ly, R, chi, h, mixing, chains, sweeps, seed)
+WORKLOADS = {
+    "tiny_fp64":     dict(lx=3, ly=3, R=2, chi=8, h=3.0, mixing=False, chains=64, sweeps=1000, seed=22719),
+    "plain_6x6":     dict(lx=6, ly=6, R=2, chi=64, h=3.0, mixing=True, chains=4096, sweeps=2000, seed=22720),
+    "prec_10x10":    dict(lx=10, ly=10, R=3, chi=128, h=3.04, mixing=True, chains=16384, sweeps=1000, seed=22721),
+    "learned_16x16": dict(lx=16, ly=16, R=2, chi=128, h=3.044, mixing=True, chains=8192, sweeps=128, seed=22723),
+}
+
+
+def workload(name: str, **override) -> RTTInstance:
+    w = dict(WORKLOADS[name])
+    w.update(override)
+    return make_instance(w["lx"], w["ly"], w["R"], w["chi"], w["h"], w["seed"],
+                         mixing=w["mixing"], name=name)
+
+
+def batched_instances(seed: int = 22722, n: int = 64, chi_choices=(32, 64, 128, 256),
+                      sizes=(4, 6, 8, 12), reps=(2, 3, 4)) -> list:
+    """64 independent instances with lattice, R, chi and h drawn from the seed."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for t in range(n):
+        lx = int(rng.choice(sizes))
+        R = int(rng.choice(reps))
+        chi = int(rng.choice(chi_choices))
+        h = float(rng.uniform(2.5, 3.5))
+        out.append(make_instance(lx, lx, R, chi, h, seed * 1000 + t, mixing=True,
+                                 name=f"batched[{t}]"))
+    return out
