@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the RTT Monte Carlo hot path on GB300.
+
+One *step* is one Monte Carlo iteration of every chain of the workload: one
+systematic single-spin Metropolis sweep followed by one local-energy
+evaluation (Sec. 3.3; TFIM of Sec. 4), i.e. one local-energy sample per
+chain.  Default workload: 6x6 open TFIM (N = 36, h = 3.0), R = 2 (L = 72),
+chi = 64, 4096 chains; synthetic seeded tensors.
+
+value        local-energy samples/s = chains x steps / summed device step time
+e2e          the same through host buffers: every step copies the chains'
+             spins and amplitudes from pinned host memory, runs the step and
+             copies E_loc, spins and amplitudes back (all inside the timing)
+roofline     dominant kernel: algorithmic flops per launch / its mean launch
+             time (library event profiler on the launching stream) against
+             the FP32 (or FP64) CUDA-core peak, or the measured bf16 tensor peak
+cpu_baseline the FP64 oracle on this host's cores, bounded sample
+
+--impl reference runs the FP64 CPU oracle as the reference arm.
+Multi-GPU (torchrun): independent chain shards per rank (chain0 = rank * B),
+weak scaling, no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("local-energy samples/s & effective samples/s at ≤1e-4 rel. energy error, 1 GB300")
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+FP64_LANES_PER_SM = 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="plain_6x6")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x3"])
+    ap.add_argument("--chains", type=int, default=0, help="override the workload's chain count")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- algorithmic work
+def site_steps(N: int, R: int, kernel: str) -> int:
+    """Row-site vector-matrix products one chain needs in one launch."""
+    span = (R - 1) * N + 1
+    if kernel in ("simt_sweep", "tc_sweep"):
+        return (N - 1) + N * span + N            # right env + flip rows + l_j update
+    if kernel in ("simt_rows", "tc_rows"):
+        return N * span + (R - 1) * N            # N flip rows + the unflipped row
+    if kernel in ("simt_right_env", "tc_right_env"):
+        return N - 1
+    if kernel in ("simt_left_env", "tc_left_env"):
+        return N
+    if kernel in ("simt_chain_init", "tc_chain_init"):
+        return R * N
+    return 0
+
+
+# ---------------------------------------------------------------- reference arm (oracle)
+def run_reference(args):
+    from oracle import oracle as orc
+    from paper_2604_22718_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    inst = inputs.workload(args.workload)
+    o = orc.Oracle(inst)
+    cores = os.cpu_count() or 1
+    per_step = max(cores, 16)
+    spins = inputs.initial_spins(w["seed"], per_step, inst.n_spins)
+    mant, ex = o.init_chains(spins)
+    t_total = 0.0
+    for t in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        o.mcmc(w["seed"], spins, mant, ex, t, 1, measure_every=1, threads=cores)
+        dt = time.perf_counter() - t0
+        if t >= args.warmup:
+            t_total += dt
+    value = per_step * args.steps / t_total
+    line = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": _workload_desc(args.workload, inst, per_step), "chains": per_step,
+                   "sample": f"{per_step} chains per step (bounded sample of the "
+                             f"{w['chains']}-chain workload), 1 sweep + E_loc each"},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} chains x {args.steps} steps"},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _workload_desc(name, inst, chains):
+    R = inst.path.shape[0] // inst.n_spins
+    return (f"{name}: {inst.lx}x{inst.ly} open TFIM N={inst.n_spins} J={inst.J} h={inst.h}, "
+            f"R={R} L={inst.path.shape[0]} chi={inst.chi}, {chains} chains, "
+            f"1 sweep + E_loc per step")
+
+
+def cpu_baseline(inst, w, seed):
+    """The FP64 oracle on this host's cores: ~15 s of CPU work."""
+    from oracle import oracle as orc
+    from paper_2604_22718_gb300 import inputs
+    o = orc.Oracle(inst)
+    cores = os.cpu_count() or 1
+    cal = max(cores, 8)
+    spins = inputs.initial_spins(seed + 1, cal, inst.n_spins)
+    mant, ex = o.init_chains(spins)
+    t0 = time.perf_counter()
+    o.mcmc(seed, spins, mant, ex, 0, 1, measure_every=1, threads=cores)
+    dt = time.perf_counter() - t0
+    cpu_per_chain = dt * cores / cal
+    n = int(min(20000, max(cal, 15.0 / max(cpu_per_chain, 1e-6))))
+    n = max(cores, (n // cores) * cores)
+    spins = inputs.initial_spins(seed + 2, n, inst.n_spins)
+    mant, ex = o.init_chains(spins)
+    t0 = time.perf_counter()
+    o.mcmc(seed, spins, mant, ex, 0, 1, measure_every=1, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} chains x 1 sweep + E_loc (FP64 oracle, {cores} threads, "
+                      f"{dt:.1f} s wall)"}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_2604_22718_gb300 import inputs, rtt
+
+    w = inputs.WORKLOADS[args.workload]
+    inst = inputs.workload(args.workload)
+    B = args.chains or w["chains"]
+    N = inst.n_spins
+    R = inst.path.shape[0] // N
+    chain0 = rank * B
+    m = rtt.RTT(inst, args.precision, seed=w["seed"])
+    m.reserve(B)
+    spins = torch.from_numpy(inputs.initial_spins(w["seed"], B, N)).cuda()
+    # chains of other ranks: distinct start configurations, same generator
+    if rank:
+        spins = torch.from_numpy(inputs.initial_spins(w["seed"] + 7919 * rank, B, N)).cuda()
+    _, _, state = m.log_amplitudes(spins)
+    K, W = args.steps, args.warmup
+    trace = torch.empty((K, B), dtype=torch.float64, device="cuda")
+    scratch_row = torch.empty((1, B), dtype=torch.float64, device="cuda")
+    acc = torch.zeros(B, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sweep = 0
+    for _ in range(W):
+        m.mcmc_sweep(spins, state, sweep, 1, 1, scratch_row, None, chain0=chain0)
+        sweep += 1
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(dev)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    m.profile(True)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for t in range(K):
+        flush.zero_()                       # L2 flush outside the timed events
+        starts[t].record(stream)
+        m.mcmc_sweep(spins, state, sweep, 1, 1, trace[t:t + 1], acc, chain0=chain0)
+        ends[t].record(stream)
+        sweep += 1
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    prof = m.profile_read()
+    m.profile(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if dist:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        dist.barrier()
+    value = world * B * K / (total_ms / 1e3)
+    stats = m.observables(trace, acc, K * N)
+    ess_per_s = world * stats["ess"] / (total_ms / 1e3)
+
+    # dominant kernel roofline
+    peaks, peak_kind = measured_peaks()
+    dom = max((k for k in prof if k != "eloc_reduce"), key=lambda k: prof[k][1]) if prof else None
+    roof = None
+    if dom:
+        launches, ms = prof[dom]
+        flops = 2.0 * inst.chi * inst.chi * site_steps(N, R, dom) * B
+        achieved = flops / (ms / launches / 1e3) / 1e12
+        if args.precision == "bf16x3":
+            peak = peaks["bf16_tflops_sustained"] / 1.0
+            bound, pk = "tensor", f"bf16 sustained, {peak_kind}"
+        else:
+            lanes = FP32_LANES_PER_SM if args.precision == "fp32" else FP64_LANES_PER_SM
+            peak = SM_COUNT * lanes * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            bound, pk = "alu", (f"{args.precision} CUDA-core fma peak: {SM_COUNT} SMs x {lanes} "
+                                f"lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz")
+        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "peak_source": pk, "flops_per_launch": flops,
+                "launch_ms": ms / launches,
+                "kernel_share": ms / sum(v[1] for v in prof.values())}
+    launches_total = sum(v[0] for v in prof.values())
+
+    # end to end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        spins_h = spins.cpu().pin_memory()
+        state_h = state.cpu().pin_memory()
+        eloc_h = torch.empty((1, B), dtype=torch.float64).pin_memory()
+        spins_d = torch.empty_like(spins)
+        state_d = torch.empty_like(state)
+        row_d = torch.empty((1, B), dtype=torch.float64, device="cuda")
+        e_st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        e_en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        torch.cuda.synchronize()
+        for t in range(K):
+            flush.zero_()
+            e_st[t].record(stream)
+            spins_d.copy_(spins_h, non_blocking=True)
+            state_d.copy_(state_h, non_blocking=True)
+            m.mcmc_sweep(spins_d, state_d, sweep, 1, 1, row_d, None, chain0=chain0)
+            eloc_h.copy_(row_d, non_blocking=True)
+            spins_h.copy_(spins_d, non_blocking=True)
+            state_h.copy_(state_d, non_blocking=True)
+            e_en[t].record(stream)
+            sweep += 1
+        torch.cuda.synchronize()
+        e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_st, e_en))
+        if dist:
+            tt = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tt.item())
+        e2e = {"value": world * B * K / (e2e_ms / 1e3), "unit": "samples/s",
+               "h2d_bytes_per_step": B * N + 16 * B,
+               "d2h_bytes_per_step": 8 * B + B * N + 16 * B}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": _workload_desc(args.workload, inst, B), "chains_per_gpu": B,
+                       "precision": args.precision, "parallelism": f"replicas over chains x{world}",
+                       "l2": "flushed (256 MiB write) between timed steps, outside the events"},
+            "ess_per_s": ess_per_s, "tau_int": stats["tau_int"], "accept_rate": stats["accept_rate"],
+            "e_mean": stats["mean"], "e_se": stats["se"], "v_score": stats["v_score"],
+            "roofline": roof, "gpu_launches": launches_total,
+            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
+            "clocks": clk, "e2e": e2e, "wall_s_timed_region": t_wall,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(inst, w, w["seed"])
+        print(json.dumps(line), flush=True)
+    m.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        run_reference(args)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * rtt.h -- C ABI of the GB300 replica-tensor-train (RTT) Monte Carlo library.
+ *
+ * An RTT (arxiv 2604.22718, Sec. 2.2.1, Eq. RTT) is a tensor train of length
+ * L whose site k carries two chi x chi matrices A_k[0], A_k[1] and is tied to
+ * physical spin path[k]:
+ *
+ *     psi(s) = b_L^T A_0[s_path(0)] A_1[s_path(1)] ... A_{L-1}[s_path(L-1)] b_R
+ *
+ * (the trace of Eq. RTT with the first and last bond of dimension one, Sec.
+ * 2.1, written with boundary vectors b_L, b_R).  The library samples
+ * P(s) = |psi(s)|^2 / Z with single-spin Metropolis (Sec. 3.3) over many
+ * independent chains and evaluates the transverse-field Ising local energy
+ *
+ *     E_loc(s) = J sum_<ij> z_i z_j - h sum_i psi(s^(i)) / psi(s)
+ *
+ * (Sec. 3.3, mixed local energy with psi^1 = psi^2; Hamiltonian Sec. 4, Eq.
+ * ising-model), z_i = 1 - 2 s_i, s^(i) = s with spin i flipped.
+ *
+ * Conventions shared by all calls
+ *   - Spins are uint8 in {0,1}, row-major [B][N] (chain-major).
+ *   - Pointers documented "device" must be device memory of the handle's GPU;
+ *     "host" pointers are read before the call returns.
+ *   - Every call is asynchronous and ordered on `stream` (a cudaStream_t;
+ *     NULL = the legacy default stream) unless documented otherwise.
+ *   - Amplitudes are kept as psi = mant * 2^exp2 with |mant| in [1,2); the
+ *     exponent is an exact integer sum of per-site power-of-two rescalings, so
+ *     no train length over- or underflows.
+ *   - Supported paths: periodic ones, path[k] = path[k mod N] with
+ *     path[0..N-1] a permutation of the N spins (an ordering repeated R times,
+ *     L = R N -- the path sum of Sec. 2.2.1 with equal summands).  Metropolis
+ *     proposal j of a sweep flips spin path[j] (systematic scan).
+ *   - Errors: argument errors are detected before anything is launched and
+ *     leave all outputs untouched; CUDA errors (including asynchronous ones of
+ *     earlier launches on the device) return RTT_ERR_CUDA.  rtt_last_error()
+ *     gives a message for the calling thread.  No call aborts the process.
+ */
+#ifndef RTT_H
+#define RTT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rtt_s *rtt_handle;
+
+typedef enum {
+    RTT_OK = 0,
+    RTT_ERR_INVALID_ARG = 1,
+    RTT_ERR_CUDA = 2,
+    RTT_ERR_OOM = 3,
+    RTT_ERR_NUMERIC = 4,
+    RTT_ERR_TIMEOUT = 5,
+    RTT_ERR_UNSUPPORTED = 6
+} rtt_status;
+
+/* Arithmetic of the site contractions (exponents are always exact integers,
+ * energies and statistics are always reduced in FP64). */
+typedef enum {
+    RTT_FP64 = 0,   /* FP64 fma chains in the oracle's canonical order         */
+    RTT_FP32 = 1,   /* FP32 fma chains                                         */
+    RTT_BF16X3 = 2  /* tensor cores: bf16 hi/lo split operands, 3 products
+                       (hi*hi + hi*lo + lo*hi), FP32 accumulation             */
+} rtt_precision;
+
+typedef struct {
+    int32_t n_spins;          /* N >= 1                                          */
+    int32_t length;           /* L = number of train sites, a multiple of N      */
+    int32_t chi;              /* bond dimension, 1..256                          */
+    int32_t n_bonds;          /* number of ZZ bonds (may be 0)                   */
+    const int32_t *path;      /* host [L]; path[k] in [0,N)                      */
+    const double *tensors;    /* host [L][2][chi][chi]; A_k[s][a][b], finite     */
+    const double *b_left;     /* host [chi]                                      */
+    const double *b_right;    /* host [chi]                                      */
+    const int32_t *bonds;     /* host [n_bonds][2] spin pairs (i != j)           */
+    double J;                 /* ZZ coupling                                     */
+    double h;                 /* transverse field                                */
+    int32_t precision;        /* rtt_precision                                   */
+    int32_t device;           /* CUDA device ordinal, or -1 for the current one  */
+    uint64_t seed;            /* key of the Metropolis random stream             */
+} rtt_desc;
+
+/* psi = mant * 2^exp2, |mant| in [1,2) or mant == 0. */
+typedef struct {
+    double mant;
+    int64_t exp2;
+} rtt_chain_state;
+
+/* Summary statistics of a local-energy trace (rtt_observables). */
+typedef struct {
+    double mean;         /* grand mean of E_loc                                     */
+    double var;          /* (1/n) sum (E_loc - mean)^2                              */
+    double se;           /* sqrt(var * 2 tau_int / n)                               */
+    double se_bin;       /* binned SE, bins of ceil(20 tau_int) sweeps per chain    */
+    double se_chain;     /* std of chain means / sqrt(B)                            */
+    double tau_int;      /* 1/2 + sum_{t<=W} rho(t), Sokal window W >= 5 tau(W)     */
+    double ess;          /* n / (2 tau_int)                                         */
+    double v_score;      /* N var / mean^2 (Sec. 4.3, Table 1 and Fig. 6)           */
+    double accept_rate;  /* accepted / proposed, NaN if no counts given             */
+    int64_t n;           /* T * B                                                   */
+    int32_t window;      /* W                                                       */
+    int32_t pad;
+} rtt_stats;
+
+/* Create a handle: validates the description (periodic path, finite tensors,
+ * bond indices in range), copies every host array to the device in the
+ * requested precision and returns the handle in *out.  The handle owns its
+ * device copies and its scratch; the caller keeps ownership of `desc` and its
+ * arrays.  Unsupported combinations (non-periodic path, chi > 256, BF16X3 with
+ * chi not in {16,32,64,128}) return RTT_ERR_UNSUPPORTED. */
+rtt_status rtt_create(const rtt_desc *desc, rtt_handle *out);
+
+/* Release every device allocation of the handle (synchronises its device). */
+rtt_status rtt_destroy(rtt_handle h);
+
+/* Pre-allocate the scratch used for batches of up to B chains so that later
+ * calls with B' <= B allocate nothing.  Scratch grows on demand otherwise. */
+rtt_status rtt_reserve(rtt_handle h, int64_t B);
+
+/* log|psi(s)| and sign for B configurations (Eq. RTT, evaluated left to
+ * right).  spins: device [B][N]; log_abs: device [B] (-inf where psi = 0);
+ * sign: device int8 [B] (+1, -1, 0); state: device [B] or NULL, receives
+ * (mant, exp2) -- the chain state rtt_mcmc_sweep expects. */
+rtt_status rtt_log_amplitudes(rtt_handle h, const uint8_t *spins, int64_t B,
+                              double *log_abs, int8_t *sign, rtt_chain_state *state,
+                              void *stream);
+
+/* Local energy E_loc(s) for B configurations (Sec. 3.3 with Sec. 4 Eq.
+ * ising-model).  psi(s^(i)) is evaluated by the factorisation
+ * l_{a-1} A_a .. A_b r_{b+1} over the replica span [a,b] of spin i using
+ * cached left (first N sites) and right (last N sites) environments; psi(s)
+ * by a full left-to-right pass.  spins: device [B][N]; e_loc: device [B]
+ * (NaN where psi(s) = 0); ratios: device [B][N] or NULL, receives
+ * psi(s^(i))/psi(s) indexed by spin i. */
+rtt_status rtt_local_energy(rtt_handle h, const uint8_t *spins, int64_t B, double *e_loc,
+                            double *ratios, void *stream);
+
+/* Run n_sweeps systematic single-spin Metropolis sweeps on B chains (Sec. 3.3:
+ * sampling of P(s) = |psi(s)|^2/Z).  Proposal j of sweep t flips spin path[j]
+ * and is accepted iff u < (psi(s')/psi(s))^2 with
+ * u = (Philox4x64-10(counter = (chain0+c, t, j, 0), key = (seed, 0x4D434D43))[0] >> 11) * 2^-53,
+ * t = sweep0 + sweep index, so a run split into several calls, or chains split
+ * across calls by chain0, reproduces the unsplit run bit for bit in FP64.
+ *   spins     device [B][N]   in/out
+ *   state     device [B]      in/out, psi of the current spins (from
+ *                             rtt_log_amplitudes), updated on acceptance
+ *   e_loc_trace device [n_sweeps/measure_every][B] or NULL: E_loc after every
+ *             measure_every-th sweep of this call (measure_every >= 1)
+ *   n_accept  device int64 [B] or NULL: accepted proposals are added
+ * Chains whose psi is 0 or not finite accept any proposal with a finite,
+ * nonzero amplitude. */
+rtt_status rtt_mcmc_sweep(rtt_handle h, uint8_t *spins, rtt_chain_state *state, int64_t B,
+                          int64_t chain0, int64_t sweep0, int32_t n_sweeps, int32_t measure_every,
+                          double *e_loc_trace, int64_t *n_accept, void *stream);
+
+/* Statistics of a local-energy trace (V-score of Sec. 4.3; tau_int by Sokal's
+ * automatic window with c = 5).  e_loc_trace: device [T][B]; n_accept: device
+ * [B] or NULL; proposals_per_chain: divisor of the acceptance rate; out: host.
+ * SYNCHRONOUS: returns after the device work on `stream` has finished. */
+rtt_status rtt_observables(rtt_handle h, const double *e_loc_trace, int32_t T, int64_t B,
+                           const int64_t *n_accept, int64_t proposals_per_chain, rtt_stats *out,
+                           void *stream);
+
+/* The Metropolis uniforms themselves, for checking the device generator:
+ * counters: device uint64 [n][3] = (chain, sweep, proposal); out: device [n]. */
+rtt_status rtt_mcmc_uniforms(uint64_t seed, int64_t n, const uint64_t *counters, double *out,
+                             void *stream);
+
+/* Per-kernel device time.  While profiling is enabled, the library brackets
+ * every kernel it launches for this handle with a pair of CUDA events on the
+ * launching stream.  rtt_profile_read synchronises the handle's device, writes
+ * up to `capacity` entries (one per kernel kind that ran: static name, number
+ * of launches, summed milliseconds), stores the number of kinds in *count and
+ * resets the counters.  Enabling or disabling also resets them. */
+typedef struct {
+    const char *name;
+    int64_t launches;
+    double ms;
+} rtt_kernel_time;
+rtt_status rtt_profile(rtt_handle h, int32_t enable);
+rtt_status rtt_profile_read(rtt_handle h, rtt_kernel_time *out, int32_t capacity, int32_t *count);
+
+/* Bytes of device scratch a handle holds for batches of B chains. */
+rtt_status rtt_scratch_bytes(rtt_handle h, int64_t B, size_t *bytes);
+
+const char *rtt_status_string(rtt_status s);
+const char *rtt_last_error(void);   /* thread-local; "" when none */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTT_H */

@@ -1,0 +1,246 @@
+"""Thin ctypes binding of librtt.so (include/rtt.h).
+
+Argument marshalling only: every step of the sampler runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the current CUDA stream.
+If librtt.so is missing this module raises at import of the library -- there
+is no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librtt.so")
+
+RTT_FP64, RTT_FP32, RTT_BF16X3 = 0, 1, 2
+PRECISIONS = {"fp64": RTT_FP64, "fp32": RTT_FP32, "bf16x3": RTT_BF16X3}
+STATUS = {0: "RTT_OK", 1: "RTT_ERR_INVALID_ARG", 2: "RTT_ERR_CUDA", 3: "RTT_ERR_OOM",
+          4: "RTT_ERR_NUMERIC", 5: "RTT_ERR_TIMEOUT", 6: "RTT_ERR_UNSUPPORTED"}
+
+
+class RTTError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("n_spins", ctypes.c_int32), ("length", ctypes.c_int32),
+                ("chi", ctypes.c_int32), ("n_bonds", ctypes.c_int32),
+                ("path", ctypes.c_void_p), ("tensors", ctypes.c_void_p),
+                ("b_left", ctypes.c_void_p), ("b_right", ctypes.c_void_p),
+                ("bonds", ctypes.c_void_p), ("J", ctypes.c_double), ("h", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class _KTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_double), ("var", ctypes.c_double), ("se", ctypes.c_double),
+                ("se_bin", ctypes.c_double), ("se_chain", ctypes.c_double),
+                ("tau_int", ctypes.c_double), ("ess", ctypes.c_double),
+                ("v_score", ctypes.c_double), ("accept_rate", ctypes.c_double),
+                ("n", ctypes.c_int64), ("window", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load librtt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_2604_22718_gb300.build.build() (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+        L.rtt_create.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(P)]
+        L.rtt_destroy.argtypes = [P]
+        L.rtt_reserve.argtypes = [P, I64]
+        L.rtt_scratch_bytes.argtypes = [P, I64, ctypes.POINTER(ctypes.c_size_t)]
+        L.rtt_log_amplitudes.argtypes = [P, P, I64, P, P, P, P]
+        L.rtt_local_energy.argtypes = [P, P, I64, P, P, P]
+        L.rtt_mcmc_sweep.argtypes = [P, P, P, I64, I64, I64, I32, I32, P, P, P]
+        L.rtt_observables.argtypes = [P, P, I32, I64, P, I64, ctypes.POINTER(_Stats), P]
+        L.rtt_mcmc_uniforms.argtypes = [U64, I64, P, P, P]
+        L.rtt_profile.argtypes = [P, I32]
+        L.rtt_profile_read.argtypes = [P, ctypes.POINTER(_KTime), I32, ctypes.POINTER(I32)]
+        L.rtt_status_string.argtypes = [I32]
+        L.rtt_status_string.restype = ctypes.c_char_p
+        L.rtt_last_error.restype = ctypes.c_char_p
+        for name in ("rtt_create", "rtt_destroy", "rtt_reserve", "rtt_scratch_bytes",
+                     "rtt_log_amplitudes", "rtt_local_energy", "rtt_mcmc_sweep",
+                     "rtt_observables", "rtt_mcmc_uniforms", "rtt_profile", "rtt_profile_read"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise RTTError(status, where, lib().rtt_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_check(t: torch.Tensor, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+def new_state(B: int, device="cuda") -> torch.Tensor:
+    """Chain-state buffer: int64 [B, 2] holding (mant as float64 bits, exp2)."""
+    return torch.zeros((B, 2), dtype=torch.int64, device=device)
+
+
+def state_mant(state: torch.Tensor) -> torch.Tensor:
+    return state.view(torch.float64)[:, 0]
+
+
+def state_exp(state: torch.Tensor) -> torch.Tensor:
+    return state[:, 1]
+
+
+class RTT:
+    """One RTT instance on one GPU (wraps an rtt_handle)."""
+
+    def __init__(self, inst, precision: str | int = "fp32", device: int | None = None,
+                 seed: int = 22718):
+        self.inst = inst
+        self.n = int(inst.n_spins)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self._path = np.ascontiguousarray(inst.path, dtype=np.int32)
+        self._t = np.ascontiguousarray(inst.tensors, dtype=np.float64)
+        self._bl = np.ascontiguousarray(inst.b_left, dtype=np.float64)
+        self._br = np.ascontiguousarray(inst.b_right, dtype=np.float64)
+        self._bonds = np.ascontiguousarray(inst.bonds, dtype=np.int32).reshape(-1, 2)
+        L, _, chi, _ = self._t.shape
+        self.L, self.chi = L, chi
+        d = _Desc(self.n, L, chi, self._bonds.shape[0], self._path.ctypes.data,
+                  self._t.ctypes.data, self._bl.ctypes.data, self._br.ctypes.data,
+                  self._bonds.ctypes.data if self._bonds.size else None,
+                  float(inst.J), float(inst.h), self.precision, self.device, int(seed))
+        self.seed = int(seed)
+        h = ctypes.c_void_p()
+        _check(lib().rtt_create(ctypes.byref(d), ctypes.byref(h)), "rtt_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rtt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def reserve(self, B: int):
+        _check(lib().rtt_reserve(self._h, int(B)), "rtt_reserve")
+
+    def scratch_bytes(self, B: int) -> int:
+        out = ctypes.c_size_t()
+        _check(lib().rtt_scratch_bytes(self._h, int(B), ctypes.byref(out)), "rtt_scratch_bytes")
+        return int(out.value)
+
+    def profile(self, enable: bool = True):
+        _check(lib().rtt_profile(self._h, 1 if enable else 0), "rtt_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total ms)} since the last read (synchronises)."""
+        buf = (_KTime * 32)()
+        n = ctypes.c_int32()
+        _check(lib().rtt_profile_read(self._h, buf, 32, ctypes.byref(n)), "rtt_profile_read")
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms))
+                for i in range(min(n.value, 32))}
+
+    def log_amplitudes(self, spins: torch.Tensor, stream=None):
+        B = spins.shape[0]
+        _dev_check(spins, torch.uint8, (B, self.n), "spins")
+        la = torch.empty(B, dtype=torch.float64, device=spins.device)
+        sg = torch.empty(B, dtype=torch.int8, device=spins.device)
+        st = new_state(B, spins.device)
+        _check(lib().rtt_log_amplitudes(self._h, _ptr(spins), B, _ptr(la), _ptr(sg), _ptr(st),
+                                        _stream(stream)), "rtt_log_amplitudes")
+        return la, sg, st
+
+    def local_energy(self, spins: torch.Tensor, with_ratios: bool = False, stream=None):
+        B = spins.shape[0]
+        _dev_check(spins, torch.uint8, (B, self.n), "spins")
+        e = torch.empty(B, dtype=torch.float64, device=spins.device)
+        r = torch.empty((B, self.n), dtype=torch.float64, device=spins.device) if with_ratios else None
+        _check(lib().rtt_local_energy(self._h, _ptr(spins), B, _ptr(e), _ptr(r), _stream(stream)),
+               "rtt_local_energy")
+        return (e, r) if with_ratios else e
+
+    def mcmc_sweep(self, spins: torch.Tensor, state: torch.Tensor, sweep0: int, n_sweeps: int,
+                   measure_every: int = 1, trace: torch.Tensor | None = None,
+                   n_accept: torch.Tensor | None = None, chain0: int = 0, stream=None):
+        B = spins.shape[0]
+        _dev_check(spins, torch.uint8, (B, self.n), "spins")
+        _dev_check(state, torch.int64, (B, 2), "state")
+        if trace is not None:
+            _dev_check(trace, torch.float64, (n_sweeps // measure_every, B), "trace")
+        if n_accept is not None:
+            _dev_check(n_accept, torch.int64, (B,), "n_accept")
+        _check(lib().rtt_mcmc_sweep(self._h, _ptr(spins), _ptr(state), B, int(chain0), int(sweep0),
+                                    int(n_sweeps), int(measure_every), _ptr(trace), _ptr(n_accept),
+                                    _stream(stream)), "rtt_mcmc_sweep")
+
+    def observables(self, trace: torch.Tensor, n_accept: torch.Tensor | None = None,
+                    proposals_per_chain: int = 0, stream=None) -> dict:
+        T, B = trace.shape
+        _dev_check(trace, torch.float64, (T, B), "trace")
+        out = _Stats()
+        _check(lib().rtt_observables(self._h, _ptr(trace), T, B, _ptr(n_accept),
+                                     int(proposals_per_chain), ctypes.byref(out), _stream(stream)),
+               "rtt_observables")
+        return {k: getattr(out, k) for k, _ in _Stats._fields_ if k != "pad"}
+
+
+def mcmc_uniforms(seed: int, counters: torch.Tensor, stream=None) -> torch.Tensor:
+    """Device Philox uniforms for counters int64/uint64 [n][3] (chain, sweep, proposal)."""
+    n = counters.shape[0]
+    if counters.dtype not in (torch.int64, torch.uint64) or tuple(counters.shape) != (n, 3):
+        raise ValueError("counters must be int64 [n][3]")
+    out = torch.empty(n, dtype=torch.float64, device=counters.device)
+    _check(lib().rtt_mcmc_uniforms(int(seed), n, _ptr(counters.contiguous()), _ptr(out),
+                                   _stream(stream)), "rtt_mcmc_uniforms")
+    return out

@@ -1,0 +1,107 @@
+"""The C-ABI library builds, loads and exports what include/rtt.h declares;
+argument errors are reported without touching a GPU (CPU only)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2604_22718_gb300 import build as rtt_build
+from paper_2604_22718_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    rtt_build.build()
+    from paper_2604_22718_gb300 import rtt
+    return rtt.lib()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(rtt_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"rtt_create", "rtt_destroy", "rtt_log_amplitudes", "rtt_local_energy",
+            "rtt_mcmc_sweep", "rtt_observables"} <= names
+    for n in sorted(names):
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_status_strings(lib):
+    lib.rtt_status_string.restype = ctypes.c_char_p
+    assert lib.rtt_status_string(0) == b"RTT_OK"
+    assert lib.rtt_status_string(6) == b"RTT_ERR_UNSUPPORTED"
+
+
+def _desc(inst, **kw):
+    from paper_2604_22718_gb300 import rtt
+    keep = dict(path=np.ascontiguousarray(inst.path, np.int32),
+                t=np.ascontiguousarray(inst.tensors), bl=np.ascontiguousarray(inst.b_left),
+                br=np.ascontiguousarray(inst.b_right),
+                bonds=np.ascontiguousarray(inst.bonds, np.int32))
+    keep.update(kw)
+    d = rtt._Desc(inst.n_spins, keep["path"].shape[0], keep["t"].shape[2], keep["bonds"].shape[0],
+                  keep["path"].ctypes.data, keep["t"].ctypes.data, keep["bl"].ctypes.data,
+                  keep["br"].ctypes.data, keep["bonds"].ctypes.data, 1.0, 3.0,
+                  kw.get("precision", 0), -1, 1)
+    return d, keep
+
+
+@pytest.mark.parametrize("mutate,expect", [
+    ("path_out_of_range", 1),
+    ("not_periodic", 6),
+    ("not_permutation", 6),
+    ("nan_tensor", 4),
+    ("bad_precision", 1),
+    ("self_bond", 1),
+])
+def test_create_rejects_bad_descriptions_before_any_cuda_call(lib, mutate, expect):
+    inst = inputs.make_instance(3, 3, 2, 4, 3.0, seed=1, mixing=False)
+    path = inst.path.copy()
+    t = inst.tensors.copy()
+    bonds = inst.bonds.copy()
+    prec = 0
+    if mutate == "path_out_of_range":
+        path[3] = 9
+    elif mutate == "not_periodic":
+        path[10], path[11] = path[11], path[10]
+    elif mutate == "not_permutation":
+        path[1] = path[0]
+        path[10] = path[9]
+    elif mutate == "nan_tensor":
+        t[2, 1, 0, 0] = np.nan
+    elif mutate == "bad_precision":
+        prec = 7
+    elif mutate == "self_bond":
+        bonds[0, 1] = bonds[0, 0]
+    d, keep = _desc(inst, path=path, t=t, bonds=bonds, precision=prec)
+    h = ctypes.c_void_p()
+    st = lib.rtt_create(ctypes.byref(d), ctypes.byref(h))
+    assert st == expect
+    assert h.value is None
+    lib.rtt_last_error.restype = ctypes.c_char_p
+    assert lib.rtt_last_error().startswith(b"rtt_create")
+
+
+def test_null_handle_is_an_argument_error(lib):
+    assert lib.rtt_log_amplitudes(None, None, 4, None, None, None, None) == 1
+    assert lib.rtt_local_energy(None, None, 4, None, None, None) == 1
+    assert lib.rtt_mcmc_sweep(None, None, None, 4, 0, 0, 1, 1, None, None, None) == 1
+    assert lib.rtt_reserve(None, 4) == 1
+
+
+def test_uniforms_empty_request_needs_no_gpu(lib):
+    assert lib.rtt_mcmc_uniforms(1, 0, None, None, None) == 0
+    assert lib.rtt_mcmc_uniforms(1, -1, None, None, None) == 1
