@@ -79,6 +79,7 @@ def _load():
             lib.orc_local_energies.argtypes = [P, P, I64, P, P]
             lib.orc_local_energies.restype = ctypes.c_int
             lib.orc_flip_amplitudes.argtypes = [P, P, I64, P, P]
+            lib.orc_amplitude_cond.argtypes = [P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -167,6 +168,19 @@ class Oracle:
         with ThreadPoolExecutor(threads) as ex:
             list(ex.map(run, range(threads)))
         return (e, r) if with_ratios else e
+
+    def amplitude_cond(self, spins):
+        """Per configuration: (sum_k kappa_k, max_k kappa_k, kappa_fin) of the
+        left-to-right evaluation (see orc_amplitude_cond)."""
+        spins = np.ascontiguousarray(spins, dtype=np.uint8)
+        B = spins.shape[0]
+        out = np.empty((B, 3))
+        for c in range(B):
+            a, b, k = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            self.lib.orc_amplitude_cond(self._p, _ptr(spins[c]), ctypes.byref(a),
+                                        ctypes.byref(b), ctypes.byref(k))
+            out[c] = (a.value, b.value, k.value)
+        return out
 
     def all_amplitudes(self):
         assert self.n <= 22

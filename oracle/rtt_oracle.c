@@ -187,6 +187,50 @@ void orc_flip_amplitude(const orc_rtt *m, const uint8_t *s, int flip,
     free(w);
 }
 
+/* Conditioning of the left-to-right evaluation of psi(s), for stating
+ * floating-point tolerances: for every site kappa_k = || |v| |A_k| ||_2 /
+ * || v A_k ||_2 (v the incoming row, |.| elementwise), and for the closing
+ * contraction kappa_fin = sum_b |v_b b_R[b]| / |sum_b v_b b_R[b]|.  Returns
+ * sum_k kappa_k in *sum_kappa, max_k kappa_k in *max_kappa and kappa_fin. */
+void orc_amplitude_cond(const orc_rtt *m, const uint8_t *s, double *sum_kappa,
+                        double *max_kappa, double *kappa_fin)
+{
+    const int chi = m->chi;
+    double *v = (double *)malloc(sizeof(double) * chi);
+    double *w = (double *)malloc(sizeof(double) * chi);
+    memcpy(v, m->b_left, sizeof(double) * chi);
+    double sk = 0.0, mk = 0.0;
+    for (int k = 0; k < m->length; ++k) {
+        const double *A = site_matrix(m, k, s[m->path[k]]);
+        double num = 0.0, den = 0.0;
+        for (int b = 0; b < chi; ++b) {
+            double acc = 0.0, aacc = 0.0;
+            for (int a = 0; a < chi; ++a) {
+                acc = fma(v[a], A[(size_t)a * chi + b], acc);
+                aacc += fabs(v[a]) * fabs(A[(size_t)a * chi + b]);
+            }
+            w[b] = acc;
+            num += aacc * aacc;
+            den += acc * acc;
+        }
+        double kap = (den > 0.0) ? sqrt(num / den) : INFINITY;
+        sk += kap;
+        if (kap > mk) mk = kap;
+        double *t = v; v = w; w = t;
+        renorm(v, chi);
+    }
+    double num = 0.0, den = 0.0;
+    for (int b = 0; b < chi; ++b) {
+        num += fabs(v[b] * m->b_right[b]);
+        den = fma(v[b], m->b_right[b], den);
+    }
+    *sum_kappa = sk;
+    *max_kappa = mk;
+    *kappa_fin = (den != 0.0) ? num / fabs(den) : INFINITY;
+    free(v);
+    free(w);
+}
+
 /* ---------------------------------------------------------------- energy */
 
 static int64_t zz_sum(const orc_rtt *m, const uint8_t *s)

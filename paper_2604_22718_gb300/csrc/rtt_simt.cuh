@@ -66,15 +66,17 @@ struct RowOps {
         return e;
     }
 
-    // sum_b u[b] r[b], fma in increasing b; every lane of the group gets it.
-    static __device__ __forceinline__ T dot(const T (&u)[NQ], const T (&r)[NQ]) {
-        T acc = T(0);
+    // sum_b u[b] r[b] accumulated in FP64 (exact products of FP32 inputs; for
+    // T = double this is the oracle's fma order), in increasing b; every lane
+    // of the group gets it.
+    static __device__ __forceinline__ double dot(const T (&u)[NQ], const T (&r)[NQ]) {
+        double acc = 0.0;
 #pragma unroll
         for (int aq = 0; aq < NQ; ++aq) {
 #pragma unroll(G < 8 ? G : 8)
             for (int al = 0; al < G; ++al) {
-                const T ua = __shfl_sync(FULL, u[aq], al, G);
-                const T ra = __shfl_sync(FULL, r[aq], al, G);
+                const double ua = (double)__shfl_sync(FULL, u[aq], al, G);
+                const double ra = (double)__shfl_sync(FULL, r[aq], al, G);
                 acc = fma(ua, ra, acc);
             }
         }
@@ -192,13 +194,20 @@ __global__ void __launch_bounds__(256) k_rows(KArgs a, const uint8_t *__restrict
                                               double *__restrict__ rows_mant,
                                               int64_t *__restrict__ rows_exp) {
     using O = RowOps<T, CHI>;
+    constexpr int RPW = Geo<CHI>::RPW;
     const int lane = threadIdx.x & 31, gl = lane % O::G;
+    // group g -> (chain block cb, j, r): the RPW groups of one warp share j
+    // (hence the loop length), so the warp's shuffles never diverge.
     const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / O::G;
-    const int64_t n_rows = B * (int64_t)(a.N + 1);
-    const bool active = g0 < n_rows;
-    const int64_t g = active ? g0 : n_rows - 1;
-    const int64_t c = g / (a.N + 1);
-    const int j = (int)(g % (a.N + 1));
+    const int64_t n_cb = (B + RPW - 1) / RPW;
+    const int64_t total = n_cb * (a.N + 1) * RPW;
+    const int64_t gg = g0 < total ? g0 : total - 1;
+    const int r_in = (int)(gg % RPW);
+    const int j = (int)((gg / RPW) % (a.N + 1));
+    const int64_t c0 = (gg / RPW / (a.N + 1)) * RPW + r_in;
+    const bool active = g0 < total && c0 < B;
+    const int64_t c = c0 < B ? c0 : B - 1;
+    const int64_t g = c * (a.N + 1) + j;
     const uint8_t *s = spins + c * a.N;
     const T *A = (const T *)a.A;
     T u[O::NQ];
@@ -222,7 +231,7 @@ __global__ void __launch_bounds__(256) k_rows(KArgs a, const uint8_t *__restrict
     T r[O::NQ];
     O::load(rstack + ((size_t)c * a.N + rq) * CHI, r, gl);
     E += rexp[(size_t)c * a.N + rq];
-    double m = (double)O::dot(u, r);
+    double m = O::dot(u, r);
     normalize_scalar(m, E);
     if (active && gl == 0) {
         rows_mant[g] = m;
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(256) k_chain_init(KArgs a, const uint8_t *__re
     }
     T r[O::NQ];
     O::load((const T *)a.br, r, gl);
-    double m = (double)O::dot(v, r);
+    double m = O::dot(v, r);
     normalize_scalar(m, E);
     if (active && gl == 0) {
         if (state) {
@@ -332,7 +341,7 @@ __global__ void __launch_bounds__(256) k_sweep(KArgs a, uint8_t *__restrict__ sp
             T r[O::NQ];
             O::load(rst + (size_t)j * CHI, r, gl);
             Eu += rex[j];
-            double m = (double)O::dot(u, r);
+            double m = O::dot(u, r);
             normalize_scalar(m, Eu);
             const double ratio = ldexp(m / pm, (int)(Eu - pe));
             const double x = mcmc_uniform(seed, (uint64_t)(chain0 + c), (uint64_t)(sweep0 + sw),
@@ -396,7 +405,10 @@ struct SimtLaunch {
                     a, (const uint8_t *)p0, B, (T *)p1, (int32_t *)p2);
                 break;
             case 2:
-                k_rows<T, CHI><<<(unsigned)blocks_for<CHI>(B * (sa.N + 1)), 256, 0, st>>>(
+                k_rows<T, CHI><<<(unsigned)blocks_for<CHI>(
+                                     (B + Geo<CHI>::RPW - 1) / Geo<CHI>::RPW * (sa.N + 1) *
+                                     Geo<CHI>::RPW),
+                                 256, 0, st>>>(
                     a, (const uint8_t *)p0, B, (const T *)p1, (const int32_t *)p2,
                     (const T *)p3, (const int32_t *)p4, (double *)p5, (int64_t *)p6);
                 break;
