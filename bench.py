@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="plain_6x6")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16x3"])
+    ap.add_argument("--precision", default="fp16x3", choices=["fp32", "fp64", "bf16x3", "fp16x3"])
     ap.add_argument("--chains", type=int, default=0, help="override the workload's chain count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -281,16 +281,20 @@ def run_ours(args):
         launches, ms = prof[dom]
         flops = 2.0 * inst.chi * inst.chi * site_steps(N, R, dom) * B
         achieved = flops / (ms / launches / 1e3) / 1e12
-        if args.precision == "bf16x3":
-            peak = peaks["bf16_tflops_sustained"] / 1.0
-            bound, pk = "tensor", f"bf16 sustained, {peak_kind}"
+        if args.precision in ("bf16x3", "fp16x3"):
+            # fp16 and bf16 dense tensor rates are equal on this part
+            peak = peaks["bf16_tflops_sustained"]
+            bound, pk = "tensor", (f"bf16 dense sustained ({peak_kind}); fp16 = bf16 rate; "
+                                   f"executed = 6x algorithmic (both slices x 3 split products)")
         else:
             lanes = FP32_LANES_PER_SM if args.precision == "fp32" else FP64_LANES_PER_SM
             peak = SM_COUNT * lanes * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             bound, pk = "alu", (f"{args.precision} CUDA-core fma peak: {SM_COUNT} SMs x {lanes} "
                                 f"lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz")
+        executed = achieved * (6.0 if bound == "tensor" else 1.0)
         roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "executed_tflops": executed, "executed_frac": executed / peak,
                 "peak_source": pk, "flops_per_launch": flops,
                 "launch_ms": ms / launches,
                 "kernel_share": ms / sum(v[1] for v in prof.values())}
@@ -334,7 +338,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3"}[args.precision],
+            "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3",
+                      "fp16x3": "fp16x3"}[args.precision],
             "data": "synthetic",
             "config": {"workload": _workload_desc(args.workload, inst, B), "chains_per_gpu": B,
                        "precision": args.precision, "parallelism": f"replicas over chains x{world}",

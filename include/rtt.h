@@ -62,8 +62,11 @@ typedef enum {
 typedef enum {
     RTT_FP64 = 0,   /* FP64 fma chains in the oracle's canonical order         */
     RTT_FP32 = 1,   /* FP32 fma chains                                         */
-    RTT_BF16X3 = 2  /* tensor cores: bf16 hi/lo split operands, 3 products
+    RTT_BF16X3 = 2, /* tensor cores: bf16 hi/lo split operands, 3 products
                        (hi*hi + hi*lo + lo*hi), FP32 accumulation             */
+    RTT_FP16X3 = 3  /* as RTT_BF16X3 with fp16 hi/lo operands (11-bit
+                       significands; site tensors prescaled by exact powers
+                       of two into fp16's normal range)                       */
 } rtt_precision;
 
 typedef struct {
@@ -109,8 +112,8 @@ typedef struct {
  * bond indices in range), copies every host array to the device in the
  * requested precision and returns the handle in *out.  The handle owns its
  * device copies and its scratch; the caller keeps ownership of `desc` and its
- * arrays.  Unsupported combinations (non-periodic path, chi > 256, BF16X3 with
- * chi not in {16,32,64,128}) return RTT_ERR_UNSUPPORTED. */
+ * arrays.  Unsupported combinations (non-periodic path, chi > 256, BF16X3 or
+ * FP16X3 with chi not in {64,128}) return RTT_ERR_UNSUPPORTED. */
 rtt_status rtt_create(const rtt_desc *desc, rtt_handle *out);
 
 /* Release every device allocation of the handle (synchronises its device). */
@@ -182,6 +185,13 @@ typedef struct {
 } rtt_kernel_time;
 rtt_status rtt_profile(rtt_handle h, int32_t enable);
 rtt_status rtt_profile_read(rtt_handle h, rtt_kernel_time *out, int32_t capacity, int32_t *count);
+
+/* Device-side error flags of the handle's kernels since the last call
+ * (bit 0: a bounded wait inside a tensor-core kernel ran out of its clock
+ * budget; that kernel recorded the flag, drained its own copies, freed its
+ * tensor memory and returned without writing results).  SYNCHRONOUS.
+ * Returns RTT_ERR_TIMEOUT if bit 0 is set, and clears the flags. */
+rtt_status rtt_device_status(rtt_handle h, int32_t *flags);
 
 /* Bytes of device scratch a handle holds for batches of B chains. */
 rtt_status rtt_scratch_bytes(rtt_handle h, int64_t B, size_t *bytes);

@@ -122,7 +122,7 @@ rtt_status check_handle(rtt_handle h) {
 // If `have_left` the left stack already holds l_j for these spins.
 rtt_status energy_pipeline(rtt_s *h, const uint8_t *spins, int64_t B, double *e_loc,
                            double *ratios, bool have_left, cudaStream_t st) {
-    if (h->precision == RTT_BF16X3) {
+    if (h->precision >= RTT_BF16X3) {
         rtt_status s;
         if (!have_left && (s = tc_left_env(h, spins, B, st)) != RTT_OK) return s;
         if ((s = tc_right_env(h, spins, B, st)) != RTT_OK) return s;
@@ -255,7 +255,7 @@ rtt_status rtt_create(const rtt_desc *d, rtt_handle *out) {
         return fail(RTT_ERR_INVALID_ARG, "rtt_create: null path/tensors/boundary");
     if (d->n_bonds < 0 || (d->n_bonds > 0 && !d->bonds))
         return fail(RTT_ERR_INVALID_ARG, "rtt_create: bad bonds");
-    if (d->precision < RTT_FP64 || d->precision > RTT_BF16X3)
+    if (d->precision < RTT_FP64 || d->precision > RTT_FP16X3)
         return fail(RTT_ERR_INVALID_ARG, "rtt_create: unknown precision");
     const int N = d->n_spins, L = d->length, chi = d->chi;
     for (int k = 0; k < L; ++k)
@@ -284,8 +284,9 @@ rtt_status rtt_create(const rtt_desc *d, rtt_handle *out) {
     for (int a = 0; a < chi; ++a)
         if (!isfinite(d->b_left[a]) || !isfinite(d->b_right[a]))
             return fail(RTT_ERR_NUMERIC, "rtt_create: non-finite boundary entry");
-    if (d->precision == RTT_BF16X3 && !tc_supported_chi(chi))
-        return fail(RTT_ERR_UNSUPPORTED, "rtt_create: BF16X3 needs chi in {16,32,64,128}");
+    const bool tensor_core = d->precision == RTT_BF16X3 || d->precision == RTT_FP16X3;
+    if (tensor_core && !tc_supported_chi(chi))
+        return fail(RTT_ERR_UNSUPPORTED, "rtt_create: BF16X3/FP16X3 need chi in {64,128}");
 
     int dev = d->device;
     if (dev < 0) API_CUDA(cudaGetDevice(&dev), "rtt_create: cudaGetDevice");
@@ -389,7 +390,7 @@ rtt_status rtt_log_amplitudes(rtt_handle h, const uint8_t *spins, int64_t B, dou
     DeviceGuard guard(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     API_CUDA(cudaGetLastError(), "rtt_log_amplitudes: pending error");
-    if (h->precision == RTT_BF16X3) return tc_chain_init(h, spins, B, log_abs, sign, state, st);
+    if (h->precision >= RTT_BF16X3) return tc_chain_init(h, spins, B, log_abs, sign, state, st);
     const SimtArgs a = simt_args(h);
     prof_begin(h, KID_CHAIN_INIT, st);
     API_CUDA(h->precision == RTT_FP64 ? simt_chain_init_f64(a, spins, B, log_abs, sign, state, st)
@@ -433,7 +434,7 @@ rtt_status rtt_mcmc_sweep(rtt_handle h, uint8_t *spins, rtt_chain_state *state, 
     const SimtArgs a = simt_args(h);
     auto sweeps = [&](int64_t sw0, int32_t n, bool keep_left) -> rtt_status {
         if (n <= 0) return RTT_OK;
-        if (h->precision == RTT_BF16X3) {
+        if (h->precision >= RTT_BF16X3) {
             return tc_sweep(h, spins, state, B, chain0, sw0, n, n_accept, st);
         }
         void *ls = keep_left ? h->d_lstack : nullptr;
@@ -452,8 +453,8 @@ rtt_status rtt_mcmc_sweep(rtt_handle h, uint8_t *spins, rtt_chain_state *state, 
     const int32_t n_meas = n_sweeps / measure_every;
     int64_t sw = sweep0;
     for (int32_t m = 0; m < n_meas; ++m) {
-        // the tensor-core sweep does not keep l_j, the SIMT one does
-        const bool keep = h->precision != RTT_BF16X3;
+        // the sweep leaves l_j (j < N) of the final spins in the left stack
+        const bool keep = true;
         if ((s = sweeps(sw, measure_every, keep)) != RTT_OK) return s;
         sw += measure_every;
         if ((s = energy_pipeline(h, spins, B, e_loc_trace + (size_t)m * B, nullptr, keep, st)) !=
@@ -608,6 +609,24 @@ rtt_status rtt_profile_read(rtt_handle h, rtt_kernel_time *out, int32_t capacity
     const bool on = p->on;
     p->reset();
     p->on = on;
+    return RTT_OK;
+}
+
+rtt_status rtt_device_status(rtt_handle h, int32_t *flags) {
+    rtt_status s = check_handle(h);
+    if (s != RTT_OK) return s;
+    if (!flags) return fail(RTT_ERR_INVALID_ARG, "rtt_device_status: null flags");
+    DeviceGuard guard(h->device);
+    API_CUDA(cudaDeviceSynchronize(), "rtt_device_status: sync");
+    *flags = 0;
+    int *w = tc_error_word(h);
+    if (w) {
+        int v = 0;
+        API_CUDA(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost), "rtt_device_status: read");
+        API_CUDA(cudaMemset(w, 0, sizeof(int)), "rtt_device_status: clear");
+        *flags = v;
+    }
+    if (*flags & 1) return fail(RTT_ERR_TIMEOUT, "a bounded device wait expired");
     return RTT_OK;
 }
 

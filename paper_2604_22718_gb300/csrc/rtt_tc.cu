@@ -1,19 +1,926 @@
-// rtt_tc.cu -- tensor-core (tcgen05, BF16 hi/lo split) form of the site chain.
+// rtt_tc.cu -- tensor-core form of the RTT site chain (sm_103a, tcgen05).
+//
+// Per site k the rows of a 128-chain tile are contracted with both spin
+// slices at once, D[128 x 2chi] = V[128 x chi] . [A_k[0] | A_k[1]] (Eq. RTT
+// evaluated left to right; right-to-left steps use the transposed slices),
+// on the 5th-generation tensor cores:
+//   - operands in 16-bit hi/lo split form, x = hi + lo + O(u^2 |x|) with u
+//     the unit roundoff of the 16-bit type (BF16: 2^-8, FP16: 2^-11); three
+//     products hi.hi + hi.lo + lo.hi accumulate in FP32 in TMEM.  Each site
+//     tensor is prescaled by an exact power of two 2^c_k (max entry in [1,2))
+//     so that FP16 stays in its normal range; c_k is taken back out of the
+//     integer exponent sum;
+//   - the site tensors are streamed by TMA (128-byte swizzle, K-major) into a
+//     two-stage shared-memory ring; the rows live in shared memory in the
+//     same swizzled K-major layout, written by the epilogue;
+//   - epilogue (one thread per row = TMEM lane): load both accumulator
+//     halves, keep the half of the row's spin at site k, rescale by an exact
+//     power of two (exponent summed in an integer), split to hi/lo BF16 and
+//     store the row back as the next site's A operand.
+// Thread 0 issues TMA and MMA; every wait is bounded by a clock budget after
+// which the CTA records an error flag, drains its own copies, frees its TMEM
+// and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "rtt_internal.cuh"
 
-bool tc_supported_chi(int) { return false; }
-rtt_status tc_plan_create(rtt_s *, const double *, const double *, const double *) {
-    return RTT_ERR_UNSUPPORTED;
+struct TcPlan {
+    int chi = 0;
+    bool f16 = false;              // FP16 operands (else BF16)
+    uint16_t *d_B = nullptr;       // [4][L][2chi][chi]: BT hi, BT lo, B hi, B lo
+    int32_t *d_cexp = nullptr;     // [L] prescale exponents c_k
+    float *d_bl = nullptr, *d_br = nullptr;
+    CUtensorMap map;
+    float *d_tmp = nullptr;  // [B][chi] sweep scratch (flipped start of a row)
+    int32_t *d_tmp_exp = nullptr;
+    int64_t tmp_cap = 0;
+    int *d_err = nullptr;    // device error flags (bit 0: a bounded wait expired)
+};
+
+bool tc_supported_chi(int chi) { return chi == 64 || chi == 128; }
+
+namespace tcd {
+
+constexpr int NT = 128;  // threads per CTA = rows per tile = TMEM lanes
+constexpr int NS = 2;    // B-operand ring stages
+constexpr unsigned FULL = 0xffffffffu;
+
+enum { M_ROWS = 0, M_LEFT = 1, M_RIGHT = 2, M_INIT = 3, M_SWEEP = 4 };
+
+template <int CHI, bool F16 = false>
+struct Cfg {
+    static constexpr int KA = CHI / 64;            // 64-element K atoms per row
+    static constexpr int A_ATOM = 128 * 128;       // bytes: 128 rows x 128 B
+    static constexpr int A_BYTES = KA * A_ATOM;    // one of hi / lo
+    static constexpr int BOX = 2 * CHI * 128;      // bytes: 2chi rows x 128 B
+    static constexpr int STAGE = 2 * BOX;          // hi box + lo box
+    static constexpr int TCOLS = 2 * CHI;          // accumulator columns
+    // kind::f16, (BF16 or FP16) x same -> FP32, both K-major, N = 2chi, M = 128
+    static constexpr uint32_t FMT = F16 ? 0u : 1u;
+    static constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) |
+                                      ((uint32_t)((2 * CHI) >> 3) << 17) |
+                                      ((uint32_t)(128 >> 4) << 24);
+    static constexpr int CTRL = 128;
+    static size_t smem_bytes(int N) {
+        return 1024 + 2 * (size_t)A_BYTES + (size_t)NS * STAGE + CTRL + (size_t)16 * N;
+    }
+};
+
+struct Args {
+    const float *bl, *br;
+    const int32_t *q;
+    const int32_t *cexp;
+    int N, L, R;
+    int64_t B;
+    const uint8_t *spins_in;
+    uint8_t *spins_out;
+    float *lstack;
+    int32_t *lexp;
+    float *rstack;
+    int32_t *rexp;
+    double *rows_mant;
+    int64_t *rows_exp;
+    double *log_abs;
+    int8_t *sign;
+    rtt_chain_state *state;
+    float *tmp;
+    int32_t *tmp_exp;
+    int64_t chain0, sweep0;
+    int n_sweeps;
+    uint64_t seed;
+    int64_t *n_accept;
+    int *err;
+    long long wait_limit;
+};
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t sa(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
-void tc_plan_destroy(rtt_s *) {}
-rtt_status tc_left_env(rtt_s *, const uint8_t *, int64_t, cudaStream_t) { return RTT_ERR_UNSUPPORTED; }
-rtt_status tc_right_env(rtt_s *, const uint8_t *, int64_t, cudaStream_t) { return RTT_ERR_UNSUPPORTED; }
-rtt_status tc_rows(rtt_s *, const uint8_t *, int64_t, cudaStream_t) { return RTT_ERR_UNSUPPORTED; }
-rtt_status tc_chain_init(rtt_s *, const uint8_t *, int64_t, double *, int8_t *, rtt_chain_state *,
-                         cudaStream_t) {
-    return RTT_ERR_UNSUPPORTED;
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
-rtt_status tc_sweep(rtt_s *, uint8_t *, rtt_chain_state *, int64_t, int64_t, int64_t, int32_t,
-                    int64_t *, cudaStream_t) {
-    return RTT_ERR_UNSUPPORTED;
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
 }
+__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok;
+}
+// Bounded wait: false if the clock budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 B apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+// Two 32-column loads of this warp's 32 TMEM lanes and the wait, in one
+// statement so that no use of the registers can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld_2x32(uint32_t t0, uint32_t t1, uint32_t (&x)[32],
+                                             uint32_t (&y)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]),
+          "=r"(x[7]), "=r"(x[8]), "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]),
+          "=r"(x[13]), "=r"(x[14]), "=r"(x[15]), "=r"(x[16]), "=r"(x[17]), "=r"(x[18]),
+          "=r"(x[19]), "=r"(x[20]), "=r"(x[21]), "=r"(x[22]), "=r"(x[23]), "=r"(x[24]),
+          "=r"(x[25]), "=r"(x[26]), "=r"(x[27]), "=r"(x[28]), "=r"(x[29]), "=r"(x[30]),
+          "=r"(x[31]), "=r"(y[0]), "=r"(y[1]), "=r"(y[2]), "=r"(y[3]), "=r"(y[4]), "=r"(y[5]),
+          "=r"(y[6]), "=r"(y[7]), "=r"(y[8]), "=r"(y[9]), "=r"(y[10]), "=r"(y[11]),
+          "=r"(y[12]), "=r"(y[13]), "=r"(y[14]), "=r"(y[15]), "=r"(y[16]), "=r"(y[17]),
+          "=r"(y[18]), "=r"(y[19]), "=r"(y[20]), "=r"(y[21]), "=r"(y[22]), "=r"(y[23]),
+          "=r"(y[24]), "=r"(y[25]), "=r"(y[26]), "=r"(y[27]), "=r"(y[28]), "=r"(y[29]),
+          "=r"(y[30]), "=r"(y[31])
+        : "r"(t0), "r"(t1)
+        : "memory");
+}
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                             uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+                 "r"(d)
+                 : "memory");
+}
+
+// ------------------------------------------------------------------ row helpers
+template <int CHI>
+__device__ __forceinline__ void acc_select(uint32_t tw, int sel, float (&v)[CHI]) {
+#pragma unroll
+    for (int c = 0; c < CHI; c += 32) {
+        uint32_t x0[32], x1[32];
+        tmem_ld_2x32(tw + c, tw + CHI + c, x0, x1);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[c + i] = __uint_as_float(sel ? x1[i] : x0[i]);
+    }
+}
+
+template <int CHI>
+__device__ __forceinline__ int renorm(float (&v)[CHI]) {
+    float mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < CHI; ++i) mx = fmaxf(mx, fabsf(v[i]));
+    if (!(mx > 0.f) || !isfinite(mx)) return 0;
+    const int e = rttd::exponent_of(mx);
+#pragma unroll
+    for (int i = 0; i < CHI; ++i) v[i] = rttd::scale2(v[i], -e);
+    return e;
+}
+
+// Split the row into 16-bit hi/lo and store it as row m of the A operand
+// (K-major, 128-byte swizzle: 16-byte chunk c of row m sits at c ^ (m & 7)).
+template <bool F16>
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t &h, uint32_t &l) {
+    if (F16) {
+        const __half2 hb = __floats2half2_rn(x0, x1);
+        const float2 hf = __half22float2(hb);
+        const __half2 lb = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+        h = *reinterpret_cast<const uint32_t *>(&hb);
+        l = *reinterpret_cast<const uint32_t *>(&lb);
+    } else {
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(x0, x1);
+        const float2 hf = __bfloat1622float2(hb);
+        const __nv_bfloat162 lb = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+        h = *reinterpret_cast<const uint32_t *>(&hb);
+        l = *reinterpret_cast<const uint32_t *>(&lb);
+    }
+}
+
+template <int CHI, bool F16>
+__device__ __forceinline__ void write_A(uint32_t a_hi, uint32_t a_lo, int m, const float (&v)[CHI]) {
+#pragma unroll
+    for (int at = 0; at < CHI / 64; ++at) {
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+                split2<F16>(v[at * 64 + ch * 8 + 2 * p], v[at * 64 + ch * 8 + 2 * p + 1], h[p], l[p]);
+            const uint32_t off =
+                (uint32_t)(at * Cfg<CHI>::A_ATOM + m * 128 + ((ch ^ (m & 7)) << 4));
+            st_shared_v4(a_hi + off, h[0], h[1], h[2], h[3]);
+            st_shared_v4(a_lo + off, l[0], l[1], l[2], l[3]);
+        }
+    }
+}
+
+template <int CHI>
+__device__ __forceinline__ void load_vec(const float *__restrict__ p, float (&v)[CHI]) {
+    const float4 *p4 = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < CHI / 4; ++i) {
+        const float4 x = p4[i];
+        v[4 * i] = x.x;
+        v[4 * i + 1] = x.y;
+        v[4 * i + 2] = x.z;
+        v[4 * i + 3] = x.w;
+    }
+}
+template <int CHI>
+__device__ __forceinline__ void store_vec(float *__restrict__ p, const float (&v)[CHI]) {
+    float4 *p4 = reinterpret_cast<float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < CHI / 4; ++i) p4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+template <int CHI>
+__device__ __forceinline__ double dot(const float (&v)[CHI], const float *__restrict__ r) {
+    double acc = 0.0;
+    const float4 *r4 = reinterpret_cast<const float4 *>(r);
+#pragma unroll
+    for (int i = 0; i < CHI / 4; ++i) {
+        const float4 x = r4[i];
+        acc = fma((double)v[4 * i], (double)x.x, acc);
+        acc = fma((double)v[4 * i + 1], (double)x.y, acc);
+        acc = fma((double)v[4 * i + 2], (double)x.z, acc);
+        acc = fma((double)v[4 * i + 3], (double)x.w, acc);
+    }
+    return acc;
+}
+
+__device__ __forceinline__ void normalize_scalar(double &m, int64_t &e) {
+    if (m == 0.0 || !isfinite(m)) return;
+    const int k = rttd::exponent_of(m);
+    m = rttd::scale2(m, -k);
+    e += k;
+}
+
+// ------------------------------------------------------------------ site program
+struct Step {
+    int k, form;  // form 0: left-to-right (BT planes), 1: right-to-left (B planes)
+};
+
+template <int MODE>
+__device__ __forceinline__ Step step_of(const Args &a, int j, int t) {
+    if (MODE == M_ROWS) return {j + t, 0};
+    if (MODE == M_LEFT || MODE == M_INIT) return {t, 0};
+    if (MODE == M_RIGHT) return {a.L - 1 - t, 1};
+    const int span = (a.R - 1) * a.N + 1;
+    const int S = (a.N - 1) + a.N * span;
+    const int tt = t % S;
+    if (tt < a.N - 1) return {a.L - 1 - tt, 1};
+    const int u = tt - (a.N - 1);
+    return {u / span + u % span, 0};
+}
+
+template <int MODE>
+__device__ __forceinline__ long long n_steps_of(const Args &a, int j) {
+    const int span = (a.R - 1) * a.N + 1;
+    if (MODE == M_ROWS) return (j < a.N) ? span : (long long)(a.R - 1) * a.N;
+    if (MODE == M_LEFT) return a.N;
+    if (MODE == M_RIGHT) return a.N - 1;
+    if (MODE == M_INIT) return a.L;
+    return (long long)a.n_sweeps * ((a.N - 1) + (long long)a.N * span);
+}
+
+// ------------------------------------------------------------------ kernel
+template <int CHI, int MODE, bool F16>
+__global__ void __launch_bounds__(NT, 1)
+    k_tc(const __grid_constant__ CUtensorMap map, const Args a) {
+    using C = Cfg<CHI, F16>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t A_hi = sa(base), A_lo = A_hi + C::A_BYTES;
+    const uint32_t stage0 = A_lo + C::A_BYTES;
+    uint64_t *bars = (uint64_t *)(base + 2 * C::A_BYTES + NS * C::STAGE);
+    const uint32_t bar0 = sa(bars);
+    // bars: full[0..NS), empty[0..NS), mma_done
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (NS + s); };
+    const uint32_t done_bar = bar0 + 8u * (2 * NS);
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NS + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    uint32_t *bits = (uint32_t *)(base + 2 * C::A_BYTES + NS * C::STAGE + C::CTRL);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t c_raw = (int64_t)blockIdx.x * NT + tid;
+    const bool active = c_raw < a.B;
+    const int64_t c = active ? c_raw : a.B - 1;
+    const int j = (MODE == M_ROWS) ? (int)blockIdx.y : 0;
+    const int N = a.N;
+    const long long total_steps = n_steps_of<MODE>(a, j);
+    const long long total_atoms = total_steps * C::KA;
+
+    if (warp == 0) tmem_alloc(sa(tmem_slot), C::TCOLS);
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        mbar_init(done_bar, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    // spin bits: word (i, warp) holds bit (row & 31) = s_i of that row's chain
+    for (int i = 0; i < N; ++i) {
+        const uint32_t w = __ballot_sync(FULL, a.spins_in[c * N + i] != 0);
+        if (lane == 0) bits[i * 4 + warp] = w;
+    }
+    auto spin = [&](int i) -> int { return (int)((bits[i * 4 + warp] >> lane) & 1u); };
+
+    // start vector
+    float v[CHI];
+    int64_t E = 0;      // exponent of the current row
+    int64_t El = 0;     // sweep: exponent of l_{j-1};  keep/flip exponents below
+    int64_t Ekeep = 0, Eflip = 0;
+    double pm = 0.0;
+    int64_t pe = 0, acc_count = 0;
+    if (MODE == M_ROWS) {
+        if (j == 0) {
+            load_vec<CHI>(a.bl, v);
+        } else {
+            const size_t jm = (size_t)(j > 0 ? j - 1 : 0);
+            load_vec<CHI>(a.lstack + ((size_t)c * N + jm) * CHI, v);
+            E = a.lexp[(size_t)c * N + jm];
+        }
+    } else if (MODE == M_RIGHT || MODE == M_SWEEP) {
+        // a sweep opens with the right environment, unless N = 1 (no steps)
+        load_vec<CHI>(a.br, v);
+        if (active) {
+            store_vec<CHI>(a.rstack + ((size_t)c * N + (N - 1)) * CHI, v);
+            a.rexp[(size_t)c * N + (N - 1)] = 0;
+        }
+        if (MODE == M_SWEEP) {
+            pm = a.state[c].mant;
+            pe = a.state[c].exp2;
+            if (N == 1) load_vec<CHI>(a.bl, v);  // no right-environment steps
+        }
+    } else {
+        load_vec<CHI>(a.bl, v);
+    }
+    __syncthreads();
+    if (total_steps > 0) write_A<CHI, F16>(A_hi, A_lo, tid, v);
+    fence_async_smem();
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's lanes
+
+    // producer state (thread 0)
+    long long g_issued = 0, g_waited = 0;
+    auto issue_atom = [&](long long g) {
+        const long long t = g / C::KA;
+        const int at = (int)(g % C::KA);
+        const Step sp = step_of<MODE>(a, j, (int)t);
+        const int st = (int)(g % NS);
+        const int y_hi = ((sp.form * 2 + 0) * a.L + sp.k) * 2 * CHI;
+        const int y_lo = ((sp.form * 2 + 1) * a.L + sp.k) * 2 * CHI;
+        const uint32_t dst = stage0 + (uint32_t)st * C::STAGE;
+        mbar_expect_tx(full_bar(st), (uint32_t)C::STAGE);
+        tma_load_2d(dst, &map, at * 64, y_hi, full_bar(st));
+        tma_load_2d(dst + C::BOX, &map, at * 64, y_lo, full_bar(st));
+    };
+    if (tid == 0) {
+        while (g_issued < total_atoms && g_issued < NS) issue_atom(g_issued++);
+    }
+
+    const int span = (a.R - 1) * N + 1;
+    const int S_sweep = (N - 1) + N * span;
+    const int rbase = (a.R - 1) * N + 1;
+    bool aborted = false;
+
+    for (long long t = 0; t < total_steps; ++t) {
+        // ---------------- MMA issue (thread 0)
+        if (tid == 0) {
+            for (int at = 0; at < C::KA; ++at) {
+                const long long g = t * C::KA + at;
+                const int st = (int)(g % NS);
+                if (!mbar_wait(full_bar(st), (uint32_t)((g / NS) & 1), a.wait_limit)) {
+                    atomicOr(a.err, 1);
+                    *abort_flag = 1;
+                    break;
+                }
+                g_waited = g + 1;
+                tc_after();
+                const uint32_t b_hi = stage0 + (uint32_t)st * C::STAGE, b_lo = b_hi + C::BOX;
+#pragma unroll
+                for (int kb = 0; kb < 4; ++kb) {
+                    const uint32_t ao = (uint32_t)(at * C::A_ATOM + kb * 32);
+                    const uint32_t bo = (uint32_t)(kb * 32);
+                    mma_bf16(tmem, sdesc(A_hi + ao), sdesc(b_hi + bo), C::IDESC,
+                             (at | kb) != 0 ? 1u : 0u);
+                    mma_bf16(tmem, sdesc(A_hi + ao), sdesc(b_lo + bo), C::IDESC, 1u);
+                    mma_bf16(tmem, sdesc(A_lo + ao), sdesc(b_hi + bo), C::IDESC, 1u);
+                }
+                mma_commit(empty_bar(st));
+            }
+            mma_commit(done_bar);
+            // refill the ring with the atoms NS ahead
+            if (!*abort_flag) {
+                for (int at = 0; at < C::KA; ++at) {
+                    const long long g = t * C::KA + at;
+                    if (g + NS >= total_atoms) break;
+                    const int st = (int)(g % NS);
+                    if (!mbar_wait(empty_bar(st), (uint32_t)((g / NS) & 1), a.wait_limit)) {
+                        atomicOr(a.err, 1);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    issue_atom(g + NS);
+                    g_issued = g + NS + 1;
+                }
+            }
+        }
+        // ---------------- wait for the accumulator
+        if (!mbar_wait(done_bar, (uint32_t)(t & 1), a.wait_limit)) {
+            atomicOr(a.err, 1);
+            *abort_flag = 1;
+        }
+        tc_after();
+        __syncwarp();
+        bool write_next = false;
+        // ---------------- epilogue
+        if (MODE == M_ROWS) {
+            const int k = j + (int)t;
+            const int km = k % N;
+            const int sel = spin(__ldg(a.q + km)) ^ ((km == j && j < N) ? 1 : 0);
+            acc_select<CHI>(tw, sel, v);
+            E += renorm<CHI>(v) - __ldg(a.cexp + k);
+            write_next = (t + 1 < total_steps);
+        } else if (MODE == M_LEFT) {
+            const int k = (int)t;
+            acc_select<CHI>(tw, spin(__ldg(a.q + k)), v);
+            E += renorm<CHI>(v) - __ldg(a.cexp + k);
+            if (active) {
+                store_vec<CHI>(a.lstack + ((size_t)c * N + k) * CHI, v);
+                a.lexp[(size_t)c * N + k] = (int32_t)E;
+            }
+            write_next = (t + 1 < total_steps);
+        } else if (MODE == M_RIGHT) {
+            const int k = a.L - 1 - (int)t;
+            acc_select<CHI>(tw, spin(__ldg(a.q + (k % N))), v);
+            E += renorm<CHI>(v) - __ldg(a.cexp + k);
+            if (active) {
+                store_vec<CHI>(a.rstack + ((size_t)c * N + (k - rbase)) * CHI, v);
+                a.rexp[(size_t)c * N + (k - rbase)] = (int32_t)E;
+            }
+            write_next = (t + 1 < total_steps);
+        } else if (MODE == M_INIT) {
+            const int k = (int)t;
+            acc_select<CHI>(tw, spin(__ldg(a.q + (k % N))), v);
+            E += renorm<CHI>(v) - __ldg(a.cexp + k);
+            write_next = (t + 1 < total_steps);
+        } else {  // M_SWEEP
+            const int sw = (int)(t / S_sweep);
+            const int tt = (int)(t % S_sweep);
+            if (tt < N - 1) {  // right environment of the last block
+                const int k = a.L - 1 - tt;
+                acc_select<CHI>(tw, spin(__ldg(a.q + (k % N))), v);
+                E += renorm<CHI>(v) - __ldg(a.cexp + k);
+                if (active) {
+                    store_vec<CHI>(a.rstack + ((size_t)c * N + (k - rbase)) * CHI, v);
+                    a.rexp[(size_t)c * N + (k - rbase)] = (int32_t)E;
+                }
+                if (tt < N - 2) {
+                    write_next = true;
+                } else {  // next: proposal 0 starts from b_L
+                    load_vec<CHI>(a.bl, v);
+                    El = 0;
+                    write_next = true;
+                }
+            } else {
+                const int u = tt - (N - 1);
+                const int jj = u / span, i = u % span;
+                const int k = jj + i;
+                const int iq = __ldg(a.q + jj);
+                if (i == 0) {
+                    const int si = spin(iq);
+                    // unflipped continuation: l_jj if the proposal is rejected
+                    const int ck = __ldg(a.cexp + k);
+                    acc_select<CHI>(tw, si, v);
+                    Ekeep = El + renorm<CHI>(v) - ck;
+                    if (active) {
+                        store_vec<CHI>(a.lstack + ((size_t)c * N + jj) * CHI, v);
+                        a.lexp[(size_t)c * N + jj] = (int32_t)Ekeep;
+                    }
+                    // flipped start of the proposal row
+                    acc_select<CHI>(tw, si ^ 1, v);
+                    Eflip = El + renorm<CHI>(v) - ck;
+                    if (active) {
+                        store_vec<CHI>(a.tmp + (size_t)c * CHI, v);
+                        a.tmp_exp[c] = (int32_t)Eflip;
+                    }
+                    E = Eflip;
+                } else {
+                    const int km = k % N;
+                    acc_select<CHI>(tw, spin(__ldg(a.q + km)) ^ ((km == jj) ? 1 : 0), v);
+                    E += renorm<CHI>(v) - __ldg(a.cexp + k);
+                }
+                if (i + 1 < span) {
+                    write_next = true;
+                } else {
+                    // Metropolis decision of proposal jj (spin iq)
+                    const float *r = a.rstack + ((size_t)c * N + jj) * CHI;
+                    int64_t Ep = E + a.rexp[(size_t)c * N + jj];
+                    double m = dot<CHI>(v, r);
+                    normalize_scalar(m, Ep);
+                    const double ratio = ldexp(m / pm, (int)(Ep - pe));
+                    const double x = rttd::mcmc_uniform(a.seed, (uint64_t)(a.chain0 + c),
+                                                        (uint64_t)(a.sweep0 + sw), (uint64_t)jj);
+                    const bool accept = active && (x < ratio * ratio);
+                    if (accept) {
+                        pm = m;
+                        pe = Ep;
+                        ++acc_count;
+                        load_vec<CHI>(a.tmp + (size_t)c * CHI, v);
+                        store_vec<CHI>(a.lstack + ((size_t)c * N + jj) * CHI, v);
+                        a.lexp[(size_t)c * N + jj] = (int32_t)Eflip;
+                        El = Eflip;
+                    } else {
+                        El = Ekeep;
+                    }
+                    const uint32_t flips = __ballot_sync(FULL, accept);
+                    if (lane == 0) bits[iq * 4 + warp] ^= flips;
+                    __syncwarp();
+                    if (jj + 1 < N) {  // next proposal starts from l_jj
+                        load_vec<CHI>(a.lstack + ((size_t)c * N + jj) * CHI, v);
+                        write_next = true;
+                    } else if (sw + 1 < a.n_sweeps) {  // next sweep: right environment
+                        load_vec<CHI>(N > 1 ? a.br : a.bl, v);
+                        E = 0;
+                        El = 0;
+                        write_next = true;
+                    }
+                }
+            }
+        }
+        if (write_next) write_A<CHI, F16>(A_hi, A_lo, tid, v);
+        fence_async_smem();
+        tc_before();
+        __syncthreads();
+        tc_after();
+        if (*abort_flag) {
+            aborted = true;
+            break;
+        }
+    }
+
+    // ---------------- final contraction / outputs
+    if (!aborted) {
+        if (MODE == M_ROWS) {
+            const int rq = (j < N) ? j : N - 1;
+            int64_t Ep = E + a.rexp[(size_t)c * N + rq];
+            double m = dot<CHI>(v, a.rstack + ((size_t)c * N + rq) * CHI);
+            normalize_scalar(m, Ep);
+            if (active) {
+                a.rows_mant[c * (N + 1) + j] = m;
+                a.rows_exp[c * (N + 1) + j] = Ep;
+            }
+        } else if (MODE == M_INIT) {
+            double m = dot<CHI>(v, a.br);
+            int64_t Ep = E;
+            normalize_scalar(m, Ep);
+            if (active) {
+                if (a.state) {
+                    a.state[c].mant = m;
+                    a.state[c].exp2 = Ep;
+                }
+                if (a.log_abs)
+                    a.log_abs[c] = (m == 0.0) ? -INFINITY : (double)Ep * 0.6931471805599453 + log(fabs(m));
+                if (a.sign) a.sign[c] = (m > 0.0) ? 1 : ((m < 0.0) ? -1 : 0);
+            }
+        } else if (MODE == M_SWEEP) {
+            if (active) {
+                for (int i = 0; i < N; ++i) a.spins_out[c * N + i] = (uint8_t)spin(i);
+                a.state[c].mant = pm;
+                a.state[c].exp2 = pe;
+                if (a.n_accept) a.n_accept[c] += acc_count;
+            }
+        }
+    }
+    // ---------------- teardown: drain own copies (bounded), free TMEM
+    if (tid == 0 && aborted) {
+        for (long long g = g_waited; g < g_issued; ++g)
+            mbar_wait(full_bar((int)(g % NS)), (uint32_t)((g / NS) & 1), a.wait_limit);
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    if (warp == 0) tmem_dealloc(tmem, C::TCOLS);
+}
+
+}  // namespace tcd
+
+// ====================================================================== host side
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+inline void split16(double x, bool f16, uint16_t &hi, uint16_t &lo) {
+    const float xf = (float)x;
+    if (f16) {
+        const __half h = __float2half_rn(xf);
+        const __half l = __float2half_rn(xf - __half2float(h));
+        hi = *reinterpret_cast<const uint16_t *>(&h);
+        lo = *reinterpret_cast<const uint16_t *>(&l);
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(xf);
+        const __nv_bfloat16 l = __float2bfloat16_rn(xf - __bfloat162float(h));
+        hi = *reinterpret_cast<const uint16_t *>(&h);
+        lo = *reinterpret_cast<const uint16_t *>(&l);
+    }
+}
+
+tcd::Args make_args(rtt_s *h, int64_t B) {
+    tcd::Args a;
+    memset(&a, 0, sizeof(a));
+    TcPlan *p = h->tc;
+    a.bl = p->d_bl;
+    a.br = p->d_br;
+    a.q = h->d_q;
+    a.cexp = p->d_cexp;
+    a.N = h->N;
+    a.L = h->L;
+    a.R = h->R;
+    a.B = B;
+    a.lstack = (float *)h->d_lstack;
+    a.lexp = h->d_lexp;
+    a.rstack = (float *)h->d_rstack;
+    a.rexp = h->d_rexp;
+    a.rows_mant = h->d_rows_mant;
+    a.rows_exp = h->d_rows_exp;
+    a.err = p->d_err;
+    a.wait_limit = 4000000000LL;  // ~2 s at 2 GHz
+    return a;
+}
+
+template <int CHI, int MODE, bool F16>
+cudaError_t launch(const TcPlan *p, const tcd::Args &a, dim3 grid, cudaStream_t st) {
+    const size_t smem = tcd::Cfg<CHI, F16>::smem_bytes(a.N);
+    cudaError_t e = cudaFuncSetAttribute(tcd::k_tc<CHI, MODE, F16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tcd::k_tc<CHI, MODE, F16><<<grid, tcd::NT, smem, st>>>(p->map, a);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_chi(const TcPlan *p, const tcd::Args &a, dim3 grid, cudaStream_t st) {
+    if (p->chi == 64) return p->f16 ? launch<64, MODE, true>(p, a, grid, st)
+                                    : launch<64, MODE, false>(p, a, grid, st);
+    if (p->chi == 128) return p->f16 ? launch<128, MODE, true>(p, a, grid, st)
+                                     : launch<128, MODE, false>(p, a, grid, st);
+    return cudaErrorInvalidValue;
+}
+
+rtt_status status_of(cudaError_t e, const char *where) {
+    if (e == cudaSuccess) return RTT_OK;
+    rtt_set_error(std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return e == cudaErrorMemoryAllocation ? RTT_ERR_OOM : RTT_ERR_CUDA;
+}
+
+unsigned tiles(int64_t B) { return (unsigned)((B + tcd::NT - 1) / tcd::NT); }
+
+}  // namespace
+
+rtt_status tc_plan_create(rtt_s *h, const double *tensors, const double *bl, const double *br) {
+    const int chi = h->chi, L = h->L;
+    if (!tc_supported_chi(chi) || h->chip != chi) {
+        rtt_set_error("BF16X3 / FP16X3 support chi in {64, 128}");
+        return RTT_ERR_UNSUPPORTED;
+    }
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) {
+        rtt_set_error("cuTensorMapEncodeTiled unavailable from the driver");
+        return RTT_ERR_CUDA;
+    }
+    TcPlan *p = new TcPlan();
+    h->tc = p;
+    p->chi = chi;
+    p->f16 = (h->precision == RTT_FP16X3);
+    // exact per-site prescale 2^c_k bringing max|A_k| into [1,2)
+    std::vector<int32_t> cexp(L, 0);
+    for (int k = 0; k < L; ++k) {
+        double mx = 0.0;
+        for (size_t i = 0; i < (size_t)2 * chi * chi; ++i)
+            mx = std::max(mx, std::fabs(tensors[(size_t)k * 2 * chi * chi + i]));
+        cexp[k] = (mx > 0.0) ? -std::ilogb(mx) : 0;
+    }
+    const size_t rows = (size_t)4 * L * 2 * chi;
+    std::vector<uint16_t> Bh(rows * chi);
+    for (int k = 0; k < L; ++k)
+        for (int s = 0; s < 2; ++s)
+            for (int n = 0; n < chi; ++n)
+                for (int kk = 0; kk < chi; ++kk) {
+                    const double *A = tensors + ((size_t)k * 2 + s) * chi * chi;
+                    // left-to-right operand: row n = output column b, K index = a
+                    const double xt = std::ldexp(A[(size_t)kk * chi + n], cexp[k]);
+                    // right-to-left operand: row n = output index a, K index = b
+                    const double xb = std::ldexp(A[(size_t)n * chi + kk], cexp[k]);
+                    const size_t r0 = ((size_t)(0 * L + k) * 2 * chi + s * chi + n) * chi + kk;
+                    const size_t r1 = ((size_t)(1 * L + k) * 2 * chi + s * chi + n) * chi + kk;
+                    const size_t r2 = ((size_t)(2 * L + k) * 2 * chi + s * chi + n) * chi + kk;
+                    const size_t r3 = ((size_t)(3 * L + k) * 2 * chi + s * chi + n) * chi + kk;
+                    split16(xt, p->f16, Bh[r0], Bh[r1]);
+                    split16(xb, p->f16, Bh[r2], Bh[r3]);
+                }
+    cudaError_t e;
+    if ((e = cudaMalloc((void **)&p->d_B, Bh.size() * sizeof(uint16_t))) != cudaSuccess)
+        return status_of(e, "tc plan: tensors");
+    if ((e = cudaMemcpy(p->d_B, Bh.data(), Bh.size() * sizeof(uint16_t),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return status_of(e, "tc plan: tensors copy");
+    if ((e = cudaMalloc((void **)&p->d_cexp, (size_t)L * sizeof(int32_t))) != cudaSuccess)
+        return status_of(e, "tc plan: prescale");
+    cudaMemcpy(p->d_cexp, cexp.data(), (size_t)L * sizeof(int32_t), cudaMemcpyHostToDevice);
+    std::vector<float> blf(chi), brf(chi);
+    for (int i = 0; i < chi; ++i) {
+        blf[i] = (float)bl[i];
+        brf[i] = (float)br[i];
+    }
+    if ((e = cudaMalloc((void **)&p->d_bl, chi * 4)) != cudaSuccess) return status_of(e, "tc plan");
+    if ((e = cudaMalloc((void **)&p->d_br, chi * 4)) != cudaSuccess) return status_of(e, "tc plan");
+    cudaMemcpy(p->d_bl, blf.data(), chi * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(p->d_br, brf.data(), chi * 4, cudaMemcpyHostToDevice);
+    if ((e = cudaMalloc((void **)&p->d_err, sizeof(int))) != cudaSuccess) return status_of(e, "tc plan");
+    cudaMemset(p->d_err, 0, sizeof(int));
+    const cuuint64_t gdim[2] = {(cuuint64_t)chi, (cuuint64_t)rows};
+    const cuuint64_t gstride[1] = {(cuuint64_t)chi * sizeof(uint16_t)};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)(2 * chi)};
+    const cuuint32_t estride[2] = {1u, 1u};
+    CUresult r = enc(&p->map,
+                     p->f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                     p->d_B, gdim, gstride, box, estride,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        rtt_set_error("cuTensorMapEncodeTiled failed");
+        return RTT_ERR_CUDA;
+    }
+    return RTT_OK;
+}
+
+void tc_plan_destroy(rtt_s *h) {
+    TcPlan *p = h->tc;
+    if (!p) return;
+    cudaFree(p->d_B);
+    cudaFree(p->d_cexp);
+    cudaFree(p->d_bl);
+    cudaFree(p->d_br);
+    cudaFree(p->d_tmp);
+    cudaFree(p->d_tmp_exp);
+    cudaFree(p->d_err);
+    delete p;
+    h->tc = nullptr;
+}
+
+rtt_status tc_left_env(rtt_s *h, const uint8_t *spins, int64_t B, cudaStream_t st) {
+    tcd::Args a = make_args(h, B);
+    a.spins_in = spins;
+    prof_begin(h, KID_TC_LEFT_ENV, st);
+    cudaError_t e = launch_chi<tcd::M_LEFT>(h->tc, a, dim3(tiles(B)), st);
+    prof_end(h, KID_TC_LEFT_ENV, st);
+    return status_of(e, "tc left environments");
+}
+
+rtt_status tc_right_env(rtt_s *h, const uint8_t *spins, int64_t B, cudaStream_t st) {
+    tcd::Args a = make_args(h, B);
+    a.spins_in = spins;
+    prof_begin(h, KID_TC_RIGHT_ENV, st);
+    cudaError_t e = launch_chi<tcd::M_RIGHT>(h->tc, a, dim3(tiles(B)), st);
+    prof_end(h, KID_TC_RIGHT_ENV, st);
+    return status_of(e, "tc right environments");
+}
+
+rtt_status tc_rows(rtt_s *h, const uint8_t *spins, int64_t B, cudaStream_t st) {
+    tcd::Args a = make_args(h, B);
+    a.spins_in = spins;
+    prof_begin(h, KID_TC_ROWS, st);
+    cudaError_t e = launch_chi<tcd::M_ROWS>(h->tc, a, dim3(tiles(B), h->N + 1), st);
+    prof_end(h, KID_TC_ROWS, st);
+    return status_of(e, "tc flip rows");
+}
+
+rtt_status tc_chain_init(rtt_s *h, const uint8_t *spins, int64_t B, double *log_abs, int8_t *sign,
+                         rtt_chain_state *state, cudaStream_t st) {
+    tcd::Args a = make_args(h, B);
+    a.spins_in = spins;
+    a.log_abs = log_abs;
+    a.sign = sign;
+    a.state = state;
+    prof_begin(h, KID_TC_CHAIN_INIT, st);
+    cudaError_t e = launch_chi<tcd::M_INIT>(h->tc, a, dim3(tiles(B)), st);
+    prof_end(h, KID_TC_CHAIN_INIT, st);
+    return status_of(e, "tc log amplitudes");
+}
+
+rtt_status tc_sweep(rtt_s *h, uint8_t *spins, rtt_chain_state *state, int64_t B, int64_t chain0,
+                    int64_t sweep0, int32_t n_sweeps, int64_t *n_accept, cudaStream_t st) {
+    TcPlan *p = h->tc;
+    if (B > p->tmp_cap) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return status_of(e, "tc sweep scratch");
+        cudaFree(p->d_tmp);
+        cudaFree(p->d_tmp_exp);
+        p->d_tmp = nullptr;
+        p->d_tmp_exp = nullptr;
+        p->tmp_cap = 0;
+        if ((e = cudaMalloc((void **)&p->d_tmp, (size_t)B * p->chi * 4)) != cudaSuccess)
+            return status_of(e, "tc sweep scratch");
+        if ((e = cudaMalloc((void **)&p->d_tmp_exp, (size_t)B * 4)) != cudaSuccess)
+            return status_of(e, "tc sweep scratch");
+        p->tmp_cap = B;
+    }
+    tcd::Args a = make_args(h, B);
+    a.spins_in = spins;
+    a.spins_out = spins;
+    a.state = state;
+    a.tmp = p->d_tmp;
+    a.tmp_exp = p->d_tmp_exp;
+    a.chain0 = chain0;
+    a.sweep0 = sweep0;
+    a.n_sweeps = n_sweeps;
+    a.seed = h->seed;
+    a.n_accept = n_accept;
+    prof_begin(h, KID_TC_SWEEP, st);
+    cudaError_t e = launch_chi<tcd::M_SWEEP>(p, a, dim3(tiles(B)), st);
+    prof_end(h, KID_TC_SWEEP, st);
+    return status_of(e, "tc sweep");
+}
+
+int *tc_error_word(rtt_s *h) { return h->tc ? h->tc->d_err : nullptr; }

@@ -16,8 +16,8 @@ import torch
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "librtt.so")
 
-RTT_FP64, RTT_FP32, RTT_BF16X3 = 0, 1, 2
-PRECISIONS = {"fp64": RTT_FP64, "fp32": RTT_FP32, "bf16x3": RTT_BF16X3}
+RTT_FP64, RTT_FP32, RTT_BF16X3, RTT_FP16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": RTT_FP64, "fp32": RTT_FP32, "bf16x3": RTT_BF16X3, "fp16x3": RTT_FP16X3}
 STATUS = {0: "RTT_OK", 1: "RTT_ERR_INVALID_ARG", 2: "RTT_ERR_CUDA", 3: "RTT_ERR_OOM",
           4: "RTT_ERR_NUMERIC", 5: "RTT_ERR_TIMEOUT", 6: "RTT_ERR_UNSUPPORTED"}
 
@@ -217,7 +217,8 @@ class RTT:
         _dev_check(spins, torch.uint8, (B, self.n), "spins")
         _dev_check(state, torch.int64, (B, 2), "state")
         if trace is not None:
-            _dev_check(trace, torch.float64, (n_sweeps // measure_every, B), "trace")
+            rows = n_sweeps // measure_every if measure_every >= 1 else None
+            _dev_check(trace, torch.float64, None if rows is None else (rows, B), "trace")
         if n_accept is not None:
             _dev_check(n_accept, torch.int64, (B,), "n_accept")
         _check(lib().rtt_mcmc_sweep(self._h, _ptr(spins), _ptr(state), B, int(chain0), int(sweep0),

@@ -1,0 +1,228 @@
+"""GPU parity of the tensor-core split-precision paths (tcgen05; BF16 and FP16
+hi/lo operands) against the FP64 oracle, through the C ABI.
+
+Split-precision bound (first order): with 16-bit unit roundoff u_b (BF16
+2^-8, FP16 2^-11) the split x = hi + lo leaves |x - hi - lo| <= u_b^2 |x|,
+and the dropped lo.lo product is <= u_b^2 |x||y|; FP32 accumulation of chi
+terms adds chi u_32.  So
+every site product carries a componentwise error <= eps_site (|v||A|)_b with
+eps_site = 3 u_b^2 + chi u_32, i.e. a relative error <= eps_site kappa_k in
+norm, and the closing contraction <= eps_site kappa_fin.  Hence
+|d log|psi|| <= eps_site (sum_k kappa_k + kappa_fin), with the kappas computed
+per configuration by the oracle in FP64."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as orc
+from paper_2604_22718_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+UB = {"bf16x3": 2.0 ** -8, "fp16x3": 2.0 ** -11}
+U32 = 2.0 ** -24
+PRECS = ["bf16x3", "fp16x3"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2604_22718_gb300 import build
+    build.build()
+
+
+def _rtt():
+    from paper_2604_22718_gb300 import rtt
+    return rtt
+
+
+def eps_site(chi, prec):
+    return 3 * UB[prec] ** 2 + chi * U32
+
+
+def _status_ok(m):
+    rtt = _rtt()
+    flags = rtt.ctypes.c_int32()
+    st = rtt.lib().rtt_device_status(m.handle, rtt.ctypes.byref(flags))
+    return st == 0 and flags.value == 0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_first_light_tiny_train_matches_fp32(prec):
+    """Smallest case first: one partial tile, L = 8 sites, chi = 64."""
+    rtt = _rtt()
+    inst = inputs.make_instance(2, 2, 2, 64, 3.0, seed=31)
+    spins = torch.from_numpy(inputs.initial_spins(31, 37, 4)).cuda()
+    with rtt.RTT(inst, "fp32") as m32:
+        la32, sg32, _ = m32.log_amplitudes(spins)
+    with rtt.RTT(inst, prec) as mtc:
+        la, sg, _ = mtc.log_amplitudes(spins)
+        torch.cuda.synchronize()
+        assert _status_ok(mtc)
+    la, la32 = la.cpu().numpy(), la32.cpu().numpy()
+    print("first light: max |dlog| vs fp32", np.max(np.abs(la - la32)))
+    assert np.all(np.isfinite(la))
+    assert np.max(np.abs(la - la32)) < 1e-2
+    assert np.array_equal(sg.cpu().numpy(), sg32.cpu().numpy())
+
+
+CASES = [
+    ("6x6_R2_chi64", lambda: inputs.make_instance(6, 6, 2, 64, 3.0, seed=5), 300),
+    ("3x3_R2_chi64", lambda: inputs.make_instance(3, 3, 2, 64, 3.0, seed=8), 129),
+    ("4x5_R3_chi128", lambda: inputs.make_instance(4, 5, 3, 128, 3.04, seed=9), 200),
+    ("3x4_R1_chi128_mps", lambda: inputs.make_instance(3, 4, 1, 128, 3.0, seed=10), 64),
+]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name,make,B", CASES, ids=[c[0] for c in CASES])
+def test_split_log_amplitudes_within_bound(name, make, B, prec):
+    rtt = _rtt()
+    inst = make()
+    o = orc.Oracle(inst)
+    spins = inputs.initial_spins(41, B, inst.n_spins)
+    la_o, sg_o, _, _ = o.log_amplitudes(spins)
+    cond = o.amplitude_cond(spins)
+    with rtt.RTT(inst, prec) as m:
+        la, sg, _ = m.log_amplitudes(torch.from_numpy(spins).cuda())
+        torch.cuda.synchronize()
+        assert _status_ok(m)
+    la, sg = la.cpu().numpy(), sg.cpu().numpy()
+    err = np.abs(la - la_o)
+    bound = eps_site(inst.chi, prec) * (cond[:, 0] + cond[:, 2])
+    print(f"[{name}] {prec} log|psi|: median err {np.median(err):.2e}, max {err.max():.2e}, "
+          f"max err/bound {np.max(err / bound):.3f}")
+    assert np.all(err <= bound)
+    ok_sign = (sg == sg_o) | (cond[:, 2] * eps_site(inst.chi, prec) > 0.5)
+    assert np.all(ok_sign)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name,make,B", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_split_local_energy_teacher_forced(name, make, B, prec):
+    """Same configurations through the FP64 oracle and the split path.  Every
+    ratio psi(s^(i))/psi(s) obeys the split bound of its two amplitudes,
+    |dr| <= |r| eps_site (K(s) + K(s^(i))), K = sum_k kappa_k + kappa_fin from
+    the oracle; FP16X3 also meets the precision gate of the metric: the mean
+    local energy within 1e-4 relative (of the mean |E_loc| when the mean is
+    near zero)."""
+    rtt = _rtt()
+    inst = make()
+    o = orc.Oracle(inst)
+    B = min(B, 48)
+    spins = inputs.initial_spins(42, B, inst.n_spins)
+    e_o, r_o = o.local_energies(spins, with_ratios=True, threads=16)
+    with rtt.RTT(inst, prec) as m:
+        e, r = m.local_energy(torch.from_numpy(spins).cuda(), with_ratios=True)
+        torch.cuda.synchronize()
+        assert _status_ok(m)
+    e, r = e.cpu().numpy(), r.cpu().numpy()
+    eps = eps_site(inst.chi, prec)
+    K = o.amplitude_cond(spins)
+    K = K[:, 0] + K[:, 2]
+    nc = min(B, 12)
+    flipped = np.repeat(spins[:nc], inst.n_spins, axis=0)
+    idx = np.tile(np.arange(inst.n_spins), nc)
+    flipped[np.arange(flipped.shape[0]), idx] ^= 1
+    Kf = o.amplitude_cond(flipped)
+    Kf = (Kf[:, 0] + Kf[:, 2]).reshape(nc, inst.n_spins)
+    bound = np.abs(r_o[:nc]) * eps * (K[:nc, None] + Kf)
+    dr = np.abs(r[:nc] - r_o[:nc])
+    de = abs(e.mean() - e_o.mean())
+    rel_mean = de / max(abs(e_o.mean()), np.mean(np.abs(e_o)))
+    print(f"[{name}] {prec} E_loc: mean rel err {rel_mean:.2e} (|dE| {de:.2e}), "
+          f"max |dr|/bound {np.max(dr / bound):.3f}, median |dr|/|r| {np.median(dr / np.abs(r_o[:nc])):.2e}")
+    assert np.all(dr <= bound)
+    if prec == "fp16x3":
+        assert rel_mean <= 1e-4
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_split_sampler_energy_matches_exact(prec):
+    rtt = _rtt()
+    inst = inputs.make_instance(3, 3, 2, 64, 3.0, seed=8)
+    e_exact = orc.Oracle(inst).exact_energy()
+    B, T = 512, 300
+    with rtt.RTT(inst, prec, seed=7) as m:
+        sg = torch.from_numpy(inputs.initial_spins(43, B, 9)).cuda()
+        _, _, st = m.log_amplitudes(sg)
+        m.mcmc_sweep(sg, st, 0, 60, 1, None)
+        tr = torch.empty((T, B), dtype=torch.float64, device="cuda")
+        acc = torch.zeros(B, dtype=torch.int64, device="cuda")
+        m.mcmc_sweep(sg, st, 60, T, 1, tr, acc)
+        stats = m.observables(tr, acc, T * 9)
+        assert _status_ok(m)
+    print(prec, "sampler", stats, "exact", e_exact)
+    assert abs(stats["mean"] - e_exact) < 3.5 * stats["se"], (stats, e_exact)
+    assert 0 < stats["accept_rate"] < 1
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_split_sweep_follows_oracle_decisions(prec):
+    """One sweep from the same start: BF16X3 and FP64 take the same decisions
+    except where a proposal is a near tie (|u - r^2| small)."""
+    rtt = _rtt()
+    inst = inputs.make_instance(6, 6, 2, 64, 3.0, seed=5)
+    o = orc.Oracle(inst)
+    B = 64
+    s0 = inputs.initial_spins(44, B, 36)
+    so = s0.copy()
+    mo, eo = o.init_chains(so)
+    _, acc_o = o.mcmc(11, so, mo, eo, 0, 1, record=False, threads=16)
+    with rtt.RTT(inst, prec, seed=11) as m:
+        sg = torch.from_numpy(s0.copy()).cuda()
+        _, _, st = m.log_amplitudes(sg)
+        acc = torch.zeros(B, dtype=torch.int64, device="cuda")
+        m.mcmc_sweep(sg, st, 0, 1, 1, None, acc)
+        torch.cuda.synchronize()
+        assert _status_ok(m)
+    same = np.all(sg.cpu().numpy() == so, axis=1)
+    print(prec, "sweep: identical chains", same.mean())
+    assert same.mean() >= 0.9
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_split_measured_trace_equals_standalone_energy(prec):
+    rtt = _rtt()
+    inst = inputs.make_instance(4, 5, 3, 128, 3.04, seed=9)
+    B = 200
+    with rtt.RTT(inst, prec, seed=3) as m:
+        sg = torch.from_numpy(inputs.initial_spins(45, B, 20)).cuda()
+        _, _, st = m.log_amplitudes(sg)
+        tr = torch.empty((2, B), dtype=torch.float64, device="cuda")
+        m.mcmc_sweep(sg, st, 0, 2, 1, tr)
+        e = m.local_energy(sg)
+        torch.cuda.synchronize()
+        assert _status_ok(m)
+    np.testing.assert_allclose(tr[1].cpu().numpy(), e.cpu().numpy(), rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_prec_10x10_full_batch_sampled_against_oracle(prec):
+    """The 10x10 / R=3 / chi=128 workload at its full 16384 chains: amplitudes
+    and local energies of sampled chains against the oracle one by one."""
+    rtt = _rtt()
+    w = inputs.WORKLOADS["prec_10x10"]
+    inst = inputs.workload("prec_10x10")
+    o = orc.Oracle(inst)
+    B = w["chains"]
+    s0 = inputs.initial_spins(w["seed"], B, inst.n_spins)
+    pick = np.array([0, 5000, B - 1])
+    with rtt.RTT(inst, prec, seed=w["seed"]) as m:
+        sg = torch.from_numpy(s0.copy()).cuda()
+        la, _, st = m.log_amplitudes(sg)
+        e = m.local_energy(sg)
+        tr = torch.empty((1, B), dtype=torch.float64, device="cuda")
+        m.mcmc_sweep(sg, st, 0, 1, 1, tr)
+        torch.cuda.synchronize()
+        assert _status_ok(m)
+    la, e = la.cpu().numpy(), e.cpu().numpy()
+    la_o, _, _, _ = o.log_amplitudes(s0[pick])
+    cond = o.amplitude_cond(s0[pick])
+    assert np.all(np.abs(la[pick] - la_o) <= eps_site(128, prec) * (cond[:, 0] + cond[:, 2]))
+    e_o = o.local_energies(s0[pick], threads=3)
+    print("prec_10x10 E_loc sampled", e[pick], e_o)
+    scale = inst.bonds.shape[0] + inst.h * inst.n_spins
+    assert np.all(np.abs(e[pick] - e_o) <= 1e-3 * scale)
+    assert np.all(np.isfinite(tr.cpu().numpy()))
