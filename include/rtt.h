@@ -186,6 +186,28 @@ typedef struct {
 rtt_status rtt_profile(rtt_handle h, int32_t enable);
 rtt_status rtt_profile_read(rtt_handle h, rtt_kernel_time *out, int32_t capacity, int32_t *count);
 
+/* The local energy of rtt_local_energy (same kernels, same results) from a
+ * call that allocates no device memory.  The paper has no counterpart: this
+ * is an operational variant for callers that cannot allocate at the time of
+ * the call -- code recorded into a CUDA graph by stream capture (no cudaMalloc
+ * during capture), loops that forbid allocator calls after start-up, or
+ * programs whose device memory is owned by an external pool manager.
+ *   Scratch comes from one 32 MiB array compiled into the library as a device
+ * global (every GPU that loads the library holds it until the process exits);
+ * a batch whose scratch -- two stacks of B*N*chi_p values (8 B in FP64, 4 B in
+ * FP32) plus 4 B exponents each, and 16 B * B*(N+1) for the rows -- exceeds
+ * 32 MiB is rejected with RTT_ERR_INVALID_ARG before anything is launched
+ * (split the batch).  FP64 and FP32 handles only (RTT_ERR_UNSUPPORTED else).
+ *   The first call on a device looks up the array's device address with that
+ * device current (once per device); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * nothing needs clearing (every entry is written before it is read), but
+ * calls that overlap on the GPU -- on different streams, or from threads
+ * without ordering -- race on it; serialize them.  spins, e_loc, ratios and
+ * stream as for rtt_local_energy. */
+rtt_status rtt_local_energy_noalloc(rtt_handle h, const uint8_t *spins, int64_t B,
+                                    double *e_loc, double *ratios, void *stream);
+
 /* Device-side error flags of the handle's kernels since the last call
  * (bit 0: a bounded wait inside a tensor-core kernel ran out of its clock
  * budget; that kernel recorded the flag, drained its own copies, freed its
