@@ -68,8 +68,9 @@ struct Cfg {
                                       ((uint32_t)((2 * CHI) >> 3) << 17) |
                                       ((uint32_t)(128 >> 4) << 24);
     static constexpr int CTRL = 128;
-    static size_t smem_bytes(int N) {
-        return 1024 + 2 * (size_t)A_BYTES + (size_t)NS * STAGE + CTRL + (size_t)16 * N;
+    static size_t smem_bytes(int N, int L) {
+        return 1024 + 2 * (size_t)A_BYTES + (size_t)NS * STAGE + CTRL + (size_t)16 * N +
+               (size_t)4 * L;
     }
 };
 
@@ -212,23 +213,81 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
                  : "memory");
 }
 
+// Two 64-column loads (32x32b.x64) -- the same column block of both
+// accumulator halves -- and the wait, in one statement.
+__device__ __forceinline__ void tmem_ld_2x64(uint32_t t0, uint32_t t1, uint32_t (&x)[64],
+                                             uint32_t (&y)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%128];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%64,%65,%66,%67,%68,%69,%70,%71,%72,%73,%74,%75,%76,%77,%78,%79,"
+        "%80,%81,%82,%83,%84,%85,%86,%87,%88,%89,%90,%91,%92,%93,%94,%95,"
+        "%96,%97,%98,%99,%100,%101,%102,%103,%104,%105,%106,%107,%108,%109,%110,%111,"
+        "%112,%113,%114,%115,%116,%117,%118,%119,%120,%121,%122,%123,%124,%125,%126,%127}, [%129];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]),
+          "=r"(x[7]), "=r"(x[8]), "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]),
+          "=r"(x[13]), "=r"(x[14]), "=r"(x[15]), "=r"(x[16]), "=r"(x[17]), "=r"(x[18]),
+          "=r"(x[19]), "=r"(x[20]), "=r"(x[21]), "=r"(x[22]), "=r"(x[23]), "=r"(x[24]),
+          "=r"(x[25]), "=r"(x[26]), "=r"(x[27]), "=r"(x[28]), "=r"(x[29]), "=r"(x[30]),
+          "=r"(x[31]), "=r"(x[32]), "=r"(x[33]), "=r"(x[34]), "=r"(x[35]), "=r"(x[36]),
+          "=r"(x[37]), "=r"(x[38]), "=r"(x[39]), "=r"(x[40]), "=r"(x[41]), "=r"(x[42]),
+          "=r"(x[43]), "=r"(x[44]), "=r"(x[45]), "=r"(x[46]), "=r"(x[47]), "=r"(x[48]),
+          "=r"(x[49]), "=r"(x[50]), "=r"(x[51]), "=r"(x[52]), "=r"(x[53]), "=r"(x[54]),
+          "=r"(x[55]), "=r"(x[56]), "=r"(x[57]), "=r"(x[58]), "=r"(x[59]), "=r"(x[60]),
+          "=r"(x[61]), "=r"(x[62]), "=r"(x[63]), "=r"(y[0]), "=r"(y[1]), "=r"(y[2]),
+          "=r"(y[3]), "=r"(y[4]), "=r"(y[5]), "=r"(y[6]), "=r"(y[7]), "=r"(y[8]), "=r"(y[9]),
+          "=r"(y[10]), "=r"(y[11]), "=r"(y[12]), "=r"(y[13]), "=r"(y[14]), "=r"(y[15]),
+          "=r"(y[16]), "=r"(y[17]), "=r"(y[18]), "=r"(y[19]), "=r"(y[20]), "=r"(y[21]),
+          "=r"(y[22]), "=r"(y[23]), "=r"(y[24]), "=r"(y[25]), "=r"(y[26]), "=r"(y[27]),
+          "=r"(y[28]), "=r"(y[29]), "=r"(y[30]), "=r"(y[31]), "=r"(y[32]), "=r"(y[33]),
+          "=r"(y[34]), "=r"(y[35]), "=r"(y[36]), "=r"(y[37]), "=r"(y[38]), "=r"(y[39]),
+          "=r"(y[40]), "=r"(y[41]), "=r"(y[42]), "=r"(y[43]), "=r"(y[44]), "=r"(y[45]),
+          "=r"(y[46]), "=r"(y[47]), "=r"(y[48]), "=r"(y[49]), "=r"(y[50]), "=r"(y[51]),
+          "=r"(y[52]), "=r"(y[53]), "=r"(y[54]), "=r"(y[55]), "=r"(y[56]), "=r"(y[57]),
+          "=r"(y[58]), "=r"(y[59]), "=r"(y[60]), "=r"(y[61]), "=r"(y[62]), "=r"(y[63])
+        : "r"(t0), "r"(t1)
+        : "memory");
+}
+
 // ------------------------------------------------------------------ row helpers
+// Accumulator half `sel` (0: columns [0,chi), 1: [chi,2chi)) of this thread's
+// TMEM lane.  The column address of tcgen05.ld is warp-uniform, so both halves
+// are loaded and the row's half is selected in registers.
 template <int CHI>
 __device__ __forceinline__ void acc_select(uint32_t tw, int sel, float (&v)[CHI]) {
+    if constexpr (CHI == 64) {
+        uint32_t x0[64], x1[64];
+        tmem_ld_2x64(tw, tw + CHI, x0, x1);
 #pragma unroll
-    for (int c = 0; c < CHI; c += 32) {
-        uint32_t x0[32], x1[32];
-        tmem_ld_2x32(tw + c, tw + CHI + c, x0, x1);
+        for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(sel ? x1[i] : x0[i]);
+    } else {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[c + i] = __uint_as_float(sel ? x1[i] : x0[i]);
+        for (int c = 0; c < CHI; c += 32) {
+            uint32_t x0[32], x1[32];
+            tmem_ld_2x32(tw + c, tw + CHI + c, x0, x1);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[c + i] = __uint_as_float(sel ? x1[i] : x0[i]);
+        }
     }
 }
 
+// Rescale by an exact power of two so that max|v| lies in [1,2); returns the
+// exponent taken out.  Eight independent partial maxima keep the dependency
+// chain short.
 template <int CHI>
 __device__ __forceinline__ int renorm(float (&v)[CHI]) {
-    float mx = 0.f;
+    float m[8];
 #pragma unroll
-    for (int i = 0; i < CHI; ++i) mx = fmaxf(mx, fabsf(v[i]));
+    for (int p = 0; p < 8; ++p) m[p] = fabsf(v[p]);
+#pragma unroll
+    for (int i = 8; i < CHI; ++i) m[i & 7] = fmaxf(m[i & 7], fabsf(v[i]));
+    const float mx = fmaxf(fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3])),
+                           fmaxf(fmaxf(m[4], m[5]), fmaxf(m[6], m[7])));
     if (!(mx > 0.f) || !isfinite(mx)) return 0;
     const int e = rttd::exponent_of(mx);
 #pragma unroll
@@ -291,19 +350,27 @@ __device__ __forceinline__ void store_vec(float *__restrict__ p, const float (&v
 #pragma unroll
     for (int i = 0; i < CHI / 4; ++i) p4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
 }
+// Closing contraction sum_b v_b r_b: eight FP32 partial sums (fma), combined
+// in FP64.
 template <int CHI>
 __device__ __forceinline__ double dot(const float (&v)[CHI], const float *__restrict__ r) {
-    double acc = 0.0;
+    float acc[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) acc[p] = 0.f;
     const float4 *r4 = reinterpret_cast<const float4 *>(r);
 #pragma unroll
     for (int i = 0; i < CHI / 4; ++i) {
         const float4 x = r4[i];
-        acc = fma((double)v[4 * i], (double)x.x, acc);
-        acc = fma((double)v[4 * i + 1], (double)x.y, acc);
-        acc = fma((double)v[4 * i + 2], (double)x.z, acc);
-        acc = fma((double)v[4 * i + 3], (double)x.w, acc);
+        const int p = (2 * i) & 7;
+        acc[p] = fmaf(v[4 * i], x.x, acc[p]);
+        acc[p + 1] = fmaf(v[4 * i + 1], x.y, acc[p + 1]);
+        acc[(p + 2) & 7] = fmaf(v[4 * i + 2], x.z, acc[(p + 2) & 7]);
+        acc[(p + 3) & 7] = fmaf(v[4 * i + 3], x.w, acc[(p + 3) & 7]);
     }
-    return acc;
+    double s = 0.0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) s += (double)acc[p];
+    return s;
 }
 
 __device__ __forceinline__ void normalize_scalar(double &m, int64_t &e) {
@@ -314,21 +381,68 @@ __device__ __forceinline__ void normalize_scalar(double &m, int64_t &e) {
 }
 
 // ------------------------------------------------------------------ site program
-struct Step {
+// A cursor walks the sites a CTA visits, in order, without divisions:
+//   ROWS   k = j, j+1, ...            (left to right)
+//   LEFT   k = 0 .. N-1               INIT  k = 0 .. L-1
+//   RIGHT  k = L-1 .. (R-1)N+1        (right to left)
+//   SWEEP  per sweep: right environment (form 1, k = L-1 .. (R-1)N+1),
+//          then for jj = 0..N-1 the flip row k = jj .. jj + (R-1)N (form 0)
+struct Cursor {
     int k, form;  // form 0: left-to-right (BT planes), 1: right-to-left (B planes)
+    int tt;       // sweep: right-environment step
+    int jj, i;    // sweep: proposal and position in its row
+    int sw;       // sweep number
 };
 
 template <int MODE>
-__device__ __forceinline__ Step step_of(const Args &a, int j, int t) {
-    if (MODE == M_ROWS) return {j + t, 0};
-    if (MODE == M_LEFT || MODE == M_INIT) return {t, 0};
-    if (MODE == M_RIGHT) return {a.L - 1 - t, 1};
-    const int span = (a.R - 1) * a.N + 1;
-    const int S = (a.N - 1) + a.N * span;
-    const int tt = t % S;
-    if (tt < a.N - 1) return {a.L - 1 - tt, 1};
-    const int u = tt - (a.N - 1);
-    return {u / span + u % span, 0};
+__device__ __forceinline__ Cursor cursor_start(const Args &a, int j) {
+    Cursor c{0, 0, 0, 0, 0, 0};
+    if (MODE == M_ROWS) c.k = j;
+    if (MODE == M_RIGHT) {
+        c.k = a.L - 1;
+        c.form = 1;
+    }
+    if (MODE == M_SWEEP && a.N > 1) {
+        c.k = a.L - 1;
+        c.form = 1;
+    }
+    return c;
+}
+
+template <int MODE>
+__device__ __forceinline__ void cursor_next(Cursor &c, const Args &a, int span) {
+    if (MODE == M_ROWS || MODE == M_LEFT || MODE == M_INIT) {
+        ++c.k;
+    } else if (MODE == M_RIGHT) {
+        --c.k;
+    } else if (c.form == 1) {
+        ++c.tt;
+        --c.k;
+        if (c.tt == a.N - 1) {
+            c.form = 0;
+            c.jj = 0;
+            c.i = 0;
+            c.k = 0;
+        }
+    } else {
+        ++c.i;
+        ++c.k;
+        if (c.i == span) {
+            ++c.jj;
+            c.i = 0;
+            c.k = c.jj;
+            if (c.jj == a.N) {
+                ++c.sw;
+                c.jj = 0;
+                c.k = 0;
+                c.tt = 0;
+                if (a.N > 1) {
+                    c.form = 1;
+                    c.k = a.L - 1;
+                }
+            }
+        }
+    }
 }
 
 template <int MODE>
@@ -359,6 +473,8 @@ __global__ void __launch_bounds__(NT, 1)
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NS + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     uint32_t *bits = (uint32_t *)(base + 2 * C::A_BYTES + NS * C::STAGE + C::CTRL);
+    // site table: low 16 bits spin q[k mod N], high 16 bits the prescale c_k
+    uint32_t *tab = bits + 4 * a.N;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t c_raw = (int64_t)blockIdx.x * NT + tid;
@@ -366,6 +482,8 @@ __global__ void __launch_bounds__(NT, 1)
     const int64_t c = active ? c_raw : a.B - 1;
     const int j = (MODE == M_ROWS) ? (int)blockIdx.y : 0;
     const int N = a.N;
+    const int span = (a.R - 1) * N + 1;
+    const int rbase = (a.R - 1) * N + 1;
     const long long total_steps = n_steps_of<MODE>(a, j);
     const long long total_atoms = total_steps * C::KA;
 
@@ -379,17 +497,22 @@ __global__ void __launch_bounds__(NT, 1)
         *abort_flag = 0;
         fence_barrier_init();
     }
+    for (int k = tid; k < a.L; k += NT)
+        tab[k] = ((uint32_t)__ldg(a.q + (k % N)) & 0xffffu) |
+                 ((uint32_t)(__ldg(a.cexp + k) & 0xffff) << 16);
     // spin bits: word (i, warp) holds bit (row & 31) = s_i of that row's chain
     for (int i = 0; i < N; ++i) {
         const uint32_t w = __ballot_sync(FULL, a.spins_in[c * N + i] != 0);
         if (lane == 0) bits[i * 4 + warp] = w;
     }
     auto spin = [&](int i) -> int { return (int)((bits[i * 4 + warp] >> lane) & 1u); };
+    auto site_spin = [&](int k) -> int { return (int)(tab[k] & 0xffffu); };
+    auto site_cexp = [&](int k) -> int { return (int)(int16_t)(tab[k] >> 16); };
 
     // start vector
     float v[CHI];
     int64_t E = 0;      // exponent of the current row
-    int64_t El = 0;     // sweep: exponent of l_{j-1};  keep/flip exponents below
+    int64_t El = 0;     // sweep: exponent of l_{jj-1}
     int64_t Ekeep = 0, Eflip = 0;
     double pm = 0.0;
     int64_t pe = 0, acc_count = 0;
@@ -402,7 +525,6 @@ __global__ void __launch_bounds__(NT, 1)
             E = a.lexp[(size_t)c * N + jm];
         }
     } else if (MODE == M_RIGHT || MODE == M_SWEEP) {
-        // a sweep opens with the right environment, unless N = 1 (no steps)
         load_vec<CHI>(a.br, v);
         if (active) {
             store_vec<CHI>(a.rstack + ((size_t)c * N + (N - 1)) * CHI, v);
@@ -425,27 +547,30 @@ __global__ void __launch_bounds__(NT, 1)
     const uint32_t tmem = *tmem_slot;
     const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's lanes
 
-    // producer state (thread 0)
+    // producer (thread 0): cursor over atoms; atom g = step * KA + at
     long long g_issued = 0, g_waited = 0;
-    auto issue_atom = [&](long long g) {
-        const long long t = g / C::KA;
-        const int at = (int)(g % C::KA);
-        const Step sp = step_of<MODE>(a, j, (int)t);
+    Cursor pc = cursor_start<MODE>(a, j);
+    int p_at = 0;
+    auto issue_next = [&]() {
+        const long long g = g_issued;
         const int st = (int)(g % NS);
-        const int y_hi = ((sp.form * 2 + 0) * a.L + sp.k) * 2 * CHI;
-        const int y_lo = ((sp.form * 2 + 1) * a.L + sp.k) * 2 * CHI;
+        const int y_hi = ((pc.form * 2 + 0) * a.L + pc.k) * 2 * CHI;
+        const int y_lo = ((pc.form * 2 + 1) * a.L + pc.k) * 2 * CHI;
         const uint32_t dst = stage0 + (uint32_t)st * C::STAGE;
         mbar_expect_tx(full_bar(st), (uint32_t)C::STAGE);
-        tma_load_2d(dst, &map, at * 64, y_hi, full_bar(st));
-        tma_load_2d(dst + C::BOX, &map, at * 64, y_lo, full_bar(st));
+        tma_load_2d(dst, &map, p_at * 64, y_hi, full_bar(st));
+        tma_load_2d(dst + C::BOX, &map, p_at * 64, y_lo, full_bar(st));
+        ++g_issued;
+        if (++p_at == C::KA) {
+            p_at = 0;
+            cursor_next<MODE>(pc, a, span);
+        }
     };
     if (tid == 0) {
-        while (g_issued < total_atoms && g_issued < NS) issue_atom(g_issued++);
+        while (g_issued < total_atoms && g_issued < NS) issue_next();
     }
 
-    const int span = (a.R - 1) * N + 1;
-    const int S_sweep = (N - 1) + N * span;
-    const int rbase = (a.R - 1) * N + 1;
+    Cursor cc = cursor_start<MODE>(a, j);
     bool aborted = false;
 
     for (long long t = 0; t < total_steps; ++t) {
@@ -474,7 +599,7 @@ __global__ void __launch_bounds__(NT, 1)
                 mma_commit(empty_bar(st));
             }
             mma_commit(done_bar);
-            // refill the ring with the atoms NS ahead
+            // refill: each stage as soon as the MMAs that read it are done
             if (!*abort_flag) {
                 for (int at = 0; at < C::KA; ++at) {
                     const long long g = t * C::KA + at;
@@ -485,8 +610,7 @@ __global__ void __launch_bounds__(NT, 1)
                         *abort_flag = 1;
                         break;
                     }
-                    issue_atom(g + NS);
-                    g_issued = g + NS + 1;
+                    issue_next();
                 }
             }
         }
@@ -498,64 +622,54 @@ __global__ void __launch_bounds__(NT, 1)
         tc_after();
         __syncwarp();
         bool write_next = false;
+        const int k = cc.k;
+        const int sk = site_spin(k);
+        const int ck = site_cexp(k);
         // ---------------- epilogue
         if (MODE == M_ROWS) {
-            const int k = j + (int)t;
-            const int km = k % N;
-            const int sel = spin(__ldg(a.q + km)) ^ ((km == j && j < N) ? 1 : 0);
-            acc_select<CHI>(tw, sel, v);
-            E += renorm<CHI>(v) - __ldg(a.cexp + k);
+            const int iflip = (j < N) ? site_spin(j) : -1;
+            acc_select<CHI>(tw, spin(sk) ^ (sk == iflip ? 1 : 0), v);
+            E += renorm<CHI>(v) - ck;
             write_next = (t + 1 < total_steps);
         } else if (MODE == M_LEFT) {
-            const int k = (int)t;
-            acc_select<CHI>(tw, spin(__ldg(a.q + k)), v);
-            E += renorm<CHI>(v) - __ldg(a.cexp + k);
+            acc_select<CHI>(tw, spin(sk), v);
+            E += renorm<CHI>(v) - ck;
             if (active) {
                 store_vec<CHI>(a.lstack + ((size_t)c * N + k) * CHI, v);
                 a.lexp[(size_t)c * N + k] = (int32_t)E;
             }
             write_next = (t + 1 < total_steps);
         } else if (MODE == M_RIGHT) {
-            const int k = a.L - 1 - (int)t;
-            acc_select<CHI>(tw, spin(__ldg(a.q + (k % N))), v);
-            E += renorm<CHI>(v) - __ldg(a.cexp + k);
+            acc_select<CHI>(tw, spin(sk), v);
+            E += renorm<CHI>(v) - ck;
             if (active) {
                 store_vec<CHI>(a.rstack + ((size_t)c * N + (k - rbase)) * CHI, v);
                 a.rexp[(size_t)c * N + (k - rbase)] = (int32_t)E;
             }
             write_next = (t + 1 < total_steps);
         } else if (MODE == M_INIT) {
-            const int k = (int)t;
-            acc_select<CHI>(tw, spin(__ldg(a.q + (k % N))), v);
-            E += renorm<CHI>(v) - __ldg(a.cexp + k);
+            acc_select<CHI>(tw, spin(sk), v);
+            E += renorm<CHI>(v) - ck;
             write_next = (t + 1 < total_steps);
         } else {  // M_SWEEP
-            const int sw = (int)(t / S_sweep);
-            const int tt = (int)(t % S_sweep);
-            if (tt < N - 1) {  // right environment of the last block
-                const int k = a.L - 1 - tt;
-                acc_select<CHI>(tw, spin(__ldg(a.q + (k % N))), v);
-                E += renorm<CHI>(v) - __ldg(a.cexp + k);
+            if (cc.form == 1) {  // right environment of the last block
+                acc_select<CHI>(tw, spin(sk), v);
+                E += renorm<CHI>(v) - ck;
                 if (active) {
                     store_vec<CHI>(a.rstack + ((size_t)c * N + (k - rbase)) * CHI, v);
                     a.rexp[(size_t)c * N + (k - rbase)] = (int32_t)E;
                 }
-                if (tt < N - 2) {
-                    write_next = true;
-                } else {  // next: proposal 0 starts from b_L
+                if (cc.tt == N - 2) {  // next: proposal 0 starts from b_L
                     load_vec<CHI>(a.bl, v);
                     El = 0;
-                    write_next = true;
                 }
+                write_next = true;
             } else {
-                const int u = tt - (N - 1);
-                const int jj = u / span, i = u % span;
-                const int k = jj + i;
-                const int iq = __ldg(a.q + jj);
-                if (i == 0) {
+                const int jj = cc.jj;
+                const int iq = site_spin(jj);
+                if (cc.i == 0) {
                     const int si = spin(iq);
                     // unflipped continuation: l_jj if the proposal is rejected
-                    const int ck = __ldg(a.cexp + k);
                     acc_select<CHI>(tw, si, v);
                     Ekeep = El + renorm<CHI>(v) - ck;
                     if (active) {
@@ -571,11 +685,10 @@ __global__ void __launch_bounds__(NT, 1)
                     }
                     E = Eflip;
                 } else {
-                    const int km = k % N;
-                    acc_select<CHI>(tw, spin(__ldg(a.q + km)) ^ ((km == jj) ? 1 : 0), v);
-                    E += renorm<CHI>(v) - __ldg(a.cexp + k);
+                    acc_select<CHI>(tw, spin(sk) ^ (sk == iq ? 1 : 0), v);
+                    E += renorm<CHI>(v) - ck;
                 }
-                if (i + 1 < span) {
+                if (cc.i + 1 < span) {
                     write_next = true;
                 } else {
                     // Metropolis decision of proposal jj (spin iq)
@@ -585,7 +698,7 @@ __global__ void __launch_bounds__(NT, 1)
                     normalize_scalar(m, Ep);
                     const double ratio = ldexp(m / pm, (int)(Ep - pe));
                     const double x = rttd::mcmc_uniform(a.seed, (uint64_t)(a.chain0 + c),
-                                                        (uint64_t)(a.sweep0 + sw), (uint64_t)jj);
+                                                        (uint64_t)(a.sweep0 + cc.sw), (uint64_t)jj);
                     const bool accept = active && (x < ratio * ratio);
                     if (accept) {
                         pm = m;
@@ -604,7 +717,7 @@ __global__ void __launch_bounds__(NT, 1)
                     if (jj + 1 < N) {  // next proposal starts from l_jj
                         load_vec<CHI>(a.lstack + ((size_t)c * N + jj) * CHI, v);
                         write_next = true;
-                    } else if (sw + 1 < a.n_sweeps) {  // next sweep: right environment
+                    } else if (cc.sw + 1 < a.n_sweeps) {  // next sweep
                         load_vec<CHI>(N > 1 ? a.br : a.bl, v);
                         E = 0;
                         El = 0;
@@ -614,6 +727,7 @@ __global__ void __launch_bounds__(NT, 1)
             }
         }
         if (write_next) write_A<CHI, F16>(A_hi, A_lo, tid, v);
+        cursor_next<MODE>(cc, a, span);
         fence_async_smem();
         tc_before();
         __syncthreads();
@@ -731,7 +845,7 @@ tcd::Args make_args(rtt_s *h, int64_t B) {
 
 template <int CHI, int MODE, bool F16>
 cudaError_t launch(const TcPlan *p, const tcd::Args &a, dim3 grid, cudaStream_t st) {
-    const size_t smem = tcd::Cfg<CHI, F16>::smem_bytes(a.N);
+    const size_t smem = tcd::Cfg<CHI, F16>::smem_bytes(a.N, a.L);
     cudaError_t e = cudaFuncSetAttribute(tcd::k_tc<CHI, MODE, F16>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
