@@ -186,6 +186,47 @@ typedef struct {
 rtt_status rtt_profile(rtt_handle h, int32_t enable);
 rtt_status rtt_profile_read(rtt_handle h, rtt_kernel_time *out, int32_t capacity, int32_t *count);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent RTT instances of uneven N, R and chi sampled
+ * together.  Each instance is an rtt_desc (FP32 precision, periodic path,
+ * 17 <= chi <= 256, all on one device); each gets its own chains.  One call of
+ * rtt_batch_step performs one Monte Carlo iteration of every chain of every
+ * instance -- one systematic sweep (Sec. 3.3) followed by the local energy
+ * (Sec. 3.3 / Sec. 4 Eq. ising-model) -- in ONE persistent kernel launch
+ * (optionally through a CUDA graph).  Results of instance i equal, bit for
+ * bit, those of an FP32 rtt_handle of the same description running
+ * rtt_mcmc_sweep with chain0 = 0, sweep0 = sweep, measure_every = 1.
+ *
+ * Device buffers are packed instance after instance: spins [sum_i B_i N_i]
+ * (instance i at spin offset so_i, chain c at so_i + c N_i), chain state and
+ * e_loc [sum_i B_i] (instance i at chain offset co_i); rtt_batch_layout returns
+ * the offsets.  The batch owns its per-instance handles and scratch.
+ * --------------------------------------------------------------------------- */
+typedef struct rtt_batch_s *rtt_batch;
+rtt_status rtt_batch_create(const rtt_desc *descs, int32_t n_instances, const int64_t *chains,
+                            rtt_batch *out);
+rtt_status rtt_batch_destroy(rtt_batch b);
+/* totals and per-instance offsets (host arrays of n_instances, or NULL) */
+rtt_status rtt_batch_layout(rtt_batch b, int64_t *total_chains, int64_t *total_spins,
+                            int64_t *chain_off, int64_t *spin_off);
+/* chain states (psi of the current spins) of every instance, Eq. RTT */
+rtt_status rtt_batch_init(rtt_batch b, const uint8_t *spins, rtt_chain_state *state, void *stream);
+/* one iteration (sweep index `sweep`) of every chain; e_loc [sum B_i] receives
+ * E_loc after the sweep; n_accept [sum B_i] (or NULL) accumulates acceptances.
+ * use_graph != 0 launches through a CUDA graph built on first use (its kernel
+ * node is updated per call). */
+rtt_status rtt_batch_step(rtt_batch b, uint8_t *spins, rtt_chain_state *state, int64_t sweep,
+                          double *e_loc, int64_t *n_accept, int32_t use_graph, void *stream);
+/* Autotuner: for every (chi, L) bucket (L <= 64, <= 256, > 256) time each tile
+ * shape -- 32 or 16 lanes per row, 1 or 2 blocks of rows per work item -- on
+ * up to probe_chains chains per instance of the bucket and keep the fastest
+ * per chain.  cache_path (or NULL): buckets found there are not re-timed; the
+ * file is rewritten with every bucket's choice (JSON).  SYNCHRONOUS; results
+ * of later steps do not depend on the shapes chosen. */
+rtt_status rtt_batch_tune(rtt_batch b, const char *cache_path, int32_t probe_chains, void *stream);
+/* tile shape currently used for instance i */
+rtt_status rtt_batch_shape(rtt_batch b, int32_t instance, int32_t *lanes, int32_t *chains_per_item);
+
 /* The local energy of rtt_local_energy (same kernels, same results) from a
  * call that allocates no device memory.  The paper has no counterpart: this
  * is an operational variant for callers that cannot allocate at the time of

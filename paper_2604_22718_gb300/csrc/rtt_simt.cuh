@@ -27,10 +27,12 @@ struct Geo {
     static constexpr int RPW = 32 / G;              // rows per warp
 };
 
-template <typename T, int CHI>
+// GG lanes per row (default min(CHI, 32)); results do not depend on GG: every
+// output column accumulates over a in increasing order whatever the split.
+template <typename T, int CHI, int GG = Geo<CHI>::G>
 struct RowOps {
-    static constexpr int G = Geo<CHI>::G;
-    static constexpr int NQ = Geo<CHI>::NQ;
+    static constexpr int G = GG;
+    static constexpr int NQ = CHI / GG;
 
     // out[b] = sum_a v[a] M[a][b]; M row-major [CHI][CHI].
     static __device__ __forceinline__ void vecmat(const T *__restrict__ M, const T (&v)[NQ],
@@ -143,10 +145,10 @@ __global__ void __launch_bounds__(256) k_left_env(KArgs a, const uint8_t *__rest
 // right environments of the last block: entry q holds r_{(R-1)N+1+q}
 // (q = N-1 is b_R itself), one group per chain
 // ---------------------------------------------------------------------------
-template <typename T, int CHI>
+template <typename T, int CHI, int GG = Geo<CHI>::G>
 __device__ __forceinline__ void right_env_chain(const KArgs &a, const uint8_t *s, T *rstack_c,
                                                 int32_t *rexp_c, bool active, int gl) {
-    using O = RowOps<T, CHI>;
+    using O = RowOps<T, CHI, GG>;
     const T *AT = (const T *)a.AT;
     T r[O::NQ];
     O::load((const T *)a.br, r, gl);

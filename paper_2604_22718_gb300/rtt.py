@@ -73,6 +73,16 @@ def lib():
         L.rtt_mcmc_uniforms.argtypes = [U64, I64, P, P, P]
         L.rtt_profile.argtypes = [P, I32]
         L.rtt_profile_read.argtypes = [P, ctypes.POINTER(_KTime), I32, ctypes.POINTER(I32)]
+        L.rtt_batch_create.argtypes = [P, I32, P, ctypes.POINTER(P)]
+        L.rtt_batch_destroy.argtypes = [P]
+        L.rtt_batch_layout.argtypes = [P, P, P, P, P]
+        L.rtt_batch_init.argtypes = [P, P, P, P]
+        L.rtt_batch_step.argtypes = [P, P, P, I64, P, P, I32, P]
+        L.rtt_batch_tune.argtypes = [P, ctypes.c_char_p, I32, P]
+        L.rtt_batch_shape.argtypes = [P, I32, P, P]
+        for name in ("rtt_batch_create", "rtt_batch_destroy", "rtt_batch_layout", "rtt_batch_init",
+                     "rtt_batch_step", "rtt_batch_tune", "rtt_batch_shape"):
+            getattr(L, name).restype = ctypes.c_int
         L.rtt_status_string.argtypes = [I32]
         L.rtt_status_string.restype = ctypes.c_char_p
         L.rtt_last_error.restype = ctypes.c_char_p
@@ -245,3 +255,84 @@ def mcmc_uniforms(seed: int, counters: torch.Tensor, stream=None) -> torch.Tenso
     _check(lib().rtt_mcmc_uniforms(int(seed), n, _ptr(counters.contiguous()), _ptr(out),
                                    _stream(stream)), "rtt_mcmc_uniforms")
     return out
+
+
+class RTTBatch:
+    """Many FP32 RTT instances sampled by one persistent kernel per iteration."""
+
+    def __init__(self, instances, chains, device: int | None = None, seeds=None):
+        n = len(instances)
+        chains = [int(c) for c in (chains if hasattr(chains, "__len__") else [chains] * n)]
+        self.instances = list(instances)
+        self.n = n
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self._keep = []
+        descs = (_Desc * n)()
+        for i, inst in enumerate(instances):
+            path = np.ascontiguousarray(inst.path, dtype=np.int32)
+            t = np.ascontiguousarray(inst.tensors, dtype=np.float64)
+            bl = np.ascontiguousarray(inst.b_left, dtype=np.float64)
+            br = np.ascontiguousarray(inst.b_right, dtype=np.float64)
+            bonds = np.ascontiguousarray(inst.bonds, dtype=np.int32).reshape(-1, 2)
+            self._keep += [path, t, bl, br, bonds]
+            seed = int(seeds[i]) if seeds is not None else 22722 + i
+            descs[i] = _Desc(int(inst.n_spins), t.shape[0], t.shape[2], bonds.shape[0],
+                             path.ctypes.data, t.ctypes.data, bl.ctypes.data, br.ctypes.data,
+                             bonds.ctypes.data if bonds.size else None, float(inst.J),
+                             float(inst.h), RTT_FP32, self.device, seed)
+        self._chains = np.asarray(chains, dtype=np.int64)
+        b = ctypes.c_void_p()
+        _check(lib().rtt_batch_create(descs, n, self._chains.ctypes.data, ctypes.byref(b)),
+               "rtt_batch_create")
+        self._b = b
+        tc, ts = ctypes.c_int64(), ctypes.c_int64()
+        self.chain_off = np.zeros(n, dtype=np.int64)
+        self.spin_off = np.zeros(n, dtype=np.int64)
+        _check(lib().rtt_batch_layout(b, ctypes.byref(tc), ctypes.byref(ts),
+                                      self.chain_off.ctypes.data, self.spin_off.ctypes.data),
+               "rtt_batch_layout")
+        self.total_chains, self.total_spins = tc.value, ts.value
+        self.chains = chains
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            lib().rtt_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def init(self, spins: torch.Tensor, stream=None) -> torch.Tensor:
+        _dev_check(spins, torch.uint8, (self.total_spins,), "spins")
+        st = new_state(self.total_chains, spins.device)
+        _check(lib().rtt_batch_init(self._b, _ptr(spins), _ptr(st), _stream(stream)), "rtt_batch_init")
+        return st
+
+    def step(self, spins, state, sweep: int, e_loc, n_accept=None, use_graph=True, stream=None):
+        _dev_check(spins, torch.uint8, (self.total_spins,), "spins")
+        _dev_check(state, torch.int64, (self.total_chains, 2), "state")
+        _dev_check(e_loc, torch.float64, (self.total_chains,), "e_loc")
+        if n_accept is not None:
+            _dev_check(n_accept, torch.int64, (self.total_chains,), "n_accept")
+        _check(lib().rtt_batch_step(self._b, _ptr(spins), _ptr(state), int(sweep), _ptr(e_loc),
+                                    _ptr(n_accept), 1 if use_graph else 0, _stream(stream)),
+               "rtt_batch_step")
+
+    def tune(self, cache_path: str | None = None, probe_chains: int = 64, stream=None):
+        _check(lib().rtt_batch_tune(self._b, cache_path.encode() if cache_path else None,
+                                    int(probe_chains), _stream(stream)), "rtt_batch_tune")
+
+    def shape(self, i: int):
+        g, c = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().rtt_batch_shape(self._b, int(i), ctypes.byref(g), ctypes.byref(c)),
+               "rtt_batch_shape")
+        return g.value, c.value

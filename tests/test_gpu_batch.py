@@ -1,0 +1,110 @@
+"""Batched form: many FP32 instances of uneven N, R, chi in one persistent
+launch.  Instance i must reproduce, bit for bit, a single-instance FP32 handle
+of the same description (same row arithmetic in the same order, same Philox
+stream per chain), whatever tile shape the autotuner picks and whether the
+launch goes through the CUDA graph or not; sampled chains are checked against
+the FP64 oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as orc
+from paper_2604_22718_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2604_22718_gb300 import build
+    build.build()
+
+
+def _small_batch():
+    # the batched-workload generator on reduced lattices and chi
+    return inputs.batched_instances(seed=7, n=9, chi_choices=(32, 64, 128), sizes=(4, 6),
+                                    reps=(2, 3, 4))
+
+
+def _single_reference(rtt, inst, seed, spins, n_steps, sweep0):
+    B = spins.shape[0]
+    with rtt.RTT(inst, "fp32", seed=seed) as m:
+        sg = torch.from_numpy(spins.copy()).cuda()
+        _, _, st = m.log_amplitudes(sg)
+        tr = torch.empty((n_steps, B), dtype=torch.float64, device="cuda")
+        acc = torch.zeros(B, dtype=torch.int64, device="cuda")
+        m.mcmc_sweep(sg, st, sweep0, n_steps, 1, tr, acc)
+        torch.cuda.synchronize()
+        return sg.cpu().numpy(), st.cpu().numpy(), tr.cpu().numpy(), acc.cpu().numpy()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_matches_single_instances_bit_for_bit(use_graph, tmp_path):
+    from paper_2604_22718_gb300 import rtt
+    insts = _small_batch()
+    chains = [37 + 11 * i for i in range(len(insts))]       # ragged, not tile multiples
+    seeds = [500 + i for i in range(len(insts))]
+    n_steps = 3
+    with rtt.RTTBatch(insts, chains, seeds=seeds) as b:
+        if use_graph:
+            b.tune(str(tmp_path / "tiles.json"), probe_chains=32)
+        spins0 = np.concatenate([inputs.initial_spins(900 + i, c, inst.n_spins).ravel()
+                                 for i, (inst, c) in enumerate(zip(insts, chains))])
+        sp = torch.from_numpy(spins0.copy()).cuda()
+        st = b.init(sp)
+        e = torch.empty(b.total_chains, dtype=torch.float64, device="cuda")
+        acc = torch.zeros(b.total_chains, dtype=torch.int64, device="cuda")
+        traces = []
+        for t in range(n_steps):
+            b.step(sp, st, 4 + t, e, acc, use_graph=use_graph)
+            traces.append(e.clone())
+        torch.cuda.synchronize()
+        tr = torch.stack(traces).cpu().numpy()
+        sp, st, acc = sp.cpu().numpy(), st.cpu().numpy(), acc.cpu().numpy()
+        shapes = [b.shape(i) for i in range(len(insts))]
+    print("tile shapes", shapes)
+    for i, inst in enumerate(insts):
+        co, so = int(b.chain_off[i]), int(b.spin_off[i])
+        B, N = chains[i], inst.n_spins
+        s_ref, st_ref, tr_ref, acc_ref = _single_reference(
+            rtt, inst, seeds[i], spins0[so:so + B * N].reshape(B, N), n_steps, 4)
+        assert np.array_equal(sp[so:so + B * N].reshape(B, N), s_ref), i
+        assert np.array_equal(st[co:co + B], st_ref), i
+        assert np.array_equal(acc[co:co + B], acc_ref), i
+        assert np.array_equal(tr[:, co:co + B], tr_ref), i
+    if use_graph:
+        cache = json.loads((tmp_path / "tiles.json").read_text())
+        assert len(cache["tile_shapes"]) >= 1
+
+
+def test_batch_sampled_chains_against_oracle():
+    from paper_2604_22718_gb300 import rtt
+    insts = _small_batch()[:3]
+    chains = [64, 40, 50]
+    with rtt.RTTBatch(insts, chains, seeds=[1, 2, 3]) as b:
+        spins0 = np.concatenate([inputs.initial_spins(70 + i, c, inst.n_spins).ravel()
+                                 for i, (inst, c) in enumerate(zip(insts, chains))])
+        sp = torch.from_numpy(spins0.copy()).cuda()
+        st = b.init(sp)
+        e = torch.empty(b.total_chains, dtype=torch.float64, device="cuda")
+        b.step(sp, st, 0, e)
+        torch.cuda.synchronize()
+        sp, e = sp.cpu().numpy(), e.cpu().numpy()
+    for i, inst in enumerate(insts):
+        o = orc.Oracle(inst)
+        co, so, N = int(b.chain_off[i]), int(b.spin_off[i]), inst.n_spins
+        pick = [0, chains[i] - 1]
+        s_now = sp[so:so + chains[i] * N].reshape(chains[i], N)[pick]
+        e_o = o.local_energies(s_now, threads=2)
+        scale = inst.bonds.shape[0] + inst.h * N
+        assert np.all(np.abs(e[co + np.array(pick)] - e_o) <= 1e-4 * scale), (i, e[co + np.array(pick)], e_o)
+
+
+def test_batch_rejects_non_fp32_and_small_chi():
+    from paper_2604_22718_gb300 import rtt
+    tiny = inputs.make_instance(3, 3, 2, 8, 3.0, seed=1, mixing=False)
+    with pytest.raises(rtt.RTTError):
+        rtt.RTTBatch([tiny], [4])
