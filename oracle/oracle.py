@@ -80,6 +80,8 @@ def _load():
             lib.orc_local_energies.restype = ctypes.c_int
             lib.orc_flip_amplitudes.argtypes = [P, P, I64, P, P]
             lib.orc_amplitude_cond.argtypes = [P, P, P, P, P]
+            lib.orc_uniform_keyed.argtypes = [U64, U64, U64, U64, U64]
+            lib.orc_uniform_keyed.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -242,6 +244,10 @@ def philox4x64(counter, key):
     out = np.empty(4, dtype=np.uint64)
     lib.orc_philox4x64(_ptr(c), _ptr(k), _ptr(out))
     return out
+
+
+def uniform_keyed(seed, stream, c0, c1, c2):
+    return _load().orc_uniform_keyed(int(seed), int(stream), int(c0), int(c1), int(c2))
 
 
 def mcmc_uniform(seed, chain, sweep, proposal):

@@ -317,6 +317,19 @@ double orc_mcmc_uniform(uint64_t seed, uint64_t chain, uint64_t sweep, uint64_t 
     return (double)(x[0] >> 11) * 0x1.0p-53;
 }
 
+/* Uniform of an arbitrary keyed stream: key = (seed, stream), counter =
+ * (c0, c1, c2, 0); u = (x0 >> 11) * 2^-53.  The learned proposal draws its
+ * bits with stream 0x4D414445 ("MADE"), counter (chain, round, position) and
+ * its acceptance uniform at position N. */
+double orc_uniform_keyed(uint64_t seed, uint64_t stream, uint64_t c0, uint64_t c1, uint64_t c2)
+{
+    uint64_t ctr[4] = {c0, c1, c2, 0};
+    uint64_t key[2] = {seed, stream};
+    uint64_t x[4];
+    orc_philox4x64(ctr, key, x);
+    return (double)(x[0] >> 11) * 0x1.0p-53;
+}
+
 /* ---------------------------------------------------------------- Metropolis */
 
 /* Systematic single-spin Metropolis on P_s = |psi_s|^2 / Z.

@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "RTTInstance", "snake_order", "open_bonds", "periodic_path",
     "gaussian_tensors", "mixed_tensors", "make_instance", "initial_spins",
-    "WORKLOADS", "workload", "batched_instances",
+    "WORKLOADS", "workload", "batched_instances", "made_init_weights",
 ]
 
 
@@ -157,3 +157,15 @@ def batched_instances(seed: int = 22722, n: int = 64, chi_choices=(32, 64, 128, 
         out.append(make_instance(lx, lx, R, chi, h, seed * 1000 + t, mixing=True,
                                  name=f"batched[{t}]"))
     return out
+
+
+def made_init_weights(seed: int, n_spins: int, hidden: int) -> np.ndarray:
+    """Initial weights of the autoregressive proposal network, flat float64 in
+    the order W1 [H,N], b1 [H], W2 [H,H], b2 [H], W3 [N,H], b3 [N]: weights
+    U(-1, 1)/sqrt(fan_in), biases zero.  Unmasked (masking is the model's)."""
+    rng = np.random.Generator(np.random.PCG64([seed, 0x4D414445]))
+    N, H = int(n_spins), int(hidden)
+    parts = [rng.uniform(-1, 1, (H, N)) / np.sqrt(N), np.zeros(H),
+             rng.uniform(-1, 1, (H, H)) / np.sqrt(H), np.zeros(H),
+             rng.uniform(-1, 1, (N, H)) / np.sqrt(H), np.zeros(N)]
+    return np.concatenate([x.ravel() for x in parts])
