@@ -227,6 +227,48 @@ rtt_status rtt_batch_tune(rtt_batch b, const char *cache_path, int32_t probe_cha
 /* tile shape currently used for instance i */
 rtt_status rtt_batch_shape(rtt_batch b, int32_t instance, int32_t *lanes, int32_t *chains_per_item);
 
+/* ---------------------------------------------------------------------------
+ * Learned independence proposal.  A MADE (masked autoregressive MLP, Germain et
+ * al. 2015) with two ReLU hidden layers of width H models q(s) as a product of
+ * conditionals q(s_order[d] | s_order[<d]) = sigmoid(logit_d); it is trained by
+ * this library's kernels (FP32) on configurations the RTT chains produce and
+ * proposes s' ~ q for an independence Metropolis-Hastings step on
+ * P = |psi|^2/Z (Sec. 3.3): accept iff log u < 2(log|psi(s')| - log|psi(s)|)
+ * + log q(s) - log q(s').  The exact RTT ratio decides every acceptance.
+ *   Parameters are flat FP32 in the order W1 [H][N], b1 [H], W2 [H][H], b2 [H],
+ * W3 [N][H], b3 [N]; masks keep W1[k][d] iff m_k >= d+1, W2[k2][k1] iff
+ * m_k2 >= m_k1, W3[d][k] iff d+1 > m_k, with hidden degrees m_k = (k mod
+ * (N-1)) + 1.  Random bits come from Philox4x64-10 with key (seed, 0x4D414445)
+ * and counter (chain, round, position d) for the sample bits, position N for
+ * the acceptance uniform.  The paper's method has no learned proposal; this is
+ * the sampler extension the hot path carries beside local flips.
+ * --------------------------------------------------------------------------- */
+typedef struct rtt_made_s *rtt_made;
+/* order: host [N] permutation (position -> spin); init_weights: host flat
+ * double [P] (masked on load); seed keys the sampling stream. */
+rtt_status rtt_made_create(int32_t n_spins, int32_t hidden, const int32_t *order,
+                           const double *init_weights, uint64_t seed, int32_t device, rtt_made *out);
+rtt_status rtt_made_destroy(rtt_made m);
+/* parameters to host float [P] (SYNCHRONOUS) */
+rtt_status rtt_made_get_params(rtt_made m, float *host_out);
+/* mean NLL gradient of a batch of spins (device [B][N]) into grads (device
+ * float [P]); nll (device double, or NULL) receives the mean NLL. */
+rtt_status rtt_made_gradients(rtt_made m, const uint8_t *spins, int64_t B, float *grads,
+                              double *nll, void *stream);
+/* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean NLL of a batch */
+rtt_status rtt_made_train_step(rtt_made m, const uint8_t *spins, int64_t B, float lr, double *nll,
+                               void *stream);
+/* log q(s) for B configurations: logq device double [B] */
+rtt_status rtt_made_log_prob(rtt_made m, const uint8_t *spins, int64_t B, double *logq, void *stream);
+/* B samples s' ~ q (device [B][N]) with their log q (device [B]) */
+rtt_status rtt_made_sample(rtt_made m, int64_t B, int64_t chain0, int64_t round, uint8_t *spins,
+                           double *logq, void *stream);
+/* One independence proposal per chain: s' ~ q, psi(s') by the handle's
+ * precision, accept/reject as above; spins and state updated in place,
+ * n_accept (device [B] or NULL) counts acceptances. */
+rtt_status rtt_indep_mh(rtt_handle h, rtt_made m, uint8_t *spins, rtt_chain_state *state,
+                        int64_t B, int64_t chain0, int64_t round, int64_t *n_accept, void *stream);
+
 /* The local energy of rtt_local_energy (same kernels, same results) from a
  * call that allocates no device memory.  The paper has no counterpart: this
  * is an operational variant for callers that cannot allocate at the time of

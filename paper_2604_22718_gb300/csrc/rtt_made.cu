@@ -1,0 +1,573 @@
+// rtt_made.cu -- learned independence proposal: a MADE (masked autoregressive
+// MLP, Germain et al., ICML 2015) trained and sampled by this library's own
+// kernels, and the independence Metropolis-Hastings step that uses it on the
+// RTT target P = |psi|^2 / Z (Sec. 3.3).
+//
+// Model: position d of the autoregressive order carries spin order[d]; input
+// x_d = 1 - 2 s_order[d]; two ReLU hidden layers of width H; output logit_d,
+// q(s_order[d] = 1 | s_<d) = sigmoid(logit_d).  Degrees: input d -> d+1,
+// hidden unit k -> (k mod (N-1)) + 1, output d -> d+1; W1[k,d] kept iff
+// m_k >= d+1, W2[k2,k1] iff m_k2 >= m_k1, W3[d,k] iff d+1 > m_k.
+//
+// Arithmetic (FP32 SIMT): every matrix product accumulates each output from
+// its bias with one fma per term in increasing contraction index.  Ancestral
+// sampling builds the first hidden layer incrementally in the same order, so
+// the conditionals it samples from, and the log q it reports, are bit for
+// bit those of the full forward pass: the acceptance test uses exactly the
+// density the proposal was drawn from.
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "rtt_internal.cuh"
+
+struct rtt_made_s {
+    int device = 0, N = 0, H = 0;
+    uint64_t seed = 0;
+    int64_t P = 0;        // number of parameters
+    int64_t step = 0;     // Adam step counter
+    int32_t *d_order = nullptr;
+    float *d_p = nullptr, *d_g = nullptr, *d_m = nullptr, *d_v = nullptr;
+    float *d_mask = nullptr;   // masks of W1, W2, W3 in parameter layout (1 elsewhere)
+    // workspace for batches of up to cap rows
+    int64_t cap = 0;
+    float *d_x = nullptr, *d_h1 = nullptr, *d_h2 = nullptr, *d_lg = nullptr;
+    float *d_d3 = nullptr, *d_dh2 = nullptr, *d_dh1 = nullptr;
+    double *d_logq = nullptr, *d_nll_parts = nullptr;
+    uint8_t *d_prop = nullptr;          // proposals [cap][N]
+    rtt_chain_state *d_pstate = nullptr;
+    double *d_plogq = nullptr;
+    size_t off_W1 = 0, off_b1 = 0, off_W2 = 0, off_b2 = 0, off_W3 = 0, off_b3 = 0;
+};
+
+namespace mk {
+
+constexpr uint64_t MADE_STREAM = 0x4D414445ull;
+
+__device__ __forceinline__ double log_sigmoid(double y) {
+    return fmin(y, 0.0) - log1p(exp(-fabs(y)));
+}
+
+// C[m][n] = epi(bias[n] + sum_k opA[m][k] opB[k][n]), fma in increasing k.
+// opA[m][k] = TA ? A[k lda + m] : A[m lda + k];  opB[k][n] = TB ? B[n ldb + k] : B[k ldb + n]
+// epi: ReLU (relu), * [gate[m][n] > 0] (gate), * mask[m][n] (mask); leading dim ldc.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float *__restrict__ A,
+                                              int lda, const float *__restrict__ B, int ldb,
+                                              float *__restrict__ C, int ldc,
+                                              const float *__restrict__ bias, int relu,
+                                              const float *__restrict__ gate,
+                                              const float *__restrict__ mask) {
+    __shared__ float As[16][64 + 1];
+    __shared__ float Bs[16][64 + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx + 16 * j;
+            acc[i][j] = (bias && n < N) ? bias[n] : 0.f;
+        }
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        // 16 x 64 tiles, 4 elements per thread each
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = threadIdx.x + 256 * r;   // 0..1023
+            const int kk = e >> 6, mm = e & 63;
+            const int k = k0 + kk;
+            const int m = m0 + mm, n = n0 + mm;
+            float av = 0.f, bv = 0.f;
+            if (k < K && m < M) av = TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
+            if (k < K && n < N) bv = TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
+            As[kk][mm] = av;
+            Bs[kk][mm] = bv;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            if (m >= M || n >= N) continue;
+            float c = acc[i][j];
+            if (relu) c = fmaxf(c, 0.f);
+            if (gate && !(gate[(size_t)m * ldc + n] > 0.f)) c = 0.f;
+            if (mask) c *= mask[(size_t)m * ldc + n];
+            C[(size_t)m * ldc + n] = c;
+        }
+}
+
+// inputs in autoregressive order: x[b][d] = 1 - 2 s[b][order[d]]
+__global__ void k_inputs(const uint8_t *__restrict__ s, int64_t B, int N,
+                         const int32_t *__restrict__ order, float *__restrict__ x) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B * N) return;
+    const int64_t b = t / N;
+    const int d = (int)(t % N);
+    x[t] = 1.f - 2.f * (float)s[b * N + order[d]];
+}
+
+// log q per row (double, increasing d) and, if d3, the NLL gradient
+// (sigmoid(logit) - t) / B; nll_parts[b] = -log q
+__global__ void k_loss(const float *__restrict__ lg, const uint8_t *__restrict__ s, int64_t B,
+                       int N, const int32_t *__restrict__ order, double *__restrict__ logq,
+                       float *__restrict__ d3) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double acc = 0.0;
+    for (int d = 0; d < N; ++d) {
+        const double y = (double)lg[b * N + d];
+        const int t = s[b * N + order[d]];
+        acc += log_sigmoid(t ? y : -y);
+        if (d3) {
+            const double sg = 1.0 / (1.0 + exp(-y));
+            d3[b * N + d] = (float)((sg - (double)t) / (double)B);
+        }
+    }
+    logq[b] = acc;
+}
+
+// out[n] = sum_b D[b][n] (increasing b); one thread per column
+__global__ void k_colsum(const float *__restrict__ D, int64_t B, int N, float *__restrict__ out) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float acc = 0.f;
+    for (int64_t b = 0; b < B; ++b) acc += D[b * N + n];
+    out[n] = acc;
+}
+
+__global__ void k_sum_neg(const double *__restrict__ x, int64_t n, double *__restrict__ out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double acc = 0.0;
+    for (int64_t i = 0; i < n; ++i) acc += x[i];
+    *out = -acc / (double)n;
+}
+
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / c1, vh = vi / c2;
+    p[i] = p[i] - lr * mh / (sqrtf(vh) + eps);
+}
+
+__global__ void k_fill_rows(float *__restrict__ x, int64_t B, int H, const float *__restrict__ b) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B * H) return;
+    x[t] = b[t % H];
+}
+
+__global__ void k_relu(const float *__restrict__ x, float *__restrict__ y, int64_t n) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    y[t] = fmaxf(x[t], 0.f);
+}
+
+// Position d of ancestral sampling, one thread per chain: logit_d from h2
+// (bias then increasing k, as the forward product), draw the bit, add its
+// log-probability, then add input d into the first-layer pre-activations.
+__global__ void k_sample_pos(int d, int64_t B, int N, int H, const float *__restrict__ W1,
+                             const float *__restrict__ W3, const float *__restrict__ b3,
+                             const float *__restrict__ h2, float *__restrict__ h1pre,
+                             const int32_t *__restrict__ order, uint8_t *__restrict__ spins,
+                             double *__restrict__ logq, uint64_t seed, int64_t chain0,
+                             int64_t round) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    float lg = b3[d];
+    const float *w = W3 + (size_t)d * H;
+    const float *hb = h2 + (size_t)b * H;
+    for (int k = 0; k < H; ++k) lg = fmaf(hb[k], w[k], lg);
+    const double y = (double)lg;
+    uint64_t r[4];
+    rttd::philox4x64_10((uint64_t)(chain0 + b), (uint64_t)round, (uint64_t)d, 0ull, seed,
+                        MADE_STREAM, r);
+    const double u = (double)(r[0] >> 11) * 0x1.0p-53;
+    const double pr = 1.0 / (1.0 + exp(-y));
+    const int t = u < pr ? 1 : 0;
+    logq[b] = (d == 0 ? 0.0 : logq[b]) + log_sigmoid(t ? y : -y);
+    spins[b * N + order[d]] = (uint8_t)t;
+    const float x = t ? -1.f : 1.f;
+    float *h = h1pre + (size_t)b * H;
+    for (int k = 0; k < H; ++k) h[k] = fmaf(x, W1[(size_t)k * N + d], h[k]);
+}
+
+// Independence Metropolis-Hastings decision, one thread per chain.
+__global__ void k_indep_decide(int64_t B, int N, uint8_t *__restrict__ spins,
+                               rtt_chain_state *__restrict__ state, const double *__restrict__ logq,
+                               const uint8_t *__restrict__ prop,
+                               const rtt_chain_state *__restrict__ pstate,
+                               const double *__restrict__ plogq, uint64_t seed, int64_t chain0,
+                               int64_t round, int64_t *__restrict__ n_accept) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const double m0 = state[b].mant, m1 = pstate[b].mant;
+    const double la0 = (m0 == 0.0) ? -INFINITY : (double)state[b].exp2 * 0.6931471805599453 + log(fabs(m0));
+    const double la1 = (m1 == 0.0) ? -INFINITY : (double)pstate[b].exp2 * 0.6931471805599453 + log(fabs(m1));
+    uint64_t r[4];
+    rttd::philox4x64_10((uint64_t)(chain0 + b), (uint64_t)round, (uint64_t)N, 0ull, seed, MADE_STREAM, r);
+    const double u = (double)(r[0] >> 11) * 0x1.0p-53;
+    const double lhs = log(u);
+    const double rhs = 2.0 * (la1 - la0) + logq[b] - plogq[b];
+    const bool accept = (m1 != 0.0) && isfinite(m1) && (u == 0.0 || lhs < rhs);
+    if (!accept) return;
+    for (int i = 0; i < N; ++i) spins[b * N + i] = prop[b * N + i];
+    state[b] = pstate[b];
+    if (n_accept) n_accept[b] += 1;
+}
+
+// masks in parameter layout (1 on biases)
+__global__ void k_masks(float *__restrict__ mask, int N, int H, size_t oW1, size_t oW2, size_t oW3,
+                        int64_t P) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    auto deg = [&](int k) { return N > 1 ? (k % (N - 1)) + 1 : 1; };
+    float v = 1.f;
+    if (i >= (int64_t)oW1 && i < (int64_t)(oW1 + (size_t)H * N)) {
+        const int64_t e = i - oW1;
+        const int k = (int)(e / N), d = (int)(e % N);
+        v = deg(k) >= d + 1 ? 1.f : 0.f;
+    } else if (i >= (int64_t)oW2 && i < (int64_t)(oW2 + (size_t)H * H)) {
+        const int64_t e = i - oW2;
+        const int k2 = (int)(e / H), k1 = (int)(e % H);
+        v = deg(k2) >= deg(k1) ? 1.f : 0.f;
+    } else if (i >= (int64_t)oW3 && i < (int64_t)(oW3 + (size_t)N * H)) {
+        const int64_t e = i - oW3;
+        const int d = (int)(e / H), k = (int)(e % H);
+        v = (d + 1) > deg(k) ? 1.f : 0.f;
+    }
+    mask[i] = v;
+}
+
+__global__ void k_mul(float *__restrict__ x, const float *__restrict__ y, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] *= y[i];
+}
+
+inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <bool TA, bool TB>
+cudaError_t gemm(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C,
+                 int ldc, const float *bias, int relu, const float *gate, const float *mask,
+                 cudaStream_t st) {
+    dim3 grid(nb(N, 64), nb(M, 64));
+    k_gemm<TA, TB><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, gate, mask);
+    return cudaGetLastError();
+}
+
+}  // namespace mk
+
+// ============================================================================ host
+namespace {
+
+rtt_status mfail(rtt_status s, const std::string &m) {
+    rtt_set_error(m);
+    return s;
+}
+rtt_status mcuda(cudaError_t e, const char *w) {
+    return mfail(e == cudaErrorMemoryAllocation ? RTT_ERR_OOM : RTT_ERR_CUDA,
+                 std::string(w) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+#define MC(expr, w)                                                                                \
+    do {                                                                                           \
+        cudaError_t _e = (expr);                                                                   \
+        if (_e != cudaSuccess) return mcuda(_e, w);                                                \
+    } while (0)
+
+struct MGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit MGuard(int d) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != d) changed = cudaSetDevice(d) == cudaSuccess;
+    }
+    ~MGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+void free_ws(rtt_made_s *m) {
+    void *bufs[] = {m->d_x, m->d_h1, m->d_h2, m->d_lg, m->d_d3, m->d_dh2, m->d_dh1,
+                    m->d_logq, m->d_nll_parts, m->d_prop, m->d_pstate, m->d_plogq};
+    for (void *b : bufs) cudaFree(b);
+    m->d_x = m->d_h1 = m->d_h2 = m->d_lg = m->d_d3 = m->d_dh2 = m->d_dh1 = nullptr;
+    m->d_logq = m->d_nll_parts = m->d_plogq = nullptr;
+    m->d_prop = nullptr;
+    m->d_pstate = nullptr;
+    m->cap = 0;
+}
+
+rtt_status ensure_ws(rtt_made_s *m, int64_t B) {
+    if (B <= m->cap) return RTT_OK;
+    MC(cudaDeviceSynchronize(), "made workspace");
+    free_ws(m);
+    const size_t N = m->N, H = m->H;
+    MC(cudaMalloc((void **)&m->d_x, B * N * 4), "made ws");
+    MC(cudaMalloc((void **)&m->d_h1, B * H * 4), "made ws");
+    MC(cudaMalloc((void **)&m->d_h2, B * H * 4), "made ws");
+    MC(cudaMalloc((void **)&m->d_lg, B * N * 4), "made ws");
+    MC(cudaMalloc((void **)&m->d_d3, B * N * 4), "made ws");
+    MC(cudaMalloc((void **)&m->d_dh2, B * H * 4), "made ws");
+    MC(cudaMalloc((void **)&m->d_dh1, B * H * 4), "made ws");
+    MC(cudaMalloc((void **)&m->d_logq, B * 8), "made ws");
+    MC(cudaMalloc((void **)&m->d_nll_parts, B * 8), "made ws");
+    MC(cudaMalloc((void **)&m->d_prop, B * N), "made ws");
+    MC(cudaMalloc((void **)&m->d_pstate, B * sizeof(rtt_chain_state)), "made ws");
+    MC(cudaMalloc((void **)&m->d_plogq, B * 8), "made ws");
+    m->cap = B;
+    return RTT_OK;
+}
+
+// forward pass for rows of spins -> m->d_h1, d_h2, d_lg (and x)
+rtt_status forward(rtt_made_s *m, const uint8_t *spins, int64_t B, cudaStream_t st) {
+    const int N = m->N, H = m->H;
+    const float *p = m->d_p;
+    mk::k_inputs<<<mk::nb(B * N, 256), 256, 0, st>>>(spins, B, N, m->d_order, m->d_x);
+    MC(cudaGetLastError(), "made inputs");
+    MC((mk::gemm<false, true>((int)B, H, N, m->d_x, N, p + m->off_W1, N, m->d_h1, H,
+                              p + m->off_b1, 1, nullptr, nullptr, st)), "made layer 1");
+    MC((mk::gemm<false, true>((int)B, H, H, m->d_h1, H, p + m->off_W2, H, m->d_h2, H,
+                              p + m->off_b2, 1, nullptr, nullptr, st)), "made layer 2");
+    MC((mk::gemm<false, true>((int)B, N, H, m->d_h2, H, p + m->off_W3, H, m->d_lg, N,
+                              p + m->off_b3, 0, nullptr, nullptr, st)), "made output");
+    return RTT_OK;
+}
+
+// gradient of the mean NLL into m->d_g (masked); nll into *nll_dev if given
+rtt_status gradients(rtt_made_s *m, const uint8_t *spins, int64_t B, double *nll_dev,
+                     cudaStream_t st) {
+    const int N = m->N, H = m->H;
+    const float *p = m->d_p;
+    float *g = m->d_g;
+    rtt_status s = forward(m, spins, B, st);
+    if (s != RTT_OK) return s;
+    mk::k_loss<<<mk::nb(B, 128), 128, 0, st>>>(m->d_lg, spins, B, N, m->d_order, m->d_logq, m->d_d3);
+    MC(cudaGetLastError(), "made loss");
+    if (nll_dev) {
+        mk::k_sum_neg<<<1, 1, 0, st>>>(m->d_logq, B, nll_dev);
+        MC(cudaGetLastError(), "made nll");
+    }
+    const float *mask = m->d_mask;
+    // output layer: dW3 = d3^T h2 (masked), db3 = colsum d3
+    MC((mk::gemm<true, false>(N, H, (int)B, m->d_d3, N, m->d_h2, H, g + m->off_W3, H, nullptr, 0,
+                              nullptr, mask + m->off_W3, st)), "made dW3");
+    mk::k_colsum<<<mk::nb(N, 128), 128, 0, st>>>(m->d_d3, B, N, g + m->off_b3);
+    // dh2 = (d3 W3) * [h2 > 0]
+    MC((mk::gemm<false, false>((int)B, H, N, m->d_d3, N, p + m->off_W3, H, m->d_dh2, H, nullptr, 0,
+                               m->d_h2, nullptr, st)), "made dh2");
+    MC((mk::gemm<true, false>(H, H, (int)B, m->d_dh2, H, m->d_h1, H, g + m->off_W2, H, nullptr, 0,
+                              nullptr, mask + m->off_W2, st)), "made dW2");
+    mk::k_colsum<<<mk::nb(H, 128), 128, 0, st>>>(m->d_dh2, B, H, g + m->off_b2);
+    // dh1 = (dh2 W2) * [h1 > 0]
+    MC((mk::gemm<false, false>((int)B, H, H, m->d_dh2, H, p + m->off_W2, H, m->d_dh1, H, nullptr, 0,
+                               m->d_h1, nullptr, st)), "made dh1");
+    MC((mk::gemm<true, false>(H, N, (int)B, m->d_dh1, H, m->d_x, N, g + m->off_W1, N, nullptr, 0,
+                              nullptr, mask + m->off_W1, st)), "made dW1");
+    mk::k_colsum<<<mk::nb(H, 128), 128, 0, st>>>(m->d_dh1, B, H, g + m->off_b1);
+    MC(cudaGetLastError(), "made gradients");
+    return RTT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rtt_status rtt_made_create(int32_t n_spins, int32_t hidden, const int32_t *order,
+                           const double *init_weights, uint64_t seed, int32_t device,
+                           rtt_made *out) {
+    if (!out || !order || !init_weights || n_spins < 1 || hidden < 1)
+        return mfail(RTT_ERR_INVALID_ARG, "rtt_made_create: bad arguments");
+    *out = nullptr;
+    std::vector<int> seen(n_spins, 0);
+    for (int d = 0; d < n_spins; ++d) {
+        if (order[d] < 0 || order[d] >= n_spins || seen[order[d]]++)
+            return mfail(RTT_ERR_INVALID_ARG, "rtt_made_create: order is not a permutation");
+    }
+    int dev = device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess)
+        return mfail(RTT_ERR_CUDA, "rtt_made_create: cudaGetDevice");
+    MGuard guard(dev);
+    rtt_made_s *m = new rtt_made_s();
+    m->device = dev;
+    m->N = n_spins;
+    m->H = hidden;
+    m->seed = seed;
+    const size_t N = n_spins, H = hidden;
+    m->off_W1 = 0;
+    m->off_b1 = H * N;
+    m->off_W2 = m->off_b1 + H;
+    m->off_b2 = m->off_W2 + H * H;
+    m->off_W3 = m->off_b2 + H;
+    m->off_b3 = m->off_W3 + N * H;
+    m->P = (int64_t)(m->off_b3 + N);
+    std::vector<float> hp(m->P);
+    for (int64_t i = 0; i < m->P; ++i) hp[i] = (float)init_weights[i];
+    auto cleanup = [&](rtt_status s) {
+        rtt_made_destroy(m);
+        return s;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc((void **)&m->d_order, N * 4)) != cudaSuccess) return cleanup(mcuda(e, "made"));
+    cudaMemcpy(m->d_order, order, N * 4, cudaMemcpyHostToDevice);
+    float **bufs[] = {&m->d_p, &m->d_g, &m->d_m, &m->d_v, &m->d_mask};
+    for (float **b : bufs)
+        if ((e = cudaMalloc((void **)b, m->P * 4)) != cudaSuccess) return cleanup(mcuda(e, "made params"));
+    cudaMemcpy(m->d_p, hp.data(), m->P * 4, cudaMemcpyHostToDevice);
+    cudaMemset(m->d_m, 0, m->P * 4);
+    cudaMemset(m->d_v, 0, m->P * 4);
+    cudaMemset(m->d_g, 0, m->P * 4);
+    mk::k_masks<<<mk::nb(m->P, 256), 256>>>(m->d_mask, (int)N, (int)H, m->off_W1, m->off_W2,
+                                             m->off_W3, m->P);
+    mk::k_mul<<<mk::nb(m->P, 256), 256>>>(m->d_p, m->d_mask, m->P);
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cleanup(mcuda(e, "made masks"));
+    *out = m;
+    return RTT_OK;
+}
+
+rtt_status rtt_made_destroy(rtt_made m) {
+    if (!m) return RTT_OK;
+    MGuard guard(m->device);
+    cudaDeviceSynchronize();
+    free_ws(m);
+    cudaFree(m->d_order);
+    cudaFree(m->d_p);
+    cudaFree(m->d_g);
+    cudaFree(m->d_m);
+    cudaFree(m->d_v);
+    cudaFree(m->d_mask);
+    delete m;
+    return RTT_OK;
+}
+
+rtt_status rtt_made_get_params(rtt_made m, float *host_out) {
+    if (!m || !host_out) return mfail(RTT_ERR_INVALID_ARG, "rtt_made_get_params: null argument");
+    MGuard guard(m->device);
+    MC(cudaDeviceSynchronize(), "rtt_made_get_params");
+    MC(cudaMemcpy(host_out, m->d_p, m->P * 4, cudaMemcpyDeviceToHost), "rtt_made_get_params");
+    return RTT_OK;
+}
+
+rtt_status rtt_made_gradients(rtt_made m, const uint8_t *spins, int64_t B, float *grads,
+                              double *nll, void *stream) {
+    if (!m || !spins || !grads || B < 1) return mfail(RTT_ERR_INVALID_ARG, "rtt_made_gradients: bad arguments");
+    MGuard guard(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    rtt_status s = ensure_ws(m, B);
+    if (s != RTT_OK) return s;
+    if ((s = gradients(m, spins, B, nll, st)) != RTT_OK) return s;
+    MC(cudaMemcpyAsync(grads, m->d_g, m->P * 4, cudaMemcpyDeviceToDevice, st), "made grads copy");
+    return RTT_OK;
+}
+
+rtt_status rtt_made_train_step(rtt_made m, const uint8_t *spins, int64_t B, float lr, double *nll,
+                               void *stream) {
+    if (!m || !spins || B < 1 || !(lr > 0.f))
+        return mfail(RTT_ERR_INVALID_ARG, "rtt_made_train_step: bad arguments");
+    MGuard guard(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    rtt_status s = ensure_ws(m, B);
+    if (s != RTT_OK) return s;
+    if ((s = gradients(m, spins, B, nll, st)) != RTT_OK) return s;
+    m->step += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 - pow(b1, (double)m->step));
+    const float c2 = (float)(1.0 - pow(b2, (double)m->step));
+    mk::k_adam<<<mk::nb(m->P, 256), 256, 0, st>>>(m->d_p, m->d_g, m->d_m, m->d_v, m->P, lr,
+                                                   (float)b1, (float)b2, 1e-8f, c1, c2);
+    MC(cudaGetLastError(), "made adam");
+    return RTT_OK;
+}
+
+rtt_status rtt_made_log_prob(rtt_made m, const uint8_t *spins, int64_t B, double *logq, void *stream) {
+    if (!m || !spins || !logq || B < 0) return mfail(RTT_ERR_INVALID_ARG, "rtt_made_log_prob: bad arguments");
+    if (B == 0) return RTT_OK;
+    MGuard guard(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    rtt_status s = ensure_ws(m, B);
+    if (s != RTT_OK) return s;
+    if ((s = forward(m, spins, B, st)) != RTT_OK) return s;
+    mk::k_loss<<<mk::nb(B, 128), 128, 0, st>>>(m->d_lg, spins, B, m->N, m->d_order, logq, nullptr);
+    MC(cudaGetLastError(), "made log prob");
+    return RTT_OK;
+}
+
+static rtt_status made_sample_into(rtt_made m, int64_t B, int64_t chain0, int64_t round,
+                                   uint8_t *spins, double *logq, cudaStream_t st) {
+    const int N = m->N, H = m->H;
+    const float *p = m->d_p;
+    // first-layer pre-activations start at the bias; x is not used here
+    mk::k_fill_rows<<<mk::nb(B * H, 256), 256, 0, st>>>(m->d_dh1, B, H, p + m->off_b1);
+    MC(cudaGetLastError(), "made sample init");
+    for (int d = 0; d < N; ++d) {
+        mk::k_relu<<<mk::nb(B * H, 256), 256, 0, st>>>(m->d_dh1, m->d_h1, B * H);
+        MC((mk::gemm<false, true>((int)B, H, H, m->d_h1, H, p + m->off_W2, H, m->d_h2, H,
+                                  p + m->off_b2, 1, nullptr, nullptr, st)), "made sample layer 2");
+        mk::k_sample_pos<<<mk::nb(B, 128), 128, 0, st>>>(d, B, N, H, p + m->off_W1, p + m->off_W3,
+                                                          p + m->off_b3, m->d_h2, m->d_dh1,
+                                                          m->d_order, spins, logq, m->seed, chain0,
+                                                          round);
+        MC(cudaGetLastError(), "made sample position");
+    }
+    return RTT_OK;
+}
+
+rtt_status rtt_made_sample(rtt_made m, int64_t B, int64_t chain0, int64_t round, uint8_t *spins,
+                           double *logq, void *stream) {
+    if (!m || !spins || !logq || B < 0 || chain0 < 0 || round < 0)
+        return mfail(RTT_ERR_INVALID_ARG, "rtt_made_sample: bad arguments");
+    if (B == 0) return RTT_OK;
+    MGuard guard(m->device);
+    rtt_status s = ensure_ws(m, B);
+    if (s != RTT_OK) return s;
+    return made_sample_into(m, B, chain0, round, spins, logq, (cudaStream_t)stream);
+}
+
+rtt_status rtt_indep_mh(rtt_handle h, rtt_made m, uint8_t *spins, rtt_chain_state *state,
+                        int64_t B, int64_t chain0, int64_t round, int64_t *n_accept, void *stream) {
+    if (!h || !m || !spins || !state || B < 0 || chain0 < 0 || round < 0)
+        return mfail(RTT_ERR_INVALID_ARG, "rtt_indep_mh: bad arguments");
+    if (m->N != h->N) return mfail(RTT_ERR_INVALID_ARG, "rtt_indep_mh: model and state sizes differ");
+    if (B == 0) return RTT_OK;
+    MGuard guard(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    rtt_status s = ensure_ws(m, B);
+    if (s != RTT_OK) return s;
+    // log q(s) of the current configurations
+    if ((s = forward(m, spins, B, st)) != RTT_OK) return s;
+    mk::k_loss<<<mk::nb(B, 128), 128, 0, st>>>(m->d_lg, spins, B, m->N, m->d_order, m->d_logq, nullptr);
+    MC(cudaGetLastError(), "indep log q");
+    // proposals s' ~ q with log q(s'), and psi(s')
+    if ((s = made_sample_into(m, B, chain0, round, m->d_prop, m->d_plogq, st)) != RTT_OK) return s;
+    if ((s = rtt_log_amplitudes(h, m->d_prop, B, nullptr, nullptr, m->d_pstate, stream)) != RTT_OK)
+        return s;
+    mk::k_indep_decide<<<mk::nb(B, 128), 128, 0, st>>>(B, m->N, spins, state, m->d_logq, m->d_prop,
+                                                        m->d_pstate, m->d_plogq, m->seed, chain0,
+                                                        round, n_accept);
+    MC(cudaGetLastError(), "indep decide");
+    return RTT_OK;
+}
+
+}  // extern "C"

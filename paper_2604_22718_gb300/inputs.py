@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "RTTInstance", "snake_order", "open_bonds", "periodic_path",
     "gaussian_tensors", "mixed_tensors", "make_instance", "initial_spins",
-    "WORKLOADS", "workload", "batched_instances", "made_init_weights",
+    "WORKLOADS", "workload", "batched_instances", "made_init_weights", "ferro_chain_instance",
 ]
 
 
@@ -169,3 +169,32 @@ def made_init_weights(seed: int, n_spins: int, hidden: int) -> np.ndarray:
              rng.uniform(-1, 1, (H, H)) / np.sqrt(H), np.zeros(H),
              rng.uniform(-1, 1, (N, H)) / np.sqrt(H), np.zeros(N)]
     return np.concatenate([x.ravel() for x in parts])
+
+
+def ferro_chain_instance(lx: int, ly: int, kappa: float, field: float = 0.0, h: float = 3.0,
+                         R: int = 1) -> RTTInstance:
+    """An RTT whose amplitude is exp(kappa sum_k z_k z_(k+1) + field sum_k z_k)
+    along the snake ordering (a ferromagnetic chain; bond index = previous
+    spin), chi = 2; with R > 1 the extra blocks carry identity slices.  Local
+    single-spin moves mix it slowly for large kappa; the field makes the two
+    polarised modes unequal."""
+    order = snake_order(lx, ly)
+    N = lx * ly
+    path = periodic_path(order, R)
+    L = path.shape[0]
+    t = np.zeros((L, 2, 2, 2))
+    for k in range(L):
+        for s in (0, 1):
+            z = 1 - 2 * s
+            for a in (0, 1):
+                if k >= N:
+                    t[k, s, a, a] = 1.0
+                    continue
+                w = float(np.exp(field * z))
+                if k > 0:
+                    w *= float(np.exp(kappa * (1 - 2 * a) * z))
+                t[k, s, a, s] = w
+    ones = np.ones(2)
+    return RTTInstance(n_spins=N, path=path, tensors=t, b_left=ones.copy(), b_right=ones.copy(),
+                       bonds=open_bonds(lx, ly), J=1.0, h=float(h), name=f"ferro{lx}x{ly}",
+                       lx=lx, ly=ly, R=R)

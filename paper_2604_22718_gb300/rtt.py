@@ -83,6 +83,18 @@ def lib():
         for name in ("rtt_batch_create", "rtt_batch_destroy", "rtt_batch_layout", "rtt_batch_init",
                      "rtt_batch_step", "rtt_batch_tune", "rtt_batch_shape"):
             getattr(L, name).restype = ctypes.c_int
+        L.rtt_made_create.argtypes = [I32, I32, P, P, U64, I32, ctypes.POINTER(P)]
+        L.rtt_made_destroy.argtypes = [P]
+        L.rtt_made_get_params.argtypes = [P, P]
+        L.rtt_made_gradients.argtypes = [P, P, I64, P, P, P]
+        L.rtt_made_train_step.argtypes = [P, P, I64, ctypes.c_float, P, P]
+        L.rtt_made_log_prob.argtypes = [P, P, I64, P, P]
+        L.rtt_made_sample.argtypes = [P, I64, I64, I64, P, P, P]
+        L.rtt_indep_mh.argtypes = [P, P, P, P, I64, I64, I64, P, P]
+        for name in ("rtt_made_create", "rtt_made_destroy", "rtt_made_get_params",
+                     "rtt_made_gradients", "rtt_made_train_step", "rtt_made_log_prob",
+                     "rtt_made_sample", "rtt_indep_mh"):
+            getattr(L, name).restype = ctypes.c_int
         L.rtt_status_string.argtypes = [I32]
         L.rtt_status_string.restype = ctypes.c_char_p
         L.rtt_last_error.restype = ctypes.c_char_p
@@ -336,3 +348,108 @@ class RTTBatch:
         _check(lib().rtt_batch_shape(self._b, int(i), ctypes.byref(g), ctypes.byref(c)),
                "rtt_batch_shape")
         return g.value, c.value
+
+
+class MADE:
+    """Learned autoregressive proposal (masked MLP) trained and sampled on the GPU."""
+
+    def __init__(self, n_spins: int, hidden: int, order, init_weights, seed: int = 22723,
+                 device: int | None = None):
+        self.n, self.hidden = int(n_spins), int(hidden)
+        self.order = np.ascontiguousarray(order, dtype=np.int32)
+        w = np.ascontiguousarray(init_weights, dtype=np.float64)
+        N, H = self.n, self.hidden
+        self.P = H * N + H + H * H + H + N * H + N
+        if w.shape != (self.P,):
+            raise ValueError(f"init_weights must have {self.P} entries")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        m = ctypes.c_void_p()
+        _check(lib().rtt_made_create(N, H, self.order.ctypes.data, w.ctypes.data, int(seed),
+                                     self.device, ctypes.byref(m)), "rtt_made_create")
+        self._m = m
+        self.seed = int(seed)
+
+    def close(self):
+        if getattr(self, "_m", None) is not None and self._m.value:
+            lib().rtt_made_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._m
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.P, dtype=np.float32)
+        _check(lib().rtt_made_get_params(self._m, out.ctypes.data), "rtt_made_get_params")
+        return out
+
+    def gradients(self, spins, stream=None):
+        B = spins.shape[0]
+        _dev_check(spins, torch.uint8, (B, self.n), "spins")
+        g = torch.empty(self.P, dtype=torch.float32, device=spins.device)
+        nll = torch.empty(1, dtype=torch.float64, device=spins.device)
+        _check(lib().rtt_made_gradients(self._m, _ptr(spins), B, _ptr(g), _ptr(nll), _stream(stream)),
+               "rtt_made_gradients")
+        return g, nll
+
+    def train_step(self, spins, lr: float = 1e-3, nll=None, stream=None):
+        B = spins.shape[0]
+        _dev_check(spins, torch.uint8, (B, self.n), "spins")
+        _check(lib().rtt_made_train_step(self._m, _ptr(spins), B, float(lr), _ptr(nll),
+                                         _stream(stream)), "rtt_made_train_step")
+
+    def log_prob(self, spins, stream=None):
+        B = spins.shape[0]
+        _dev_check(spins, torch.uint8, (B, self.n), "spins")
+        out = torch.empty(B, dtype=torch.float64, device=spins.device)
+        _check(lib().rtt_made_log_prob(self._m, _ptr(spins), B, _ptr(out), _stream(stream)),
+               "rtt_made_log_prob")
+        return out
+
+    def sample(self, B: int, chain0: int = 0, round: int = 0, stream=None):
+        sp = torch.empty((B, self.n), dtype=torch.uint8, device="cuda")
+        lq = torch.empty(B, dtype=torch.float64, device="cuda")
+        _check(lib().rtt_made_sample(self._m, int(B), int(chain0), int(round), _ptr(sp), _ptr(lq),
+                                     _stream(stream)), "rtt_made_sample")
+        return sp, lq
+
+    def fit(self, data: torch.Tensor, epochs: int, batch: int = 1024, lr: float = 1e-3,
+            seed: int = 0, stream=None):
+        """Minibatch Adam over `data` (device uint8 [n][N]); returns mean NLL per epoch."""
+        n = data.shape[0]
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        nll = torch.zeros(1, dtype=torch.float64, device=data.device)
+        hist = []
+        for _ in range(epochs):
+            perm = torch.randperm(n, generator=g).to(data.device)
+            tot, cnt = torch.zeros((), dtype=torch.float64, device=data.device), 0
+            for s in range(0, n - batch + 1, batch):
+                self.train_step(data[perm[s:s + batch]].contiguous(), lr, nll, stream)
+                tot += nll[0]
+                cnt += 1
+            hist.append(float(tot) / max(cnt, 1))
+        return hist
+
+
+def indep_mh(model: RTT, made: MADE, spins, state, round: int, n_accept=None, chain0: int = 0,
+             stream=None):
+    """One learned independence proposal per chain (in place)."""
+    B = spins.shape[0]
+    _dev_check(spins, torch.uint8, (B, model.n), "spins")
+    _dev_check(state, torch.int64, (B, 2), "state")
+    if n_accept is not None:
+        _dev_check(n_accept, torch.int64, (B,), "n_accept")
+    _check(lib().rtt_indep_mh(model.handle, made.handle, _ptr(spins), _ptr(state), B, int(chain0),
+                              int(round), _ptr(n_accept), _stream(stream)), "rtt_indep_mh")
