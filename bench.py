@@ -32,6 +32,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -183,7 +185,11 @@ def cpu_baseline(inst, w, seed):
     from paper_2604_22718_gb300 import inputs
     o = orc.Oracle(inst)
     cores = os.cpu_count() or 1
-    cal = max(cores, 8)
+    # warm call (library load, first-touch), then a timed calibration
+    warm = inputs.initial_spins(seed + 3, 2, inst.n_spins)
+    wm, we = o.init_chains(warm)
+    o.mcmc(seed, warm, wm, we, 0, 1, measure_every=1, threads=1)
+    cal = 2 * cores
     spins = inputs.initial_spins(seed + 1, cal, inst.n_spins)
     mant, ex = o.init_chains(spins)
     t0 = time.perf_counter()
@@ -440,6 +446,96 @@ def run_batched(args):
     b.close()
 
 
+def run_learned(args):
+    """Learned-proposal form: 16x16 TFIM (N = 256, h = 3.044), R = 2 (L = 512),
+    chi = 128, 8192 chains.  A MADE 256 -> 512 -> 512 -> 256 is trained on
+    configurations of the plain local sampler (chains x thinned sweeps), then
+    plain iterations (1 sweep + E_loc) and mixed iterations (1 sweep + 1
+    independence proposal + E_loc) are timed; tau_int and ESS/s of each."""
+    import torch
+    from paper_2604_22718_gb300 import inputs, rtt
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS["learned_16x16"]
+    inst = inputs.workload("learned_16x16")
+    N = inst.n_spins
+    B = args.chains or w["chains"]
+    prec = args.precision
+    K, W = args.steps, args.warmup
+    n_data_sweeps = int(os.environ.get("RTT_LEARNED_DATA_SWEEPS", "128"))
+    m = rtt.RTT(inst, prec, seed=w["seed"])
+    m.reserve(B)
+    stream = torch.cuda.current_stream()
+    sp = torch.from_numpy(inputs.initial_spins(w["seed"], B, N)).cuda()
+    _, _, st = m.log_amplitudes(sp)
+    t0 = time.perf_counter()
+    m.mcmc_sweep(sp, st, 0, 16)                       # burn-in
+    data = torch.empty((n_data_sweeps * B, N), dtype=torch.uint8, device="cuda")
+    for r in range(n_data_sweeps):
+        m.mcmc_sweep(sp, st, 16 + r, 1)
+        data[r * B:(r + 1) * B].copy_(sp)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    order = inst.path[:N].astype(np.int32)
+    made = rtt.MADE(N, 512, order, inputs.made_init_weights(w["seed"], N, 512), seed=w["seed"])
+    t0 = time.perf_counter()
+    epochs = int(os.environ.get("RTT_LEARNED_EPOCHS", "20"))
+    hist = made.fit(data, epochs=epochs, batch=1024, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del data
+
+    def run(mixed, sweep0):
+        s2 = sp.clone()
+        st2 = st.clone()
+        tr = torch.empty((K, B), dtype=torch.float64, device="cuda")
+        acc = torch.zeros(B, dtype=torch.int64, device="cuda")
+        junk = torch.empty((1, B), dtype=torch.float64, device="cuda")
+        for t in range(W):
+            m.mcmc_sweep(s2, st2, sweep0 + t, 1, 1, junk)
+            if mixed:
+                rtt.indep_mh(m, made, s2, st2, sweep0 + t)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        torch.cuda.synchronize()
+        for t in range(K):
+            ev[t][0].record(stream)
+            if mixed:
+                rtt.indep_mh(m, made, s2, st2, sweep0 + W + t, acc)
+            m.mcmc_sweep(s2, st2, sweep0 + W + t, 1, 1, tr[t:t + 1])
+            ev[t][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(z) for a, z in ev)
+        stats = m.observables(tr)
+        return ms, stats, float(acc.sum()) / (B * K)
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ms_p, st_p, _ = run(False, 10000)
+    ms_m, st_m, acc_m = run(True, 20000)
+    clk = clocks.stop()
+    sps_p = B * K / (ms_p / 1e3)
+    sps_m = B * K / (ms_m / 1e3)
+    line = {
+        "metric": METRIC, "value": sps_m, "unit": "samples/s", "n_gpus": 1, "steps": K,
+        "warmup": W, "ms_per_step": ms_m / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": {"workload": _workload_desc("learned_16x16", inst, B) +
+                   "; mixed 1:1 with a learned independence proposal (MADE 256-512-512-256, FP32)",
+                   "training_configs": n_data_sweeps * B, "epochs": epochs},
+        "plain": {"samples_per_s": sps_p, "ess_per_s": st_p["ess"] / (ms_p / 1e3),
+                  "tau_int": st_p["tau_int"], "e_mean": st_p["mean"], "e_se": st_p["se"]},
+        "mixed": {"samples_per_s": sps_m, "ess_per_s": st_m["ess"] / (ms_m / 1e3),
+                  "tau_int": st_m["tau_int"], "e_mean": st_m["mean"], "e_se": st_m["se"],
+                  "indep_acceptance": acc_m},
+        "ess_speedup_mixed_vs_plain": (st_m["ess"] / ms_m) / (st_p["ess"] / ms_p),
+        "made_nll_first_last_epoch": [hist[0], hist[-1]] if hist else None,
+        "data_s": t_data, "train_s": t_train, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    made.close()
+    m.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -450,6 +546,10 @@ def main():
     if args.workload == "batched64":
         if int(os.environ.get("RANK", "0")) == 0:
             run_batched(args)
+        return
+    if args.workload == "learned_16x16":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_learned(args)
         return
     run_ours(args)
 
