@@ -782,6 +782,339 @@ __global__ void __launch_bounds__(NT, 1)
     if (warp == 0) tmem_dealloc(tmem, C::TCOLS);
 }
 
+// ------------------------------------------------------------------ split-row sweep (chi = 64)
+// Each proposal row psi(s') = l_{j-1} A_j' ... A_m . (A_{m+1} ... A'_{(R-1)N+j} r)
+// is computed as two half-rows at once: the left tile walks sites j..m from
+// l_{j-1} (left to right), the right tile walks (R-1)N+j..m+1 from the cached
+// right environment (right to left); the halves meet in one dot product and
+// the Metropolis decision.  Warps 0-3 run the left epilogue, warps 4-7 the
+// right one (same 128 chains), warp 8 issues the MMAs, warp 9 the TMA loads.
+// Each tile has its own accumulator (TMEM columns [0,128) and [128,256)), A
+// operand and B ring, so one tile's MMA overlaps the other's epilogue and the
+// critical path of a proposal is half a row.  Every wait is bounded; after an
+// expired wait every role walks the rest of its program without issuing work
+// (waits return at once), so the named barriers between the two epilogue
+// groups always meet.
+constexpr int SP_THREADS = 320;
+
+inline size_t sweep2_smem(int N, int L) {
+    return 1024 + 4 * (size_t)Cfg<64>::A_BYTES + 2 * (size_t)NS * Cfg<64>::STAGE + 256 +
+           (size_t)16 * N + (size_t)4 * L;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void named_sync_256() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+template <bool F16>
+__global__ void __launch_bounds__(SP_THREADS, 1)
+    k_tc_sweep2(const __grid_constant__ CUtensorMap map, const Args a) {
+    constexpr int CHI = 64;
+    using C = Cfg<CHI, F16>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t AL_hi = sa(base), AL_lo = AL_hi + C::A_BYTES;
+    const uint32_t AR_hi = AL_lo + C::A_BYTES, AR_lo = AR_hi + C::A_BYTES;
+    const uint32_t ring0 = AR_lo + C::A_BYTES;  // ring L: stages 0,1; ring R: stages 2,3
+    uint64_t *bars = (uint64_t *)(base + 4 * C::A_BYTES + 2 * NS * C::STAGE);
+    const uint32_t bar0 = sa(bars);
+    // bars: full[4] (L0 L1 R0 R1), empty[4], done[2] (L R), ready[2] (L R)
+    auto full_bar = [&](int X, int s) { return bar0 + 8u * (X * NS + s); };
+    auto empty_bar = [&](int X, int s) { return bar0 + 8u * (4 + X * NS + s); };
+    auto done_bar = [&](int X) { return bar0 + 8u * (8 + X); };
+    auto ready_bar = [&](int X) { return bar0 + 8u * (10 + X); };
+    uint32_t *tmem_slot = (uint32_t *)(bars + 12);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    long long *issued = (long long *)(bars + 14);  // loads issued per tile
+    uint32_t *bits = (uint32_t *)(base + 4 * C::A_BYTES + 2 * NS * C::STAGE + 256);
+    uint32_t *tab = bits + 4 * a.N;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = a.N, L = a.L;
+    const int span = (a.R - 1) * N + 1;
+    const int nL = (span + 1) / 2, nR = span - nL;
+    const int rbase = (a.R - 1) * N + 1;
+    const int m = tid & 127;  // row of the epilogue threads
+    const int64_t c_raw = (int64_t)blockIdx.x * NT + m;
+    const bool active = c_raw < a.B;
+    const int64_t c = active ? c_raw : a.B - 1;
+
+    if (warp == 0) tmem_alloc(sa(tmem_slot), 256);
+    if (tid == 0) {
+        for (int i = 0; i < 8; ++i) mbar_init(bar0 + 8u * i, 1);
+        mbar_init(done_bar(0), 1);
+        mbar_init(done_bar(1), 1);
+        mbar_init(ready_bar(0), 128);
+        mbar_init(ready_bar(1), 128);
+        *abort_flag = 0;
+        issued[0] = issued[1] = 0;
+        fence_barrier_init();
+    }
+    for (int k = tid; k < L; k += SP_THREADS)
+        tab[k] = ((uint32_t)__ldg(a.q + (k % N)) & 0xffffu) |
+                 ((uint32_t)(__ldg(a.cexp + k) & 0xffff) << 16);
+    if (warp < 4) {
+        for (int i = 0; i < N; ++i) {
+            const uint32_t w = __ballot_sync(FULL, a.spins_in[c * N + i] != 0);
+            if (lane == 0) bits[i * 4 + warp] = w;
+        }
+    }
+    __syncthreads();
+    const uint32_t tmem = *tmem_slot;
+    auto spin = [&](int i) -> int { return (int)((bits[i * 4 + (warp & 3)] >> lane) & 1u); };
+    auto site_spin = [&](int k) -> int { return (int)(tab[k] & 0xffffu); };
+    auto site_cexp = [&](int k) -> int { return (int)(int16_t)(tab[k] >> 16); };
+    auto bwait = [&](uint32_t bar, uint32_t parity) -> bool {
+        if (*abort_flag) return false;
+        if (!mbar_wait(bar, parity, a.wait_limit)) {
+            atomicOr(a.err, 1);
+            *abort_flag = 1;
+            return false;
+        }
+        return true;
+    };
+
+    if (warp == 8) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            long long n[2] = {0, 0};
+            auto issue = [&](int X) {
+                const long long g = n[X]++;
+                const int s = (int)(g % NS);
+                if (!bwait(full_bar(X, s), (uint32_t)((g / NS) & 1))) return;
+                if (!bwait(ready_bar(X), (uint32_t)(g & 1))) return;
+                tc_after();
+                const uint32_t ahi = X ? AR_hi : AL_hi, alo = X ? AR_lo : AL_lo;
+                const uint32_t b_hi = ring0 + (uint32_t)(X * NS + s) * C::STAGE, b_lo = b_hi + C::BOX;
+                const uint32_t d = tmem + (uint32_t)(X * 128);
+#pragma unroll
+                for (int kb = 0; kb < 4; ++kb) {
+                    const uint32_t o = (uint32_t)(kb * 32);
+                    mma_bf16(d, sdesc(ahi + o), sdesc(b_hi + o), C::IDESC, kb != 0 ? 1u : 0u);
+                    mma_bf16(d, sdesc(ahi + o), sdesc(b_lo + o), C::IDESC, 1u);
+                    mma_bf16(d, sdesc(alo + o), sdesc(b_hi + o), C::IDESC, 1u);
+                }
+                mma_commit(empty_bar(X, s));
+                mma_commit(done_bar(X));
+            };
+            for (int sw = 0; sw < a.n_sweeps; ++sw) {
+                for (int u = 0; u < N - 1; ++u) issue(1);
+                for (int j = 0; j < N; ++j)
+                    for (int t = 0; t < nL; ++t) {
+                        issue(0);
+                        if (t < nR) issue(1);
+                    }
+            }
+        }
+    } else if (warp == 9) {
+        // ---------------------------------------------------------- TMA loader
+        if (lane == 0) {
+            long long n[2] = {0, 0};
+            auto load = [&](int X, int k) {
+                const long long g = n[X]++;
+                const int s = (int)(g % NS);
+                if (*abort_flag) return;
+                if (g >= NS && !bwait(empty_bar(X, s), (uint32_t)(((g / NS) - 1) & 1))) return;
+                const int y_hi = ((X * 2 + 0) * L + k) * 2 * CHI;
+                const int y_lo = ((X * 2 + 1) * L + k) * 2 * CHI;
+                const uint32_t dst = ring0 + (uint32_t)(X * NS + s) * C::STAGE;
+                mbar_expect_tx(full_bar(X, s), (uint32_t)C::STAGE);
+                tma_load_2d(dst, &map, 0, y_hi, full_bar(X, s));
+                tma_load_2d(dst + C::BOX, &map, 0, y_lo, full_bar(X, s));
+                issued[X] = g + 1;
+            };
+            for (int sw = 0; sw < a.n_sweeps; ++sw) {
+                for (int u = 0; u < N - 1; ++u) load(1, L - 1 - u);
+                for (int j = 0; j < N; ++j)
+                    for (int t = 0; t < nL; ++t) {
+                        load(0, j + t);
+                        if (t < nR) load(1, (a.R - 1) * N + j - t);
+                    }
+            }
+        }
+    } else if (warp < 4) {
+        // ---------------------------------------------------------- left epilogue
+        const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+        float v[CHI];
+        load_vec<CHI>(a.bl, v);
+        write_A<CHI, F16>(AL_hi, AL_lo, m, v);
+        fence_async_smem();
+        tc_before();
+        mbar_arrive(ready_bar(0));
+        double pm = a.state[c].mant;
+        int64_t pe = a.state[c].exp2, acc_count = 0;
+        int64_t El = 0, E = 0, Ekeep = 0, Eflip = 0;
+        long long nd = 0;
+        for (int sw = 0; sw < a.n_sweeps; ++sw) {
+            for (int j = 0; j < N; ++j) {
+                const int iq = site_spin(j);
+                for (int t = 0; t < nL; ++t) {
+                    const int k = j + t;
+                    bwait(done_bar(0), (uint32_t)(nd++ & 1));
+                    tc_after();
+                    __syncwarp();
+                    const int sk = site_spin(k), ck = site_cexp(k);
+                    if (t == 0) {
+                        const int si = spin(iq);
+                        acc_select<CHI>(tw, si, v);
+                        Ekeep = El + renorm<CHI>(v) - ck;
+                        if (active) {
+                            store_vec<CHI>(a.lstack + ((size_t)c * N + j) * CHI, v);
+                            a.lexp[(size_t)c * N + j] = (int32_t)Ekeep;
+                        }
+                        acc_select<CHI>(tw, si ^ 1, v);
+                        Eflip = El + renorm<CHI>(v) - ck;
+                        if (active) {
+                            store_vec<CHI>(a.tmp + (size_t)c * CHI, v);
+                            a.tmp_exp[c] = (int32_t)Eflip;
+                        }
+                        E = Eflip;
+                    } else {
+                        acc_select<CHI>(tw, spin(sk) ^ (sk == iq ? 1 : 0), v);
+                        E += renorm<CHI>(v) - ck;
+                    }
+                    if (t + 1 < nL) {
+                        write_A<CHI, F16>(AL_hi, AL_lo, m, v);
+                        fence_async_smem();
+                        tc_before();
+                        mbar_arrive(ready_bar(0));
+                    }
+                }
+                named_sync_256();  // the right half-row is published
+                const float *vr = a.tmp + ((size_t)a.B + c) * CHI;
+                int64_t Ep = E + a.tmp_exp[a.B + c];
+                double mm = dot<CHI>(v, vr);
+                normalize_scalar(mm, Ep);
+                const double ratio = ldexp(mm / pm, (int)(Ep - pe));
+                const double x = rttd::mcmc_uniform(a.seed, (uint64_t)(a.chain0 + c),
+                                                    (uint64_t)(a.sweep0 + sw), (uint64_t)j);
+                const bool accept = active && !*abort_flag && (x < ratio * ratio);
+                if (accept) {
+                    pm = mm;
+                    pe = Ep;
+                    ++acc_count;
+                    load_vec<CHI>(a.tmp + (size_t)c * CHI, v);
+                    store_vec<CHI>(a.lstack + ((size_t)c * N + j) * CHI, v);
+                    a.lexp[(size_t)c * N + j] = (int32_t)Eflip;
+                    El = Eflip;
+                } else {
+                    El = Ekeep;
+                }
+                const uint32_t flips = __ballot_sync(FULL, accept);
+                if (lane == 0) bits[iq * 4 + warp] ^= flips;
+                named_sync_256();  // the decision is published
+                const bool more = (j + 1 < N) || (sw + 1 < a.n_sweeps);
+                if (more) {
+                    if (j + 1 < N) {
+                        load_vec<CHI>(a.lstack + ((size_t)c * N + j) * CHI, v);
+                    } else {
+                        load_vec<CHI>(a.bl, v);
+                        El = 0;
+                    }
+                    write_A<CHI, F16>(AL_hi, AL_lo, m, v);
+                    fence_async_smem();
+                    tc_before();
+                    mbar_arrive(ready_bar(0));
+                }
+            }
+        }
+        if (active && !*abort_flag) {
+            a.state[c].mant = pm;
+            a.state[c].exp2 = pe;
+            if (a.n_accept) a.n_accept[c] += acc_count;
+        }
+    } else {
+        // ---------------------------------------------------------- right epilogue
+        const uint32_t tw = tmem + ((uint32_t)((warp & 3) * 32) << 16) + 128u;
+        float v[CHI];
+        load_vec<CHI>(a.br, v);
+        if (active) {
+            store_vec<CHI>(a.rstack + ((size_t)c * N + (N - 1)) * CHI, v);
+            a.rexp[(size_t)c * N + (N - 1)] = 0;
+        }
+        write_A<CHI, F16>(AR_hi, AR_lo, m, v);
+        fence_async_smem();
+        tc_before();
+        mbar_arrive(ready_bar(1));
+        int64_t E = 0;
+        long long nd = 0;
+        for (int sw = 0; sw < a.n_sweeps; ++sw) {
+            E = 0;
+            for (int u = 0; u < N - 1; ++u) {  // right environment of the last block
+                const int k = L - 1 - u;
+                bwait(done_bar(1), (uint32_t)(nd++ & 1));
+                tc_after();
+                __syncwarp();
+                acc_select<CHI>(tw, spin(site_spin(k)), v);
+                E += renorm<CHI>(v) - site_cexp(k);
+                if (active) {
+                    store_vec<CHI>(a.rstack + ((size_t)c * N + (k - rbase)) * CHI, v);
+                    a.rexp[(size_t)c * N + (k - rbase)] = (int32_t)E;
+                }
+                // next: the next environment step, or (u = N-2) the first right
+                // half-row, which starts from this very vector r_{(R-1)N+1}
+                write_A<CHI, F16>(AR_hi, AR_lo, m, v);
+                fence_async_smem();
+                tc_before();
+                mbar_arrive(ready_bar(1));
+            }
+            for (int j = 0; j < N; ++j) {
+                const int iq = site_spin(j);
+                if (j > 0) E = a.rexp[(size_t)c * N + j];
+                for (int t = 0; t < nR; ++t) {
+                    const int k = (a.R - 1) * N + j - t;
+                    bwait(done_bar(1), (uint32_t)(nd++ & 1));
+                    tc_after();
+                    __syncwarp();
+                    const int sk = site_spin(k);
+                    acc_select<CHI>(tw, spin(sk) ^ (sk == iq ? 1 : 0), v);
+                    E += renorm<CHI>(v) - site_cexp(k);
+                    if (t + 1 < nR) {
+                        write_A<CHI, F16>(AR_hi, AR_lo, m, v);
+                        fence_async_smem();
+                        tc_before();
+                        mbar_arrive(ready_bar(1));
+                    }
+                }
+                if (active) {
+                    store_vec<CHI>(a.tmp + ((size_t)a.B + c) * CHI, v);
+                    a.tmp_exp[a.B + c] = (int32_t)E;
+                }
+                // the next half-row's start does not depend on this decision
+                const bool more = (j + 1 < N) || (sw + 1 < a.n_sweeps);
+                if (more) {
+                    if (j + 1 < N) {
+                        load_vec<CHI>(a.rstack + ((size_t)c * N + (j + 1)) * CHI, v);
+                    } else {
+                        load_vec<CHI>(a.br, v);
+                    }
+                    write_A<CHI, F16>(AR_hi, AR_lo, m, v);
+                    fence_async_smem();
+                    tc_before();
+                    mbar_arrive(ready_bar(1));
+                }
+                named_sync_256();  // publish the right half-row
+                named_sync_256();  // wait for the decision
+            }
+        }
+    }
+    __syncthreads();
+    if (warp < 4 && active && !*abort_flag) {
+        for (int i = 0; i < N; ++i) a.spins_out[c * N + i] = (uint8_t)spin(i);
+    }
+    // teardown: drain this CTA's own copies after an expired wait (bounded)
+    if (tid == 0 && *abort_flag) {
+        for (int X = 0; X < 2; ++X)
+            for (long long g = (issued[X] > NS ? issued[X] - NS : 0); g < issued[X]; ++g)
+                mbar_wait(full_bar(X, (int)(g % NS)), (uint32_t)((g / NS) & 1), a.wait_limit);
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
 }  // namespace tcd
 
 // ====================================================================== host side
@@ -1014,9 +1347,10 @@ rtt_status tc_sweep(rtt_s *h, uint8_t *spins, rtt_chain_state *state, int64_t B,
         p->d_tmp = nullptr;
         p->d_tmp_exp = nullptr;
         p->tmp_cap = 0;
-        if ((e = cudaMalloc((void **)&p->d_tmp, (size_t)B * p->chi * 4)) != cudaSuccess)
+        // [2][B][chi]: flipped row starts, then right half-rows of the split sweep
+        if ((e = cudaMalloc((void **)&p->d_tmp, (size_t)2 * B * p->chi * 4)) != cudaSuccess)
             return status_of(e, "tc sweep scratch");
-        if ((e = cudaMalloc((void **)&p->d_tmp_exp, (size_t)B * 4)) != cudaSuccess)
+        if ((e = cudaMalloc((void **)&p->d_tmp_exp, (size_t)2 * B * 4)) != cudaSuccess)
             return status_of(e, "tc sweep scratch");
         p->tmp_cap = B;
     }
@@ -1031,8 +1365,26 @@ rtt_status tc_sweep(rtt_s *h, uint8_t *spins, rtt_chain_state *state, int64_t B,
     a.n_sweeps = n_sweeps;
     a.seed = h->seed;
     a.n_accept = n_accept;
+    cudaError_t e;
     prof_begin(h, KID_TC_SWEEP, st);
-    cudaError_t e = launch_chi<tcd::M_SWEEP>(p, a, dim3(tiles(B)), st);
+    if (p->chi == 64 && h->R >= 2 && h->N >= 2) {
+        // split-row sweep: two half-row tiles per CTA
+        const size_t smem = tcd::sweep2_smem(h->N, h->L);
+        if (p->f16) {
+            e = cudaFuncSetAttribute(tcd::k_tc_sweep2<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                tcd::k_tc_sweep2<true><<<tiles(B), tcd::SP_THREADS, smem, st>>>(p->map, a);
+        } else {
+            e = cudaFuncSetAttribute(tcd::k_tc_sweep2<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                tcd::k_tc_sweep2<false><<<tiles(B), tcd::SP_THREADS, smem, st>>>(p->map, a);
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
+    } else {
+        e = launch_chi<tcd::M_SWEEP>(p, a, dim3(tiles(B)), st);
+    }
     prof_end(h, KID_TC_SWEEP, st);
     return status_of(e, "tc sweep");
 }
