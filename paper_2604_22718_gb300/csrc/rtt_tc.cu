@@ -876,8 +876,11 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
     };
 
     if (warp == 8) {
-        // ---------------------------------------------------------- MMA issuer
-        if (lane == 0) {
+        // ---------------------------------------------------------- MMA issuers
+        // lane 0 issues the left tile's MMAs, lane 1 the right tile's, so a
+        // half-row never waits behind the other tile's epilogue
+        if (lane < 2) {
+            const int XX = lane;
             long long n[2] = {0, 0};
             auto issue = [&](int X) {
                 const long long g = n[X]++;
@@ -899,17 +902,17 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                 mma_commit(done_bar(X));
             };
             for (int sw = 0; sw < a.n_sweeps; ++sw) {
-                for (int u = 0; u < N - 1; ++u) issue(1);
+                if (XX == 1)
+                    for (int u = 0; u < N - 1; ++u) issue(1);
                 for (int j = 0; j < N; ++j)
-                    for (int t = 0; t < nL; ++t) {
-                        issue(0);
-                        if (t < nR) issue(1);
-                    }
+                    for (int t = 0; t < (XX == 0 ? nL : nR); ++t) issue(XX);
             }
         }
     } else if (warp == 9) {
-        // ---------------------------------------------------------- TMA loader
-        if (lane == 0) {
+        // ---------------------------------------------------------- TMA loaders
+        // lane 0 feeds the left ring, lane 1 the right ring
+        if (lane < 2) {
+            const int XX = lane;
             long long n[2] = {0, 0};
             auto load = [&](int X, int k) {
                 const long long g = n[X]++;
@@ -925,12 +928,14 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                 issued[X] = g + 1;
             };
             for (int sw = 0; sw < a.n_sweeps; ++sw) {
-                for (int u = 0; u < N - 1; ++u) load(1, L - 1 - u);
-                for (int j = 0; j < N; ++j)
-                    for (int t = 0; t < nL; ++t) {
-                        load(0, j + t);
-                        if (t < nR) load(1, (a.R - 1) * N + j - t);
-                    }
+                if (XX == 1)
+                    for (int u = 0; u < N - 1; ++u) load(1, L - 1 - u);
+                for (int j = 0; j < N; ++j) {
+                    if (XX == 0)
+                        for (int t = 0; t < nL; ++t) load(0, j + t);
+                    else
+                        for (int t = 0; t < nR; ++t) load(1, (a.R - 1) * N + j - t);
+                }
             }
         }
     } else if (warp < 4) {
