@@ -179,6 +179,14 @@ __device__ __forceinline__ float scale2(float x, int e) {
     return ldexpf(x, e);
 }
 
+// Whether 2^e is a normal number of x's type, and that power itself.
+__device__ __forceinline__ bool pow2_normal(double, int e) { return e >= -1022 && e <= 1023; }
+__device__ __forceinline__ bool pow2_normal(float, int e) { return e >= -126 && e <= 127; }
+__device__ __forceinline__ double pow2(double, int e) {
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+__device__ __forceinline__ float pow2(float, int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
 }  // namespace rttd
 
 #define RTT_CUDA_TRY(expr)                                                                         \

@@ -63,8 +63,14 @@ struct RowOps {
         for (int off = G / 2; off >= 1; off >>= 1) m = fmax(m, __shfl_xor_sync(FULL, m, off, G));
         if (!(m > T(0)) || !isfinite(m)) return 0;
         const int e = exponent_of(m);
+        if (pow2_normal(T(0), -e)) {  // one exact multiply per entry
+            const T sc = pow2(T(0), -e);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) v[q] = scale2(v[q], -e);
+            for (int q = 0; q < NQ; ++q) v[q] *= sc;
+        } else {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) v[q] = scale2(v[q], -e);
+        }
         return e;
     }
 

@@ -290,8 +290,14 @@ __device__ __forceinline__ int renorm(float (&v)[CHI]) {
                            fmaxf(fmaxf(m[4], m[5]), fmaxf(m[6], m[7])));
     if (!(mx > 0.f) || !isfinite(mx)) return 0;
     const int e = rttd::exponent_of(mx);
+    if (rttd::pow2_normal(0.f, -e)) {  // one exact multiply per entry
+        const float sc = rttd::pow2(0.f, -e);
 #pragma unroll
-    for (int i = 0; i < CHI; ++i) v[i] = rttd::scale2(v[i], -e);
+        for (int i = 0; i < CHI; ++i) v[i] *= sc;
+    } else {
+#pragma unroll
+        for (int i = 0; i < CHI; ++i) v[i] = rttd::scale2(v[i], -e);
+    }
     return e;
 }
 
