@@ -150,8 +150,14 @@ rtt_status rtt_local_energy(rtt_handle h, const uint8_t *spins, int64_t B, doubl
  *   spins     device [B][N]   in/out
  *   state     device [B]      in/out, psi of the current spins (from
  *                             rtt_log_amplitudes), updated on acceptance
- *   e_loc_trace device [n_sweeps/measure_every][B] or NULL: E_loc after every
- *             measure_every-th sweep of this call (measure_every >= 1)
+ *   e_loc_trace device [n_sweeps/measure_every][B] or NULL (measure_every >= 1):
+ *             row g holds E_loc of the configuration entering sweep
+ *             g*measure_every of this call -- each measured iteration
+ *             evaluates the configuration it starts from, then runs its
+ *             measure_every sweeps; trailing sweeps are not measured.  The
+ *             library evaluates it on a second, internal stream from a copy
+ *             of the spins, concurrently with the sweeps; all of the call's
+ *             work is ordered before later work on `stream`.
  *   n_accept  device int64 [B] or NULL: accepted proposals are added
  * Chains whose psi is 0 or not finite accept any proposal with a finite,
  * nonzero amplitude. */
@@ -191,8 +197,9 @@ rtt_status rtt_profile_read(rtt_handle h, rtt_kernel_time *out, int32_t capacity
  * together.  Each instance is an rtt_desc (FP32 precision, periodic path,
  * 17 <= chi <= 256, all on one device); each gets its own chains.  One call of
  * rtt_batch_step performs one Monte Carlo iteration of every chain of every
- * instance -- one systematic sweep (Sec. 3.3) followed by the local energy
- * (Sec. 3.3 / Sec. 4 Eq. ising-model) -- in ONE persistent kernel launch
+ * instance -- the local energy of the configuration it starts from
+ * (Sec. 3.3 / Sec. 4 Eq. ising-model), then one systematic sweep (Sec. 3.3)
+ * -- in ONE persistent kernel launch
  * (optionally through a CUDA graph).  Results of instance i equal, bit for
  * bit, those of an FP32 rtt_handle of the same description running
  * rtt_mcmc_sweep with chain0 = 0, sweep0 = sweep, measure_every = 1.

@@ -203,7 +203,8 @@ class Oracle:
 
     def mcmc(self, seed, spins, mant, ex, sweep0, n_sweeps, measure_every=1,
              chain0=0, threads: int = 1, record=True):
-        """Runs the sampler in place on (spins, mant, ex).  Returns (trace, n_accept)."""
+        """Runs the sampler in place on (spins, mant, ex).  Returns (trace, n_accept);
+        trace[g] is E_loc of the configuration entering sweep g * measure_every."""
         assert spins.flags.c_contiguous and spins.dtype == np.uint8
         assert mant.flags.c_contiguous and ex.flags.c_contiguous
         B = spins.shape[0]

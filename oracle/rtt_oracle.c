@@ -339,8 +339,12 @@ double orc_uniform_keyed(uint64_t seed, uint64_t stream, uint64_t c0, uint64_t c
  * the flipped amplitude as computed by orc_flip_amplitude.
  *
  * spins   [B][N] in/out;  mant/ex [B] in/out: psi = mant * 2^ex of the
- * current state;  trace [n_meas][B] (may be NULL) receives E_loc after every
- * measure_every-th sweep;  n_accept [B] accumulates accepted proposals.
+ * current state;  trace [n_meas][B] (may be NULL), n_meas = n_sweeps /
+ * measure_every: trace[g] is E_loc of the configuration that enters sweep
+ * g * measure_every of this call (each measured iteration evaluates the
+ * configuration it starts from, then runs its measure_every sweeps; trailing
+ * sweeps beyond n_meas * measure_every are not measured);  n_accept [B]
+ * accumulates accepted proposals.
  * Chains are numbered chain0 + c for the random stream.  Returns the number
  * of chains whose amplitude or local energy was undefined. */
 int orc_mcmc(const orc_rtt *m, uint64_t seed, uint8_t *spins, double *mant, int64_t *ex,
@@ -351,9 +355,16 @@ int orc_mcmc(const orc_rtt *m, uint64_t seed, uint8_t *spins, double *mant, int6
     int bad = 0;
     for (int64_t c = 0; c < B; ++c) {
         uint8_t *s = spins + (size_t)c * N;
-        int meas = 0;
+        const int32_t n_meas = (trace && measure_every > 0) ? n_sweeps / measure_every : 0;
+        int32_t meas = 0;
         for (int32_t t = 0; t < n_sweeps; ++t) {
             int64_t sweep = sweep0 + t;
+            if (meas < n_meas && (t % measure_every) == 0) {
+                double e;
+                bad += orc_local_energy(m, s, &e, NULL);
+                trace[(size_t)meas * B + c] = e;
+                ++meas;
+            }
             for (int j = 0; j < N; ++j) {
                 int i = m->path[j];
                 double mf;
@@ -368,12 +379,6 @@ int orc_mcmc(const orc_rtt *m, uint64_t seed, uint8_t *spins, double *mant, int6
                     ex[c] = ef;
                     if (n_accept) n_accept[c] += 1;
                 }
-            }
-            if (trace && measure_every > 0 && ((t + 1) % measure_every) == 0) {
-                double e;
-                bad += orc_local_energy(m, s, &e, NULL);
-                trace[(size_t)meas * B + c] = e;
-                ++meas;
             }
         }
     }

@@ -43,6 +43,13 @@ rtt_status cuda_fail(cudaError_t e, const char *where) {
         if (_e != cudaSuccess) return cuda_fail(_e, where);                                        \
     } while (0)
 
+// As API_CUDA inside rtt_create, where a failure also frees the handle.
+#define API_CUDA_CLEANUP(expr, where)                                                              \
+    do {                                                                                           \
+        cudaError_t _e = (expr);                                                                   \
+        if (_e != cudaSuccess) return cleanup(cuda_fail(_e, where));                               \
+    } while (0)
+
 int padded_chi(int chi) {
     int p = 1;
     while (p < chi) p <<= 1;
@@ -79,10 +86,19 @@ void free_scratch(rtt_s *h) {
     cudaFree(h->d_rexp);
     cudaFree(h->d_rows_mant);
     cudaFree(h->d_rows_exp);
+    cudaFree(h->d_sw_lstack);
+    cudaFree(h->d_sw_lexp);
+    cudaFree(h->d_sw_rstack);
+    cudaFree(h->d_sw_rexp);
+    cudaFree(h->d_snap[0]);
+    cudaFree(h->d_snap[1]);
     h->d_lstack = h->d_rstack = nullptr;
     h->d_lexp = h->d_rexp = nullptr;
     h->d_rows_mant = nullptr;
     h->d_rows_exp = nullptr;
+    h->d_sw_lstack = h->d_sw_rstack = nullptr;
+    h->d_sw_lexp = h->d_sw_rexp = nullptr;
+    h->d_snap[0] = h->d_snap[1] = nullptr;
     h->cap_B = 0;
 }
 
@@ -90,7 +106,8 @@ size_t scratch_bytes_for(const rtt_s *h, int64_t B) {
     const size_t eb = h->elem_bytes();
     const size_t stack = (size_t)B * h->N * h->chip * eb + (size_t)B * h->N * 4;
     const size_t rows = (size_t)B * (h->N + 1) * 16;
-    return 2 * stack + rows;
+    const size_t snap = (size_t)B * h->N;
+    return 4 * stack + rows + 2 * snap;
 }
 
 rtt_status ensure_scratch(rtt_s *h, int64_t B) {
@@ -105,6 +122,12 @@ rtt_status ensure_scratch(rtt_s *h, int64_t B) {
     API_CUDA(cudaMalloc((void **)&h->d_rexp, nv * 4), "scratch r-exp");
     API_CUDA(cudaMalloc((void **)&h->d_rows_mant, (size_t)B * (h->N + 1) * 8), "scratch rows");
     API_CUDA(cudaMalloc((void **)&h->d_rows_exp, (size_t)B * (h->N + 1) * 8), "scratch rows");
+    API_CUDA(cudaMalloc(&h->d_sw_lstack, nv * h->chip * eb), "scratch sweep l-stack");
+    API_CUDA(cudaMalloc((void **)&h->d_sw_lexp, nv * 4), "scratch sweep l-exp");
+    API_CUDA(cudaMalloc(&h->d_sw_rstack, nv * h->chip * eb), "scratch sweep r-stack");
+    API_CUDA(cudaMalloc((void **)&h->d_sw_rexp, nv * 4), "scratch sweep r-exp");
+    API_CUDA(cudaMalloc((void **)&h->d_snap[0], nv), "scratch spin snapshot");
+    API_CUDA(cudaMalloc((void **)&h->d_snap[1], nv), "scratch spin snapshot");
     h->cap_B = B;
     return RTT_OK;
 }
@@ -308,6 +331,12 @@ rtt_status rtt_create(const rtt_desc *d, rtt_handle *out) {
         return s;
     };
     rtt_status s;
+    API_CUDA_CLEANUP(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking),
+                     "rtt_create: second stream");
+    API_CUDA_CLEANUP(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "rtt_create: events");
+    for (int i = 0; i < 2; ++i)
+        API_CUDA_CLEANUP(cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming),
+                         "rtt_create: events");
     std::vector<int32_t> q(d->path, d->path + N);
     if ((s = upload(q, (void **)&h->d_q, "rtt_create: path")) != RTT_OK) return cleanup(s);
     if ((s = upload(pos, (void **)&h->d_pos, "rtt_create: positions")) != RTT_OK) return cleanup(s);
@@ -347,6 +376,10 @@ rtt_status rtt_destroy(rtt_handle h) {
     DeviceGuard guard(h->device);
     cudaDeviceSynchronize();
     free_scratch(h);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    for (int i = 0; i < 2; ++i)
+        if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
     tc_plan_destroy(h);
     delete (Profiler *)h->prof;
     h->prof = nullptr;
@@ -432,36 +465,48 @@ rtt_status rtt_mcmc_sweep(rtt_handle h, uint8_t *spins, rtt_chain_state *state, 
     API_CUDA(cudaGetLastError(), "rtt_mcmc_sweep: pending error");
     if ((s = ensure_scratch(h, B)) != RTT_OK) return s;
     const SimtArgs a = simt_args(h);
-    auto sweeps = [&](int64_t sw0, int32_t n, bool keep_left) -> rtt_status {
+    auto sweeps = [&](int64_t sw0, int32_t n) -> rtt_status {
         if (n <= 0) return RTT_OK;
         if (h->precision >= RTT_BF16X3) {
             return tc_sweep(h, spins, state, B, chain0, sw0, n, n_accept, st);
         }
-        void *ls = keep_left ? h->d_lstack : nullptr;
-        int32_t *le = keep_left ? h->d_lexp : nullptr;
         prof_begin(h, KID_SWEEP, st);
         API_CUDA(h->precision == RTT_FP64
-                     ? simt_sweep_f64(a, spins, state, B, chain0, sw0, n, h->seed, h->d_rstack,
-                                      h->d_rexp, ls, le, n_accept, st)
-                     : simt_sweep_f32(a, spins, state, B, chain0, sw0, n, h->seed, h->d_rstack,
-                                      h->d_rexp, ls, le, n_accept, st),
+                     ? simt_sweep_f64(a, spins, state, B, chain0, sw0, n, h->seed, h->d_sw_rstack,
+                                      h->d_sw_rexp, nullptr, nullptr, n_accept, st)
+                     : simt_sweep_f32(a, spins, state, B, chain0, sw0, n, h->seed, h->d_sw_rstack,
+                                      h->d_sw_rexp, nullptr, nullptr, n_accept, st),
                  "rtt_mcmc_sweep: sweep kernel");
         prof_end(h, KID_SWEEP, st);
         return RTT_OK;
     };
-    if (!e_loc_trace) return sweeps(sweep0, n_sweeps, false);
+    if (!e_loc_trace) return sweeps(sweep0, n_sweeps);
+    // Measured group g: the local energy of the configuration entering the
+    // group runs on the handle's second stream, from a snapshot of the spins,
+    // while the group's sweeps run on `stream`; the sweeps keep their own
+    // environment stacks.  A snapshot buffer is reused two groups later, after
+    // the energy that read it has finished; `stream` waits for the last energy
+    // before the call's work ends.
     const int32_t n_meas = n_sweeps / measure_every;
+    const size_t snap_bytes = (size_t)B * h->N;
     int64_t sw = sweep0;
-    for (int32_t m = 0; m < n_meas; ++m) {
-        // the sweep leaves l_j (j < N) of the final spins in the left stack
-        const bool keep = true;
-        if ((s = sweeps(sw, measure_every, keep)) != RTT_OK) return s;
-        sw += measure_every;
-        if ((s = energy_pipeline(h, spins, B, e_loc_trace + (size_t)m * B, nullptr, keep, st)) !=
-            RTT_OK)
+    for (int32_t g = 0; g < n_meas; ++g) {
+        uint8_t *snap = h->d_snap[g & 1];
+        if (g >= 2) API_CUDA(cudaStreamWaitEvent(st, h->ev_done[g & 1], 0), "rtt_mcmc_sweep: wait");
+        API_CUDA(cudaMemcpyAsync(snap, spins, snap_bytes, cudaMemcpyDeviceToDevice, st),
+                 "rtt_mcmc_sweep: spin snapshot");
+        API_CUDA(cudaEventRecord(h->ev_fork, st), "rtt_mcmc_sweep: fork");
+        API_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0), "rtt_mcmc_sweep: fork");
+        if ((s = energy_pipeline(h, snap, B, e_loc_trace + (size_t)g * B, nullptr, false,
+                                 h->side)) != RTT_OK)
             return s;
+        API_CUDA(cudaEventRecord(h->ev_done[g & 1], h->side), "rtt_mcmc_sweep: join");
+        if ((s = sweeps(sw, measure_every)) != RTT_OK) return s;
+        sw += measure_every;
     }
-    return sweeps(sw, n_sweeps - n_meas * measure_every, false);
+    if (n_meas > 0)
+        API_CUDA(cudaStreamWaitEvent(st, h->ev_done[(n_meas - 1) & 1], 0), "rtt_mcmc_sweep: join");
+    return sweeps(sw, n_sweeps - n_meas * measure_every);
 }
 
 rtt_status rtt_observables(rtt_handle h, const double *x, int32_t T, int64_t B,

@@ -106,62 +106,22 @@ __device__ void iterate_chain(const BInst &I, int64_t cl, bool active, uint8_t *
     int64_t pe = p.state[cg].exp2;
     int64_t acc_count = 0;
     const int span = (I.R - 1) * N;
-    // ---- one sweep (as k_sweep)
+    // ---- local energy of the configuration entering the sweep (as k_left_env,
+    // k_right_env, k_rows, k_eloc_reduce); the sweep reuses the right environments
     rttd::right_env_chain<float, CHI, GG>(a, s, rst, rex, active, gl);
-    __syncwarp();
-    float l[O::NQ];
-    O::load(I.bl, l, gl);
-    int64_t El = 0;
-    for (int j = 0; j < N; ++j) {
-        const int i = __ldg(I.q + j);
-        const int si = s[i];
-        float u[O::NQ], keep[O::NQ];
-        O::vecmat(rttd::site<float, CHI>(A, j, si ^ 1), l, u, gl);
-        const int64_t Eu0 = El + O::renorm(u);
-        O::vecmat(rttd::site<float, CHI>(A, j, si), l, keep, gl);
-        const int64_t Ek = El + O::renorm(keep);
-        float uf[O::NQ];
-#pragma unroll
-        for (int qq = 0; qq < O::NQ; ++qq) uf[qq] = u[qq];
-        int64_t Eu = Eu0;
-        int t = j + 1 == N ? 0 : j + 1;
-        for (int k = j + 1; k <= j + span; ++k) {
-            const int sp = s[__ldg(I.q + t)] ^ ((t == j) ? 1 : 0);
-            O::vecmat(rttd::site<float, CHI>(A, k, sp), u, u, gl);
-            Eu += O::renorm(u);
-            if (++t == N) t = 0;
-        }
-        float r[O::NQ];
-        O::load(rst + (size_t)j * CHI, r, gl);
-        Eu += rex[j];
-        double m = O::dot(u, r);
-        rttd::normalize_scalar(m, Eu);
-        const double rr = ldexp(m / pm, (int)(Eu - pe));
-        const double x = rttd::mcmc_uniform(I.seed, (uint64_t)cl, (uint64_t)p.sweep, (uint64_t)j);
-        const bool accept = x < rr * rr;
-        if (accept) {
-            pm = m;
-            pe = Eu;
-            ++acc_count;
-#pragma unroll
-            for (int qq = 0; qq < O::NQ; ++qq) l[qq] = uf[qq];
-            El = Eu0;
-        } else {
-#pragma unroll
-            for (int qq = 0; qq < O::NQ; ++qq) l[qq] = keep[qq];
-            El = Ek;
-        }
-        __syncwarp();
-        if (accept && gl == 0) s[i] = (uint8_t)(si ^ 1);
-        __syncwarp();
-        if (active) {
-            O::store(lst + (size_t)j * CHI, l, gl);
-            if (gl == 0) lex[j] = (int32_t)El;
+    {
+        float u[O::NQ];
+        O::load(I.bl, u, gl);
+        int32_t E = 0;
+        for (int j = 0; j < N; ++j) {
+            O::vecmat(rttd::site<float, CHI>(A, j, s[__ldg(I.q + j)]), u, u, gl);
+            E += O::renorm(u);
+            if (active) {
+                O::store(lst + (size_t)j * CHI, u, gl);
+                if (gl == 0) lex[j] = E;
+            }
         }
     }
-    __syncwarp();
-    // ---- local energy of the new state (as k_right_env, k_rows, k_eloc_reduce)
-    rttd::right_env_chain<float, CHI, GG>(a, s, rst, rex, active, gl);
     __syncwarp();
     double m0 = 0.0;
     int64_t e0 = 0;
@@ -214,6 +174,57 @@ __device__ void iterate_chain(const BInst &I, int64_t cl, bool active, uint8_t *
             el = I.J * (double)zz - I.h * sum;
         }
         p.e_loc[cg] = el;
+    }
+    __syncwarp();
+    // ---- one sweep (as k_sweep), from the right environments above
+    float l[O::NQ];
+    O::load(I.bl, l, gl);
+    int64_t El = 0;
+    for (int j = 0; j < N; ++j) {
+        const int i = __ldg(I.q + j);
+        const int si = s[i];
+        float u[O::NQ], keep[O::NQ];
+        O::vecmat(rttd::site<float, CHI>(A, j, si ^ 1), l, u, gl);
+        const int64_t Eu0 = El + O::renorm(u);
+        O::vecmat(rttd::site<float, CHI>(A, j, si), l, keep, gl);
+        const int64_t Ek = El + O::renorm(keep);
+        float uf[O::NQ];
+#pragma unroll
+        for (int qq = 0; qq < O::NQ; ++qq) uf[qq] = u[qq];
+        int64_t Eu = Eu0;
+        int t = j + 1 == N ? 0 : j + 1;
+        for (int k = j + 1; k <= j + span; ++k) {
+            const int sp = s[__ldg(I.q + t)] ^ ((t == j) ? 1 : 0);
+            O::vecmat(rttd::site<float, CHI>(A, k, sp), u, u, gl);
+            Eu += O::renorm(u);
+            if (++t == N) t = 0;
+        }
+        float r[O::NQ];
+        O::load(rst + (size_t)j * CHI, r, gl);
+        Eu += rex[j];
+        double m = O::dot(u, r);
+        rttd::normalize_scalar(m, Eu);
+        const double rr = ldexp(m / pm, (int)(Eu - pe));
+        const double x = rttd::mcmc_uniform(I.seed, (uint64_t)cl, (uint64_t)p.sweep, (uint64_t)j);
+        const bool accept = x < rr * rr;
+        if (accept) {
+            pm = m;
+            pe = Eu;
+            ++acc_count;
+#pragma unroll
+            for (int qq = 0; qq < O::NQ; ++qq) l[qq] = uf[qq];
+            El = Eu0;
+        } else {
+#pragma unroll
+            for (int qq = 0; qq < O::NQ; ++qq) l[qq] = keep[qq];
+            El = Ek;
+        }
+        __syncwarp();
+        if (accept && gl == 0) s[i] = (uint8_t)(si ^ 1);
+        __syncwarp();
+    }
+    __syncwarp();
+    if (active && gl == 0) {
         p.state[cg].mant = pm;
         p.state[cg].exp2 = pe;
         if (p.n_accept) p.n_accept[cg] += acc_count;

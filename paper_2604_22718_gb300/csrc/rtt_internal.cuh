@@ -38,6 +38,19 @@ struct rtt_s {
     int32_t *d_rexp = nullptr;    // [B][N]
     double *d_rows_mant = nullptr;   // [B][N+1]   psi(s^(path[j])) and psi(s) (j = N)
     int64_t *d_rows_exp = nullptr;   // [B][N+1]
+    // the sampler's own environments (the local energy measured beside a
+    // sweep uses the stacks above), and two snapshots of the spins entering
+    // a measured sweep group
+    void *d_sw_lstack = nullptr;  // [B][N][chip]
+    int32_t *d_sw_lexp = nullptr; // [B][N]
+    void *d_sw_rstack = nullptr;  // [B][N][chip]
+    int32_t *d_sw_rexp = nullptr; // [B][N]
+    uint8_t *d_snap[2] = {nullptr, nullptr};  // [B][N] each
+
+    // second stream on which the measured local energy runs beside the
+    // sweeps, and its events (created with the handle)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_done[2] = {nullptr, nullptr};
 
     void *prof = nullptr;         // per-kernel event profiler (rtt_api.cu)
 

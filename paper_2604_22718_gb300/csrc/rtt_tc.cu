@@ -793,25 +793,57 @@ __global__ void __launch_bounds__(NT, 1)
 // is computed as two half-rows at once: the left tile walks sites j..m from
 // l_{j-1} (left to right), the right tile walks (R-1)N+j..m+1 from the cached
 // right environment (right to left); the halves meet in one dot product and
-// the Metropolis decision.  Warps 0-3 run the left epilogue, warps 4-7 the
-// right one (same 128 chains), warp 8 issues the MMAs, warp 9 the TMA loads.
-// Each tile has its own accumulator (TMEM columns [0,128) and [128,256)), A
-// operand and B ring, so one tile's MMA overlaps the other's epilogue and the
-// critical path of a proposal is half a row.  Every wait is bounded; after an
-// expired wait every role walks the rest of its program without issuing work
-// (waits return at once), so the named barriers between the two epilogue
-// groups always meet.
-constexpr int SP_THREADS = 320;
+// the Metropolis decision.  Roles: warps 0-3 left epilogue, 4-7 right
+// epilogue (same 128 chains, row m = TMEM lane m in both), warp 8 issues the
+// left tile's MMAs, warp 9 the right tile's, warp 10 runs the TMA loads.
+// An epilogue hands its A operand to its issuer with a named-barrier arrive.
+// TMEM columns: [0,128) left accumulator, [128,256) right accumulator,
+// [256,384) the accumulator of the first site of each left half-row (kept
+// until the decision, which reads l_j = l_{j-1} A_j[s_j] from it), [384,448)
+// the finished right half-row handed to the left epilogue.  Every mbarrier
+// wait is bounded; after an expired wait every role walks the rest of its
+// program without issuing work (waits return at once), so the named barriers
+// always meet.
+constexpr int SP_THREADS = 352;
+constexpr uint32_t SP_TCOLS = 512;
 
 inline size_t sweep2_smem(int N, int L) {
     return 1024 + 4 * (size_t)Cfg<64>::A_BYTES + 2 * (size_t)NS * Cfg<64>::STAGE + 256 +
-           (size_t)16 * N + (size_t)4 * L;
+           (size_t)16 * N + (size_t)4 * L + 4 * NT;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 __device__ __forceinline__ void named_sync_256() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void named_arrive(int id, int n) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// Store 64 columns of this warp's 32 TMEM lanes and wait for the store.
+__device__ __forceinline__ void tmem_st_64(uint32_t t, const float (&v)[64]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x64.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63, %64};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(t),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31])), "r"(__float_as_uint(v[32])), "r"(__float_as_uint(v[33])), "r"(__float_as_uint(v[34])), "r"(__float_as_uint(v[35])), "r"(__float_as_uint(v[36])), "r"(__float_as_uint(v[37])), "r"(__float_as_uint(v[38])), "r"(__float_as_uint(v[39])), "r"(__float_as_uint(v[40])), "r"(__float_as_uint(v[41])), "r"(__float_as_uint(v[42])), "r"(__float_as_uint(v[43])), "r"(__float_as_uint(v[44])), "r"(__float_as_uint(v[45])), "r"(__float_as_uint(v[46])), "r"(__float_as_uint(v[47])), "r"(__float_as_uint(v[48])), "r"(__float_as_uint(v[49])), "r"(__float_as_uint(v[50])), "r"(__float_as_uint(v[51])), "r"(__float_as_uint(v[52])), "r"(__float_as_uint(v[53])), "r"(__float_as_uint(v[54])), "r"(__float_as_uint(v[55])), "r"(__float_as_uint(v[56])), "r"(__float_as_uint(v[57])), "r"(__float_as_uint(v[58])), "r"(__float_as_uint(v[59])), "r"(__float_as_uint(v[60])), "r"(__float_as_uint(v[61])), "r"(__float_as_uint(v[62])), "r"(__float_as_uint(v[63]))
+        : "memory");
+}
+// sum_b v_b w_b with w read from 64 TMEM columns: eight FP32 partial sums
+// (fma), combined in FP64.
+__device__ __forceinline__ double dot_tmem64(const float (&v)[64], uint32_t t) {
+    uint32_t x[32], y[32];
+    tmem_ld_2x32(t, t + 32u, x, y);
+    float acc[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) acc[p] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i & 7] = fmaf(v[i], __uint_as_float(x[i]), acc[i & 7]);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i & 7] = fmaf(v[32 + i], __uint_as_float(y[i]), acc[i & 7]);
+    double s = 0.0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) s += (double)acc[p];
+    return s;
+}
 
 template <bool F16>
 __global__ void __launch_bounds__(SP_THREADS, 1)
@@ -825,34 +857,30 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
     const uint32_t ring0 = AR_lo + C::A_BYTES;  // ring L: stages 0,1; ring R: stages 2,3
     uint64_t *bars = (uint64_t *)(base + 4 * C::A_BYTES + 2 * NS * C::STAGE);
     const uint32_t bar0 = sa(bars);
-    // bars: full[4] (L0 L1 R0 R1), empty[4], done[2] (L R), ready[2] (L R)
+    // bars: full[4] (L0 L1 R0 R1), empty[4], done[2] (L R)
     auto full_bar = [&](int X, int s) { return bar0 + 8u * (X * NS + s); };
     auto empty_bar = [&](int X, int s) { return bar0 + 8u * (4 + X * NS + s); };
     auto done_bar = [&](int X) { return bar0 + 8u * (8 + X); };
-    auto ready_bar = [&](int X) { return bar0 + 8u * (10 + X); };
     uint32_t *tmem_slot = (uint32_t *)(bars + 12);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     long long *issued = (long long *)(bars + 14);  // loads issued per tile
     uint32_t *bits = (uint32_t *)(base + 4 * C::A_BYTES + 2 * NS * C::STAGE + 256);
     uint32_t *tab = bits + 4 * a.N;
+    int32_t *rexp_s = (int32_t *)(tab + a.L);  // exponent of the handed-over right half-row
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = a.N, L = a.L;
     const int span = (a.R - 1) * N + 1;
-    const int nL = (span + 1) / 2, nR = span - nL;
+    const int nL = span / 2, nR = span - nL;
     const int rbase = (a.R - 1) * N + 1;
     const int m = tid & 127;  // row of the epilogue threads
     const int64_t c_raw = (int64_t)blockIdx.x * NT + m;
     const bool active = c_raw < a.B;
     const int64_t c = active ? c_raw : a.B - 1;
 
-    if (warp == 0) tmem_alloc(sa(tmem_slot), 256);
+    if (warp == 0) tmem_alloc(sa(tmem_slot), SP_TCOLS);
     if (tid == 0) {
-        for (int i = 0; i < 8; ++i) mbar_init(bar0 + 8u * i, 1);
-        mbar_init(done_bar(0), 1);
-        mbar_init(done_bar(1), 1);
-        mbar_init(ready_bar(0), 128);
-        mbar_init(ready_bar(1), 128);
+        for (int i = 0; i < 10; ++i) mbar_init(bar0 + 8u * i, 1);
         *abort_flag = 0;
         issued[0] = issued[1] = 0;
         fence_barrier_init();
@@ -880,41 +908,52 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         }
         return true;
     };
+    // epilogue of tile X: its A operand is written; hand it to the issuer
+    auto publish = [&](int X) {
+        fence_async_smem();
+        tc_before();
+        named_arrive(2 + X, NT + 32);
+    };
 
-    if (warp == 8) {
+    if (warp == 8 || warp == 9) {
         // ---------------------------------------------------------- MMA issuers
-        // lane 0 issues the left tile's MMAs, lane 1 the right tile's, so a
-        // half-row never waits behind the other tile's epilogue
-        if (lane < 2) {
-            const int XX = lane;
-            long long n[2] = {0, 0};
-            auto issue = [&](int X) {
-                const long long g = n[X]++;
+        const int X = warp - 8;
+        long long g = 0;
+        auto issue = [&](uint32_t dcol) {
+            named_sync(2 + X, NT + 32);  // the A operand is in shared memory
+            if (lane == 0) {
                 const int s = (int)(g % NS);
-                if (!bwait(full_bar(X, s), (uint32_t)((g / NS) & 1))) return;
-                if (!bwait(ready_bar(X), (uint32_t)(g & 1))) return;
-                tc_after();
-                const uint32_t ahi = X ? AR_hi : AL_hi, alo = X ? AR_lo : AL_lo;
-                const uint32_t b_hi = ring0 + (uint32_t)(X * NS + s) * C::STAGE, b_lo = b_hi + C::BOX;
-                const uint32_t d = tmem + (uint32_t)(X * 128);
+                if (bwait(full_bar(X, s), (uint32_t)((g / NS) & 1))) {
+                    tc_after();
+                    const uint32_t ahi = X ? AR_hi : AL_hi, alo = X ? AR_lo : AL_lo;
+                    const uint32_t b_hi = ring0 + (uint32_t)(X * NS + s) * C::STAGE;
+                    const uint32_t b_lo = b_hi + C::BOX;
+                    const uint32_t d = tmem + dcol;
 #pragma unroll
-                for (int kb = 0; kb < 4; ++kb) {
-                    const uint32_t o = (uint32_t)(kb * 32);
-                    mma_bf16(d, sdesc(ahi + o), sdesc(b_hi + o), C::IDESC, kb != 0 ? 1u : 0u);
-                    mma_bf16(d, sdesc(ahi + o), sdesc(b_lo + o), C::IDESC, 1u);
-                    mma_bf16(d, sdesc(alo + o), sdesc(b_hi + o), C::IDESC, 1u);
+                    for (int kb = 0; kb < 4; ++kb) {
+                        const uint32_t o = (uint32_t)(kb * 32);
+                        mma_bf16(d, sdesc(ahi + o), sdesc(b_hi + o), C::IDESC, kb != 0 ? 1u : 0u);
+                        mma_bf16(d, sdesc(ahi + o), sdesc(b_lo + o), C::IDESC, 1u);
+                        mma_bf16(d, sdesc(alo + o), sdesc(b_hi + o), C::IDESC, 1u);
+                    }
+                    mma_commit(empty_bar(X, s));
+                    mma_commit(done_bar(X));
                 }
-                mma_commit(empty_bar(X, s));
-                mma_commit(done_bar(X));
-            };
-            for (int sw = 0; sw < a.n_sweeps; ++sw) {
-                if (XX == 1)
-                    for (int u = 0; u < N - 1; ++u) issue(1);
+            }
+            ++g;
+            __syncwarp();
+        };
+        for (int sw = 0; sw < a.n_sweeps; ++sw) {
+            if (X == 1) {
+                for (int u = 0; u < N - 1; ++u) issue(128u);
                 for (int j = 0; j < N; ++j)
-                    for (int t = 0; t < (XX == 0 ? nL : nR); ++t) issue(XX);
+                    for (int t = 0; t < nR; ++t) issue(128u);
+            } else {
+                for (int j = 0; j < N; ++j)
+                    for (int t = 0; t < nL; ++t) issue(t == 0 ? 256u : 0u);
             }
         }
-    } else if (warp == 9) {
+    } else if (warp == 10) {
         // ---------------------------------------------------------- TMA loaders
         // lane 0 feeds the left ring, lane 1 the right ring
         if (lane < 2) {
@@ -946,87 +985,73 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         }
     } else if (warp < 4) {
         // ---------------------------------------------------------- left epilogue
-        const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t tq = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t tw = tq, tw0 = tq + 256u, twh = tq + 384u;
         float v[CHI];
         load_vec<CHI>(a.bl, v);
         write_A<CHI, F16>(AL_hi, AL_lo, m, v);
-        fence_async_smem();
-        tc_before();
-        mbar_arrive(ready_bar(0));
+        publish(0);
         double pm = a.state[c].mant;
         int64_t pe = a.state[c].exp2, acc_count = 0;
-        int64_t El = 0, E = 0, Ekeep = 0, Eflip = 0;
+        int64_t El = 0, E = 0;
         long long nd = 0;
         for (int sw = 0; sw < a.n_sweeps; ++sw) {
             for (int j = 0; j < N; ++j) {
                 const int iq = site_spin(j);
+                const int si = spin(iq);
+                double x = 0.0;
                 for (int t = 0; t < nL; ++t) {
                     const int k = j + t;
                     bwait(done_bar(0), (uint32_t)(nd++ & 1));
                     tc_after();
                     __syncwarp();
-                    const int sk = site_spin(k), ck = site_cexp(k);
+                    const int sk = site_spin(k);
                     if (t == 0) {
-                        const int si = spin(iq);
-                        acc_select<CHI>(tw, si, v);
-                        Ekeep = El + renorm<CHI>(v) - ck;
-                        if (active) {
-                            store_vec<CHI>(a.lstack + ((size_t)c * N + j) * CHI, v);
-                            a.lexp[(size_t)c * N + j] = (int32_t)Ekeep;
-                        }
-                        acc_select<CHI>(tw, si ^ 1, v);
-                        Eflip = El + renorm<CHI>(v) - ck;
-                        if (active) {
-                            store_vec<CHI>(a.tmp + (size_t)c * CHI, v);
-                            a.tmp_exp[c] = (int32_t)Eflip;
-                        }
-                        E = Eflip;
+                        acc_select<CHI>(tw0, si ^ 1, v);
+                        E = El + renorm<CHI>(v) - site_cexp(k);
                     } else {
                         acc_select<CHI>(tw, spin(sk) ^ (sk == iq ? 1 : 0), v);
-                        E += renorm<CHI>(v) - ck;
+                        E += renorm<CHI>(v) - site_cexp(k);
                     }
                     if (t + 1 < nL) {
                         write_A<CHI, F16>(AL_hi, AL_lo, m, v);
-                        fence_async_smem();
-                        tc_before();
-                        mbar_arrive(ready_bar(0));
+                        publish(0);
                     }
+                    // the uniform is drawn while the next MMA runs
+                    if (t == 0)
+                        x = rttd::mcmc_uniform(a.seed, (uint64_t)(a.chain0 + c),
+                                               (uint64_t)(a.sweep0 + sw), (uint64_t)j);
                 }
-                named_sync_256();  // the right half-row is published
-                const float *vr = a.tmp + ((size_t)a.B + c) * CHI;
-                int64_t Ep = E + a.tmp_exp[a.B + c];
-                double mm = dot<CHI>(v, vr);
+                named_sync_256();  // the right half-row is in TMEM
+                tc_after();
+                double mm = dot_tmem64(v, twh);
+                int64_t Ep = E + rexp_s[m];
                 normalize_scalar(mm, Ep);
                 const double ratio = ldexp(mm / pm, (int)(Ep - pe));
-                const double x = rttd::mcmc_uniform(a.seed, (uint64_t)(a.chain0 + c),
-                                                    (uint64_t)(a.sweep0 + sw), (uint64_t)j);
                 const bool accept = active && !*abort_flag && (x < ratio * ratio);
                 if (accept) {
                     pm = mm;
                     pe = Ep;
                     ++acc_count;
-                    load_vec<CHI>(a.tmp + (size_t)c * CHI, v);
-                    store_vec<CHI>(a.lstack + ((size_t)c * N + j) * CHI, v);
-                    a.lexp[(size_t)c * N + j] = (int32_t)Eflip;
-                    El = Eflip;
-                } else {
-                    El = Ekeep;
                 }
                 const uint32_t flips = __ballot_sync(FULL, accept);
                 if (lane == 0) bits[iq * 4 + warp] ^= flips;
+                tc_before();
                 named_sync_256();  // the decision is published
+                tc_after();
+                // l_j = l_{j-1} A_j[s_j] with the decided spin, from the kept accumulator
+                acc_select<CHI>(tw0, si ^ (accept ? 1 : 0), v);
+                El += renorm<CHI>(v) - site_cexp(j);
                 const bool more = (j + 1 < N) || (sw + 1 < a.n_sweeps);
-                if (more) {
-                    if (j + 1 < N) {
-                        load_vec<CHI>(a.lstack + ((size_t)c * N + j) * CHI, v);
-                    } else {
-                        load_vec<CHI>(a.bl, v);
-                        El = 0;
-                    }
+                if (j + 1 < N) {
                     write_A<CHI, F16>(AL_hi, AL_lo, m, v);
-                    fence_async_smem();
-                    tc_before();
-                    mbar_arrive(ready_bar(0));
+                    publish(0);
+                }
+                if (j + 1 == N && more) {
+                    load_vec<CHI>(a.bl, v);
+                    El = 0;
+                    write_A<CHI, F16>(AL_hi, AL_lo, m, v);
+                    publish(0);
                 }
             }
         }
@@ -1037,7 +1062,8 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         }
     } else {
         // ---------------------------------------------------------- right epilogue
-        const uint32_t tw = tmem + ((uint32_t)((warp & 3) * 32) << 16) + 128u;
+        const uint32_t tq = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        const uint32_t tw = tq + 128u, twh = tq + 384u;
         float v[CHI];
         load_vec<CHI>(a.br, v);
         if (active) {
@@ -1045,9 +1071,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
             a.rexp[(size_t)c * N + (N - 1)] = 0;
         }
         write_A<CHI, F16>(AR_hi, AR_lo, m, v);
-        fence_async_smem();
-        tc_before();
-        mbar_arrive(ready_bar(1));
+        publish(1);
         int64_t E = 0;
         long long nd = 0;
         for (int sw = 0; sw < a.n_sweeps; ++sw) {
@@ -1066,9 +1090,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                 // next: the next environment step, or (u = N-2) the first right
                 // half-row, which starts from this very vector r_{(R-1)N+1}
                 write_A<CHI, F16>(AR_hi, AR_lo, m, v);
-                fence_async_smem();
-                tc_before();
-                mbar_arrive(ready_bar(1));
+                publish(1);
             }
             for (int j = 0; j < N; ++j) {
                 const int iq = site_spin(j);
@@ -1083,15 +1105,13 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                     E += renorm<CHI>(v) - site_cexp(k);
                     if (t + 1 < nR) {
                         write_A<CHI, F16>(AR_hi, AR_lo, m, v);
-                        fence_async_smem();
-                        tc_before();
-                        mbar_arrive(ready_bar(1));
+                        publish(1);
                     }
                 }
-                if (active) {
-                    store_vec<CHI>(a.tmp + ((size_t)a.B + c) * CHI, v);
-                    a.tmp_exp[a.B + c] = (int32_t)E;
-                }
+                // hand the half-row to the left epilogue (same TMEM lane)
+                tmem_st_64(twh, v);
+                rexp_s[m] = (int32_t)E;
+                tc_before();
                 // the next half-row's start does not depend on this decision
                 const bool more = (j + 1 < N) || (sw + 1 < a.n_sweeps);
                 if (more) {
@@ -1101,9 +1121,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                         load_vec<CHI>(a.br, v);
                     }
                     write_A<CHI, F16>(AR_hi, AR_lo, m, v);
-                    fence_async_smem();
-                    tc_before();
-                    mbar_arrive(ready_bar(1));
+                    publish(1);
                 }
                 named_sync_256();  // publish the right half-row
                 named_sync_256();  // wait for the decision
@@ -1123,7 +1141,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
     tc_before();
     __syncthreads();
     tc_after();
-    if (warp == 0) tmem_dealloc(tmem, 256);
+    if (warp == 0) tmem_dealloc(tmem, SP_TCOLS);
 }
 
 }  // namespace tcd
@@ -1366,6 +1384,10 @@ rtt_status tc_sweep(rtt_s *h, uint8_t *spins, rtt_chain_state *state, int64_t B,
         p->tmp_cap = B;
     }
     tcd::Args a = make_args(h, B);
+    a.lstack = (float *)h->d_sw_lstack;
+    a.lexp = h->d_sw_lexp;
+    a.rstack = (float *)h->d_sw_rstack;
+    a.rexp = h->d_sw_rexp;
     a.spins_in = spins;
     a.spins_out = spins;
     a.state = state;

@@ -97,8 +97,9 @@ def test_batch_sampled_chains_against_oracle():
         o = orc.Oracle(inst)
         co, so, N = int(b.chain_off[i]), int(b.spin_off[i]), inst.n_spins
         pick = [0, chains[i] - 1]
-        s_now = sp[so:so + chains[i] * N].reshape(chains[i], N)[pick]
-        e_o = o.local_energies(s_now, threads=2)
+        # the step measures the configuration it starts from
+        s_in = spins0[so:so + chains[i] * N].reshape(chains[i], N)[pick]
+        e_o = o.local_energies(s_in, threads=2)
         scale = inst.bonds.shape[0] + inst.h * N
         assert np.all(np.abs(e[co + np.array(pick)] - e_o) <= 1e-4 * scale), (i, e[co + np.array(pick)], e_o)
 

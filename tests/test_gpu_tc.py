@@ -190,12 +190,18 @@ def test_split_measured_trace_equals_standalone_energy(prec):
     with rtt.RTT(inst, prec, seed=3) as m:
         sg = torch.from_numpy(inputs.initial_spins(45, B, 20)).cuda()
         _, _, st = m.log_amplitudes(sg)
+        e0 = m.local_energy(sg)
         tr = torch.empty((2, B), dtype=torch.float64, device="cuda")
-        m.mcmc_sweep(sg, st, 0, 2, 1, tr)
-        e = m.local_energy(sg)
+        m.mcmc_sweep(sg, st, 0, 2, 1, tr)      # measures the states entering sweeps 0 and 1
+        e2 = m.local_energy(sg)
+        tr2 = torch.empty((1, B), dtype=torch.float64, device="cuda")
+        m.mcmc_sweep(sg, st, 2, 1, 1, tr2)
         torch.cuda.synchronize()
         assert _status_ok(m)
-    np.testing.assert_allclose(tr[1].cpu().numpy(), e.cpu().numpy(), rtol=1e-6, atol=1e-6)
+    # the measurement beside the sweep runs the standalone kernels on a snapshot
+    assert np.array_equal(tr[0].cpu().numpy(), e0.cpu().numpy())
+    assert np.array_equal(tr2[0].cpu().numpy(), e2.cpu().numpy())
+    assert not np.array_equal(tr[1].cpu().numpy(), tr[0].cpu().numpy())
 
 
 @pytest.mark.parametrize("prec", PRECS)
