@@ -1,10 +1,12 @@
 #!/usr/bin/env python
 """Benchmark of the RTT Monte Carlo hot path on GB300.
 
-One *step* is one Monte Carlo iteration of every chain of the workload: one
-systematic single-spin Metropolis sweep followed by one local-energy
-evaluation (Sec. 3.3; TFIM of Sec. 4), i.e. one local-energy sample per
-chain.  Default workload: 6x6 open TFIM (N = 36, h = 3.0), R = 2 (L = 72),
+One *step* is one Monte Carlo iteration of every chain of the workload: the
+local energy of the configuration the iteration starts from and one
+systematic single-spin Metropolis sweep (Sec. 3.3; TFIM of Sec. 4), i.e. one
+local-energy sample per chain.  The library runs the energy on a second
+stream beside the sweep (the sweep of a 4096-chain batch fills 32 of the 152
+SMs).  Default workload: 6x6 open TFIM (N = 36, h = 3.0), R = 2 (L = 72),
 chi = 64, 4096 chains; synthetic seeded tensors.
 
 value        local-energy samples/s = chains x steps / summed device step time
@@ -13,7 +15,10 @@ e2e          the same through host buffers: every step copies the chains'
              copies E_loc, spins and amplitudes back (all inside the timing)
 roofline     dominant kernel: algorithmic flops per launch / its mean launch
              time (library event profiler on the launching stream) against
-             the FP32 (or FP64) CUDA-core peak, or the measured bf16 tensor peak
+             the FP32 (or FP64) CUDA-core peak, or the measured bf16 tensor peak;
+             step_* : the flops of every kernel of a step / the step time
+             (kernels of one step overlap, so per-kernel times add up to more
+             than the step)
 cpu_baseline the FP64 oracle on this host's cores, bounded sample
 
 --impl reference runs the FP64 CPU oracle as the reference arm.
@@ -118,6 +123,17 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- DRAM traffic
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from an ncu capture
+# of the same command on this kernel build (profiles/ names the capture); None
+# where no capture of the current kernel exists.
+MEASURED_TRAFFIC = {}
+
+
+def measured_traffic(args, kernel, B):
+    return MEASURED_TRAFFIC.get((args.workload, args.precision, kernel, B))
 
 
 # ---------------------------------------------------------------- algorithmic work
@@ -297,13 +313,19 @@ def run_ours(args):
             peak = SM_COUNT * lanes * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             bound, pk = "alu", (f"{args.precision} CUDA-core fma peak: {SM_COUNT} SMs x {lanes} "
                                 f"lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz")
-        executed = achieved * (6.0 if bound == "tensor" else 1.0)
+        mult = 6.0 if bound == "tensor" else 1.0
+        executed = achieved * mult
+        step_flops = sum(2.0 * inst.chi * inst.chi * site_steps(N, R, k) * B * v[0]
+                         for k, v in prof.items()) / K
+        step_tf = step_flops / (total_ms / K / 1e3) / 1e12
         roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "frac": achieved / peak, "traffic": measured_traffic(args, dom, B), "kernel": dom,
                 "executed_tflops": executed, "executed_frac": executed / peak,
                 "peak_source": pk, "flops_per_launch": flops,
                 "launch_ms": ms / launches,
-                "kernel_share": ms / sum(v[1] for v in prof.values())}
+                "kernel_share": ms / sum(v[1] for v in prof.values()),
+                "step_tflops": step_tf, "step_frac": step_tf / peak,
+                "step_executed_frac": step_tf * mult / peak}
     launches_total = sum(v[0] for v in prof.values())
 
     # end to end through host buffers

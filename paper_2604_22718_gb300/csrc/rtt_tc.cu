@@ -62,6 +62,8 @@ struct Cfg {
     static constexpr int BOX = 2 * CHI * 128;      // bytes: 2chi rows x 128 B
     static constexpr int STAGE = 2 * BOX;          // hi box + lo box
     static constexpr int TCOLS = 2 * CHI;          // accumulator columns
+    static constexpr int A_COL = 2 * CHI;          // row hi at A_COL, lo at A_COL + CHI/2
+    static constexpr int TALLOC = 3 * CHI <= 256 ? 256 : 512;  // columns allocated
     // kind::f16, (BF16 or FP16) x same -> FP32, both K-major, N = 2chi, M = 128
     static constexpr uint32_t FMT = F16 ? 0u : 1u;
     static constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) |
@@ -69,8 +71,7 @@ struct Cfg {
                                       ((uint32_t)(128 >> 4) << 24);
     static constexpr int CTRL = 128;
     static size_t smem_bytes(int N, int L) {
-        return 1024 + 2 * (size_t)A_BYTES + (size_t)NS * STAGE + CTRL + (size_t)16 * N +
-               (size_t)4 * L;
+        return 1024 + (size_t)NS * STAGE + CTRL + (size_t)16 * N + (size_t)4 * L;
     }
 };
 
@@ -386,6 +387,39 @@ __device__ __forceinline__ void normalize_scalar(double &m, int64_t &e) {
     e += k;
 }
 
+// Store 32 columns at t0 and 32 at t1 of this warp's 32 TMEM lanes, then wait.
+__device__ __forceinline__ void tmem_st_2x32(uint32_t t0, uint32_t t1, const uint32_t (&x)[32],
+                                             const uint32_t (&y)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%1], {%34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63, %64, %65};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(t0), "r"(t1), "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(x[7]), "r"(x[8]), "r"(x[9]), "r"(x[10]), "r"(x[11]), "r"(x[12]), "r"(x[13]), "r"(x[14]), "r"(x[15]), "r"(x[16]), "r"(x[17]), "r"(x[18]), "r"(x[19]), "r"(x[20]), "r"(x[21]), "r"(x[22]), "r"(x[23]), "r"(x[24]), "r"(x[25]), "r"(x[26]), "r"(x[27]), "r"(x[28]), "r"(x[29]), "r"(x[30]), "r"(x[31]), "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]), "r"(y[4]), "r"(y[5]), "r"(y[6]), "r"(y[7]), "r"(y[8]), "r"(y[9]), "r"(y[10]), "r"(y[11]), "r"(y[12]), "r"(y[13]), "r"(y[14]), "r"(y[15]), "r"(y[16]), "r"(y[17]), "r"(y[18]), "r"(y[19]), "r"(y[20]), "r"(y[21]), "r"(y[22]), "r"(y[23]), "r"(y[24]), "r"(y[25]), "r"(y[26]), "r"(y[27]), "r"(y[28]), "r"(y[29]), "r"(y[30]), "r"(y[31])
+        : "memory");
+}
+// Row m of the A operand in TMEM: the 16-bit hi/lo split of v, entries 2c and
+// 2c+1 in column c (lower index in the low half), hi at t_hi, lo at
+// t_hi + CHI/2.
+template <int CHI, bool F16>
+__device__ __forceinline__ void write_A_tmem(uint32_t t_hi, const float (&v)[CHI]) {
+#pragma unroll
+    for (int c0 = 0; c0 < CHI; c0 += 64) {
+        uint32_t h[32], l[32];
+#pragma unroll
+        for (int p = 0; p < 32; ++p) split2<F16>(v[c0 + 2 * p], v[c0 + 2 * p + 1], h[p], l[p]);
+        tmem_st_2x32(t_hi + (uint32_t)(c0 / 2), t_hi + (uint32_t)(CHI / 2 + c0 / 2), h, l);
+    }
+}
+// D (+)= A . B with A read from TMEM (K-major rows in TMEM lanes) and B from a
+// shared-memory descriptor.
+__device__ __forceinline__ void mma_f16_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                           uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
 // ------------------------------------------------------------------ site program
 // A cursor walks the sites a CTA visits, in order, without divisions:
 //   ROWS   k = j, j+1, ...            (left to right)
@@ -468,9 +502,8 @@ __global__ void __launch_bounds__(NT, 1)
     using C = Cfg<CHI, F16>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const uint32_t A_hi = sa(base), A_lo = A_hi + C::A_BYTES;
-    const uint32_t stage0 = A_lo + C::A_BYTES;
-    uint64_t *bars = (uint64_t *)(base + 2 * C::A_BYTES + NS * C::STAGE);
+    const uint32_t stage0 = sa(base);
+    uint64_t *bars = (uint64_t *)(base + NS * C::STAGE);
     const uint32_t bar0 = sa(bars);
     // bars: full[0..NS), empty[0..NS), mma_done
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
@@ -478,7 +511,7 @@ __global__ void __launch_bounds__(NT, 1)
     const uint32_t done_bar = bar0 + 8u * (2 * NS);
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NS + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
-    uint32_t *bits = (uint32_t *)(base + 2 * C::A_BYTES + NS * C::STAGE + C::CTRL);
+    uint32_t *bits = (uint32_t *)(base + NS * C::STAGE + C::CTRL);
     // site table: low 16 bits spin q[k mod N], high 16 bits the prescale c_k
     uint32_t *tab = bits + 4 * a.N;
 
@@ -493,7 +526,7 @@ __global__ void __launch_bounds__(NT, 1)
     const long long total_steps = n_steps_of<MODE>(a, j);
     const long long total_atoms = total_steps * C::KA;
 
-    if (warp == 0) tmem_alloc(sa(tmem_slot), C::TCOLS);
+    if (warp == 0) tmem_alloc(sa(tmem_slot), C::TALLOC);
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(full_bar(s), 1);
@@ -544,14 +577,16 @@ __global__ void __launch_bounds__(NT, 1)
     } else {
         load_vec<CHI>(a.bl, v);
     }
-    __syncthreads();
-    if (total_steps > 0) write_A<CHI, F16>(A_hi, A_lo, tid, v);
-    fence_async_smem();
     tc_before();
     __syncthreads();
     tc_after();
     const uint32_t tmem = *tmem_slot;
     const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's lanes
+    const uint32_t ta = tw + (uint32_t)C::A_COL;                // this warp's rows of A
+    if (total_steps > 0) write_A_tmem<CHI, F16>(ta, v);
+    tc_before();
+    __syncthreads();
+    tc_after();
 
     // producer (thread 0): cursor over atoms; atom g = step * KA + at
     long long g_issued = 0, g_waited = 0;
@@ -593,14 +628,14 @@ __global__ void __launch_bounds__(NT, 1)
                 g_waited = g + 1;
                 tc_after();
                 const uint32_t b_hi = stage0 + (uint32_t)st * C::STAGE, b_lo = b_hi + C::BOX;
+                const uint32_t a_hi = tmem + (uint32_t)C::A_COL, a_lo = a_hi + (uint32_t)(CHI / 2);
 #pragma unroll
                 for (int kb = 0; kb < 4; ++kb) {
-                    const uint32_t ao = (uint32_t)(at * C::A_ATOM + kb * 32);
+                    const uint32_t ao = (uint32_t)(at * 32 + kb * 8);
                     const uint32_t bo = (uint32_t)(kb * 32);
-                    mma_bf16(tmem, sdesc(A_hi + ao), sdesc(b_hi + bo), C::IDESC,
-                             (at | kb) != 0 ? 1u : 0u);
-                    mma_bf16(tmem, sdesc(A_hi + ao), sdesc(b_lo + bo), C::IDESC, 1u);
-                    mma_bf16(tmem, sdesc(A_lo + ao), sdesc(b_hi + bo), C::IDESC, 1u);
+                    mma_f16_ts(tmem, a_hi + ao, sdesc(b_hi + bo), C::IDESC, (at | kb) != 0 ? 1u : 0u);
+                    mma_f16_ts(tmem, a_hi + ao, sdesc(b_lo + bo), C::IDESC, 1u);
+                    mma_f16_ts(tmem, a_lo + ao, sdesc(b_hi + bo), C::IDESC, 1u);
                 }
                 mma_commit(empty_bar(st));
             }
@@ -732,9 +767,8 @@ __global__ void __launch_bounds__(NT, 1)
                 }
             }
         }
-        if (write_next) write_A<CHI, F16>(A_hi, A_lo, tid, v);
+        if (write_next) write_A_tmem<CHI, F16>(ta, v);
         cursor_next<MODE>(cc, a, span);
-        fence_async_smem();
         tc_before();
         __syncthreads();
         tc_after();
@@ -785,7 +819,7 @@ __global__ void __launch_bounds__(NT, 1)
     tc_before();
     __syncthreads();
     tc_after();
-    if (warp == 0) tmem_dealloc(tmem, C::TCOLS);
+    if (warp == 0) tmem_dealloc(tmem, C::TALLOC);
 }
 
 // ------------------------------------------------------------------ split-row sweep (chi = 64)
@@ -796,20 +830,26 @@ __global__ void __launch_bounds__(NT, 1)
 // the Metropolis decision.  Roles: warps 0-3 left epilogue, 4-7 right
 // epilogue (same 128 chains, row m = TMEM lane m in both), warp 8 issues the
 // left tile's MMAs, warp 9 the right tile's, warp 10 runs the TMA loads.
-// An epilogue hands its A operand to its issuer with a named-barrier arrive.
+// The rows (A operands) live in TMEM: an epilogue stores its row's 16-bit
+// hi/lo split with tcgen05.st and hands it to its issuer with a named-barrier
+// arrive; the MMAs read A from TMEM and B from shared memory.
 // TMEM columns: [0,128) left accumulator, [128,256) right accumulator,
 // [256,384) the accumulator of the first site of each left half-row (kept
-// until the decision, which reads l_j = l_{j-1} A_j[s_j] from it), [384,448)
-// the finished right half-row handed to the left epilogue.  Every mbarrier
+// until the decision, which reads l_j = l_{j-1} A_j[s_j] from it), [384,416)
+// and [416,448) left A hi / lo (two 16-bit entries per column), [448,512)
+// right A hi / lo.  The finished right half-row reaches the left epilogue
+// through shared memory.  Every mbarrier
 // wait is bounded; after an expired wait every role walks the rest of its
 // program without issuing work (waits return at once), so the named barriers
 // always meet.
 constexpr int SP_THREADS = 352;
 constexpr uint32_t SP_TCOLS = 512;
 
+constexpr int SP_HAND = 64 * NT * 4;  // right half-rows, [64][128] floats
+
 inline size_t sweep2_smem(int N, int L) {
-    return 1024 + 4 * (size_t)Cfg<64>::A_BYTES + 2 * (size_t)NS * Cfg<64>::STAGE + 256 +
-           (size_t)16 * N + (size_t)4 * L + 4 * NT;
+    return 1024 + 2 * (size_t)NS * Cfg<64>::STAGE + SP_HAND + 256 + (size_t)16 * N +
+           (size_t)4 * L + 4 * NT;
 }
 
 __device__ __forceinline__ void named_sync_256() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
@@ -819,32 +859,6 @@ __device__ __forceinline__ void named_arrive(int id, int n) {
 __device__ __forceinline__ void named_sync(int id, int n) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
-// Store 64 columns of this warp's 32 TMEM lanes and wait for the store.
-__device__ __forceinline__ void tmem_st_64(uint32_t t, const float (&v)[64]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x64.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63, %64};\n\t"
-        "tcgen05.wait::st.sync.aligned;" ::"r"(t),
-        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31])), "r"(__float_as_uint(v[32])), "r"(__float_as_uint(v[33])), "r"(__float_as_uint(v[34])), "r"(__float_as_uint(v[35])), "r"(__float_as_uint(v[36])), "r"(__float_as_uint(v[37])), "r"(__float_as_uint(v[38])), "r"(__float_as_uint(v[39])), "r"(__float_as_uint(v[40])), "r"(__float_as_uint(v[41])), "r"(__float_as_uint(v[42])), "r"(__float_as_uint(v[43])), "r"(__float_as_uint(v[44])), "r"(__float_as_uint(v[45])), "r"(__float_as_uint(v[46])), "r"(__float_as_uint(v[47])), "r"(__float_as_uint(v[48])), "r"(__float_as_uint(v[49])), "r"(__float_as_uint(v[50])), "r"(__float_as_uint(v[51])), "r"(__float_as_uint(v[52])), "r"(__float_as_uint(v[53])), "r"(__float_as_uint(v[54])), "r"(__float_as_uint(v[55])), "r"(__float_as_uint(v[56])), "r"(__float_as_uint(v[57])), "r"(__float_as_uint(v[58])), "r"(__float_as_uint(v[59])), "r"(__float_as_uint(v[60])), "r"(__float_as_uint(v[61])), "r"(__float_as_uint(v[62])), "r"(__float_as_uint(v[63]))
-        : "memory");
-}
-// sum_b v_b w_b with w read from 64 TMEM columns: eight FP32 partial sums
-// (fma), combined in FP64.
-__device__ __forceinline__ double dot_tmem64(const float (&v)[64], uint32_t t) {
-    uint32_t x[32], y[32];
-    tmem_ld_2x32(t, t + 32u, x, y);
-    float acc[8];
-#pragma unroll
-    for (int p = 0; p < 8; ++p) acc[p] = 0.f;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) acc[i & 7] = fmaf(v[i], __uint_as_float(x[i]), acc[i & 7]);
-#pragma unroll
-    for (int i = 0; i < 32; ++i) acc[i & 7] = fmaf(v[32 + i], __uint_as_float(y[i]), acc[i & 7]);
-    double s = 0.0;
-#pragma unroll
-    for (int p = 0; p < 8; ++p) s += (double)acc[p];
-    return s;
-}
-
 template <bool F16>
 __global__ void __launch_bounds__(SP_THREADS, 1)
     k_tc_sweep2(const __grid_constant__ CUtensorMap map, const Args a) {
@@ -852,10 +866,9 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
     using C = Cfg<CHI, F16>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const uint32_t AL_hi = sa(base), AL_lo = AL_hi + C::A_BYTES;
-    const uint32_t AR_hi = AL_lo + C::A_BYTES, AR_lo = AR_hi + C::A_BYTES;
-    const uint32_t ring0 = AR_lo + C::A_BYTES;  // ring L: stages 0,1; ring R: stages 2,3
-    uint64_t *bars = (uint64_t *)(base + 4 * C::A_BYTES + 2 * NS * C::STAGE);
+    const uint32_t ring0 = sa(base);  // ring L: stages 0,1; ring R: stages 2,3
+    float *hand = (float *)(base + 2 * NS * C::STAGE);  // [64][128] right half-rows
+    uint64_t *bars = (uint64_t *)(base + 2 * NS * C::STAGE + SP_HAND);
     const uint32_t bar0 = sa(bars);
     // bars: full[4] (L0 L1 R0 R1), empty[4], done[2] (L R)
     auto full_bar = [&](int X, int s) { return bar0 + 8u * (X * NS + s); };
@@ -864,7 +877,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
     uint32_t *tmem_slot = (uint32_t *)(bars + 12);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     long long *issued = (long long *)(bars + 14);  // loads issued per tile
-    uint32_t *bits = (uint32_t *)(base + 4 * C::A_BYTES + 2 * NS * C::STAGE + 256);
+    uint32_t *bits = (uint32_t *)(base + 2 * NS * C::STAGE + SP_HAND + 256);
     uint32_t *tab = bits + 4 * a.N;
     int32_t *rexp_s = (int32_t *)(tab + a.L);  // exponent of the handed-over right half-row
 
@@ -908,9 +921,8 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         }
         return true;
     };
-    // epilogue of tile X: its A operand is written; hand it to the issuer
+    // epilogue of tile X: its A operand is stored in TMEM; hand it to the issuer
     auto publish = [&](int X) {
-        fence_async_smem();
         tc_before();
         named_arrive(2 + X, NT + 32);
     };
@@ -925,16 +937,16 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                 const int s = (int)(g % NS);
                 if (bwait(full_bar(X, s), (uint32_t)((g / NS) & 1))) {
                     tc_after();
-                    const uint32_t ahi = X ? AR_hi : AL_hi, alo = X ? AR_lo : AL_lo;
+                    const uint32_t ahi = tmem + (X ? 448u : 384u), alo = ahi + 32u;
                     const uint32_t b_hi = ring0 + (uint32_t)(X * NS + s) * C::STAGE;
                     const uint32_t b_lo = b_hi + C::BOX;
                     const uint32_t d = tmem + dcol;
 #pragma unroll
                     for (int kb = 0; kb < 4; ++kb) {
-                        const uint32_t o = (uint32_t)(kb * 32);
-                        mma_bf16(d, sdesc(ahi + o), sdesc(b_hi + o), C::IDESC, kb != 0 ? 1u : 0u);
-                        mma_bf16(d, sdesc(ahi + o), sdesc(b_lo + o), C::IDESC, 1u);
-                        mma_bf16(d, sdesc(alo + o), sdesc(b_hi + o), C::IDESC, 1u);
+                        const uint32_t o = (uint32_t)(kb * 32), ka = (uint32_t)(kb * 8);
+                        mma_f16_ts(d, ahi + ka, sdesc(b_hi + o), C::IDESC, kb != 0 ? 1u : 0u);
+                        mma_f16_ts(d, ahi + ka, sdesc(b_lo + o), C::IDESC, 1u);
+                        mma_f16_ts(d, alo + ka, sdesc(b_hi + o), C::IDESC, 1u);
                     }
                     mma_commit(empty_bar(X, s));
                     mma_commit(done_bar(X));
@@ -986,10 +998,10 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
     } else if (warp < 4) {
         // ---------------------------------------------------------- left epilogue
         const uint32_t tq = tmem + ((uint32_t)(warp * 32) << 16);
-        const uint32_t tw = tq, tw0 = tq + 256u, twh = tq + 384u;
+        const uint32_t tw = tq, tw0 = tq + 256u, ta = tq + 384u;
         float v[CHI];
         load_vec<CHI>(a.bl, v);
-        write_A<CHI, F16>(AL_hi, AL_lo, m, v);
+        write_A_tmem<CHI, F16>(ta, v);
         publish(0);
         double pm = a.state[c].mant;
         int64_t pe = a.state[c].exp2, acc_count = 0;
@@ -1014,7 +1026,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                         E += renorm<CHI>(v) - site_cexp(k);
                     }
                     if (t + 1 < nL) {
-                        write_A<CHI, F16>(AL_hi, AL_lo, m, v);
+                        write_A_tmem<CHI, F16>(ta, v);
                         publish(0);
                     }
                     // the uniform is drawn while the next MMA runs
@@ -1022,9 +1034,18 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                         x = rttd::mcmc_uniform(a.seed, (uint64_t)(a.chain0 + c),
                                                (uint64_t)(a.sweep0 + sw), (uint64_t)j);
                 }
-                named_sync_256();  // the right half-row is in TMEM
-                tc_after();
-                double mm = dot_tmem64(v, twh);
+                named_sync_256();  // the right half-row is in shared memory
+                double mm;
+                {
+                    float acc[8];
+#pragma unroll
+                    for (int p = 0; p < 8; ++p) acc[p] = 0.f;
+#pragma unroll
+                    for (int i = 0; i < CHI; ++i) acc[i & 7] = fmaf(v[i], hand[i * NT + m], acc[i & 7]);
+                    mm = 0.0;
+#pragma unroll
+                    for (int p = 0; p < 8; ++p) mm += (double)acc[p];
+                }
                 int64_t Ep = E + rexp_s[m];
                 normalize_scalar(mm, Ep);
                 const double ratio = ldexp(mm / pm, (int)(Ep - pe));
@@ -1044,13 +1065,13 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                 El += renorm<CHI>(v) - site_cexp(j);
                 const bool more = (j + 1 < N) || (sw + 1 < a.n_sweeps);
                 if (j + 1 < N) {
-                    write_A<CHI, F16>(AL_hi, AL_lo, m, v);
+                    write_A_tmem<CHI, F16>(ta, v);
                     publish(0);
                 }
                 if (j + 1 == N && more) {
                     load_vec<CHI>(a.bl, v);
                     El = 0;
-                    write_A<CHI, F16>(AL_hi, AL_lo, m, v);
+                    write_A_tmem<CHI, F16>(ta, v);
                     publish(0);
                 }
             }
@@ -1063,14 +1084,14 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
     } else {
         // ---------------------------------------------------------- right epilogue
         const uint32_t tq = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        const uint32_t tw = tq + 128u, twh = tq + 384u;
+        const uint32_t tw = tq + 128u, ta = tq + 448u;
         float v[CHI];
         load_vec<CHI>(a.br, v);
         if (active) {
             store_vec<CHI>(a.rstack + ((size_t)c * N + (N - 1)) * CHI, v);
             a.rexp[(size_t)c * N + (N - 1)] = 0;
         }
-        write_A<CHI, F16>(AR_hi, AR_lo, m, v);
+        write_A_tmem<CHI, F16>(ta, v);
         publish(1);
         int64_t E = 0;
         long long nd = 0;
@@ -1089,7 +1110,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                 }
                 // next: the next environment step, or (u = N-2) the first right
                 // half-row, which starts from this very vector r_{(R-1)N+1}
-                write_A<CHI, F16>(AR_hi, AR_lo, m, v);
+                write_A_tmem<CHI, F16>(ta, v);
                 publish(1);
             }
             for (int j = 0; j < N; ++j) {
@@ -1104,12 +1125,13 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                     acc_select<CHI>(tw, spin(sk) ^ (sk == iq ? 1 : 0), v);
                     E += renorm<CHI>(v) - site_cexp(k);
                     if (t + 1 < nR) {
-                        write_A<CHI, F16>(AR_hi, AR_lo, m, v);
+                        write_A_tmem<CHI, F16>(ta, v);
                         publish(1);
                     }
                 }
-                // hand the half-row to the left epilogue (same TMEM lane)
-                tmem_st_64(twh, v);
+                // hand the half-row to the left epilogue (column-major: no bank conflicts)
+#pragma unroll
+                for (int i = 0; i < CHI; ++i) hand[i * NT + m] = v[i];
                 rexp_s[m] = (int32_t)E;
                 tc_before();
                 // the next half-row's start does not depend on this decision
@@ -1120,7 +1142,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                     } else {
                         load_vec<CHI>(a.br, v);
                     }
-                    write_A<CHI, F16>(AR_hi, AR_lo, m, v);
+                    write_A_tmem<CHI, F16>(ta, v);
                     publish(1);
                 }
                 named_sync_256();  // publish the right half-row
