@@ -80,6 +80,10 @@ def _load():
             lib.orc_local_energies.restype = ctypes.c_int
             lib.orc_flip_amplitudes.argtypes = [P, P, I64, P, P]
             lib.orc_amplitude_cond.argtypes = [P, P, P, P, P]
+            lib.orc_mixed_local_energy.argtypes = [P, P, P, P, P]
+            lib.orc_mixed_local_energy.restype = ctypes.c_int
+            lib.orc_mixed_local_energies.argtypes = [P, P, P, I64, P, P]
+            lib.orc_mixed_local_energies.restype = ctypes.c_int
             lib.orc_uniform_keyed.argtypes = [U64, U64, U64, U64, U64]
             lib.orc_uniform_keyed.restype = ctypes.c_double
             _lib = lib

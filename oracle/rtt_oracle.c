@@ -19,6 +19,8 @@
  *   - Metropolis sampling of P_s = |psi_s|^2 / Z (Sec. 3.3) by systematic
  *     single-spin sweeps; uniforms from Philox4x64-10 (Salmon et al., SC'11).
  *   - exact <H> by enumerating all 2^N configurations (N <= 20).
+ *   - the mixed local energy and overlap ratio of dual Monte Carlo (Sec. 3.3)
+ *     between two RTTs on the same lattice.
  *
  * Arithmetic conventions (the canonical order the FP64 GPU path reproduces):
  *   - vector x matrix: out[b] = sum_a v[a] A[a][b], accumulated with fma()
@@ -482,4 +484,51 @@ void orc_flip_amplitudes(const orc_rtt *m, const uint8_t *spins, int64_t B,
         for (int i = 0; i < N; ++i)
             orc_flip_amplitude(m, spins + (size_t)c * N, i, mant + (size_t)c * N + i,
                                ex + (size_t)c * N + i);
+}
+
+/* ---------------------------------------------------------------- dual Monte Carlo */
+
+/* Mixed local energy of dual Monte Carlo (Sec. 3.3):
+ *   E^{ab}(s) = sum_sbar H_{s,sbar} psi^b_sbar / psi^a_s
+ *             = [J sum_<ij> z_i z_j psi^b(s) - h sum_i psi^b(s^(i))] / psi^a(s)
+ * (Hamiltonian of Sec. 4 taken from b), and the overlap ratio
+ * r^{ab}(s) = psi^b(s) / psi^a(s), whose P^a averages are H~_ab and S~_ab.
+ * Every amplitude ratio is ldexp(mant_b / mant_a, ex_b - ex_a); the field term
+ * adds the N flip ratios in increasing spin index; E = (J zz) r - h sum.
+ * Returns 1, with both outputs NaN, when psi^a(s) is zero or not finite. */
+int orc_mixed_local_energy(const orc_rtt *ma, const orc_rtt *mb, const uint8_t *s,
+                           double *e_mixed, double *ratio)
+{
+    double m_a, m_b;
+    int64_t e_a, e_b;
+    orc_amplitude(ma, s, &m_a, &e_a);
+    if (m_a == 0.0 || !isfinite(m_a)) {
+        *e_mixed = NAN;
+        *ratio = NAN;
+        return 1;
+    }
+    orc_amplitude(mb, s, &m_b, &e_b);
+    const double r0 = ldexp(m_b / m_a, (int)(e_b - e_a));
+    double sum = 0.0;
+    for (int i = 0; i < mb->n_spins; ++i) {
+        double mi;
+        int64_t ei;
+        orc_flip_amplitude(mb, s, i, &mi, &ei);
+        sum += ldexp(mi / m_a, (int)(ei - e_a));
+    }
+    const double zz = (double)zz_sum(mb, s);
+    *e_mixed = mb->J * zz * r0 - mb->h * sum;
+    *ratio = r0;
+    return 0;
+}
+
+/* The same for B configurations [B][N]; outputs [B]. */
+int orc_mixed_local_energies(const orc_rtt *ma, const orc_rtt *mb, const uint8_t *spins,
+                             int64_t B, double *e_mixed, double *ratio)
+{
+    const int N = mb->n_spins;
+    int bad = 0;
+    for (int64_t c = 0; c < B; ++c)
+        bad += orc_mixed_local_energy(ma, mb, spins + (size_t)c * N, e_mixed + c, ratio + c);
+    return bad;
 }
