@@ -173,6 +173,57 @@ rtt_status rtt_observables(rtt_handle h, const double *e_loc_trace, int32_t T, i
                            const int64_t *n_accept, int64_t proposals_per_chain, rtt_stats *out,
                            void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Dual Monte Carlo (Sec. 3.3): matrix elements between M RTT states psi^1..psi^M
+ * of one lattice, each sampled from its own P^a = |psi^a|^2 / Z_a.
+ *
+ * Mixed local energy and overlap ratio of configurations s (typically drawn
+ * from P^a by rtt_mcmc_sweep on handle a):
+ *   E^{ab}(s) = sum_sbar H_{s,sbar} psi^b(sbar) / psi^a(s)
+ *             = [J sum_<ij> z_i z_j psi^b(s) - h sum_i psi^b(s^(i))] / psi^a(s)
+ *   r^{ab}(s) = psi^b(s) / psi^a(s)
+ * so that H~_ab = <E^{ab}>_{P^a} and S~_ab = <r^{ab}>_{P^a} (the un-symmetrised
+ * matrices of Eq. gen_eig2; rtt_observables gives their means and errors).
+ * Each amplitude ratio is ldexp(mant_b / mant_a, exp_b - exp_a); the field term
+ * adds the N flip ratios in increasing spin index; E = (J zz) r - h sum, all in
+ * FP64 (bit-identical to the FP64 oracle for FP64 handles).  Handles a and b
+ * (a may equal b, giving E_loc and r = 1) must be on one device and share N, the
+ * bond list, J and h; their tensors, R, chi and precision may differ.
+ *   spins   device [B][N]
+ *   e_mixed device [B]
+ *   ratio   device [B] or NULL
+ * Configurations with psi^a(s) zero or not finite give NaN.  Asynchronous on
+ * `stream`; uses both handles' scratch. */
+rtt_status rtt_mixed_local_energy(rtt_handle a, rtt_handle b, const uint8_t *spins, int64_t B,
+                                  double *e_mixed, double *ratio, void *stream);
+
+/* One RTT for a linear combination psi(s) = sum_m coef[m] psi^m(s) of M RTTs on
+ * the same path (Sec. 3.2: psi' is turned back into an RTT by summing tensor
+ * trains; the stochastic Gram-Schmidt states of Sec. 3.3, Eq. Gram-Schmid, are
+ * such combinations).  A sum of TTs is a TT: site tensors block-diagonal,
+ * A_k[s] = diag(A^1_k[s], ..., A^M_k[s]); b_R = (b^1_R, ..., b^M_R);
+ * b_L = (coef[0] b^1_L, ..., coef[M-1] b^M_L).  All descriptions must share
+ * n_spins, length, path, bonds, J and h; chi = sum of the chi_m (<= 256, and
+ * 64 or 128 for the tensor-core precisions); precision, device and seed are
+ * those of descs[0].  descs: host [M]; coef: host [M]; *out as rtt_create. */
+rtt_status rtt_create_sum(const rtt_desc *descs, int32_t M, const double *coef, rtt_handle *out);
+
+/* Generalized eigenproblem H~ c = lambda S~ c of Eq. gen_eig2 (Sec. 3.3), whose
+ * lowest eigenvalue is the energy of the optimal combination sum_a c_a psi^a.
+ * Solved as the eigenvalues of S~^-1 H~ (LU with partial pivoting, Householder
+ * Hessenberg reduction, shifted complex QR), host FP64.
+ *   M       1..8
+ *   Ht, St  host [M][M] row-major, (H~_ab, S~_ab)
+ *   eig_re, eig_im  host [M]: eigenvalues by increasing real part (ties by
+ *           imaginary part)
+ *   c0      host [M] or NULL: for a real lowest eigenvalue (|Im| <= 1e-9 max|lambda|)
+ *           its eigenvector (inverse iteration on S~^-1 H~), scaled to
+ *           |c^T S~ c| = 1 with its largest-magnitude entry positive; NaN otherwise
+ * RTT_ERR_NUMERIC if S~ is singular or the QR iteration does not converge.
+ * Host computation only; no device work, callable without a GPU. */
+rtt_status rtt_dual_solve(int32_t M, const double *Ht, const double *St, double *eig_re,
+                          double *eig_im, double *c0);
+
 /* The Metropolis uniforms themselves, for checking the device generator:
  * counters: device uint64 [n][3] = (chain, sweep, proposal); out: device [n]. */
 rtt_status rtt_mcmc_uniforms(uint64_t seed, int64_t n, const uint64_t *counters, double *out,

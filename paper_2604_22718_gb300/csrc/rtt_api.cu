@@ -92,6 +92,8 @@ void free_scratch(rtt_s *h) {
     cudaFree(h->d_sw_rexp);
     cudaFree(h->d_snap[0]);
     cudaFree(h->d_snap[1]);
+    cudaFree(h->d_amp);
+    h->d_amp = nullptr;
     h->d_lstack = h->d_rstack = nullptr;
     h->d_lexp = h->d_rexp = nullptr;
     h->d_rows_mant = nullptr;
@@ -107,7 +109,7 @@ size_t scratch_bytes_for(const rtt_s *h, int64_t B) {
     const size_t stack = (size_t)B * h->N * h->chip * eb + (size_t)B * h->N * 4;
     const size_t rows = (size_t)B * (h->N + 1) * 16;
     const size_t snap = (size_t)B * h->N;
-    return 4 * stack + rows + 2 * snap;
+    return 4 * stack + rows + 2 * snap + (size_t)B * sizeof(rtt_chain_state);
 }
 
 rtt_status ensure_scratch(rtt_s *h, int64_t B) {
@@ -128,6 +130,7 @@ rtt_status ensure_scratch(rtt_s *h, int64_t B) {
     API_CUDA(cudaMalloc((void **)&h->d_sw_rexp, nv * 4), "scratch sweep r-exp");
     API_CUDA(cudaMalloc((void **)&h->d_snap[0], nv), "scratch spin snapshot");
     API_CUDA(cudaMalloc((void **)&h->d_snap[1], nv), "scratch spin snapshot");
+    API_CUDA(cudaMalloc((void **)&h->d_amp, (size_t)B * sizeof(rtt_chain_state)), "scratch amplitudes");
     h->cap_B = B;
     return RTT_OK;
 }
@@ -143,8 +146,11 @@ rtt_status check_handle(rtt_handle h) {
 
 // Environments + rows + reduction for the spins currently in `spins`.
 // If `have_left` the left stack already holds l_j for these spins.
-rtt_status energy_pipeline(rtt_s *h, const uint8_t *spins, int64_t B, double *e_loc,
-                           double *ratios, bool have_left, cudaStream_t st) {
+// Environments and flip rows (psi(s^(path[j])) and psi(s)) for the spins in
+// `spins`, into the handle's rows.  If `have_left` the left stack already holds
+// l_j for these spins.
+rtt_status rows_pipeline(rtt_s *h, const uint8_t *spins, int64_t B, bool have_left,
+                         cudaStream_t st) {
     if (h->precision >= RTT_BF16X3) {
         rtt_status s;
         if (!have_left && (s = tc_left_env(h, spins, B, st)) != RTT_OK) return s;
@@ -173,6 +179,13 @@ rtt_status energy_pipeline(rtt_s *h, const uint8_t *spins, int64_t B, double *e_
                  "flip rows");
         prof_end(h, KID_ROWS, st);
     }
+    return RTT_OK;
+}
+
+rtt_status energy_pipeline(rtt_s *h, const uint8_t *spins, int64_t B, double *e_loc,
+                           double *ratios, bool have_left, cudaStream_t st) {
+    rtt_status s = rows_pipeline(h, spins, B, have_left, st);
+    if (s != RTT_OK) return s;
     prof_begin(h, KID_ELOC_REDUCE, st);
     API_CUDA(eloc_reduce(spins, B, h->N, h->d_pos, h->d_bonds, h->n_bonds, h->J, h->h,
                          h->d_rows_mant, h->d_rows_exp, e_loc, ratios, st),
@@ -341,6 +354,7 @@ rtt_status rtt_create(const rtt_desc *d, rtt_handle *out) {
     if ((s = upload(q, (void **)&h->d_q, "rtt_create: path")) != RTT_OK) return cleanup(s);
     if ((s = upload(pos, (void **)&h->d_pos, "rtt_create: positions")) != RTT_OK) return cleanup(s);
     std::vector<int32_t> bonds(d->bonds, d->bonds + 2 * d->n_bonds);
+    h->bonds_host = bonds;
     if (bonds.empty()) bonds.push_back(0);
     if ((s = upload(bonds, (void **)&h->d_bonds, "rtt_create: bonds")) != RTT_OK) return cleanup(s);
     const int chip = h->chip;
@@ -446,6 +460,48 @@ rtt_status rtt_local_energy(rtt_handle h, const uint8_t *spins, int64_t B, doubl
     API_CUDA(cudaGetLastError(), "rtt_local_energy: pending error");
     if ((s = ensure_scratch(h, B)) != RTT_OK) return s;
     return energy_pipeline(h, spins, B, e_loc, ratios, false, st);
+}
+
+rtt_status rtt_mixed_local_energy(rtt_handle a, rtt_handle b, const uint8_t *spins, int64_t B,
+                                  double *e_mixed, double *ratio, void *stream) {
+    g_last_error.clear();
+    if (!a || !b) return fail(RTT_ERR_INVALID_ARG, "rtt_mixed_local_energy: null handle");
+    if (B < 0) return fail(RTT_ERR_INVALID_ARG, "rtt_mixed_local_energy: B < 0");
+    if (a->device != b->device)
+        return fail(RTT_ERR_INVALID_ARG, "rtt_mixed_local_energy: handles on different devices");
+    if (a->N != b->N || a->n_bonds != b->n_bonds || a->bonds_host != b->bonds_host ||
+        a->J != b->J || a->h != b->h)
+        return fail(RTT_ERR_INVALID_ARG,
+                    "rtt_mixed_local_energy: handles differ in N, bonds, J or h");
+    if (B == 0) return RTT_OK;
+    if (!spins || !e_mixed)
+        return fail(RTT_ERR_INVALID_ARG, "rtt_mixed_local_energy: null spins or e_mixed");
+    DeviceGuard guard(a->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    API_CUDA(cudaGetLastError(), "rtt_mixed_local_energy: pending error");
+    rtt_status s;
+    if ((s = ensure_scratch(a, B)) != RTT_OK) return s;
+    if ((s = ensure_scratch(b, B)) != RTT_OK) return s;
+    // psi^a(s) into a's amplitude scratch
+    if (a->precision >= RTT_BF16X3) {
+        if ((s = tc_chain_init(a, spins, B, nullptr, nullptr, a->d_amp, st)) != RTT_OK) return s;
+    } else {
+        const SimtArgs sa = simt_args(a);
+        prof_begin(a, KID_CHAIN_INIT, st);
+        API_CUDA(a->precision == RTT_FP64
+                     ? simt_chain_init_f64(sa, spins, B, nullptr, nullptr, a->d_amp, st)
+                     : simt_chain_init_f32(sa, spins, B, nullptr, nullptr, a->d_amp, st),
+                 "rtt_mixed_local_energy: amplitudes");
+        prof_end(a, KID_CHAIN_INIT, st);
+    }
+    // psi^b(s^(i)) and psi^b(s) in b's rows
+    if ((s = rows_pipeline(b, spins, B, false, st)) != RTT_OK) return s;
+    prof_begin(b, KID_ELOC_REDUCE, st);
+    API_CUDA(mixed_reduce(spins, B, b->N, b->d_pos, b->d_bonds, b->n_bonds, b->J, b->h,
+                          b->d_rows_mant, b->d_rows_exp, a->d_amp, e_mixed, ratio, st),
+             "rtt_mixed_local_energy: reduction");
+    prof_end(b, KID_ELOC_REDUCE, st);
+    return RTT_OK;
 }
 
 rtt_status rtt_mcmc_sweep(rtt_handle h, uint8_t *spins, rtt_chain_state *state, int64_t B,

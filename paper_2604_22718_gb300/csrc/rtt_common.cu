@@ -44,6 +44,44 @@ __global__ void k_eloc_reduce(const uint8_t *__restrict__ spins, int64_t B, int 
     e_loc[c] = J * (double)zz - h * sum;
 }
 
+// Mixed local energy of dual Monte Carlo: rows of handle b, amplitude of a.
+// Ratios ldexp(mant_b / mant_a, exp_b - exp_a); field term in increasing spin
+// index; E = (J zz) r0 - h sum (the FP64 oracle's order).
+__global__ void k_mixed_reduce(const uint8_t *__restrict__ spins, int64_t B, int N,
+                               const int32_t *__restrict__ pos, const int32_t *__restrict__ bonds,
+                               int n_bonds, double J, double h,
+                               const double *__restrict__ rows_mant,
+                               const int64_t *__restrict__ rows_exp,
+                               const rtt_chain_state *__restrict__ amp_a,
+                               double *__restrict__ e_mixed, double *__restrict__ ratio) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= B) return;
+    const double *rm = rows_mant + c * (N + 1);
+    const int64_t *re = rows_exp + c * (N + 1);
+    const uint8_t *s = spins + c * N;
+    const double ma = amp_a[c].mant;
+    const int64_t ea = amp_a[c].exp2;
+    if (ma == 0.0 || !isfinite(ma)) {
+        e_mixed[c] = CUDART_NAN;
+        if (ratio) ratio[c] = CUDART_NAN;
+        return;
+    }
+    const double r0 = ldexp(rm[N] / ma, (int)(re[N] - ea));
+    double sum = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const int j = pos[i];
+        sum += ldexp(rm[j] / ma, (int)(re[j] - ea));
+    }
+    int64_t zz = 0;
+    for (int b = 0; b < n_bonds; ++b) {
+        const int zi = 1 - 2 * (int)s[bonds[2 * b]];
+        const int zj = 1 - 2 * (int)s[bonds[2 * b + 1]];
+        zz += zi * zj;
+    }
+    e_mixed[c] = J * (double)zz * r0 - h * sum;
+    if (ratio) ratio[c] = r0;
+}
+
 __global__ void k_uniforms(uint64_t seed, int64_t n, const uint64_t *__restrict__ ctr,
                            double *__restrict__ out) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -130,6 +168,16 @@ cudaError_t eloc_reduce(const uint8_t *spins, int64_t B, int N, const int32_t *p
                         double *ratios, cudaStream_t st) {
     k_eloc_reduce<<<nblk(B, 128), 128, 0, st>>>(spins, B, N, pos, bonds, n_bonds, J, h, rows_mant,
                                                  rows_exp, e_loc, ratios);
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_reduce(const uint8_t *spins, int64_t B, int N, const int32_t *pos,
+                         const int32_t *bonds, int n_bonds, double J, double h,
+                         const double *rows_mant, const int64_t *rows_exp,
+                         const rtt_chain_state *amp_a, double *e_mixed, double *ratio,
+                         cudaStream_t st) {
+    k_mixed_reduce<<<nblk(B, 128), 128, 0, st>>>(spins, B, N, pos, bonds, n_bonds, J, h, rows_mant,
+                                                  rows_exp, amp_a, e_mixed, ratio);
     return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "rtt.h"
 
@@ -24,6 +25,7 @@ struct rtt_s {
     int32_t *d_q = nullptr;       // [N]    q[j] = path[j] (proposal order)
     int32_t *d_pos = nullptr;     // [N]    pos[i] = j with q[j] = i
     int32_t *d_bonds = nullptr;   // [n_bonds][2]
+    std::vector<int32_t> bonds_host;  // the same on the host (lattice checks)
     void *d_A = nullptr;          // [L][2][chip][chip]  A_k[s][a][b]   (double or float)
     void *d_AT = nullptr;         // [L][2][chip][chip]  A_k[s][b][a]
     void *d_bl = nullptr;         // [chip]
@@ -46,6 +48,7 @@ struct rtt_s {
     void *d_sw_rstack = nullptr;  // [B][N][chip]
     int32_t *d_sw_rexp = nullptr; // [B][N]
     uint8_t *d_snap[2] = {nullptr, nullptr};  // [B][N] each
+    rtt_chain_state *d_amp = nullptr;         // [B] amplitudes for mixed energies
 
     // second stream on which the measured local energy runs beside the
     // sweeps, and its events (created with the handle)
@@ -106,6 +109,12 @@ cudaError_t eloc_reduce(const uint8_t *spins, int64_t B, int N, const int32_t *p
                         const int32_t *bonds, int n_bonds, double J, double h,
                         const double *rows_mant, const int64_t *rows_exp, double *e_loc,
                         double *ratios, cudaStream_t st);
+// Mixed local energy E^{ab} and ratio psi^b/psi^a from b's rows and a's amplitudes.
+cudaError_t mixed_reduce(const uint8_t *spins, int64_t B, int N, const int32_t *pos,
+                         const int32_t *bonds, int n_bonds, double J, double h,
+                         const double *rows_mant, const int64_t *rows_exp,
+                         const rtt_chain_state *amp_a, double *e_mixed, double *ratio,
+                         cudaStream_t st);
 cudaError_t launch_uniforms(uint64_t seed, int64_t n, const uint64_t *ctr, double *out,
                             cudaStream_t st);
 cudaError_t stats_chain_means(const double *x, int T, int64_t B, double *chain_mean,

@@ -68,6 +68,9 @@ def lib():
         L.rtt_scratch_bytes.argtypes = [P, I64, ctypes.POINTER(ctypes.c_size_t)]
         L.rtt_log_amplitudes.argtypes = [P, P, I64, P, P, P, P]
         L.rtt_local_energy.argtypes = [P, P, I64, P, P, P]
+        L.rtt_mixed_local_energy.argtypes = [P, P, P, I64, P, P, P]
+        L.rtt_create_sum.argtypes = [ctypes.POINTER(_Desc), I32, P, ctypes.POINTER(P)]
+        L.rtt_dual_solve.argtypes = [I32, P, P, P, P, P]
         L.rtt_mcmc_sweep.argtypes = [P, P, P, I64, I64, I64, I32, I32, P, P, P]
         L.rtt_observables.argtypes = [P, P, I32, I64, P, I64, ctypes.POINTER(_Stats), P]
         L.rtt_mcmc_uniforms.argtypes = [U64, I64, P, P, P]
@@ -104,6 +107,33 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def _desc_of(inst, precision: int, device: int, seed: int):
+    """rtt_desc of an instance and the host arrays it points into (keep them alive)."""
+    path = np.ascontiguousarray(inst.path, dtype=np.int32)
+    t = np.ascontiguousarray(inst.tensors, dtype=np.float64)
+    bl = np.ascontiguousarray(inst.b_left, dtype=np.float64)
+    br = np.ascontiguousarray(inst.b_right, dtype=np.float64)
+    bonds = np.ascontiguousarray(inst.bonds, dtype=np.int32).reshape(-1, 2)
+    L, _, chi, _ = t.shape
+    d = _Desc(int(inst.n_spins), L, chi, bonds.shape[0], path.ctypes.data, t.ctypes.data,
+              bl.ctypes.data, br.ctypes.data, bonds.ctypes.data if bonds.size else None,
+              float(inst.J), float(inst.h), precision, device, int(seed))
+    return d, (path, t, bl, br, bonds)
+
+
+def dual_solve(Ht, St):
+    """rtt_dual_solve: eigenvalues of H~ c = lambda S~ c (complex, by increasing
+    real part) and the scaled eigenvector of the lowest one (NaN if not real)."""
+    Ht = np.ascontiguousarray(Ht, dtype=np.float64)
+    St = np.ascontiguousarray(St, dtype=np.float64)
+    M = Ht.shape[0]
+    assert Ht.shape == (M, M) and St.shape == (M, M)
+    re, im, c = np.empty(M), np.empty(M), np.empty(M)
+    _check(lib().rtt_dual_solve(M, Ht.ctypes.data, St.ctypes.data, re.ctypes.data, im.ctypes.data,
+                                c.ctypes.data), "rtt_dual_solve")
+    return re + 1j * im, c
 
 
 def _check(status: int, where: str):
@@ -154,24 +184,41 @@ class RTT:
     def __init__(self, inst, precision: str | int = "fp32", device: int | None = None,
                  seed: int = 22718):
         self.inst = inst
-        self.n = int(inst.n_spins)
+        self.n = int(inst.n_spins) if inst is not None else 0
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.device = torch.cuda.current_device() if device is None else int(device)
-        self._path = np.ascontiguousarray(inst.path, dtype=np.int32)
-        self._t = np.ascontiguousarray(inst.tensors, dtype=np.float64)
-        self._bl = np.ascontiguousarray(inst.b_left, dtype=np.float64)
-        self._br = np.ascontiguousarray(inst.b_right, dtype=np.float64)
-        self._bonds = np.ascontiguousarray(inst.bonds, dtype=np.int32).reshape(-1, 2)
-        L, _, chi, _ = self._t.shape
-        self.L, self.chi = L, chi
-        d = _Desc(self.n, L, chi, self._bonds.shape[0], self._path.ctypes.data,
-                  self._t.ctypes.data, self._bl.ctypes.data, self._br.ctypes.data,
-                  self._bonds.ctypes.data if self._bonds.size else None,
-                  float(inst.J), float(inst.h), self.precision, self.device, int(seed))
         self.seed = int(seed)
+        if inst is None:            # filled by from_sum
+            self._h = None
+            return
+        d, self._keep = _desc_of(inst, self.precision, self.device, self.seed)
+        self.L, self.chi = int(d.length), int(d.chi)
         h = ctypes.c_void_p()
         _check(lib().rtt_create(ctypes.byref(d), ctypes.byref(h)), "rtt_create")
         self._h = h
+
+    @classmethod
+    def from_sum(cls, instances, coef, precision: str | int = "fp32", device: int | None = None,
+                 seed: int = 22718):
+        """One RTT for sum_m coef[m] psi^m (rtt_create_sum: block-diagonal direct sum)."""
+        self = cls(None, precision, device, seed)
+        M = len(instances)
+        descs = (_Desc * M)()
+        keep = []
+        for m, inst in enumerate(instances):
+            d, k = _desc_of(inst, self.precision, self.device, self.seed)
+            descs[m] = d
+            keep.append(k)
+        c = np.ascontiguousarray(coef, dtype=np.float64)
+        assert c.shape == (M,)
+        h = ctypes.c_void_p()
+        _check(lib().rtt_create_sum(descs, M, c.ctypes.data, ctypes.byref(h)), "rtt_create_sum")
+        self._h = h
+        self.n = int(instances[0].n_spins)
+        self.L = int(np.asarray(instances[0].path).shape[0])
+        self.chi = int(sum(int(i.tensors.shape[2]) for i in instances))
+        self.inst = None
+        return self
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -231,6 +278,16 @@ class RTT:
         _check(lib().rtt_local_energy(self._h, _ptr(spins), B, _ptr(e), _ptr(r), _stream(stream)),
                "rtt_local_energy")
         return (e, r) if with_ratios else e
+
+    def mixed_local_energy(self, other: "RTT", spins: torch.Tensor, stream=None):
+        """(E^{ab}(s), psi^b(s)/psi^a(s)) with a = self, b = other (dual Monte Carlo)."""
+        B = spins.shape[0]
+        _dev_check(spins, torch.uint8, (B, self.n), "spins")
+        e = torch.empty(B, dtype=torch.float64, device=spins.device)
+        r = torch.empty(B, dtype=torch.float64, device=spins.device)
+        _check(lib().rtt_mixed_local_energy(self._h, other._h, _ptr(spins), B, _ptr(e), _ptr(r),
+                                            _stream(stream)), "rtt_mixed_local_energy")
+        return e, r
 
     def mcmc_sweep(self, spins: torch.Tensor, state: torch.Tensor, sweep0: int, n_sweeps: int,
                    measure_every: int = 1, trace: torch.Tensor | None = None,

@@ -1,0 +1,70 @@
+"""rtt_dual_solve (host code of the C library, no GPU) against the oracle's
+library eigen-solver, and argument errors of the dual Monte Carlo entry points."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2604_22718_gb300 import build as rtt_build
+from paper_2604_22718_gb300 import inputs
+from oracle import dual
+
+
+@pytest.fixture(scope="module")
+def rtt():
+    rtt_build.build()
+    from paper_2604_22718_gb300 import rtt as mod
+    return mod
+
+
+def _states(M, chi=3):
+    return [inputs.make_instance(3, 3, 2, chi, 3.0, seed=s, mixing=True) for s in (41, 42, 43, 44)[:M]]
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+def test_solve_matches_oracle_on_exact_matrices(rtt, M):
+    Ht, St = dual.exact_tilde_matrices(_states(M))
+    w, c = rtt.dual_solve(Ht, St)
+    w_o, c_o = dual.solve(Ht, St)
+    np.testing.assert_allclose(w.real, w_o.real, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(w.imag, 0.0, atol=1e-9 * np.abs(w).max())
+    np.testing.assert_allclose(c, c_o, rtol=1e-7, atol=1e-9)
+    np.testing.assert_allclose(Ht @ c, w.real[0] * (St @ c), atol=1e-8 * np.abs(Ht).max())
+
+
+def test_solve_random_pencils_and_complex_pairs(rtt):
+    rng = np.random.default_rng(5)
+    for M in range(1, 9):
+        for _ in range(5):
+            Ht = rng.standard_normal((M, M))
+            St = rng.standard_normal((M, M)) + M * np.eye(M)
+            w, c = rtt.dual_solve(Ht, St)
+            w_o, _ = dual.solve(Ht, St)
+            scale = np.abs(w_o).max()
+            # the same multiset (conjugate pairs may come in either order)
+            left = list(w_o)
+            for z in w:
+                k = int(np.argmin([abs(z - y) for y in left]))
+                assert abs(z - left.pop(k)) <= 1e-9 * scale, (w, w_o)
+            assert np.all(np.diff(w.real) >= -1e-12 * scale)
+            if abs(w[0].imag) <= 1e-9 * scale:
+                np.testing.assert_allclose(Ht @ c, w.real[0] * (St @ c), atol=1e-7 * scale * M)
+                assert abs(c @ St @ c) == pytest.approx(1.0, rel=1e-9)
+            else:
+                assert np.all(np.isnan(c))
+
+
+def test_solve_rejects_singular_overlap_and_bad_sizes(rtt):
+    with pytest.raises(rtt.RTTError):
+        rtt.dual_solve(np.eye(2), np.zeros((2, 2)))
+    with pytest.raises(rtt.RTTError):
+        rtt.dual_solve(np.eye(9), np.eye(9))
+    lib = rtt.lib()
+    assert lib.rtt_dual_solve(0, None, None, None, None, None) == 1
+
+
+def test_dual_entry_points_reject_null_arguments(rtt):
+    lib = rtt.lib()
+    assert lib.rtt_mixed_local_energy(None, None, None, 4, None, None, None) == 1
+    out = ctypes.c_void_p()
+    assert lib.rtt_create_sum(None, 2, None, ctypes.byref(out)) == 1
