@@ -581,6 +581,113 @@ def run_learned(args):
     m.close()
 
 
+def run_dual(args):
+    """Dual Monte Carlo (Sec. 3.3): M = 3 states of the plain_6x6 kind, 4096
+    chains each; one step = rtt_dual_step: for every state a the mixed local
+    energies and overlap ratios against all b of the configurations a's chains
+    start from (second stream), beside one sweep of a's chains."""
+    import torch
+    from paper_2604_22718_gb300 import inputs, rtt
+    name = "dual_6x6"
+    w = inputs.WORKLOADS[name]
+    states = inputs.workload_states(name)
+    M, N = len(states), states[0].n_spins
+    B = args.chains or w["chains"]
+    hs = [rtt.RTT(s, args.precision, seed=w["seed"] + 100 * m) for m, s in enumerate(states)]
+    spins = [torch.from_numpy(inputs.initial_spins(w["seed"] + m, B, N)).cuda() for m in range(M)]
+    sts = [h.log_amplitudes(x)[2] for h, x in zip(hs, spins)]
+    K, W = args.steps, args.warmup
+    e = torch.empty((K, M, M, B), dtype=torch.float64, device="cuda")
+    r = torch.empty((K, M, M, B), dtype=torch.float64, device="cuda")
+    flush = L2Flush()
+    stream = torch.cuda.current_stream()
+    for t in range(W):
+        rtt.dual_step(hs, spins, sts, t, e[0], r[0])
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    for h in hs:
+        h.profile(True)
+    clocks.start()
+    for t in range(K):
+        flush()
+        ev[t][0].record(stream)
+        rtt.dual_step(hs, spins, sts, W + t, e[t], r[t])
+        ev[t][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = {}
+    for h in hs:
+        for k, (n, ms) in h.profile_read().items():
+            a = prof.setdefault(k, [0, 0.0])
+            a[0] += n
+            a[1] += ms
+        h.profile(False)
+    total_ms = sum(a.elapsed_time(z) for a, z in ev)
+    value = M * B * K / (total_ms / 1e3)
+    Ht, St, Hse, Sse = (np.zeros((M, M)) for _ in range(4))
+    for a in range(M):
+        for b in range(M):
+            so = hs[a].observables(e[:, a, b, :].contiguous())
+            sr = hs[a].observables(r[:, a, b, :].contiguous())
+            Ht[a, b], Hse[a, b], St[a, b], Sse[a, b] = so["mean"], so["se"], sr["mean"], sr["se"]
+    eig, c0 = rtt.dual_solve(Ht, St)
+    dom = max(prof, key=lambda k: prof[k][1])
+    launches, ms = prof[dom]
+    R = states[0].path.shape[0] // N
+    chi = states[0].chi
+    flops = 2.0 * chi * chi * site_steps(N, R, dom) * B
+    achieved = flops / (ms / launches / 1e3) / 1e12
+    peaks, kind = measured_peaks()
+    peak = peaks["bf16_tflops_sustained"]
+    step_flops = sum(2.0 * chi * chi * site_steps(N, R, k) * B * v[0] for k, v in prof.items()) / K
+    step_tf = step_flops / (total_ms / K / 1e3) / 1e12
+    # oracle baseline on a bounded sample: mixed energies against all states and one sweep
+    from oracle import oracle as orc
+    from oracle import dual as odual
+    cores = os.cpu_count() or 1
+    nb = 48
+    orcs = [orc.Oracle(s) for s in states]
+    t0 = time.perf_counter()
+    for a in range(M):
+        sp = inputs.initial_spins(w["seed"] + a, nb, N)
+        for b in range(M):
+            odual.mixed_local_energies(orcs[a], orcs[b], sp, threads=cores)
+        mant, ex = orcs[a].init_chains(sp)
+        orcs[a].mcmc(w["seed"], sp, mant, ex, 0, 1, record=False, threads=cores)
+    cpu_s = time.perf_counter() - t0
+    line = {
+        "metric": "dual Monte Carlo samples/s (chains x states per step; each sample carries "
+                  "M mixed local energies and M overlap ratios)",
+        "value": value, "unit": "samples/s", "n_gpus": 1, "steps": K, "warmup": W,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3",
+                                       "fp16x3": "fp16x3"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"{name}: {M} states of 6x6 open TFIM N=36 h=3.0, R=2 L=72 chi=64, "
+                               f"{B} chains per state, rtt_dual_step per step",
+                   "l2": "flushed (256 MiB write + 256 MiB read) between timed steps"},
+        "mixed_local_energies_per_s": M * M * B * K / (total_ms / 1e3),
+        "H_tilde": Ht.tolist(), "S_tilde": St.tolist(), "H_tilde_se": Hse.tolist(),
+        "S_tilde_se": Sse.tolist(), "eigenvalues": [[float(z.real), float(z.imag)] for z in eig],
+        "lowest_combination": c0.tolist(),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": dom,
+                     "executed_frac": 6 * achieved / peak, "step_tflops": step_tf,
+                     "step_executed_frac": 6 * step_tf / peak,
+                     "peak_source": f"bf16 dense sustained ({kind}); fp16 = bf16 rate"},
+        "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
+        "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clk,
+        "cpu_baseline": {"value": M * nb / cpu_s, "unit": "samples/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{nb} chains per state: {M * M} mixed-energy sets + {M} sweeps "
+                                   f"(FP64 oracle, {cores} threads, {cpu_s:.1f} s)"},
+    }
+    print(json.dumps(line), flush=True)
+    for h in hs:
+        h.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -595,6 +702,10 @@ def main():
     if args.workload == "learned_16x16":
         if int(os.environ.get("RANK", "0")) == 0:
             run_learned(args)
+        return
+    if args.workload == "dual_6x6":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_dual(args)
         return
     run_ours(args)
 

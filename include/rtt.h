@@ -197,6 +197,21 @@ rtt_status rtt_observables(rtt_handle h, const double *e_loc_trace, int32_t T, i
 rtt_status rtt_mixed_local_energy(rtt_handle a, rtt_handle b, const uint8_t *spins, int64_t B,
                                   double *e_mixed, double *ratio, void *stream);
 
+/* One dual Monte Carlo iteration for M states (Sec. 3.3): for every state a, the
+ * mixed local energies E^{ab} and ratios r^{ab} (all b) of the configurations
+ * a's chains enter the iteration with (as rtt_mixed_local_energy), then one
+ * systematic sweep of a's chains on P^a (as rtt_mcmc_sweep with chain0 and
+ * sweep0 = sweep).  The measurements run on the first handle's second stream
+ * from copies of the spins, beside the sweeps; all work is ordered before
+ * later work on `stream`.
+ *   handles   host [M] (M >= 1), one lattice as for rtt_mixed_local_energy
+ *   spins     host [M] of device [B][N]; state host [M] of device [B]
+ *   e_mixed   device [M][M][B] (a-major, then b) or NULL; ratio likewise
+ *   n_accept  host [M] of device [B] or NULL (as may be every entry) */
+rtt_status rtt_dual_step(const rtt_handle *handles, int32_t M, uint8_t *const *spins,
+                         rtt_chain_state *const *state, int64_t B, int64_t chain0, int64_t sweep,
+                         double *e_mixed, double *ratio, int64_t *const *n_accept, void *stream);
+
 /* One RTT for a linear combination psi(s) = sum_m coef[m] psi^m(s) of M RTTs on
  * the same path (Sec. 3.2: psi' is turned back into an RTT by summing tensor
  * trains; the stochastic Gram-Schmidt states of Sec. 3.3, Eq. Gram-Schmid, are

@@ -462,27 +462,10 @@ rtt_status rtt_local_energy(rtt_handle h, const uint8_t *spins, int64_t B, doubl
     return energy_pipeline(h, spins, B, e_loc, ratios, false, st);
 }
 
-rtt_status rtt_mixed_local_energy(rtt_handle a, rtt_handle b, const uint8_t *spins, int64_t B,
-                                  double *e_mixed, double *ratio, void *stream) {
-    g_last_error.clear();
-    if (!a || !b) return fail(RTT_ERR_INVALID_ARG, "rtt_mixed_local_energy: null handle");
-    if (B < 0) return fail(RTT_ERR_INVALID_ARG, "rtt_mixed_local_energy: B < 0");
-    if (a->device != b->device)
-        return fail(RTT_ERR_INVALID_ARG, "rtt_mixed_local_energy: handles on different devices");
-    if (a->N != b->N || a->n_bonds != b->n_bonds || a->bonds_host != b->bonds_host ||
-        a->J != b->J || a->h != b->h)
-        return fail(RTT_ERR_INVALID_ARG,
-                    "rtt_mixed_local_energy: handles differ in N, bonds, J or h");
-    if (B == 0) return RTT_OK;
-    if (!spins || !e_mixed)
-        return fail(RTT_ERR_INVALID_ARG, "rtt_mixed_local_energy: null spins or e_mixed");
-    DeviceGuard guard(a->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    API_CUDA(cudaGetLastError(), "rtt_mixed_local_energy: pending error");
+namespace {
+// psi^a of the configurations into a's amplitude scratch, on stream st.
+rtt_status mixed_amplitudes(rtt_s *a, const uint8_t *spins, int64_t B, cudaStream_t st) {
     rtt_status s;
-    if ((s = ensure_scratch(a, B)) != RTT_OK) return s;
-    if ((s = ensure_scratch(b, B)) != RTT_OK) return s;
-    // psi^a(s) into a's amplitude scratch
     if (a->precision >= RTT_BF16X3) {
         if ((s = tc_chain_init(a, spins, B, nullptr, nullptr, a->d_amp, st)) != RTT_OK) return s;
     } else {
@@ -491,17 +474,119 @@ rtt_status rtt_mixed_local_energy(rtt_handle a, rtt_handle b, const uint8_t *spi
         API_CUDA(a->precision == RTT_FP64
                      ? simt_chain_init_f64(sa, spins, B, nullptr, nullptr, a->d_amp, st)
                      : simt_chain_init_f32(sa, spins, B, nullptr, nullptr, a->d_amp, st),
-                 "rtt_mixed_local_energy: amplitudes");
+                 "mixed local energy: amplitudes");
         prof_end(a, KID_CHAIN_INIT, st);
     }
-    // psi^b(s^(i)) and psi^b(s) in b's rows
+    return RTT_OK;
+}
+
+// E^{ab} and r^{ab} from b's flip rows and a's amplitudes (already computed).
+rtt_status mixed_rows(rtt_s *a, rtt_s *b, const uint8_t *spins, int64_t B, double *e_mixed,
+                      double *ratio, cudaStream_t st) {
+    rtt_status s;
     if ((s = rows_pipeline(b, spins, B, false, st)) != RTT_OK) return s;
     prof_begin(b, KID_ELOC_REDUCE, st);
     API_CUDA(mixed_reduce(spins, B, b->N, b->d_pos, b->d_bonds, b->n_bonds, b->J, b->h,
                           b->d_rows_mant, b->d_rows_exp, a->d_amp, e_mixed, ratio, st),
-             "rtt_mixed_local_energy: reduction");
+             "mixed local energy: reduction");
     prof_end(b, KID_ELOC_REDUCE, st);
     return RTT_OK;
+}
+
+rtt_status same_lattice(const rtt_s *a, const rtt_s *b, const char *where) {
+    if (a->device != b->device)
+        return fail(RTT_ERR_INVALID_ARG, std::string(where) + ": handles on different devices");
+    if (a->N != b->N || a->n_bonds != b->n_bonds || a->bonds_host != b->bonds_host ||
+        a->J != b->J || a->h != b->h)
+        return fail(RTT_ERR_INVALID_ARG, std::string(where) + ": handles differ in N, bonds, J or h");
+    return RTT_OK;
+}
+}  // namespace
+
+rtt_status rtt_dual_step(const rtt_handle *handles, int32_t M, uint8_t *const *spins,
+                         rtt_chain_state *const *state, int64_t B, int64_t chain0, int64_t sweep,
+                         double *e_mixed, double *ratio, int64_t *const *n_accept, void *stream) {
+    g_last_error.clear();
+    if (!handles || M < 1 || !spins || !state)
+        return fail(RTT_ERR_INVALID_ARG, "rtt_dual_step: null argument or M < 1");
+    if (B < 0 || chain0 < 0 || sweep < 0)
+        return fail(RTT_ERR_INVALID_ARG, "rtt_dual_step: negative B, chain0 or sweep");
+    for (int m = 0; m < M; ++m) {
+        if (!handles[m]) return fail(RTT_ERR_INVALID_ARG, "rtt_dual_step: null handle");
+        rtt_status s = same_lattice(handles[0], handles[m], "rtt_dual_step");
+        if (s != RTT_OK) return s;
+        if (B > 0 && (!spins[m] || !state[m]))
+            return fail(RTT_ERR_INVALID_ARG, "rtt_dual_step: null spins or state");
+    }
+    if (B == 0) return RTT_OK;
+    rtt_s *h0 = handles[0];
+    DeviceGuard guard(h0->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    API_CUDA(cudaGetLastError(), "rtt_dual_step: pending error");
+    rtt_status s;
+    for (int m = 0; m < M; ++m)
+        if ((s = ensure_scratch(handles[m], B)) != RTT_OK) return s;
+    const size_t nv = (size_t)B * h0->N;
+    for (int a = 0; a < M; ++a) {
+        rtt_s *ha = handles[a];
+        // measurements of a's entering configurations, on h0's second stream
+        if (e_mixed || ratio) {
+            API_CUDA(cudaMemcpyAsync(ha->d_snap[0], spins[a], nv, cudaMemcpyDeviceToDevice, st),
+                     "rtt_dual_step: spin snapshot");
+            API_CUDA(cudaEventRecord(ha->ev_fork, st), "rtt_dual_step: fork");
+            API_CUDA(cudaStreamWaitEvent(h0->side, ha->ev_fork, 0), "rtt_dual_step: fork");
+            if ((s = mixed_amplitudes(ha, ha->d_snap[0], B, h0->side)) != RTT_OK) return s;
+            for (int b = 0; b < M; ++b) {
+                const size_t off = ((size_t)a * M + b) * B;
+                double *e = e_mixed ? e_mixed + off : nullptr;
+                double *r = ratio ? ratio + off : nullptr;
+                if ((s = mixed_rows(ha, handles[b], ha->d_snap[0], B, e, r, h0->side)) != RTT_OK)
+                    return s;
+            }
+        }
+        // one sweep of a's chains on the caller's stream
+        if (ha->precision >= RTT_BF16X3) {
+            if ((s = tc_sweep(ha, spins[a], state[a], B, chain0, sweep, 1,
+                              n_accept ? n_accept[a] : nullptr, st)) != RTT_OK)
+                return s;
+        } else {
+            const SimtArgs sa = simt_args(ha);
+            prof_begin(ha, KID_SWEEP, st);
+            API_CUDA(ha->precision == RTT_FP64
+                         ? simt_sweep_f64(sa, spins[a], state[a], B, chain0, sweep, 1, ha->seed,
+                                          ha->d_sw_rstack, ha->d_sw_rexp, nullptr, nullptr,
+                                          n_accept ? n_accept[a] : nullptr, st)
+                         : simt_sweep_f32(sa, spins[a], state[a], B, chain0, sweep, 1, ha->seed,
+                                          ha->d_sw_rstack, ha->d_sw_rexp, nullptr, nullptr,
+                                          n_accept ? n_accept[a] : nullptr, st),
+                     "rtt_dual_step: sweep kernel");
+            prof_end(ha, KID_SWEEP, st);
+        }
+    }
+    if (e_mixed || ratio) {
+        API_CUDA(cudaEventRecord(h0->ev_done[0], h0->side), "rtt_dual_step: join");
+        API_CUDA(cudaStreamWaitEvent(st, h0->ev_done[0], 0), "rtt_dual_step: join");
+    }
+    return RTT_OK;
+}
+
+rtt_status rtt_mixed_local_energy(rtt_handle a, rtt_handle b, const uint8_t *spins, int64_t B,
+                                  double *e_mixed, double *ratio, void *stream) {
+    g_last_error.clear();
+    if (!a || !b) return fail(RTT_ERR_INVALID_ARG, "rtt_mixed_local_energy: null handle");
+    if (B < 0) return fail(RTT_ERR_INVALID_ARG, "rtt_mixed_local_energy: B < 0");
+    rtt_status s = same_lattice(a, b, "rtt_mixed_local_energy");
+    if (s != RTT_OK) return s;
+    if (B == 0) return RTT_OK;
+    if (!spins || !e_mixed)
+        return fail(RTT_ERR_INVALID_ARG, "rtt_mixed_local_energy: null spins or e_mixed");
+    DeviceGuard guard(a->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    API_CUDA(cudaGetLastError(), "rtt_mixed_local_energy: pending error");
+    if ((s = ensure_scratch(a, B)) != RTT_OK) return s;
+    if ((s = ensure_scratch(b, B)) != RTT_OK) return s;
+    if ((s = mixed_amplitudes(a, spins, B, st)) != RTT_OK) return s;
+    return mixed_rows(a, b, spins, B, e_mixed, ratio, st);
 }
 
 rtt_status rtt_mcmc_sweep(rtt_handle h, uint8_t *spins, rtt_chain_state *state, int64_t B,

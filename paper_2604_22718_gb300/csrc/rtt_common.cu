@@ -62,7 +62,7 @@ __global__ void k_mixed_reduce(const uint8_t *__restrict__ spins, int64_t B, int
     const double ma = amp_a[c].mant;
     const int64_t ea = amp_a[c].exp2;
     if (ma == 0.0 || !isfinite(ma)) {
-        e_mixed[c] = CUDART_NAN;
+        if (e_mixed) e_mixed[c] = CUDART_NAN;
         if (ratio) ratio[c] = CUDART_NAN;
         return;
     }
@@ -78,7 +78,7 @@ __global__ void k_mixed_reduce(const uint8_t *__restrict__ spins, int64_t B, int
         const int zj = 1 - 2 * (int)s[bonds[2 * b + 1]];
         zz += zi * zj;
     }
-    e_mixed[c] = J * (double)zz * r0 - h * sum;
+    if (e_mixed) e_mixed[c] = J * (double)zz * r0 - h * sum;
     if (ratio) ratio[c] = r0;
 }
 

@@ -15,6 +15,7 @@ of Sec. 2.2.1):
 * ``learned_16x16`` 16x16, R=2, chi=128, h=3.044, same generator
 * ``batched64``   64 instances, Lx in {4,6,8,12}, R in {2,3,4},
                   chi in {32,64,128,256}, h ~ U[2.5,3.5]
+* ``dual_6x6``    3 states of the plain_6x6 kind (dual Monte Carlo)
 
 All randomness comes from ``numpy.random.Generator(PCG64(seed))``.
 """
@@ -26,7 +27,7 @@ import numpy as np
 __all__ = [
     "RTTInstance", "snake_order", "open_bonds", "periodic_path",
     "gaussian_tensors", "mixed_tensors", "make_instance", "initial_spins",
-    "WORKLOADS", "workload", "batched_instances", "made_init_weights", "ferro_chain_instance",
+    "WORKLOADS", "workload", "workload_states", "batched_instances", "made_init_weights", "ferro_chain_instance",
 ]
 
 
@@ -134,6 +135,8 @@ WORKLOADS = {
     "plain_6x6":     dict(lx=6, ly=6, R=2, chi=64, h=3.0, mixing=True, chains=4096, sweeps=2000, seed=22720),
     "prec_10x10":    dict(lx=10, ly=10, R=3, chi=128, h=3.04, mixing=True, chains=16384, sweeps=1000, seed=22721),
     "learned_16x16": dict(lx=16, ly=16, R=2, chi=128, h=3.044, mixing=True, chains=8192, sweeps=128, seed=22723),
+    # dual Monte Carlo: M = 3 states of the plain_6x6 kind (seeds seed, seed+1, seed+2)
+    "dual_6x6":      dict(lx=6, ly=6, R=2, chi=64, h=3.0, mixing=True, chains=4096, sweeps=100, seed=22726, states=3),
 }
 
 
@@ -142,6 +145,13 @@ def workload(name: str, **override) -> RTTInstance:
     w.update(override)
     return make_instance(w["lx"], w["ly"], w["R"], w["chi"], w["h"], w["seed"],
                          mixing=w["mixing"], name=name)
+
+
+def workload_states(name: str) -> list:
+    """The M states of a multi-state workload (seeds seed .. seed + M - 1)."""
+    w = WORKLOADS[name]
+    return [make_instance(w["lx"], w["ly"], w["R"], w["chi"], w["h"], w["seed"] + m,
+                          mixing=w["mixing"], name=f"{name}[{m}]") for m in range(w["states"])]
 
 
 def batched_instances(seed: int = 22722, n: int = 64, chi_choices=(32, 64, 128, 256),

@@ -71,6 +71,7 @@ def lib():
         L.rtt_mixed_local_energy.argtypes = [P, P, P, I64, P, P, P]
         L.rtt_create_sum.argtypes = [ctypes.POINTER(_Desc), I32, P, ctypes.POINTER(P)]
         L.rtt_dual_solve.argtypes = [I32, P, P, P, P, P]
+        L.rtt_dual_step.argtypes = [P, I32, P, P, I64, I64, I64, P, P, P, P]
         L.rtt_mcmc_sweep.argtypes = [P, P, P, I64, I64, I64, I32, I32, P, P, P]
         L.rtt_observables.argtypes = [P, P, I32, I64, P, I64, ctypes.POINTER(_Stats), P]
         L.rtt_mcmc_uniforms.argtypes = [U64, I64, P, P, P]
@@ -134,6 +135,28 @@ def dual_solve(Ht, St):
     _check(lib().rtt_dual_solve(M, Ht.ctypes.data, St.ctypes.data, re.ctypes.data, im.ctypes.data,
                                 c.ctypes.data), "rtt_dual_solve")
     return re + 1j * im, c
+
+
+def dual_step(handles, spins, states, sweep: int, e_mixed=None, ratio=None, n_accept=None,
+              chain0: int = 0, stream=None):
+    """rtt_dual_step for M RTT objects: spins/states/n_accept lists of device
+    tensors [B][N] uint8, [B][2] int64, [B] int64; e_mixed, ratio [M][M][B] float64."""
+    M = len(handles)
+    B = spins[0].shape[0]
+    for m in range(M):
+        _dev_check(spins[m], torch.uint8, (B, handles[m].n), "spins")
+        _dev_check(states[m], torch.int64, (B, 2), "state")
+    for t, nm in ((e_mixed, "e_mixed"), (ratio, "ratio")):
+        if t is not None:
+            _dev_check(t, torch.float64, (M, M, B), nm)
+    H = (ctypes.c_void_p * M)(*[h._h.value for h in handles])
+    S = (ctypes.c_void_p * M)(*[_ptr(x).value for x in spins])
+    T = (ctypes.c_void_p * M)(*[_ptr(x).value for x in states])
+    A = (ctypes.c_void_p * M)(*[(_ptr(x).value if x is not None else None)
+                                for x in (n_accept or [None] * M)])
+    _check(lib().rtt_dual_step(H, M, S, T, B, int(chain0), int(sweep), _ptr(e_mixed), _ptr(ratio),
+                               A if n_accept is not None else None, _stream(stream)),
+           "rtt_dual_step")
 
 
 def _check(status: int, where: str):

@@ -212,3 +212,41 @@ def test_gram_schmidt_states_on_gpu():
     base.close()
     for mn in news:
         mn.close()
+
+
+@pytest.mark.parametrize("prec,lx,chi", [("fp64", 3, 8), ("fp16x3", 6, 64)])
+def test_dual_step_equals_separate_calls(prec, lx, chi):
+    """rtt_dual_step (measurements on the second stream beside the sweeps) gives
+    bit for bit what rtt_mixed_local_energy on the entering configurations and
+    then one rtt_mcmc_sweep per state give on one stream."""
+    rtt = _rtt()
+    states = _pair(lx, 2, chi, (81, 82, 83))
+    M, B, n = 3, 300, lx * lx
+    hs = [rtt.RTT(s, prec, seed=700 + k) for k, s in enumerate(states)]
+    sp0 = [torch.from_numpy(inputs.initial_spins(110 + k, B, n)).cuda() for k in range(M)]
+    st0 = [h.log_amplitudes(x)[2] for h, x in zip(hs, sp0)]
+    # separate calls
+    sp1 = [x.clone() for x in sp0]
+    st1 = [x.clone() for x in st0]
+    e1 = torch.empty((M, M, B), dtype=torch.float64, device="cuda")
+    r1 = torch.empty((M, M, B), dtype=torch.float64, device="cuda")
+    acc1 = [torch.zeros(B, dtype=torch.int64, device="cuda") for _ in range(M)]
+    for a in range(M):
+        for b in range(M):
+            e, r = hs[a].mixed_local_energy(hs[b], sp1[a])
+            e1[a, b], r1[a, b] = e, r
+        hs[a].mcmc_sweep(sp1[a], st1[a], 5, 1, n_accept=acc1[a])
+    # one dual step
+    sp2 = [x.clone() for x in sp0]
+    st2 = [x.clone() for x in st0]
+    e2 = torch.empty((M, M, B), dtype=torch.float64, device="cuda")
+    r2 = torch.empty((M, M, B), dtype=torch.float64, device="cuda")
+    acc2 = [torch.zeros(B, dtype=torch.int64, device="cuda") for _ in range(M)]
+    rtt.dual_step(hs, sp2, st2, 5, e2, r2, acc2)
+    torch.cuda.synchronize()
+    assert torch.equal(e1, e2) and torch.equal(r1, r2)
+    for a in range(M):
+        assert torch.equal(sp1[a], sp2[a]) and torch.equal(st1[a], st2[a])
+        assert torch.equal(acc1[a], acc2[a])
+    for h in hs:
+        h.close()
