@@ -105,11 +105,12 @@ void free_scratch(rtt_s *h) {
 }
 
 size_t scratch_bytes_for(const rtt_s *h, int64_t B) {
-    const size_t eb = h->elem_bytes();
-    const size_t stack = (size_t)B * h->N * h->chip * eb + (size_t)B * h->N * 4;
+    const size_t per = h->chip * h->elem_bytes() + 4;  // one environment entry and its exponent
+    // left (N entries) and right (nr entries) stacks, for the energy and for the sampler
+    const size_t stacks = 2 * (size_t)B * (h->N + h->nr) * per;
     const size_t rows = (size_t)B * (h->N + 1) * 16;
     const size_t snap = (size_t)B * h->N;
-    return 4 * stack + rows + 2 * snap + (size_t)B * sizeof(rtt_chain_state);
+    return stacks + rows + 2 * snap + (size_t)B * sizeof(rtt_chain_state);
 }
 
 rtt_status ensure_scratch(rtt_s *h, int64_t B) {
@@ -120,14 +121,15 @@ rtt_status ensure_scratch(rtt_s *h, int64_t B) {
     const size_t nv = (size_t)B * h->N;
     API_CUDA(cudaMalloc(&h->d_lstack, nv * h->chip * eb), "scratch l-stack");
     API_CUDA(cudaMalloc((void **)&h->d_lexp, nv * 4), "scratch l-exp");
-    API_CUDA(cudaMalloc(&h->d_rstack, nv * h->chip * eb), "scratch r-stack");
-    API_CUDA(cudaMalloc((void **)&h->d_rexp, nv * 4), "scratch r-exp");
+    const size_t nvr = (size_t)B * h->nr;  // right stacks: nr entries per chain
+    API_CUDA(cudaMalloc(&h->d_rstack, nvr * h->chip * eb), "scratch r-stack");
+    API_CUDA(cudaMalloc((void **)&h->d_rexp, nvr * 4), "scratch r-exp");
     API_CUDA(cudaMalloc((void **)&h->d_rows_mant, (size_t)B * (h->N + 1) * 8), "scratch rows");
     API_CUDA(cudaMalloc((void **)&h->d_rows_exp, (size_t)B * (h->N + 1) * 8), "scratch rows");
     API_CUDA(cudaMalloc(&h->d_sw_lstack, nv * h->chip * eb), "scratch sweep l-stack");
     API_CUDA(cudaMalloc((void **)&h->d_sw_lexp, nv * 4), "scratch sweep l-exp");
-    API_CUDA(cudaMalloc(&h->d_sw_rstack, nv * h->chip * eb), "scratch sweep r-stack");
-    API_CUDA(cudaMalloc((void **)&h->d_sw_rexp, nv * 4), "scratch sweep r-exp");
+    API_CUDA(cudaMalloc(&h->d_sw_rstack, nvr * h->chip * eb), "scratch sweep r-stack");
+    API_CUDA(cudaMalloc((void **)&h->d_sw_rexp, nvr * 4), "scratch sweep r-exp");
     API_CUDA(cudaMalloc((void **)&h->d_snap[0], nv), "scratch spin snapshot");
     API_CUDA(cudaMalloc((void **)&h->d_snap[1], nv), "scratch spin snapshot");
     API_CUDA(cudaMalloc((void **)&h->d_amp, (size_t)B * sizeof(rtt_chain_state)), "scratch amplitudes");
@@ -136,7 +138,13 @@ rtt_status ensure_scratch(rtt_s *h, int64_t B) {
 }
 
 SimtArgs simt_args(const rtt_s *h) {
-    return SimtArgs{h->d_A, h->d_AT, h->d_bl, h->d_br, h->d_q, h->N, h->L, h->R, h->chip};
+    SimtArgs a{h->d_A, h->d_AT, h->d_bl, h->d_br, h->d_q, h->N, h->L, h->R, h->chip};
+    if (!h->periodic) {
+        a.p = h->d_path;
+        a.last = h->d_last;
+        a.kmin = h->kmin;
+    }
+    return a;
 }
 
 rtt_status check_handle(rtt_handle h) {
@@ -311,9 +319,14 @@ rtt_status rtt_create(const rtt_desc *d, rtt_handle *out) {
             return fail(RTT_ERR_UNSUPPORTED, "rtt_create: first N sites are not a permutation");
         pos[d->path[j]] = j;
     }
+    bool periodic = true;
     for (int k = N; k < L; ++k)
-        if (d->path[k] != d->path[k % N])
-            return fail(RTT_ERR_UNSUPPORTED, "rtt_create: path is not periodic with period N");
+        if (d->path[k] != d->path[k % N]) periodic = false;
+    // last site of every spin, and the first site the right stacks must hold
+    std::vector<int32_t> last(N, -1);
+    for (int k = 0; k < L; ++k) last[d->path[k]] = k;
+    int kmin = L;
+    for (int i = 0; i < N; ++i) kmin = std::min(kmin, last[i] + 1);
     const size_t nt = (size_t)L * 2 * chi * chi;
     for (size_t t = 0; t < nt; ++t)
         if (!isfinite(d->tensors[t])) return fail(RTT_ERR_NUMERIC, "rtt_create: non-finite tensor entry");
@@ -321,6 +334,9 @@ rtt_status rtt_create(const rtt_desc *d, rtt_handle *out) {
         if (!isfinite(d->b_left[a]) || !isfinite(d->b_right[a]))
             return fail(RTT_ERR_NUMERIC, "rtt_create: non-finite boundary entry");
     const bool tensor_core = d->precision == RTT_BF16X3 || d->precision == RTT_FP16X3;
+    if (tensor_core && !periodic)
+        return fail(RTT_ERR_UNSUPPORTED,
+                    "rtt_create: BF16X3/FP16X3 need a periodic path (an ordering repeated R times)");
     if (tensor_core && !tc_supported_chi(chi))
         return fail(RTT_ERR_UNSUPPORTED, "rtt_create: BF16X3/FP16X3 need chi in {64,128}");
 
@@ -335,6 +351,9 @@ rtt_status rtt_create(const rtt_desc *d, rtt_handle *out) {
     h->chi = chi;
     h->chip = padded_chi(chi);
     h->n_bonds = d->n_bonds;
+    h->periodic = periodic;
+    h->kmin = kmin;
+    h->nr = L - kmin + 1;
     h->precision = d->precision;
     h->J = d->J;
     h->h = d->h;
@@ -353,6 +372,12 @@ rtt_status rtt_create(const rtt_desc *d, rtt_handle *out) {
     std::vector<int32_t> q(d->path, d->path + N);
     if ((s = upload(q, (void **)&h->d_q, "rtt_create: path")) != RTT_OK) return cleanup(s);
     if ((s = upload(pos, (void **)&h->d_pos, "rtt_create: positions")) != RTT_OK) return cleanup(s);
+    if (!periodic) {
+        std::vector<int32_t> path(d->path, d->path + L);
+        if ((s = upload(path, (void **)&h->d_path, "rtt_create: path")) != RTT_OK) return cleanup(s);
+        if ((s = upload(last, (void **)&h->d_last, "rtt_create: last sites")) != RTT_OK)
+            return cleanup(s);
+    }
     std::vector<int32_t> bonds(d->bonds, d->bonds + 2 * d->n_bonds);
     h->bonds_host = bonds;
     if (bonds.empty()) bonds.push_back(0);
@@ -400,6 +425,8 @@ rtt_status rtt_destroy(rtt_handle h) {
     cudaFree(h->d_q);
     cudaFree(h->d_pos);
     cudaFree(h->d_bonds);
+    cudaFree(h->d_path);
+    cudaFree(h->d_last);
     cudaFree(h->d_A);
     cudaFree(h->d_AT);
     cudaFree(h->d_bl);

@@ -461,6 +461,8 @@ rtt_status rtt_batch_create(const rtt_desc *descs, int32_t n, const int64_t *cha
         rtt_desc d = descs[i];
         d.device = dev;
         rtt_status s = rtt_create(&d, &b->h[i]);
+        if (s == RTT_OK && !b->h[i]->periodic)
+            s = bfail(RTT_ERR_UNSUPPORTED, "rtt_batch_create: periodic paths only");
         if (s == RTT_OK && b->h[i]->chip < 32) {
             rtt_destroy(b->h[i]);
             b->h[i] = nullptr;

@@ -25,6 +25,12 @@ struct rtt_s {
     int32_t *d_q = nullptr;       // [N]    q[j] = path[j] (proposal order)
     int32_t *d_pos = nullptr;     // [N]    pos[i] = j with q[j] = i
     int32_t *d_bonds = nullptr;   // [n_bonds][2]
+    // general (non-periodic) paths: site -> spin, last site of each spin, and
+    // the first site the right stack holds (kmin) with its entry count nr
+    bool periodic = true;
+    int32_t *d_path = nullptr;    // [L]
+    int32_t *d_last = nullptr;    // [N]
+    int kmin = 0, nr = 0;
     std::vector<int32_t> bonds_host;  // the same on the host (lattice checks)
     void *d_A = nullptr;          // [L][2][chip][chip]  A_k[s][a][b]   (double or float)
     void *d_AT = nullptr;         // [L][2][chip][chip]  A_k[s][b][a]
@@ -80,6 +86,9 @@ struct SimtArgs {
     const void *A, *AT, *bl, *br;
     const int32_t *q;
     int N, L, R, chip;
+    const int32_t *p = nullptr;     // general path [L] (nullptr: periodic)
+    const int32_t *last = nullptr;  // general path: last site of each spin [N]
+    int kmin = 0;                   // general path: first site of the right stack
 };
 
 #define RTT_DECLARE_SIMT(SUFFIX)                                                                   \

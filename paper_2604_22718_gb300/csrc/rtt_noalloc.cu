@@ -96,6 +96,9 @@ extern "C" rtt_status rtt_local_energy_noalloc(rtt_handle h, const uint8_t *spin
     if (h->precision != RTT_FP64 && h->precision != RTT_FP32)
         return noalloc_fail(RTT_ERR_UNSUPPORTED,
                             "rtt_local_energy_noalloc: only FP64 and FP32 handles are supported");
+    if (!h->periodic)
+        return noalloc_fail(RTT_ERR_UNSUPPORTED,
+                            "rtt_local_energy_noalloc: only periodic paths are supported");
     const NoallocLayout lay = layout_for(h, B);
     if (lay.total > RTT_NOALLOC_SCRATCH_BYTES) {
         const NoallocLayout one = layout_for(h, 1);

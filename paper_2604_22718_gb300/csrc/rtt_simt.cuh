@@ -10,8 +10,12 @@
 // use the transposed tensors with the same code.  After every site the row
 // is rescaled by 2^-e, e = floor(log2 max|v|) (exact), and e is summed.
 //
-// Periodic paths only: site k carries spin q[k mod N]; spin q[j] lives on
-// sites j, j+N, ..., j+(R-1)N, so its flip touches exactly those sites.
+// Periodic paths (the fast kernels): site k carries spin q[k mod N]; spin
+// q[j] lives on sites j, j+N, ..., j+(R-1)N, so its flip touches exactly
+// those sites.  General paths (Sec. 2.2.1: the replicas may visit the spins in
+// different orders, e.g. sigma^V + sigma^H + sigma^D + sigma^D'): site k
+// carries spin p[k]; the first N sites visit every spin once (proposal order);
+// spin i's flip touches the sites k with p[k] = i, the last of them last[i].
 #pragma once
 
 #include "rtt_internal.cuh"
@@ -117,6 +121,10 @@ struct KArgs {
     const void *A, *AT, *bl, *br;
     const int32_t *q;
     int N, L, R;
+    // general paths only (p == nullptr for a periodic path)
+    const int32_t *p;     // [L] spin of site k
+    const int32_t *last;  // [N] last site of spin i
+    int kmin;             // right stack entry e holds r_{kmin+e}; e = L-kmin is b_R
 };
 
 // ---------------------------------------------------------------------------
@@ -267,7 +275,7 @@ __global__ void __launch_bounds__(256) k_chain_init(KArgs a, const uint8_t *__re
     int64_t E = 0;
     int t = 0;
     for (int k = 0; k < a.L; ++k) {
-        const int sp = __ldg(s + __ldg(a.q + t));
+        const int sp = __ldg(s + __ldg(a.p ? a.p + k : a.q + t));
         O::vecmat(site<T, CHI>(A, k, sp), v, v, gl);
         E += O::renorm(v);
         if (++t == a.N) t = 0;
@@ -388,6 +396,187 @@ __global__ void __launch_bounds__(256) k_sweep(KArgs a, uint8_t *__restrict__ sp
 }
 
 // ---------------------------------------------------------------------------
+// General paths.  Right environments r_k = A_k ... A_{L-1} b_R for k >= kmin
+// (kmin = 1 + the smallest last site of a spin), from the current spins, one
+// group per chain: entry e holds r_{kmin+e}, entry L-kmin is b_R.
+// ---------------------------------------------------------------------------
+template <typename T, int CHI>
+__global__ void __launch_bounds__(256) k_right_env_gen(KArgs a, const uint8_t *__restrict__ spins,
+                                                       int64_t B, T *__restrict__ rstack,
+                                                       int32_t *__restrict__ rexp) {
+    using O = RowOps<T, CHI>;
+    const int lane = threadIdx.x & 31, gl = lane % O::G;
+    const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / O::G;
+    const bool active = c0 < B;
+    const int64_t c = active ? c0 : B - 1;
+    const int nr = a.L - a.kmin + 1;
+    const uint8_t *s = spins + c * a.N;
+    T *rst = rstack + (size_t)c * nr * CHI;
+    int32_t *rex = rexp + (size_t)c * nr;
+    const T *AT = (const T *)a.AT;
+    T r[O::NQ];
+    O::load((const T *)a.br, r, gl);
+    int32_t E = 0;
+    if (active) {
+        O::store(rst + (size_t)(nr - 1) * CHI, r, gl);
+        if (gl == 0) rex[nr - 1] = 0;
+    }
+    for (int k = a.L - 1; k >= a.kmin; --k) {
+        O::vecmat(site<T, CHI>(AT, k, __ldg(s + __ldg(a.p + k))), r, r, gl);
+        E += O::renorm(r);
+        if (active) {
+            O::store(rst + (size_t)(k - a.kmin) * CHI, r, gl);
+            if (gl == 0) rex[k - a.kmin] = E;
+        }
+    }
+}
+
+// Rows on a general path: group (c, j), j in [0, N].  j < N flips spin
+// i = p[j] (first site j): l_{j-1} . A_j[s'] ... A_last[i][s'] . r_{last[i]+1};
+// j = N: psi(s) = l_{N-1} . A_N ... A_{L-1} . b_R.  The groups of a warp share
+// j, hence the loop length.
+template <typename T, int CHI>
+__global__ void __launch_bounds__(256) k_rows_gen(KArgs a, const uint8_t *__restrict__ spins,
+                                                  int64_t B, const T *__restrict__ lstack,
+                                                  const int32_t *__restrict__ lexp,
+                                                  const T *__restrict__ rstack,
+                                                  const int32_t *__restrict__ rexp,
+                                                  double *__restrict__ rows_mant,
+                                                  int64_t *__restrict__ rows_exp) {
+    using O = RowOps<T, CHI>;
+    constexpr int RPW = Geo<CHI>::RPW;
+    const int lane = threadIdx.x & 31, gl = lane % O::G;
+    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / O::G;
+    const int64_t n_cb = (B + RPW - 1) / RPW;
+    const int64_t total = n_cb * (a.N + 1) * RPW;
+    const int64_t gg = g0 < total ? g0 : total - 1;
+    const int r_in = (int)(gg % RPW);
+    const int j = (int)((gg / RPW) % (a.N + 1));
+    const int64_t c0 = (gg / RPW / (a.N + 1)) * RPW + r_in;
+    const bool active = g0 < total && c0 < B;
+    const int64_t c = c0 < B ? c0 : B - 1;
+    const int64_t g = c * (a.N + 1) + j;
+    const uint8_t *s = spins + c * a.N;
+    const T *A = (const T *)a.A;
+    const int nr = a.L - a.kmin + 1;
+    const int i = (j < a.N) ? __ldg(a.p + j) : -1;
+    T u[O::NQ];
+    int64_t E;
+    if (j == 0) {
+        O::load((const T *)a.bl, u, gl);
+        E = 0;
+    } else {
+        O::load(lstack + ((size_t)c * a.N + (j - 1)) * CHI, u, gl);
+        E = lexp[(size_t)c * a.N + (j - 1)];
+    }
+    const int end = (j < a.N) ? __ldg(a.last + i) : a.L - 1;
+    for (int k = j; k <= end; ++k) {
+        const int pk = __ldg(a.p + k);
+        const int sp = __ldg(s + pk) ^ ((pk == i) ? 1 : 0);
+        O::vecmat(site<T, CHI>(A, k, sp), u, u, gl);
+        E += O::renorm(u);
+    }
+    const int e = end + 1 - a.kmin;  // r_{end+1}; b_R for j = N
+    T r[O::NQ];
+    O::load(rstack + ((size_t)c * nr + e) * CHI, r, gl);
+    E += rexp[(size_t)c * nr + e];
+    double m = O::dot(u, r);
+    normalize_scalar(m, E);
+    if (active && gl == 0) {
+        rows_mant[g] = m;
+        rows_exp[g] = E;
+    }
+}
+
+// Metropolis sweeps on a general path, one group per chain.  Proposal j flips
+// spin i = p[j]: the row runs from l_{j-1} (kept as in k_sweep) through
+// last[i]; the right part r_{last[i]+1} is rebuilt from b_R with the current
+// spins (sites after last[i] may carry spins flipped earlier in the sweep), as
+// the oracle's from-scratch flip amplitude does.
+template <typename T, int CHI>
+__global__ void __launch_bounds__(256) k_sweep_gen(KArgs a, uint8_t *__restrict__ spins,
+                                                   rtt_chain_state *__restrict__ state, int64_t B,
+                                                   int64_t chain0, int64_t sweep0, int n_sweeps,
+                                                   uint64_t seed, int64_t *__restrict__ n_accept) {
+    using O = RowOps<T, CHI>;
+    extern __shared__ uint8_t sm_spins[];
+    const int lane = threadIdx.x & 31, gl = lane % O::G;
+    const int grp = threadIdx.x / O::G;
+    const int64_t c0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / O::G;
+    const bool active = c0 < B;
+    const int64_t c = active ? c0 : B - 1;
+    uint8_t *s = sm_spins + (size_t)grp * a.N;
+    for (int i = gl; i < a.N; i += O::G) s[i] = spins[c * a.N + i];
+    __syncwarp();
+    const T *A = (const T *)a.A;
+    const T *AT = (const T *)a.AT;
+    double pm = state[c].mant;
+    int64_t pe = state[c].exp2;
+    int64_t acc_count = 0;
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+        T l[O::NQ];
+        O::load((const T *)a.bl, l, gl);
+        int64_t El = 0;
+        for (int j = 0; j < a.N; ++j) {
+            const int i = __ldg(a.p + j);
+            const int si = s[i];
+            const int last = __ldg(a.last + i);
+            T u[O::NQ], keep[O::NQ];
+            O::vecmat(site<T, CHI>(A, j, si ^ 1), l, u, gl);
+            const int64_t Eu0 = El + O::renorm(u);
+            O::vecmat(site<T, CHI>(A, j, si), l, keep, gl);
+            const int64_t Ek = El + O::renorm(keep);
+            T uf[O::NQ];
+#pragma unroll
+            for (int qq = 0; qq < O::NQ; ++qq) uf[qq] = u[qq];
+            int64_t Eu = Eu0;
+            for (int k = j + 1; k <= last; ++k) {
+                const int pk = __ldg(a.p + k);
+                const int sp = s[pk] ^ ((pk == i) ? 1 : 0);
+                O::vecmat(site<T, CHI>(A, k, sp), u, u, gl);
+                Eu += O::renorm(u);
+            }
+            T r[O::NQ];
+            O::load((const T *)a.br, r, gl);
+            for (int k = a.L - 1; k > last; --k) {
+                O::vecmat(site<T, CHI>(AT, k, s[__ldg(a.p + k)]), r, r, gl);
+                Eu += O::renorm(r);
+            }
+            double m = O::dot(u, r);
+            normalize_scalar(m, Eu);
+            const double ratio = ldexp(m / pm, (int)(Eu - pe));
+            const double x = mcmc_uniform(seed, (uint64_t)(chain0 + c), (uint64_t)(sweep0 + sw),
+                                          (uint64_t)j);
+            const bool accept = x < ratio * ratio;
+            if (accept) {
+                pm = m;
+                pe = Eu;
+                ++acc_count;
+#pragma unroll
+                for (int qq = 0; qq < O::NQ; ++qq) l[qq] = uf[qq];
+                El = Eu0;
+            } else {
+#pragma unroll
+                for (int qq = 0; qq < O::NQ; ++qq) l[qq] = keep[qq];
+                El = Ek;
+            }
+            __syncwarp();
+            if (accept && gl == 0) s[i] = (uint8_t)(si ^ 1);
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+    if (active) {
+        for (int i = gl; i < a.N; i += O::G) spins[c * a.N + i] = s[i];
+        if (gl == 0) {
+            state[c].mant = pm;
+            state[c].exp2 = pe;
+            if (n_accept) n_accept[c] += acc_count;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host-side dispatch over CHI
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -402,23 +591,36 @@ struct SimtLaunch {
     static cudaError_t run(int which, const SimtArgs &sa, const void *p0, void *p1, void *p2,
                            void *p3, void *p4, void *p5, void *p6, int64_t B, int64_t i0,
                            int64_t i1, int32_t i2, uint64_t u0, cudaStream_t st) {
-        KArgs a{sa.A, sa.AT, sa.bl, sa.br, sa.q, sa.N, sa.L, sa.R};
+        KArgs a{sa.A, sa.AT, sa.bl, sa.br, sa.q, sa.N, sa.L, sa.R, sa.p, sa.last, sa.kmin};
         switch (which) {
             case 0:
                 k_left_env<T, CHI><<<(unsigned)blocks_for<CHI>(B), 256, 0, st>>>(
                     a, (const uint8_t *)p0, B, (T *)p1, (int32_t *)p2);
                 break;
             case 1:
-                k_right_env<T, CHI><<<(unsigned)blocks_for<CHI>(B), 256, 0, st>>>(
-                    a, (const uint8_t *)p0, B, (T *)p1, (int32_t *)p2);
+                if (sa.p)
+                    k_right_env_gen<T, CHI><<<(unsigned)blocks_for<CHI>(B), 256, 0, st>>>(
+                        a, (const uint8_t *)p0, B, (T *)p1, (int32_t *)p2);
+                else
+                    k_right_env<T, CHI><<<(unsigned)blocks_for<CHI>(B), 256, 0, st>>>(
+                        a, (const uint8_t *)p0, B, (T *)p1, (int32_t *)p2);
                 break;
             case 2:
+                if (sa.p) {
+                k_rows_gen<T, CHI><<<(unsigned)blocks_for<CHI>(
+                                     (B + Geo<CHI>::RPW - 1) / Geo<CHI>::RPW * (sa.N + 1) *
+                                     Geo<CHI>::RPW),
+                                 256, 0, st>>>(
+                    a, (const uint8_t *)p0, B, (const T *)p1, (const int32_t *)p2,
+                    (const T *)p3, (const int32_t *)p4, (double *)p5, (int64_t *)p6);
+                } else {
                 k_rows<T, CHI><<<(unsigned)blocks_for<CHI>(
                                      (B + Geo<CHI>::RPW - 1) / Geo<CHI>::RPW * (sa.N + 1) *
                                      Geo<CHI>::RPW),
                                  256, 0, st>>>(
                     a, (const uint8_t *)p0, B, (const T *)p1, (const int32_t *)p2,
                     (const T *)p3, (const int32_t *)p4, (double *)p5, (int64_t *)p6);
+                }
                 break;
             case 3:
                 k_chain_init<T, CHI><<<(unsigned)blocks_for<CHI>(B), 256, 0, st>>>(
@@ -432,9 +634,19 @@ struct SimtLaunch {
                                                          (int)smem);
                     if (e != cudaSuccess) return e;
                 }
-                k_sweep<T, CHI><<<(unsigned)blocks_for<CHI>(B), 256, smem, st>>>(
-                    a, (uint8_t *)p0, (rtt_chain_state *)p1, B, i0, i1, i2, u0, (T *)p2,
-                    (int32_t *)p3, (T *)p4, (int32_t *)p5, (int64_t *)p6);
+                if (sa.p) {
+                    if (smem > 48 * 1024) {
+                        cudaError_t e = cudaFuncSetAttribute(
+                            k_sweep_gen<T, CHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                        if (e != cudaSuccess) return e;
+                    }
+                    k_sweep_gen<T, CHI><<<(unsigned)blocks_for<CHI>(B), 256, smem, st>>>(
+                        a, (uint8_t *)p0, (rtt_chain_state *)p1, B, i0, i1, i2, u0, (int64_t *)p6);
+                } else {
+                    k_sweep<T, CHI><<<(unsigned)blocks_for<CHI>(B), 256, smem, st>>>(
+                        a, (uint8_t *)p0, (rtt_chain_state *)p1, B, i0, i1, i2, u0, (T *)p2,
+                        (int32_t *)p3, (T *)p4, (int32_t *)p5, (int64_t *)p6);
+                }
                 break;
             }
             default:

@@ -16,6 +16,7 @@ of Sec. 2.2.1):
 * ``batched64``   64 instances, Lx in {4,6,8,12}, R in {2,3,4},
                   chi in {32,64,128,256}, h ~ U[2.5,3.5]
 * ``dual_6x6``    3 states of the plain_6x6 kind (dual Monte Carlo)
+* ``vhdd_6x6``    6x6, path sigma^V + sigma^H + sigma^D + sigma^D' (R = 4, L = 144), chi = 64
 
 All randomness comes from ``numpy.random.Generator(PCG64(seed))``.
 """
@@ -25,7 +26,8 @@ import dataclasses
 import numpy as np
 
 __all__ = [
-    "RTTInstance", "snake_order", "open_bonds", "periodic_path",
+    "RTTInstance", "snake_order", "column_snake", "diagonal_snake", "ordering", "path_sum",
+    "make_path_instance", "open_bonds", "periodic_path",
     "gaussian_tensors", "mixed_tensors", "make_instance", "initial_spins",
     "WORKLOADS", "workload", "workload_states", "batched_instances", "made_init_weights", "ferro_chain_instance",
 ]
@@ -65,6 +67,57 @@ def snake_order(lx: int, ly: int) -> np.ndarray:
         xs = range(lx) if y % 2 == 0 else range(lx - 1, -1, -1)
         out.extend(y * lx + x for x in xs)
     return np.asarray(out, dtype=np.int32)
+
+
+def column_snake(lx: int, ly: int) -> np.ndarray:
+    """Column by column (sigma^V): column x walked with increasing y for even x,
+    decreasing y for odd x; site index i = y*lx + x."""
+    out = []
+    for x in range(lx):
+        ys = range(ly) if x % 2 == 0 else range(ly - 1, -1, -1)
+        out.extend(y * lx + x for y in ys)
+    return np.asarray(out, dtype=np.int32)
+
+
+def diagonal_snake(lx: int, ly: int, anti: bool = False) -> np.ndarray:
+    """Diagonal by diagonal (sigma^D: x + y constant; sigma^D' with anti=True:
+    x - y constant), diagonal number d walked with increasing x for even d,
+    decreasing x for odd d."""
+    out = []
+    n_diag = lx + ly - 1
+    for d in range(n_diag):
+        cells = []
+        for x in range(lx):
+            y = (d - x) if not anti else (x - d + ly - 1)
+            if 0 <= y < ly:
+                cells.append(y * lx + x)
+        out.extend(cells if d % 2 == 0 else cells[::-1])
+    return np.asarray(out, dtype=np.int32)
+
+
+def ordering(name: str, lx: int, ly: int) -> np.ndarray:
+    """One of the orderings of Sec. 4: 'H' (rows), 'V' (columns), 'D', 'Dp'."""
+    return {"H": lambda: snake_order(lx, ly), "V": lambda: column_snake(lx, ly),
+            "D": lambda: diagonal_snake(lx, ly), "Dp": lambda: diagonal_snake(lx, ly, anti=True)}[name]()
+
+
+def path_sum(orders) -> np.ndarray:
+    """sigma^1 + sigma^2 + ...: the orderings one after the other (Sec. 2.2.1)."""
+    return np.concatenate([np.asarray(o, dtype=np.int32) for o in orders])
+
+
+def make_path_instance(lx: int, ly: int, names, chi: int, h: float, seed: int,
+                       mixing: bool = True, J: float = 1.0, name: str = "") -> RTTInstance:
+    """An RTT on the path sigma^{names[0]} + sigma^{names[1]} + ... (one replica
+    per ordering), tensors as make_instance."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    path = path_sum([ordering(n, lx, ly) for n in names])
+    L = path.shape[0]
+    t = mixed_tensors(rng, L, chi) if mixing else gaussian_tensors(rng, L, chi)
+    ones = np.ones(chi, dtype=np.float64)
+    return RTTInstance(n_spins=lx * ly, path=path, tensors=np.ascontiguousarray(t),
+                       b_left=ones.copy(), b_right=ones.copy(), bonds=open_bonds(lx, ly),
+                       J=float(J), h=float(h), name=name, lx=lx, ly=ly, R=len(names))
 
 
 def open_bonds(lx: int, ly: int) -> np.ndarray:
@@ -135,6 +188,9 @@ WORKLOADS = {
     "plain_6x6":     dict(lx=6, ly=6, R=2, chi=64, h=3.0, mixing=True, chains=4096, sweeps=2000, seed=22720),
     "prec_10x10":    dict(lx=10, ly=10, R=3, chi=128, h=3.04, mixing=True, chains=16384, sweeps=1000, seed=22721),
     "learned_16x16": dict(lx=16, ly=16, R=2, chi=128, h=3.044, mixing=True, chains=8192, sweeps=128, seed=22723),
+    # the path sigma^V + sigma^H + sigma^D + sigma^D' of Sec. 4 (four replicas), FP32/FP64 sampler
+    "vhdd_6x6":      dict(lx=6, ly=6, R=4, chi=64, h=3.0, mixing=True, chains=4096, sweeps=100, seed=22729,
+                          orderings=("V", "H", "D", "Dp")),
     # dual Monte Carlo: M = 3 states of the plain_6x6 kind (seeds seed, seed+1, seed+2)
     "dual_6x6":      dict(lx=6, ly=6, R=2, chi=64, h=3.0, mixing=True, chains=4096, sweeps=100, seed=22726, states=3),
 }
@@ -143,6 +199,9 @@ WORKLOADS = {
 def workload(name: str, **override) -> RTTInstance:
     w = dict(WORKLOADS[name])
     w.update(override)
+    if "orderings" in w:
+        return make_path_instance(w["lx"], w["ly"], w["orderings"], w["chi"], w["h"], w["seed"],
+                                  mixing=w["mixing"], name=name)
     return make_instance(w["lx"], w["ly"], w["R"], w["chi"], w["h"], w["seed"],
                          mixing=w["mixing"], name=name)
 

@@ -75,8 +75,9 @@ def test_create_rejects_bad_descriptions_before_any_cuda_call(lib, mutate, expec
     prec = 0
     if mutate == "path_out_of_range":
         path[3] = 9
-    elif mutate == "not_periodic":
+    elif mutate == "not_periodic":          # general paths: SIMT precisions only
         path[10], path[11] = path[11], path[10]
+        prec = 3
     elif mutate == "not_permutation":
         path[1] = path[0]
         path[10] = path[9]
@@ -93,6 +94,8 @@ def test_create_rejects_bad_descriptions_before_any_cuda_call(lib, mutate, expec
     assert h.value is None
     lib.rtt_last_error.restype = ctypes.c_char_p
     assert lib.rtt_last_error().startswith(b"rtt_create")
+    if mutate == "not_periodic":
+        assert b"periodic" in lib.rtt_last_error()
 
 
 def test_null_handle_is_an_argument_error(lib):
