@@ -160,8 +160,25 @@ def measured_traffic(args, kernel, B):
 
 
 # ---------------------------------------------------------------- algorithmic work
-def site_steps(N: int, R: int, kernel: str) -> int:
-    """Row-site vector-matrix products one chain needs in one launch."""
+def site_steps(N: int, R: int, kernel: str, path=None) -> int:
+    """Row-site vector-matrix products one chain needs in one launch (periodic
+    path; pass the path for a general one)."""
+    if path is not None and not np.array_equal(path, np.tile(path[:N], len(path) // N)):
+        L = len(path)
+        first = {int(i): k for k, i in reversed(list(enumerate(path)))}
+        last = {int(i): k for k, i in enumerate(path)}
+        kmin = min(last.values()) + 1
+        if kernel == "simt_sweep":      # per proposal j: sites j..last, then r from b_R
+            return sum(L - j for j in range(N))
+        if kernel == "simt_rows":
+            return sum(last[i] - first[i] + 1 for i in range(N)) + (L - N)
+        if kernel == "simt_right_env":
+            return L - kmin
+        if kernel == "simt_left_env":
+            return N
+        if kernel == "simt_chain_init":
+            return L
+        return 0
     span = (R - 1) * N + 1
     if kernel in ("simt_sweep", "tc_sweep"):
         return (N - 1) + N * span + N            # right env + flip rows + l_j update
@@ -324,7 +341,7 @@ def run_ours(args):
     roof = None
     if dom:
         launches, ms = prof[dom]
-        flops = 2.0 * inst.chi * inst.chi * site_steps(N, R, dom) * B
+        flops = 2.0 * inst.chi * inst.chi * site_steps(N, R, dom, inst.path) * B
         achieved = flops / (ms / launches / 1e3) / 1e12
         if args.precision in ("bf16x3", "fp16x3"):
             # fp16 and bf16 dense tensor rates are equal on this part
@@ -338,7 +355,7 @@ def run_ours(args):
                                 f"lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz")
         mult = 6.0 if bound == "tensor" else 1.0
         executed = achieved * mult
-        step_flops = sum(2.0 * inst.chi * inst.chi * site_steps(N, R, k) * B * v[0]
+        step_flops = sum(2.0 * inst.chi * inst.chi * site_steps(N, R, k, inst.path) * B * v[0]
                          for k, v in prof.items()) / K
         step_tf = step_flops / (total_ms / K / 1e3) / 1e12
         roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
