@@ -26,10 +26,16 @@
  *   - Amplitudes are kept as psi = mant * 2^exp2 with |mant| in [1,2); the
  *     exponent is an exact integer sum of per-site power-of-two rescalings, so
  *     no train length over- or underflows.
- *   - Supported paths: periodic ones, path[k] = path[k mod N] with
- *     path[0..N-1] a permutation of the N spins (an ordering repeated R times,
- *     L = R N -- the path sum of Sec. 2.2.1 with equal summands).  Metropolis
- *     proposal j of a sweep flips spin path[j] (systematic scan).
+ *   - Paths: L = R N sites with path[0..N-1] a permutation of the N spins;
+ *     Metropolis proposal j of a sweep flips spin path[j] (systematic scan).
+ *     Periodic paths, path[k] = path[k mod N] (an ordering repeated R times),
+ *     run everywhere.  General paths (the replicas visit the spins in
+ *     different orders, e.g. sigma^V + sigma^H + sigma^D + sigma^D' -- the
+ *     path sums of Sec. 2.2.1) run on FP64/FP32 handles, and on BF16X3/FP16X3
+ *     handles for amplitudes and local energies and, with chi = 64 and R >= 2,
+ *     for sweeps; the batched form and rtt_local_energy_noalloc need periodic
+ *     paths.  Each flip row of a general path spans its spin's first to last
+ *     site, and a sweep rebuilds the part after the last site per proposal.
  *   - Errors: argument errors are detected before anything is launched and
  *     leave all outputs untouched; CUDA errors (including asynchronous ones of
  *     earlier launches on the device) return RTT_ERR_CUDA.  rtt_last_error()
@@ -108,12 +114,13 @@ typedef struct {
     int32_t pad;
 } rtt_stats;
 
-/* Create a handle: validates the description (periodic path, finite tensors,
+/* Create a handle: validates the description (path as above, finite tensors,
  * bond indices in range), copies every host array to the device in the
  * requested precision and returns the handle in *out.  The handle owns its
  * device copies and its scratch; the caller keeps ownership of `desc` and its
- * arrays.  Unsupported combinations (non-periodic path, chi > 256, BF16X3 or
- * FP16X3 with chi not in {64,128}) return RTT_ERR_UNSUPPORTED. */
+ * arrays.  Unsupported combinations (first N sites not a permutation,
+ * chi > 256, BF16X3 or FP16X3 with chi not in {64,128}) return
+ * RTT_ERR_UNSUPPORTED. */
 rtt_status rtt_create(const rtt_desc *desc, rtt_handle *out);
 
 /* Release every device allocation of the handle (synchronises its device). */

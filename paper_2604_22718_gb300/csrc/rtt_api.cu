@@ -334,9 +334,6 @@ rtt_status rtt_create(const rtt_desc *d, rtt_handle *out) {
         if (!isfinite(d->b_left[a]) || !isfinite(d->b_right[a]))
             return fail(RTT_ERR_NUMERIC, "rtt_create: non-finite boundary entry");
     const bool tensor_core = d->precision == RTT_BF16X3 || d->precision == RTT_FP16X3;
-    if (tensor_core && !periodic)
-        return fail(RTT_ERR_UNSUPPORTED,
-                    "rtt_create: BF16X3/FP16X3 need a periodic path (an ordering repeated R times)");
     if (tensor_core && !tc_supported_chi(chi))
         return fail(RTT_ERR_UNSUPPORTED, "rtt_create: BF16X3/FP16X3 need chi in {64,128}");
 

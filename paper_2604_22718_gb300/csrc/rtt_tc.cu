@@ -94,6 +94,12 @@ struct Args {
     rtt_chain_state *state;
     float *tmp;
     int32_t *tmp_exp;
+    // path: general paths give the spin of every site (nullptr: periodic,
+    // site k carries q[k mod N]); last[i] is spin i's last site; the right
+    // stacks hold r_{kmin+e} at entry e < nr (entry nr-1 = L - kmin is b_R)
+    const int32_t *path;
+    const int32_t *last;
+    int kmin, nr;
     int64_t chain0, sweep0;
     int n_sweeps;
     uint64_t seed;
@@ -485,12 +491,19 @@ __device__ __forceinline__ void cursor_next(Cursor &c, const Args &a, int span) 
     }
 }
 
+// Last site of flip row j (j < N flips the spin of site j; j = N is psi(s)).
+__device__ __forceinline__ int row_end(const Args &a, int j) {
+    if (j >= a.N) return a.L - 1;
+    if (a.path) return __ldg(a.last + __ldg(a.path + j));
+    return j + (a.R - 1) * a.N;
+}
+
 template <int MODE>
 __device__ __forceinline__ long long n_steps_of(const Args &a, int j) {
     const int span = (a.R - 1) * a.N + 1;
-    if (MODE == M_ROWS) return (j < a.N) ? span : (long long)(a.R - 1) * a.N;
+    if (MODE == M_ROWS) return row_end(a, j) - j + 1;
     if (MODE == M_LEFT) return a.N;
-    if (MODE == M_RIGHT) return a.N - 1;
+    if (MODE == M_RIGHT) return a.L - a.kmin;
     if (MODE == M_INIT) return a.L;
     return (long long)a.n_sweeps * ((a.N - 1) + (long long)a.N * span);
 }
@@ -522,7 +535,7 @@ __global__ void __launch_bounds__(NT, 1)
     const int j = (MODE == M_ROWS) ? (int)blockIdx.y : 0;
     const int N = a.N;
     const int span = (a.R - 1) * N + 1;
-    const int rbase = (a.R - 1) * N + 1;
+    const int rbase = a.kmin;  // first site the right stack holds
     const long long total_steps = n_steps_of<MODE>(a, j);
     const long long total_atoms = total_steps * C::KA;
 
@@ -537,7 +550,7 @@ __global__ void __launch_bounds__(NT, 1)
         fence_barrier_init();
     }
     for (int k = tid; k < a.L; k += NT)
-        tab[k] = ((uint32_t)__ldg(a.q + (k % N)) & 0xffffu) |
+        tab[k] = ((uint32_t)__ldg(a.path ? a.path + k : a.q + (k % N)) & 0xffffu) |
                  ((uint32_t)(__ldg(a.cexp + k) & 0xffff) << 16);
     // spin bits: word (i, warp) holds bit (row & 31) = s_i of that row's chain
     for (int i = 0; i < N; ++i) {
@@ -566,8 +579,8 @@ __global__ void __launch_bounds__(NT, 1)
     } else if (MODE == M_RIGHT || MODE == M_SWEEP) {
         load_vec<CHI>(a.br, v);
         if (active) {
-            store_vec<CHI>(a.rstack + ((size_t)c * N + (N - 1)) * CHI, v);
-            a.rexp[(size_t)c * N + (N - 1)] = 0;
+            store_vec<CHI>(a.rstack + ((size_t)c * a.nr + (a.nr - 1)) * CHI, v);
+            a.rexp[(size_t)c * a.nr + (a.nr - 1)] = 0;
         }
         if (MODE == M_SWEEP) {
             pm = a.state[c].mant;
@@ -684,8 +697,8 @@ __global__ void __launch_bounds__(NT, 1)
             acc_select<CHI>(tw, spin(sk), v);
             E += renorm<CHI>(v) - ck;
             if (active) {
-                store_vec<CHI>(a.rstack + ((size_t)c * N + (k - rbase)) * CHI, v);
-                a.rexp[(size_t)c * N + (k - rbase)] = (int32_t)E;
+                store_vec<CHI>(a.rstack + ((size_t)c * a.nr + (k - rbase)) * CHI, v);
+                a.rexp[(size_t)c * a.nr + (k - rbase)] = (int32_t)E;
             }
             write_next = (t + 1 < total_steps);
         } else if (MODE == M_INIT) {
@@ -697,8 +710,8 @@ __global__ void __launch_bounds__(NT, 1)
                 acc_select<CHI>(tw, spin(sk), v);
                 E += renorm<CHI>(v) - ck;
                 if (active) {
-                    store_vec<CHI>(a.rstack + ((size_t)c * N + (k - rbase)) * CHI, v);
-                    a.rexp[(size_t)c * N + (k - rbase)] = (int32_t)E;
+                    store_vec<CHI>(a.rstack + ((size_t)c * a.nr + (k - rbase)) * CHI, v);
+                    a.rexp[(size_t)c * a.nr + (k - rbase)] = (int32_t)E;
                 }
                 if (cc.tt == N - 2) {  // next: proposal 0 starts from b_L
                     load_vec<CHI>(a.bl, v);
@@ -733,8 +746,8 @@ __global__ void __launch_bounds__(NT, 1)
                     write_next = true;
                 } else {
                     // Metropolis decision of proposal jj (spin iq)
-                    const float *r = a.rstack + ((size_t)c * N + jj) * CHI;
-                    int64_t Ep = E + a.rexp[(size_t)c * N + jj];
+                    const float *r = a.rstack + ((size_t)c * a.nr + jj) * CHI;
+                    int64_t Ep = E + a.rexp[(size_t)c * a.nr + jj];
                     double m = dot<CHI>(v, r);
                     normalize_scalar(m, Ep);
                     const double ratio = ldexp(m / pm, (int)(Ep - pe));
@@ -781,9 +794,9 @@ __global__ void __launch_bounds__(NT, 1)
     // ---------------- final contraction / outputs
     if (!aborted) {
         if (MODE == M_ROWS) {
-            const int rq = (j < N) ? j : N - 1;
-            int64_t Ep = E + a.rexp[(size_t)c * N + rq];
-            double m = dot<CHI>(v, a.rstack + ((size_t)c * N + rq) * CHI);
+            const int rq = row_end(a, j) + 1 - a.kmin;  // r_{end+1}; b_R for j = N
+            int64_t Ep = E + a.rexp[(size_t)c * a.nr + rq];
+            double m = dot<CHI>(v, a.rstack + ((size_t)c * a.nr + rq) * CHI);
             normalize_scalar(m, Ep);
             if (active) {
                 a.rows_mant[c * (N + 1) + j] = m;
@@ -859,7 +872,11 @@ __device__ __forceinline__ void named_arrive(int id, int n) {
 __device__ __forceinline__ void named_sync(int id, int n) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
-template <bool F16>
+// GEN: a general path.  Proposal j's row covers sites j..L-1 (spin p[j]
+// flipped wherever it sits); the left tile walks the first half from l_{j-1},
+// the right tile the second half backwards from b_R with the current spins,
+// so no right environment is kept.
+template <bool F16, bool GEN>
 __global__ void __launch_bounds__(SP_THREADS, 1)
     k_tc_sweep2(const __grid_constant__ CUtensorMap map, const Args a) {
     constexpr int CHI = 64;
@@ -884,8 +901,10 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = a.N, L = a.L;
     const int span = (a.R - 1) * N + 1;
-    const int nL = span / 2, nR = span - nL;
     const int rbase = (a.R - 1) * N + 1;
+    // sites of proposal j's left and right half-rows
+    auto nL_of = [&](int j) -> int { return (GEN ? L - j : span) / 2; };
+    auto nR_of = [&](int j) -> int { return (GEN ? L - j : span) - nL_of(j); };
     const int m = tid & 127;  // row of the epilogue threads
     const int64_t c_raw = (int64_t)blockIdx.x * NT + m;
     const bool active = c_raw < a.B;
@@ -899,7 +918,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         fence_barrier_init();
     }
     for (int k = tid; k < L; k += SP_THREADS)
-        tab[k] = ((uint32_t)__ldg(a.q + (k % N)) & 0xffffu) |
+        tab[k] = ((uint32_t)__ldg(GEN ? a.path + k : a.q + (k % N)) & 0xffffu) |
                  ((uint32_t)(__ldg(a.cexp + k) & 0xffff) << 16);
     if (warp < 4) {
         for (int i = 0; i < N; ++i) {
@@ -957,12 +976,13 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         };
         for (int sw = 0; sw < a.n_sweeps; ++sw) {
             if (X == 1) {
-                for (int u = 0; u < N - 1; ++u) issue(128u);
+                if (!GEN)
+                    for (int u = 0; u < N - 1; ++u) issue(128u);
                 for (int j = 0; j < N; ++j)
-                    for (int t = 0; t < nR; ++t) issue(128u);
+                    for (int t = 0; t < nR_of(j); ++t) issue(128u);
             } else {
                 for (int j = 0; j < N; ++j)
-                    for (int t = 0; t < nL; ++t) issue(t == 0 ? 256u : 0u);
+                    for (int t = 0; t < nL_of(j); ++t) issue(t == 0 ? 256u : 0u);
             }
         }
     } else if (warp == 10) {
@@ -985,13 +1005,14 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                 issued[X] = g + 1;
             };
             for (int sw = 0; sw < a.n_sweeps; ++sw) {
-                if (XX == 1)
+                if (XX == 1 && !GEN)
                     for (int u = 0; u < N - 1; ++u) load(1, L - 1 - u);
                 for (int j = 0; j < N; ++j) {
                     if (XX == 0)
-                        for (int t = 0; t < nL; ++t) load(0, j + t);
+                        for (int t = 0; t < nL_of(j); ++t) load(0, j + t);
                     else
-                        for (int t = 0; t < nR; ++t) load(1, (a.R - 1) * N + j - t);
+                        for (int t = 0; t < nR_of(j); ++t)
+                            load(1, GEN ? L - 1 - t : (a.R - 1) * N + j - t);
                 }
             }
         }
@@ -1011,6 +1032,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
             for (int j = 0; j < N; ++j) {
                 const int iq = site_spin(j);
                 const int si = spin(iq);
+                const int nL = nL_of(j);
                 double x = 0.0;
                 for (int t = 0; t < nL; ++t) {
                     const int k = j + t;
@@ -1087,7 +1109,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         const uint32_t tw = tq + 128u, ta = tq + 448u;
         float v[CHI];
         load_vec<CHI>(a.br, v);
-        if (active) {
+        if (active && !GEN) {
             store_vec<CHI>(a.rstack + ((size_t)c * N + (N - 1)) * CHI, v);
             a.rexp[(size_t)c * N + (N - 1)] = 0;
         }
@@ -1097,7 +1119,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         long long nd = 0;
         for (int sw = 0; sw < a.n_sweeps; ++sw) {
             E = 0;
-            for (int u = 0; u < N - 1; ++u) {  // right environment of the last block
+            for (int u = 0; u < (GEN ? 0 : N - 1); ++u) {  // right environment of the last block
                 const int k = L - 1 - u;
                 bwait(done_bar(1), (uint32_t)(nd++ & 1));
                 tc_after();
@@ -1115,9 +1137,13 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
             }
             for (int j = 0; j < N; ++j) {
                 const int iq = site_spin(j);
-                if (j > 0) E = a.rexp[(size_t)c * N + j];
+                const int nR = nR_of(j);
+                if (GEN)
+                    E = 0;
+                else if (j > 0)
+                    E = a.rexp[(size_t)c * N + j];
                 for (int t = 0; t < nR; ++t) {
-                    const int k = (a.R - 1) * N + j - t;
+                    const int k = GEN ? L - 1 - t : (a.R - 1) * N + j - t;
                     bwait(done_bar(1), (uint32_t)(nd++ & 1));
                     tc_after();
                     __syncwarp();
@@ -1137,7 +1163,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                 // the next half-row's start does not depend on this decision
                 const bool more = (j + 1 < N) || (sw + 1 < a.n_sweeps);
                 if (more) {
-                    if (j + 1 < N) {
+                    if (j + 1 < N && !GEN) {
                         load_vec<CHI>(a.rstack + ((size_t)c * N + (j + 1)) * CHI, v);
                     } else {
                         load_vec<CHI>(a.br, v);
@@ -1222,6 +1248,10 @@ tcd::Args make_args(rtt_s *h, int64_t B) {
     a.rexp = h->d_rexp;
     a.rows_mant = h->d_rows_mant;
     a.rows_exp = h->d_rows_exp;
+    a.path = h->periodic ? nullptr : h->d_path;
+    a.last = h->d_last;
+    a.kmin = h->kmin;
+    a.nr = h->nr;
     a.err = p->d_err;
     a.wait_limit = 4000000000LL;  // ~2 s at 2 GHz
     return a;
@@ -1422,20 +1452,25 @@ rtt_status tc_sweep(rtt_s *h, uint8_t *spins, rtt_chain_state *state, int64_t B,
     a.n_accept = n_accept;
     cudaError_t e;
     prof_begin(h, KID_TC_SWEEP, st);
+    if (!h->periodic && !(p->chi == 64 && h->R >= 2 && h->N >= 2)) {
+        prof_end(h, KID_TC_SWEEP, st);
+        rtt_set_error("rtt_mcmc_sweep: tensor-core sweeps on a general path need chi = 64 and "
+                      "at least two replicas");
+        return RTT_ERR_UNSUPPORTED;
+    }
     if (p->chi == 64 && h->R >= 2 && h->N >= 2) {
         // split-row sweep: two half-row tiles per CTA
         const size_t smem = tcd::sweep2_smem(h->N, h->L);
-        if (p->f16) {
-            e = cudaFuncSetAttribute(tcd::k_tc_sweep2<true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess)
-                tcd::k_tc_sweep2<true><<<tiles(B), tcd::SP_THREADS, smem, st>>>(p->map, a);
-        } else {
-            e = cudaFuncSetAttribute(tcd::k_tc_sweep2<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess)
-                tcd::k_tc_sweep2<false><<<tiles(B), tcd::SP_THREADS, smem, st>>>(p->map, a);
-        }
+        auto go = [&](auto kern) {
+            cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+            if (err == cudaSuccess) kern<<<tiles(B), tcd::SP_THREADS, smem, st>>>(p->map, a);
+            return err;
+        };
+        if (h->periodic)
+            e = p->f16 ? go(tcd::k_tc_sweep2<true, false>) : go(tcd::k_tc_sweep2<false, false>);
+        else
+            e = p->f16 ? go(tcd::k_tc_sweep2<true, true>) : go(tcd::k_tc_sweep2<false, true>);
         if (e == cudaSuccess) e = cudaGetLastError();
     } else {
         e = launch_chi<tcd::M_SWEEP>(p, a, dim3(tiles(B)), st);

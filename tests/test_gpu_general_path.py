@@ -107,8 +107,83 @@ def test_mixed_energy_between_periodic_and_general_paths_bit_exact():
 
 def test_general_path_rejected_where_unsupported():
     rtt = _rtt()
-    inst = inputs.make_path_instance(6, 6, ("V", "H"), 64, 3.0, seed=38)
-    with pytest.raises(rtt.RTTError):
-        rtt.RTT(inst, "fp16x3")
+    inst = inputs.make_path_instance(4, 4, ("V", "H"), 128, 3.0, seed=38)
+    with rtt.RTT(inst, "fp16x3") as m:          # chi = 128: no split-row sweep
+        sg = torch.from_numpy(inputs.initial_spins(1, 8, 16)).cuda()
+        _, _, st = m.log_amplitudes(sg)
+        with pytest.raises(rtt.RTTError):
+            m.mcmc_sweep(sg, st, 0, 1)
     with pytest.raises(rtt.RTTError):
         rtt.RTTBatch([inputs.make_path_instance(6, 6, ("V", "H"), 32, 3.0, seed=39)], [8])
+
+
+# ---------------------------------------------------------------- tensor cores
+
+UB16 = 2.0 ** -11
+
+
+def _eps_site(chi):
+    return 3 * UB16 ** 2 + chi * U32
+
+
+@pytest.mark.parametrize("lx,ly,names,chi,B", [(6, 6, ("V", "H", "D", "Dp"), 64, 300),
+                                               (4, 4, ("H", "D", "V"), 128, 140)])
+def test_fp16x3_general_path_amplitudes_and_energies(lx, ly, names, chi, B):
+    """Split-precision amplitudes within eps_site (sum kappa_k + kappa_fin) of
+    the oracle; every flip ratio within |r| eps_site (K(s) + K(s^(i))); the mean
+    local energy within 1e-4 relative (the metric's gate)."""
+    rtt = _rtt()
+    inst = inputs.make_path_instance(lx, ly, names, chi, 3.0, seed=61)
+    o = orc.Oracle(inst)
+    n = lx * ly
+    spins = inputs.initial_spins(62, B, n)
+    la_o = o.log_amplitudes(spins)[0]
+    nc = 24
+    e_o, r_o = o.local_energies(spins[:nc], with_ratios=True, threads=16)
+    with rtt.RTT(inst, "fp16x3") as m:
+        sp = torch.from_numpy(spins).cuda()
+        la = m.log_amplitudes(sp)[0].cpu().numpy()
+        e, r = m.local_energy(sp[:nc].contiguous(), with_ratios=True)
+        torch.cuda.synchronize()
+    e, r = e.cpu().numpy(), r.cpu().numpy()
+    eps = _eps_site(chi)
+    K = o.amplitude_cond(spins)
+    assert np.all(np.abs(la - la_o) <= eps * (K[:, 0] + K[:, 2]))
+    flipped = np.repeat(spins[:nc], n, axis=0)
+    flipped[np.arange(nc * n), np.tile(np.arange(n), nc)] ^= 1
+    Kf = o.amplitude_cond(flipped)
+    Kf = (Kf[:, 0] + Kf[:, 2]).reshape(nc, n)
+    bound = np.abs(r_o) * eps * ((K[:nc, 0] + K[:nc, 2])[:, None] + Kf)
+    assert np.all(np.abs(r - r_o) <= bound)
+    rel_mean = abs(e.mean() - e_o.mean()) / max(abs(e_o.mean()), np.mean(np.abs(e_o)))
+    assert rel_mean <= 1e-4, rel_mean
+
+
+def test_fp16x3_general_path_sweep_follows_oracle():
+    """The general split-row sweep (chi = 64, sigma^V + sigma^H + sigma^D +
+    sigma^D'): one sweep over three row tiles takes the oracle's decisions on at
+    least 90 % of the chains; tracked amplitudes stay those of the spins; the
+    measured trace is the standalone energy of the entering configurations."""
+    rtt = _rtt()
+    inst = inputs.workload("vhdd_6x6")
+    o = orc.Oracle(inst)
+    B = 300
+    s0 = inputs.initial_spins(63, B, 36)
+    so = s0.copy()
+    mo, eo = o.init_chains(so)
+    o.mcmc(17, so, mo, eo, 0, 1, record=False, threads=16)
+    with rtt.RTT(inst, "fp16x3", seed=17) as m:
+        sg = torch.from_numpy(s0.copy()).cuda()
+        _, _, st = m.log_amplitudes(sg)
+        e0 = m.local_energy(sg)
+        tr = torch.empty((1, B), dtype=torch.float64, device="cuda")
+        m.mcmc_sweep(sg, st, 0, 1, 1, tr)
+        la_track = (rtt.state_exp(st).double() * math.log(2) +
+                    torch.log(rtt.state_mant(st).abs())).cpu().numpy()
+        la_now = m.log_amplitudes(sg)[0].cpu().numpy()
+        torch.cuda.synchronize()
+    same = np.all(sg.cpu().numpy() == so, axis=1)
+    assert same.mean() >= 0.9, same.mean()
+    d = np.abs(la_track - la_now)
+    assert np.median(d) < 1e-5 and np.mean(d <= 1e-3) >= 0.99
+    assert torch.equal(tr[0], e0)
