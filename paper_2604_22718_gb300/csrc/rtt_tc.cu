@@ -283,10 +283,10 @@ __device__ __forceinline__ void acc_select(uint32_t tw, int sel, float (&v)[CHI]
     }
 }
 
-// Rescale by an exact power of two so that max|v| lies in [1,2); returns the
-// exponent taken out.  Eight independent partial maxima keep the dependency
-// chain short.
-template <int CHI>
+// Rescale by an exact power of two so that max|v| lies in [1,2) (or leave
+// the row alone while max|v| is in [1, 2^8), see below); returns the exponent
+// taken out.  Eight independent partial maxima keep the dependency chain short.
+template <int CHI, bool LAZY = true>
 __device__ __forceinline__ int renorm(float (&v)[CHI]) {
     float m[8];
 #pragma unroll
@@ -295,8 +295,15 @@ __device__ __forceinline__ int renorm(float (&v)[CHI]) {
     for (int i = 8; i < CHI; ++i) m[i & 7] = fmaxf(m[i & 7], fabsf(v[i]));
     const float mx = fmaxf(fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3])),
                            fmaxf(fmaxf(m[4], m[5]), fmaxf(m[6], m[7])));
-    if (!(mx > 0.f) || !isfinite(mx)) return 0;
-    const int e = rttd::exponent_of(mx);
+    const bool usable = (mx > 0.f) && isfinite(mx);
+    const int e = usable ? rttd::exponent_of(mx) : 0;
+    // A row whose max lies in [1, 2^8) can keep its scale: its 16-bit split is
+    // inside FP16's normal range with full precision relative to the max, and
+    // the next site's accumulator (FP32) is rescaled again before its split
+    // unless it too lands in the window.  The warp skips the rescale when all
+    // of its rows can (all lanes of the warp call this together).
+    if (LAZY && __all_sync(FULL, !usable || (e >= 0 && e < 8))) return 0;
+    if (!usable) return 0;
     if (rttd::pow2_normal(0.f, -e)) {  // one exact multiply per entry
         const float sc = rttd::pow2(0.f, -e);
 #pragma unroll
@@ -856,6 +863,7 @@ __global__ void __launch_bounds__(NT, 1)
 // program without issuing work (waits return at once), so the named barriers
 // always meet.
 constexpr int SP_THREADS = 352;
+constexpr bool SP_LAZY = true;  // split-row sweep: lazy renormalisation
 constexpr uint32_t SP_TCOLS = 512;
 
 constexpr int SP_HAND = 64 * NT * 4;  // right half-rows, [64][128] floats
@@ -1042,10 +1050,10 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                     const int sk = site_spin(k);
                     if (t == 0) {
                         acc_select<CHI>(tw0, si ^ 1, v);
-                        E = El + renorm<CHI>(v) - site_cexp(k);
+                        E = El + renorm<CHI, SP_LAZY>(v) - site_cexp(k);
                     } else {
                         acc_select<CHI>(tw, spin(sk) ^ (sk == iq ? 1 : 0), v);
-                        E += renorm<CHI>(v) - site_cexp(k);
+                        E += renorm<CHI, SP_LAZY>(v) - site_cexp(k);
                     }
                     if (t + 1 < nL) {
                         write_A_tmem<CHI, F16>(ta, v);
@@ -1084,7 +1092,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                 tc_after();
                 // l_j = l_{j-1} A_j[s_j] with the decided spin, from the kept accumulator
                 acc_select<CHI>(tw0, si ^ (accept ? 1 : 0), v);
-                El += renorm<CHI>(v) - site_cexp(j);
+                El += renorm<CHI, SP_LAZY>(v) - site_cexp(j);
                 const bool more = (j + 1 < N) || (sw + 1 < a.n_sweeps);
                 if (j + 1 < N) {
                     write_A_tmem<CHI, F16>(ta, v);
@@ -1125,7 +1133,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                 tc_after();
                 __syncwarp();
                 acc_select<CHI>(tw, spin(site_spin(k)), v);
-                E += renorm<CHI>(v) - site_cexp(k);
+                E += renorm<CHI, SP_LAZY>(v) - site_cexp(k);
                 if (active) {
                     store_vec<CHI>(a.rstack + ((size_t)c * N + (k - rbase)) * CHI, v);
                     a.rexp[(size_t)c * N + (k - rbase)] = (int32_t)E;
@@ -1149,7 +1157,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                     __syncwarp();
                     const int sk = site_spin(k);
                     acc_select<CHI>(tw, spin(sk) ^ (sk == iq ? 1 : 0), v);
-                    E += renorm<CHI>(v) - site_cexp(k);
+                    E += renorm<CHI, SP_LAZY>(v) - site_cexp(k);
                     if (t + 1 < nR) {
                         write_A_tmem<CHI, F16>(ta, v);
                         publish(1);
