@@ -1215,7 +1215,7 @@ constexpr int SP4_THREADS = 608;
 
 inline size_t sweep4_smem(int N, int L) {
     return 1024 + 2 * (size_t)NS * Cfg<64>::STAGE + SP_HAND + 256 + (size_t)16 * N +
-           (size_t)4 * L + 4 * NT + (size_t)2 * 2 * 2 * NT * 4 + (size_t)2 * 2 * NT * 8;
+           (size_t)4 * L + 4 * NT + 16 + (size_t)2 * 2 * 2 * NT * 4 + (size_t)2 * 2 * NT * 8;
 }
 
 // Store 16 columns at t0 and 16 at t1 of this warp's 32 TMEM lanes, then wait.
@@ -1293,8 +1293,9 @@ __global__ void __launch_bounds__(SP4_THREADS, 1)
     uint32_t *bits = (uint32_t *)(base + 2 * NS * C::STAGE + SP_HAND + 256);
     uint32_t *tab = bits + 4 * a.N;
     int32_t *rexp_s = (int32_t *)(tab + a.L);
-    float *xmax = (float *)(rexp_s + NT);              // [tile][parity][half][row]
-    double *xdot = (double *)(xmax + 2 * 2 * 2 * NT);  // [parity][half][row]
+    // exchange slots, 16-byte aligned whatever L is
+    float *xmax = (float *)(((uintptr_t)(rexp_s + NT) + 15) & ~(uintptr_t)15);  // [tile][parity][half][row]
+    double *xdot = (double *)(xmax + 2 * 2 * 2 * NT);                          // [parity][half][row]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = a.N, L = a.L;
@@ -1607,6 +1608,445 @@ __global__ void __launch_bounds__(SP4_THREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, SP_TCOLS);
 }
 
+
+// ------------------------------------------------------------------ split-row sweep on a CTA pair
+// As k_tc_sweep4, with the two half-row tiles on the two CTAs of a cluster
+// (rank 0 left, rank 1 right), i.e. on two SMs with a tensor pipe each.  Per
+// proposal the right CTA stores its finished half-row (and exponent) into the
+// left CTA's shared memory and arrives on the left's `hand` mbarrier; the left
+// decides, stores the flip bits into the right CTA's spin bits and arrives on
+// the right's `decision` mbarrier (release/acquire at cluster scope).  Every
+// wait is bounded; both CTAs meet in a cluster barrier before they exit.
+// Roles per CTA: warps 0-7 epilogue (two per TMEM lane quadrant), warp 8 MMA
+// issuer, warp 9 TMA loads.  TMEM (left): accumulator [0,128), first-site
+// accumulator [128,256), A hi/lo [256,320); (right): accumulator [0,128), A
+// hi/lo [128,192).
+constexpr int SPC_THREADS = 320;
+
+inline size_t sweepc_smem(int N, int L) {
+    return 1024 + (size_t)NS * Cfg<64>::STAGE + SP_HAND + 256 + (size_t)16 * N + (size_t)4 * L +
+           4 * NT + 16 + (size_t)2 * 2 * NT * 4 + (size_t)2 * 2 * NT * 8;
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t peer_addr(uint32_t addr, uint32_t rank) {
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(addr), "r"(rank));
+    return out;
+}
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, float a, float b, float c, float d) {
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b),
+                 "f"(c), "f"(d)
+                 : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+                 : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, long long limit) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait_cluster(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+
+template <bool F16, bool GEN>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
+    k_tc_sweep_pair(const __grid_constant__ CUtensorMap map, const Args a) {
+    constexpr int CHI = 64;
+    using C = Cfg<CHI, F16>;
+    extern __shared__ uint8_t smem_raw[];
+    // the dynamic shared memory starts at the same offset in both CTAs, so the
+    // 1024-byte alignment below gives the same layout in both
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t ring0 = sa(base);
+    float *hand = (float *)(base + NS * C::STAGE);  // [128 rows][64], float4 chunks swizzled
+    uint64_t *bars = (uint64_t *)(base + NS * C::STAGE + SP_HAND);
+    const uint32_t bar0 = sa(bars);
+    // bars: full[NS], empty[NS], done, hand (left), decision (right)
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (NS + s); };
+    const uint32_t done_bar = bar0 + 8u * (2 * NS);
+    const uint32_t hand_bar = bar0 + 8u * (2 * NS + 1);
+    const uint32_t dec_bar = bar0 + 8u * (2 * NS + 2);
+    uint32_t *tmem_slot = (uint32_t *)(bars + 8);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    long long *issued = (long long *)(bars + 10);
+    uint32_t *bits = (uint32_t *)(base + NS * C::STAGE + SP_HAND + 256);
+    uint32_t *tab = bits + 4 * a.N;
+    int32_t *rexp_s = (int32_t *)(tab + a.L);
+    // exchange slots, 16-byte aligned whatever L is
+    float *xmax = (float *)(((uintptr_t)(rexp_s + NT) + 15) & ~(uintptr_t)15);  // [parity][half][row]
+    double *xdot = (double *)(xmax + 2 * 2 * NT);                              // [parity][half][row]
+
+    const uint32_t rank = cluster_rank();
+    const int X = (int)rank;  // 0 left, 1 right
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = a.N, L = a.L;
+    const int span = (a.R - 1) * N + 1;
+    auto nL_of = [&](int j) -> int { return (GEN ? L - j : span) / 2; };
+    auto nR_of = [&](int j) -> int { return (GEN ? L - j : span) - nL_of(j); };
+    const int q = warp & 3, hf = (warp >> 2) & 1;
+    const int m = q * 32 + lane;
+    const int64_t c_raw = (int64_t)(blockIdx.x >> 1) * NT + m;
+    const bool active = c_raw < a.B;
+    const int64_t c = active ? c_raw : a.B - 1;
+    const uint32_t tcols = X == 0 ? 512u : 256u;
+
+    if (warp == 0) tmem_alloc(sa(tmem_slot), tcols);
+    if (tid == 0) {
+        for (int i = 0; i < 2 * NS + 1; ++i) mbar_init(bar0 + 8u * i, 1);
+        mbar_init(hand_bar, 8);  // one arrival per right epilogue warp
+        mbar_init(dec_bar, 8);   // one arrival per left epilogue warp
+        *abort_flag = 0;
+        issued[0] = 0;
+        fence_barrier_init();
+    }
+    for (int k = tid; k < L; k += SPC_THREADS)
+        tab[k] = ((uint32_t)__ldg(GEN ? a.path + k : a.q + (k % N)) & 0xffffu) |
+                 ((uint32_t)(__ldg(a.cexp + k) & 0xffff) << 16);
+    if (warp < 4) {
+        for (int i = 0; i < N; ++i) {
+            const uint32_t w = __ballot_sync(FULL, a.spins_in[c * N + i] != 0);
+            if (lane == 0) bits[i * 4 + warp] = w;
+        }
+    }
+    tc_before();
+    cluster_sync_all();  // barriers initialised in both CTAs before any remote arrive
+    tc_after();
+    const uint32_t tmem = *tmem_slot;
+    auto spin = [&](int i) -> int { return (int)((bits[i * 4 + q] >> lane) & 1u); };
+    auto site_spin = [&](int k) -> int { return (int)(tab[k] & 0xffffu); };
+    auto site_cexp = [&](int k) -> int { return (int)(int16_t)(tab[k] >> 16); };
+    auto fail_now = [&]() {
+        atomicOr(a.err, 1);
+        *abort_flag = 1;
+    };
+    auto bwait = [&](uint32_t bar, uint32_t parity) -> bool {
+        if (*abort_flag) return false;
+        if (!mbar_wait(bar, parity, a.wait_limit)) {
+            fail_now();
+            return false;
+        }
+        return true;
+    };
+    auto bwait_cluster = [&](uint32_t bar, uint32_t parity) -> bool {
+        if (*abort_flag) return false;
+        if (!mbar_wait_cluster(bar, parity, a.wait_limit)) {
+            fail_now();
+            return false;
+        }
+        return true;
+    };
+    auto publish = [&]() {
+        tc_before();
+        named_arrive(2, 2 * NT + 32);
+    };
+    int xpar = 0;
+    auto pair_max = [&](float mine) -> float {
+        float *slot = xmax + (xpar * 2) * NT;
+        slot[hf * NT + m] = mine;
+        named_sync(4 + q, 64);
+        const float other = slot[(hf ^ 1) * NT + m];
+        xpar ^= 1;
+        return fmaxf(mine, other);
+    };
+    int dpar = 0;
+    auto pair_dot = [&](double mine) -> double {
+        double *slot = xdot + (dpar * 2) * NT;
+        slot[hf * NT + m] = mine;
+        named_sync(4 + q, 64);
+        const double d0 = slot[m], d1 = slot[NT + m];
+        dpar ^= 1;
+        return d0 + d1;
+    };
+    const uint32_t acc_col = 0u, t0_col = 128u, a_col = X == 0 ? 256u : 128u;
+
+    if (warp == 8) {
+        // ---------------------------------------------------------- MMA issuer
+        long long g = 0;
+        auto issue = [&](uint32_t dcol) {
+            named_sync(2, 2 * NT + 32);
+            if (lane == 0) {
+                const int s = (int)(g % NS);
+                if (bwait(full_bar(s), (uint32_t)((g / NS) & 1))) {
+                    tc_after();
+                    const uint32_t ahi = tmem + a_col, alo = ahi + 32u;
+                    const uint32_t b_hi = ring0 + (uint32_t)s * C::STAGE, b_lo = b_hi + C::BOX;
+                    const uint32_t d = tmem + dcol;
+#pragma unroll
+                    for (int kb = 0; kb < 4; ++kb) {
+                        const uint32_t o = (uint32_t)(kb * 32), ka = (uint32_t)(kb * 8);
+                        mma_f16_ts(d, ahi + ka, sdesc(b_hi + o), C::IDESC, kb != 0 ? 1u : 0u);
+                        mma_f16_ts(d, ahi + ka, sdesc(b_lo + o), C::IDESC, 1u);
+                        mma_f16_ts(d, alo + ka, sdesc(b_hi + o), C::IDESC, 1u);
+                    }
+                    mma_commit(empty_bar(s));
+                    mma_commit(done_bar);
+                }
+            }
+            ++g;
+            __syncwarp();
+        };
+        for (int sw = 0; sw < a.n_sweeps; ++sw) {
+            if (X == 1) {
+                if (!GEN)
+                    for (int u = 0; u < N - 1; ++u) issue(acc_col);
+                for (int j = 0; j < N; ++j)
+                    for (int t = 0; t < nR_of(j); ++t) issue(acc_col);
+            } else {
+                for (int j = 0; j < N; ++j)
+                    for (int t = 0; t < nL_of(j); ++t) issue(t == 0 ? t0_col : acc_col);
+            }
+        }
+    } else if (warp == 9) {
+        // ---------------------------------------------------------- TMA loads
+        if (lane == 0) {
+            long long n = 0;
+            auto load = [&](int k) {
+                const long long g = n++;
+                const int s = (int)(g % NS);
+                if (*abort_flag) return;
+                if (g >= NS && !bwait(empty_bar(s), (uint32_t)(((g / NS) - 1) & 1))) return;
+                const int y_hi = ((X * 2 + 0) * L + k) * 2 * CHI;
+                const int y_lo = ((X * 2 + 1) * L + k) * 2 * CHI;
+                const uint32_t dst = ring0 + (uint32_t)s * C::STAGE;
+                mbar_expect_tx(full_bar(s), (uint32_t)C::STAGE);
+                tma_load_2d(dst, &map, 0, y_hi, full_bar(s));
+                tma_load_2d(dst + C::BOX, &map, 0, y_lo, full_bar(s));
+                issued[0] = g + 1;
+            };
+            for (int sw = 0; sw < a.n_sweeps; ++sw) {
+                if (X == 1 && !GEN)
+                    for (int u = 0; u < N - 1; ++u) load(L - 1 - u);
+                for (int j = 0; j < N; ++j) {
+                    if (X == 0)
+                        for (int t = 0; t < nL_of(j); ++t) load(j + t);
+                    else
+                        for (int t = 0; t < nR_of(j); ++t) load(GEN ? L - 1 - t : (a.R - 1) * N + j - t);
+                }
+            }
+        }
+    } else if (X == 0) {
+        // ---------------------------------------------------------- left epilogue
+        const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
+        const uint32_t tw = tq + acc_col, tw0 = tq + t0_col, ta = tq + a_col;
+        const uint32_t peer_dec = peer_addr(dec_bar, 1u);
+        float v[32];
+        load_vec<32>(a.bl + 32 * hf, v);
+        write_A_half<F16>(ta, hf, v);
+        publish();
+        double pm = a.state[c].mant;
+        int64_t pe = a.state[c].exp2, acc_count = 0;
+        int64_t El = 0, E = 0;
+        long long nd = 0, np = 0;
+        for (int sw = 0; sw < a.n_sweeps; ++sw) {
+            for (int j = 0; j < N; ++j) {
+                const int iq = site_spin(j);
+                const int si = spin(iq);
+                const int nL = nL_of(j);
+                double x = 0.0;
+                float mx_keep = 0.f, mx_flip = 0.f;
+                for (int t = 0; t < nL; ++t) {
+                    const int k = j + t;
+                    bwait(done_bar, (uint32_t)(nd++ & 1));
+                    tc_after();
+                    __syncwarp();
+                    const int sk = site_spin(k);
+                    if (t == 0) {
+                        float vk[32];
+                        acc_select_half(tw0, hf, si, vk);
+                        acc_select_half(tw0, hf, si ^ 1, v);
+                        const float a0 = half_max(vk), a1 = half_max(v);
+                        mx_keep = pair_max(a0);
+                        mx_flip = pair_max(a1);
+                        E = El + renorm_half(v, mx_flip) - site_cexp(k);
+                    } else {
+                        acc_select_half(tw, hf, spin(sk) ^ (sk == iq ? 1 : 0), v);
+                        E += renorm_half(v, pair_max(half_max(v))) - site_cexp(k);
+                    }
+                    if (t + 1 < nL) {
+                        write_A_half<F16>(ta, hf, v);
+                        publish();
+                    }
+                    if (t == 0)
+                        x = rttd::mcmc_uniform(a.seed, (uint64_t)(a.chain0 + c),
+                                               (uint64_t)(a.sweep0 + sw), (uint64_t)j);
+                }
+                // the right half-row, from the peer CTA
+                bwait_cluster(hand_bar, (uint32_t)(np++ & 1));
+                double mm;
+                {
+                    float acc[8];
+#pragma unroll
+                    for (int p = 0; p < 8; ++p) acc[p] = 0.f;
+#pragma unroll
+                    for (int cc = 0; cc < 8; ++cc) {
+                        const int ch = hf * 8 + cc;  // float4 chunk of row m
+                        const float4 w = *reinterpret_cast<const float4 *>(
+                            hand + m * 64 + ((ch ^ (m & 15)) << 2));
+                        acc[(4 * cc) & 7] = fmaf(v[4 * cc], w.x, acc[(4 * cc) & 7]);
+                        acc[(4 * cc + 1) & 7] = fmaf(v[4 * cc + 1], w.y, acc[(4 * cc + 1) & 7]);
+                        acc[(4 * cc + 2) & 7] = fmaf(v[4 * cc + 2], w.z, acc[(4 * cc + 2) & 7]);
+                        acc[(4 * cc + 3) & 7] = fmaf(v[4 * cc + 3], w.w, acc[(4 * cc + 3) & 7]);
+                    }
+                    double part = 0.0;
+#pragma unroll
+                    for (int p = 0; p < 8; ++p) part += (double)acc[p];
+                    mm = pair_dot(part);
+                }
+                int64_t Ep = E + rexp_s[m];
+                normalize_scalar(mm, Ep);
+                const double ratio = ldexp(mm / pm, (int)(Ep - pe));
+                const bool accept = active && !*abort_flag && (x < ratio * ratio);
+                if (accept) {
+                    pm = mm;
+                    pe = Ep;
+                    ++acc_count;
+                }
+                const uint32_t flips = __ballot_sync(FULL, accept);
+                if (lane == 0 && hf == 0) {
+                    const uint32_t w = bits[iq * 4 + q] ^ flips;
+                    bits[iq * 4 + q] = w;
+                    st_cluster_u32(peer_addr(sa(bits + iq * 4 + q), 1u), w);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive_remote(peer_dec);  // the decision is with the right CTA
+                acc_select_half(tw0, hf, si ^ (accept ? 1 : 0), v);
+                El += renorm_half(v, accept ? mx_flip : mx_keep) - site_cexp(j);
+                const bool more = (j + 1 < N) || (sw + 1 < a.n_sweeps);
+                if (j + 1 < N) {
+                    write_A_half<F16>(ta, hf, v);
+                    publish();
+                }
+                if (j + 1 == N && more) {
+                    load_vec<32>(a.bl + 32 * hf, v);
+                    El = 0;
+                    write_A_half<F16>(ta, hf, v);
+                    publish();
+                }
+            }
+        }
+        if (active && !*abort_flag && hf == 0) {
+            a.state[c].mant = pm;
+            a.state[c].exp2 = pe;
+            if (a.n_accept) a.n_accept[c] += acc_count;
+        }
+    } else {
+        // ---------------------------------------------------------- right epilogue
+        const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
+        const uint32_t tw = tq + acc_col, ta = tq + a_col;
+        const uint32_t peer_hand = peer_addr(hand_bar, 0u);
+        const uint32_t peer_rows = peer_addr(sa(hand), 0u);
+        const uint32_t peer_rexp = peer_addr(sa(rexp_s), 0u);
+        float v[32];
+        load_vec<32>(a.br + 32 * hf, v);
+        if (active && !GEN) {
+            store_vec<32>(a.rstack + ((size_t)c * N + (N - 1)) * CHI + 32 * hf, v);
+            if (hf == 0) a.rexp[(size_t)c * N + (N - 1)] = 0;
+        }
+        write_A_half<F16>(ta, hf, v);
+        publish();
+        int64_t E = 0;
+        long long nd = 0, ndec = 0;
+        for (int sw = 0; sw < a.n_sweeps; ++sw) {
+            E = 0;
+            for (int u = 0; u < (GEN ? 0 : N - 1); ++u) {
+                const int k = L - 1 - u;
+                bwait(done_bar, (uint32_t)(nd++ & 1));
+                tc_after();
+                __syncwarp();
+                acc_select_half(tw, hf, spin(site_spin(k)), v);
+                E += renorm_half(v, pair_max(half_max(v))) - site_cexp(k);
+                if (active) {
+                    store_vec<32>(a.rstack + ((size_t)c * N + (k - (a.R - 1) * N - 1)) * CHI + 32 * hf, v);
+                    if (hf == 0) a.rexp[(size_t)c * N + (k - (a.R - 1) * N - 1)] = (int32_t)E;
+                }
+                write_A_half<F16>(ta, hf, v);
+                publish();
+            }
+            for (int j = 0; j < N; ++j) {
+                const int iq = site_spin(j);
+                const int nR = nR_of(j);
+                if (GEN)
+                    E = 0;
+                else if (j > 0)
+                    E = a.rexp[(size_t)c * N + j];
+                for (int t = 0; t < nR; ++t) {
+                    const int k = GEN ? L - 1 - t : (a.R - 1) * N + j - t;
+                    bwait(done_bar, (uint32_t)(nd++ & 1));
+                    tc_after();
+                    __syncwarp();
+                    const int sk = site_spin(k);
+                    acc_select_half(tw, hf, spin(sk) ^ (sk == iq ? 1 : 0), v);
+                    E += renorm_half(v, pair_max(half_max(v))) - site_cexp(k);
+                    if (t + 1 < nR) {
+                        write_A_half<F16>(ta, hf, v);
+                        publish();
+                    }
+                }
+                // hand the half-row to the left CTA: row m, float4 chunks 8hf..8hf+7
+#pragma unroll
+                for (int cc = 0; cc < 8; ++cc) {
+                    const int ch = hf * 8 + cc;
+                    st_cluster_v4(peer_rows + (uint32_t)((m * 64 + ((ch ^ (m & 15)) << 2)) * 4),
+                                  v[4 * cc], v[4 * cc + 1], v[4 * cc + 2], v[4 * cc + 3]);
+                }
+                if (hf == 0) st_cluster_u32(peer_rexp + (uint32_t)(m * 4), (uint32_t)(int32_t)E);
+                __syncwarp();
+                if (lane == 0) mbar_arrive_remote(peer_hand);
+                const bool more = (j + 1 < N) || (sw + 1 < a.n_sweeps);
+                if (more) {  // the next row's first MMA does not depend on this decision
+                    if (j + 1 < N && !GEN)
+                        load_vec<32>(a.rstack + ((size_t)c * N + (j + 1)) * CHI + 32 * hf, v);
+                    else
+                        load_vec<32>(a.br + 32 * hf, v);
+                    write_A_half<F16>(ta, hf, v);
+                    publish();
+                }
+                // the decision (new spin bits) before any further epilogue
+                bwait_cluster(dec_bar, (uint32_t)(ndec++ & 1));
+            }
+        }
+    }
+    __syncthreads();
+    if (X == 0 && warp < 4 && active && !*abort_flag) {
+        for (int i = 0; i < N; ++i) a.spins_out[c * N + i] = (uint8_t)spin(i);
+    }
+    if (tid == 0 && *abort_flag) {
+        for (long long g = (issued[0] > NS ? issued[0] - NS : 0); g < issued[0]; ++g)
+            mbar_wait(full_bar((int)(g % NS)), (uint32_t)((g / NS) & 1), a.wait_limit);
+    }
+    tc_before();
+    cluster_sync_all();  // no CTA leaves while its peer may still store into it
+    tc_after();
+    if (warp == 0) tmem_dealloc(tmem, tcols);
+}
+
 }  // namespace tcd
 
 // ====================================================================== host side
@@ -1835,6 +2275,8 @@ rtt_status tc_chain_init(rtt_s *h, const uint8_t *spins, int64_t B, double *log_
 // chi = 64 sweep epilogue: one warp (k_tc_sweep2) or two warps (k_tc_sweep4)
 // per TMEM lane quadrant and tile.
 constexpr int kSweepWarpsPerQuadrant = 2;
+// chi = 64 sweep: the two half-row tiles on the two SMs of a CTA pair (cluster)
+constexpr bool kSweepOnCtaPair = true;
 
 rtt_status tc_sweep(rtt_s *h, uint8_t *spins, rtt_chain_state *state, int64_t B, int64_t chain0,
                     int64_t sweep0, int32_t n_sweeps, int64_t *n_accept, cudaStream_t st) {
@@ -1886,7 +2328,23 @@ rtt_status tc_sweep(rtt_s *h, uint8_t *spins, rtt_chain_state *state, int64_t B,
             if (err == cudaSuccess) kern<<<tiles(B), tcd::SP_THREADS, smem, st>>>(p->map, a);
             return err;
         };
-        if (kSweepWarpsPerQuadrant == 2) {
+        if (kSweepOnCtaPair) {
+            // at least 164 KB: no other CTA that allocates TMEM (a second pair CTA, a
+            // 66 KB tile kernel of the energy) fits beside a pair CTA on one SM, so
+            // no tcgen05.alloc ever waits for a CTA that waits for its cluster peer
+            const size_t smemc = std::max(tcd::sweepc_smem(h->N, h->L), (size_t)164 * 1024);
+            auto goc = [&](auto kern) {
+                cudaError_t err = cudaFuncSetAttribute(
+                    kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemc);
+                if (err == cudaSuccess)
+                    kern<<<2 * tiles(B), tcd::SPC_THREADS, smemc, st>>>(p->map, a);
+                return err;
+            };
+            if (h->periodic)
+                e = p->f16 ? goc(tcd::k_tc_sweep_pair<true, false>) : goc(tcd::k_tc_sweep_pair<false, false>);
+            else
+                e = p->f16 ? goc(tcd::k_tc_sweep_pair<true, true>) : goc(tcd::k_tc_sweep_pair<false, true>);
+        } else if (kSweepWarpsPerQuadrant == 2) {
             const size_t smem4 = tcd::sweep4_smem(h->N, h->L);
             auto go4 = [&](auto kern) {
                 cudaError_t err = cudaFuncSetAttribute(
