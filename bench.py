@@ -168,15 +168,16 @@ def site_steps(N: int, R: int, kernel: str, path=None) -> int:
         first = {int(i): k for k, i in reversed(list(enumerate(path)))}
         last = {int(i): k for k, i in enumerate(path)}
         kmin = min(last.values()) + 1
-        if kernel == "simt_sweep":      # per proposal j: sites j..last, then r from b_R
-            return sum(L - j for j in range(N))
-        if kernel == "simt_rows":
+        kind = kernel.split("_", 1)[1] if kernel.startswith(("simt_", "tc_")) else kernel
+        if kind == "sweep":             # per proposal j: sites j..L-1 (the part after the
+            return sum(L - j for j in range(N))   # spin's last site rebuilt from b_R)
+        if kind == "rows":
             return sum(last[i] - first[i] + 1 for i in range(N)) + (L - N)
-        if kernel == "simt_right_env":
+        if kind == "right_env":
             return L - kmin
-        if kernel == "simt_left_env":
+        if kind == "left_env":
             return N
-        if kernel == "simt_chain_init":
+        if kind == "chain_init":
             return L
         return 0
     span = (R - 1) * N + 1

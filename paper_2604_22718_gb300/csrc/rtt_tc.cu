@@ -1622,6 +1622,10 @@ __global__ void __launch_bounds__(SP4_THREADS, 1)
 // accumulator [128,256), A hi/lo [256,320); (right): accumulator [0,128), A
 // hi/lo [128,192).
 constexpr int SPC_THREADS = 320;
+// sites the left tile takes below half of a proposal's row; negative: more.
+// Measured on plain_6x6 (37 sites per row): -1 (19 left, 18 right) is fastest;
+// the right tile also hands its half-row over and waits for the decision.
+constexpr int kPairLeftLess = -1;
 
 inline size_t sweepc_smem(int N, int L) {
     return 1024 + (size_t)NS * Cfg<64>::STAGE + SP_HAND + 256 + (size_t)16 * N + (size_t)4 * L +
@@ -1708,7 +1712,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = a.N, L = a.L;
     const int span = (a.R - 1) * N + 1;
-    auto nL_of = [&](int j) -> int { return (GEN ? L - j : span) / 2; };
+    auto nL_of = [&](int j) -> int {
+        const int T = GEN ? L - j : span;
+        return min(T - 1, max(1, T / 2 - kPairLeftLess));
+    };
     auto nR_of = [&](int j) -> int { return (GEN ? L - j : span) - nL_of(j); };
     const int q = warp & 3, hf = (warp >> 2) & 1;
     const int m = q * 32 + lane;

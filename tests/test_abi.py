@@ -61,7 +61,7 @@ def _desc(inst, **kw):
 
 @pytest.mark.parametrize("mutate,expect", [
     ("path_out_of_range", 1),
-    ("not_periodic", 6),
+    ("tc_bad_chi", 6),
     ("not_permutation", 6),
     ("nan_tensor", 4),
     ("bad_precision", 1),
@@ -75,8 +75,8 @@ def test_create_rejects_bad_descriptions_before_any_cuda_call(lib, mutate, expec
     prec = 0
     if mutate == "path_out_of_range":
         path[3] = 9
-    elif mutate == "not_periodic":          # general paths: SIMT precisions only
-        path[10], path[11] = path[11], path[10]
+    elif mutate == "tc_bad_chi":            # FP16X3 needs chi in {64, 128}
+        path[10], path[11] = path[11], path[10]   # (a general path is accepted)
         prec = 3
     elif mutate == "not_permutation":
         path[1] = path[0]
@@ -94,8 +94,8 @@ def test_create_rejects_bad_descriptions_before_any_cuda_call(lib, mutate, expec
     assert h.value is None
     lib.rtt_last_error.restype = ctypes.c_char_p
     assert lib.rtt_last_error().startswith(b"rtt_create")
-    if mutate == "not_periodic":
-        assert b"periodic" in lib.rtt_last_error()
+    if mutate == "tc_bad_chi":
+        assert b"chi" in lib.rtt_last_error()
 
 
 def test_null_handle_is_an_argument_error(lib):
