@@ -1622,6 +1622,31 @@ __global__ void __launch_bounds__(SP4_THREADS, 1)
 // accumulator [128,256), A hi/lo [256,320); (right): accumulator [0,128), A
 // hi/lo [128,192).
 constexpr int SPC_THREADS = 320;
+
+// Float-float arithmetic for the pair sweep's Metropolis decision (GB300's FP64
+// rate is 1/64 of FP32; a warp-wide FP64 instruction costs ~64 issue cycles on
+// the decision's critical path).  two_sum is Knuth's error-free addition.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// (h, l) <- (h, l) + (h2, l2), renormalised so that |l| <= ulp(h)/2
+__device__ __forceinline__ void ff_add(float &h, float &l, float h2, float l2) {
+    float s, e;
+    two_sum(h, h2, s, e);
+    e += l + l2;
+    h = s + e;
+    l = e - (h - s);
+}
+// The Metropolis uniform of (chain, sweep, proposal) cut to its top 24 bits, as
+// a float in [0, 1): the 53-bit uniform minus less than 2^-24.
+__device__ __forceinline__ float mcmc_uniform24(uint64_t seed, uint64_t chain, uint64_t sweep,
+                                                uint64_t proposal) {
+    uint64_t x[4];
+    rttd::philox4x64_10(chain, sweep, proposal, 0ull, seed, 0x4D434D43ull, x);
+    return (float)(uint32_t)(x[0] >> 40) * 0x1.0p-24f;
+}
 // sites the left tile takes below half of a proposal's row; negative: more.
 // Measured on plain_6x6 (37 sites per row): -1 (19 left, 18 right) is fastest;
 // the right tile also hands its half-row over and waits for the decision.
@@ -1782,14 +1807,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
         xpar ^= 1;
         return fmaxf(mine, other);
     };
+    // the two halves' partial dot products as float-float pairs, summed in
+    // the same order by both warps
     int dpar = 0;
-    auto pair_dot = [&](double mine) -> double {
-        double *slot = xdot + (dpar * 2) * NT;
-        slot[hf * NT + m] = mine;
+    auto pair_dot = [&](float mh, float ml, float &h, float &l) {
+        float2 *slot = reinterpret_cast<float2 *>(xdot) + (dpar * 2) * NT;
+        slot[hf * NT + m] = make_float2(mh, ml);
         named_sync(4 + q, 64);
-        const double d0 = slot[m], d1 = slot[NT + m];
+        const float2 d0 = slot[m], d1 = slot[NT + m];
         dpar ^= 1;
-        return d0 + d1;
+        h = d0.x;
+        l = d0.y;
+        ff_add(h, l, d1.x, d1.y);
     };
     const uint32_t acc_col = 0u, t0_col = 128u, a_col = X == 0 ? 256u : 128u;
 
@@ -1867,7 +1896,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
         load_vec<32>(a.bl + 32 * hf, v);
         write_A_half<F16>(ta, hf, v);
         publish();
-        double pm = a.state[c].mant;
+        // the chain amplitude as a float-float mantissa (|pm_h| in [1,2)) and
+        // an exact exponent; converted back to FP64 once, at the end
+        const double pm0 = a.state[c].mant;
+        float pm_h = (float)pm0, pm_l = (float)(pm0 - (double)pm_h);
         int64_t pe = a.state[c].exp2, acc_count = 0;
         int64_t El = 0, E = 0;
         long long nd = 0, np = 0;
@@ -1876,7 +1908,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
                 const int iq = site_spin(j);
                 const int si = spin(iq);
                 const int nL = nL_of(j);
-                double x = 0.0;
+                float x = 0.f;
                 float mx_keep = 0.f, mx_flip = 0.f;
                 for (int t = 0; t < nL; ++t) {
                     const int k = j + t;
@@ -1901,12 +1933,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
                         publish();
                     }
                     if (t == 0)
-                        x = rttd::mcmc_uniform(a.seed, (uint64_t)(a.chain0 + c),
-                                               (uint64_t)(a.sweep0 + sw), (uint64_t)j);
+                        x = mcmc_uniform24(a.seed, (uint64_t)(a.chain0 + c),
+                                           (uint64_t)(a.sweep0 + sw), (uint64_t)j);
                 }
                 // the right half-row, from the peer CTA
                 bwait_cluster(hand_bar, (uint32_t)(np++ & 1));
-                double mm;
+                // psi(s') = (mm_h + mm_l) 2^Ep: eight FP32 partial dot products per
+                // half, added without error (float-float)
+                float mm_h, mm_l;
                 {
                     float acc[8];
 #pragma unroll
@@ -1921,17 +1955,40 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
                         acc[(4 * cc + 2) & 7] = fmaf(v[4 * cc + 2], w.z, acc[(4 * cc + 2) & 7]);
                         acc[(4 * cc + 3) & 7] = fmaf(v[4 * cc + 3], w.w, acc[(4 * cc + 3) & 7]);
                     }
-                    double part = 0.0;
+                    float ph = acc[0], pl = 0.f;
 #pragma unroll
-                    for (int p = 0; p < 8; ++p) part += (double)acc[p];
-                    mm = pair_dot(part);
+                    for (int p = 1; p < 8; ++p) ff_add(ph, pl, acc[p], 0.f);
+                    pair_dot(ph, pl, mm_h, mm_l);
                 }
                 int64_t Ep = E + rexp_s[m];
-                normalize_scalar(mm, Ep);
-                const double ratio = ldexp(mm / pm, (int)(Ep - pe));
-                const bool accept = active && !*abort_flag && (x < ratio * ratio);
+                if (mm_h != 0.f && isfinite(mm_h)) {  // |mm_h| into [1,2), exactly
+                    const int kk = rttd::exponent_of(mm_h);
+                    mm_h = rttd::scale2(mm_h, -kk);
+                    mm_l = rttd::scale2(mm_l, -kk);
+                    Ep += kk;
+                }
+                // accept iff u < (psi'/psi)^2, i.e. u < q^2 4^d with q = mm/pm in
+                // (1/2, 2) and d = Ep - pe; FP32 (the split path's ratios carry
+                // errors far above the rounding of q^2)
+                bool pass;
+                {
+                    const float qq = mm_h / pm_h;
+                    const int64_t d = Ep - pe;
+                    if (!(mm_h != 0.f && isfinite(mm_h)))
+                        pass = false;  // a zero or undefined proposal is never taken
+                    else if (pm_h == 0.f || !isfinite(pm_h))
+                        pass = true;   // a chain at psi = 0 takes any finite nonzero one
+                    else if (d >= 1)
+                        pass = true;
+                    else if (d < -75)
+                        pass = false;
+                    else
+                        pass = x < ldexpf(qq * qq, (int)(2 * d));
+                }
+                const bool accept = active && !*abort_flag && pass;
                 if (accept) {
-                    pm = mm;
+                    pm_h = mm_h;
+                    pm_l = mm_l;
                     pe = Ep;
                     ++acc_count;
                 }
@@ -1959,6 +2016,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
             }
         }
         if (active && !*abort_flag && hf == 0) {
+            double pm = (double)pm_h + (double)pm_l;
+            normalize_scalar(pm, pe);
             a.state[c].mant = pm;
             a.state[c].exp2 = pe;
             if (a.n_accept) a.n_accept[c] += acc_count;
