@@ -1654,7 +1654,7 @@ constexpr int kPairLeftLess = -1;
 
 inline size_t sweepc_smem(int N, int L) {
     return 1024 + (size_t)NS * Cfg<64>::STAGE + SP_HAND + 256 + (size_t)16 * N + (size_t)4 * L +
-           4 * NT + 16 + (size_t)2 * 2 * NT * 4 + (size_t)2 * 2 * NT * 8;
+           16 + 4 * NT + 16 + (size_t)2 * 2 * NT * 4 + (size_t)2 * 2 * NT * 8;
 }
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -1698,6 +1698,16 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
         if (clock64() - t0 > limit) return false;
     return true;
 }
+// Bulk copy (copy engine) of `bytes` from this CTA's shared memory to a peer
+// CTA's, completing as transaction bytes on the peer's mbarrier.
+__device__ __forceinline__ void bulk_copy_to_peer(uint32_t dst_cluster, uint32_t src_cta,
+                                                  uint32_t bytes, uint32_t mbar_cluster) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst_cluster),
+        "r"(src_cta), "r"(bytes), "r"(mbar_cluster)
+        : "memory");
+}
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
                      : "memory");
@@ -1727,11 +1737,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
     long long *issued = (long long *)(bars + 10);
     uint32_t *bits = (uint32_t *)(base + NS * C::STAGE + SP_HAND + 256);
     uint32_t *tab = bits + 4 * a.N;
-    int32_t *rexp_s = (int32_t *)(tab + a.L);
+    int32_t *rexp_s = (int32_t *)(((uintptr_t)(tab + a.L) + 15) & ~(uintptr_t)15);  // 16-aligned
     // exchange slots, 16-byte aligned whatever L is
     float *xmax = (float *)(((uintptr_t)(rexp_s + NT) + 15) & ~(uintptr_t)15);  // [parity][half][row]
     double *xdot = (double *)(xmax + 2 * 2 * NT);                              // [parity][half][row]
 
+    // one hand-off: the right half-rows (128 x 64 floats) and their exponents
+    constexpr uint32_t HAND_BYTES = (uint32_t)SP_HAND + 4u * NT;
     const uint32_t rank = cluster_rank();
     const int X = (int)rank;  // 0 left, 1 right
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1752,11 +1764,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
     if (warp == 0) tmem_alloc(sa(tmem_slot), tcols);
     if (tid == 0) {
         for (int i = 0; i < 2 * NS + 1; ++i) mbar_init(bar0 + 8u * i, 1);
-        mbar_init(hand_bar, 8);  // one arrival per right epilogue warp
+        mbar_init(hand_bar, 1);  // armed by the left with the bytes of one hand-off
         mbar_init(dec_bar, 8);   // one arrival per left epilogue warp
         *abort_flag = 0;
         issued[0] = 0;
         fence_barrier_init();
+        if (X == 0) mbar_expect_tx(hand_bar, HAND_BYTES);  // the first proposal's hand-off
     }
     for (int k = tid; k < L; k += SPC_THREADS)
         tab[k] = ((uint32_t)__ldg(GEN ? a.path + k : a.q + (k % N)) & 0xffffu) |
@@ -1936,8 +1949,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
                         x = mcmc_uniform24(a.seed, (uint64_t)(a.chain0 + c),
                                            (uint64_t)(a.sweep0 + sw), (uint64_t)j);
                 }
-                // the right half-row, from the peer CTA
+                // the right half-row, from the peer CTA; then arm the next hand-off
                 bwait_cluster(hand_bar, (uint32_t)(np++ & 1));
+                if (tid == 0 && (j + 1 < N || sw + 1 < a.n_sweeps)) mbar_expect_tx(hand_bar, HAND_BYTES);
                 // psi(s') = (mm_h + mm_l) 2^Ep: eight FP32 partial dot products per
                 // half, added without error (float-float)
                 float mm_h, mm_l;
@@ -2015,6 +2029,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
                 }
             }
         }
+        // after an expired wait: let a hand-off that is still in flight land
+        if (tid == 0 && *abort_flag) mbar_wait_cluster(hand_bar, (uint32_t)(np & 1), a.wait_limit);
         if (active && !*abort_flag && hf == 0) {
             double pm = (double)pm_h + (double)pm_l;
             normalize_scalar(pm, pe);
@@ -2075,16 +2091,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
                         publish();
                     }
                 }
-                // hand the half-row to the left CTA: row m, float4 chunks 8hf..8hf+7
+                // hand the half-row to the left CTA: row m (float4 chunks 8hf..8hf+7)
+                // into this CTA's buffer, then one bulk copy of all rows and exponents
 #pragma unroll
                 for (int cc = 0; cc < 8; ++cc) {
                     const int ch = hf * 8 + cc;
-                    st_cluster_v4(peer_rows + (uint32_t)((m * 64 + ((ch ^ (m & 15)) << 2)) * 4),
-                                  v[4 * cc], v[4 * cc + 1], v[4 * cc + 2], v[4 * cc + 3]);
+                    *reinterpret_cast<float4 *>(hand + m * 64 + ((ch ^ (m & 15)) << 2)) =
+                        make_float4(v[4 * cc], v[4 * cc + 1], v[4 * cc + 2], v[4 * cc + 3]);
                 }
-                if (hf == 0) st_cluster_u32(peer_rexp + (uint32_t)(m * 4), (uint32_t)(int32_t)E);
-                __syncwarp();
-                if (lane == 0) mbar_arrive_remote(peer_hand);
+                if (hf == 0) rexp_s[m] = (int32_t)E;
+                fence_async_smem();
+                named_sync(1, 2 * NT);  // the 8 epilogue warps have written
+                if (tid == 0 && !*abort_flag) {
+                    bulk_copy_to_peer(peer_rows, sa(hand), (uint32_t)SP_HAND, peer_hand);
+                    bulk_copy_to_peer(peer_rexp, sa(rexp_s), 4u * NT, peer_hand);
+                }
                 const bool more = (j + 1 < N) || (sw + 1 < a.n_sweeps);
                 if (more) {  // the next row's first MMA does not depend on this decision
                     if (j + 1 < N && !GEN)
