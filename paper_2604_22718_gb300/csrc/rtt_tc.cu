@@ -2055,6 +2055,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
         publish();
         int64_t E = 0;
         long long nd = 0, ndec = 0;
+        // The left's decision on proposal j changes only spin p(j): wait for it
+        // (its spin bits arrive with it) before the first select at a site that
+        // carries that spin, and before this CTA's hand-off buffer is rewritten
+        // (the left has consumed the previous hand-off once it decides).
+        int pend = -1;
+        auto settle = [&]() {
+            if (pend >= 0) {
+                bwait_cluster(dec_bar, (uint32_t)(ndec++ & 1));
+                pend = -1;
+            }
+        };
         for (int sw = 0; sw < a.n_sweeps; ++sw) {
             E = 0;
             for (int u = 0; u < (GEN ? 0 : N - 1); ++u) {
@@ -2062,6 +2073,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
                 bwait(done_bar, (uint32_t)(nd++ & 1));
                 tc_after();
                 __syncwarp();
+                if (site_spin(k) == pend) settle();
                 acc_select_half(tw, hf, spin(site_spin(k)), v);
                 E += renorm_half(v, pair_max(half_max(v))) - site_cexp(k);
                 if (active) {
@@ -2084,6 +2096,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
                     tc_after();
                     __syncwarp();
                     const int sk = site_spin(k);
+                    if (sk == pend) settle();
                     acc_select_half(tw, hf, spin(sk) ^ (sk == iq ? 1 : 0), v);
                     E += renorm_half(v, pair_max(half_max(v))) - site_cexp(k);
                     if (t + 1 < nR) {
@@ -2091,6 +2104,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
                         publish();
                     }
                 }
+                settle();  // the previous hand-off has been read
                 // hand the half-row to the left CTA: row m (float4 chunks 8hf..8hf+7)
                 // into this CTA's buffer, then one bulk copy of all rows and exponents
 #pragma unroll
@@ -2115,10 +2129,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
                     write_A_half<F16>(ta, hf, v);
                     publish();
                 }
-                // the decision (new spin bits) before any further epilogue
-                bwait_cluster(dec_bar, (uint32_t)(ndec++ & 1));
+                pend = iq;  // this proposal's decision is now outstanding
             }
         }
+        settle();
     }
     __syncthreads();
     if (X == 0 && warp < 4 && active && !*abort_flag) {
