@@ -150,8 +150,8 @@ class L2Flush:
 # of the same command on this kernel build (profiles/ names the capture); None
 # where no capture of the current kernel exists.
 MEASURED_TRAFFIC = {
-    # profiles/tc_sweep_split_plain6x6_fp16x3.md: 3 844 608 B read + 70 656 B written
-    ("plain_6x6", "fp16x3", "tc_sweep", 4096): 3844608 + 70656,
+    # profiles/tc_sweep_split_plain6x6_fp16x3.md: 3 847 680 B read + 66 560 B written
+    ("plain_6x6", "fp16x3", "tc_sweep", 4096): 3847680 + 66560,
 }
 
 
@@ -202,7 +202,9 @@ def run_reference(args):
     inst = inputs.workload(args.workload)
     o = orc.Oracle(inst)
     cores = os.cpu_count() or 1
-    per_step = max(cores, 16)
+    # two chains per thread: the binding splits a batch across threads only when
+    # it holds at least two chains per thread, else it runs on one core
+    per_step = 2 * cores
     spins = inputs.initial_spins(w["seed"], per_step, inst.n_spins)
     mant, ex = o.init_chains(spins)
     t_total = 0.0
@@ -222,7 +224,7 @@ def run_reference(args):
                    "sample": f"{per_step} chains per step (bounded sample of the "
                              f"{w['chains']}-chain workload), 1 sweep + E_loc each"},
         "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{per_step} chains x {args.steps} steps"},
+                         "sample": f"{per_step} chains x {args.steps} steps, {cores} threads"},
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -237,7 +239,7 @@ def _workload_desc(name, inst, chains):
 
 
 def cpu_baseline(inst, w, seed):
-    """The FP64 oracle on this host's cores: ~15 s of CPU work."""
+    """The FP64 oracle on this host's cores: ~20 core-seconds of CPU work."""
     from oracle import oracle as orc
     from paper_2604_22718_gb300 import inputs
     o = orc.Oracle(inst)
@@ -253,7 +255,7 @@ def cpu_baseline(inst, w, seed):
     o.mcmc(seed, spins, mant, ex, 0, 1, measure_every=1, threads=cores)
     dt = time.perf_counter() - t0
     cpu_per_chain = dt * cores / cal
-    n = int(min(20000, max(cal, 15.0 / max(cpu_per_chain, 1e-6))))
+    n = int(min(20000, max(cal, 20.0 / max(cpu_per_chain, 1e-6))))
     n = max(cores, (n // cores) * cores)
     spins = inputs.initial_spins(seed + 2, n, inst.n_spins)
     mant, ex = o.init_chains(spins)
