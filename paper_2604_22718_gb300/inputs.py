@@ -17,6 +17,8 @@ of Sec. 2.2.1):
                   chi in {32,64,128,256}, h ~ U[2.5,3.5]
 * ``dual_6x6``    3 states of the plain_6x6 kind (dual Monte Carlo)
 * ``vhdd_6x6``    6x6, path sigma^V + sigma^H + sigma^D + sigma^D' (R = 4, L = 144), chi = 64
+* ``replica_*``   replica-space optimization (Sec. 3.1, Sec. 4): 6x6, 10x10, 20x20 on
+                  sigma^V + sigma^H + sigma^D + sigma^D', chi = 2, tau = 0.1, h = 3, H-bar_HV
 
 All randomness comes from ``numpy.random.Generator(PCG64(seed))``.
 """
@@ -30,6 +32,8 @@ __all__ = [
     "make_path_instance", "open_bonds", "periodic_path",
     "gaussian_tensors", "mixed_tensors", "make_instance", "initial_spins",
     "WORKLOADS", "workload", "workload_states", "batched_instances", "made_init_weights", "ferro_chain_instance",
+    "BOND_STEPS", "direction_bonds", "replica_terms", "hbar_terms", "terms_arrays", "replica_start",
+    "replica_ones", "REPLICA_WORKLOADS",
 ]
 
 
@@ -267,3 +271,105 @@ def ferro_chain_instance(lx: int, ly: int, kappa: float, field: float = 0.0, h: 
     return RTTInstance(n_spins=N, path=path, tensors=t, b_left=ones.copy(), b_right=ones.copy(),
                        bonds=open_bonds(lx, ly), J=1.0, h=float(h), name=f"ferro{lx}x{ly}",
                        lx=lx, ly=ly, R=R)
+
+
+# ---------------------------------------------------------------- replica-space optimization
+# Physical operators of Sec. 4 as lists of Pauli terms, each with the replica
+# block its Z factors are sent to (the "-> C" choice of Sec. 4).  Only the
+# operator's definition lives here; lifting it to the replica space is the
+# method's and is done by the library (and, independently, by the oracle).
+
+BOND_STEPS = {"H": (1, 0), "V": (0, 1), "D": (1, -1), "Dp": (1, 1)}
+
+
+def direction_bonds(lx: int, ly: int, direction: str) -> np.ndarray:
+    """Nearest-neighbour pairs (i, j), i = y*lx + x, along one direction.
+
+    'H' and 'V' are the horizontal and vertical bonds; 'D' pairs neighbours on
+    the diagonals x + y = const that sigma^D walks, 'Dp' those on x - y = const
+    that sigma^D' walks, so that a term sent to its own ordering is local."""
+    dx, dy = BOND_STEPS[direction]
+    out = []
+    for y in range(ly):
+        for x in range(lx):
+            x2, y2 = x + dx, y + dy
+            if 0 <= x2 < lx and 0 <= y2 < ly:
+                out.append((y * lx + x, y2 * lx + x2))
+    return np.asarray(out, dtype=np.int32).reshape(-1, 2)
+
+
+def replica_terms(lx: int, ly: int, orderings, zz, h: float, x_block: int = 0):
+    """Terms of sum_(d, c, target) c O_{ZZ, d -> target} - h O_X.
+
+    zz: list of (direction, coefficient, target ordering name); the ZZ terms of
+    each entry are sent to the block of ``orderings`` with that name.  Returns
+    a list of (coef, [(spin, 'Z'|'X'), ...], block), in the order: the zz
+    entries as given (bonds by site index), then the transverse-field terms
+    (site index order).  X factors go to every replica whatever the block."""
+    orderings = list(orderings)
+    terms = []
+    for direction, coef, target in zz:
+        blk = orderings.index(target)
+        for i, j in direction_bonds(lx, ly, direction):
+            terms.append((float(coef), [(int(i), "Z"), (int(j), "Z")], blk))
+    if h != 0.0:
+        for i in range(lx * ly):
+            terms.append((-float(h), [(i, "X")], int(x_block)))
+    return terms
+
+
+def hbar_terms(kind: str, lx: int, ly: int, h: float, orderings=("V", "H", "D", "Dp"),
+               J: float = 1.0, alpha: float = 0.08):
+    """The replica Hamiltonians of Sec. 4 (Eq. H_HV and the two around it):
+    'H' (all ZZ terms on the H ordering), 'HV' (horizontal bonds on H, vertical
+    on V), 'HVDDp' ('HV' plus alpha times the diagonal bonds on D and D')."""
+    zz = {"H": [("H", J, "H"), ("V", J, "H")],
+          "HV": [("H", J, "H"), ("V", J, "V")],
+          "HVDDp": [("H", J, "H"), ("V", J, "V"), ("D", alpha, "D"), ("Dp", alpha, "Dp")]}[kind]
+    return replica_terms(lx, ly, orderings, zz, h)
+
+
+def terms_arrays(terms):
+    """Flatten a term list for the C ABI: coef [K] f64, block [K] i32,
+    offsets [K+1] i32, spins [F] i32, ops [F] u8 ('X' = 1, 'Z' = 2)."""
+    code = {"X": 1, "Z": 2, "Y": 3}
+    coef = np.asarray([t[0] for t in terms], dtype=np.float64)
+    block = np.asarray([t[2] for t in terms], dtype=np.int32)
+    off = np.zeros(len(terms) + 1, dtype=np.int32)
+    spins, ops = [], []
+    for k, (_, factors, _) in enumerate(terms):
+        for j, op in factors:
+            spins.append(int(j))
+            ops.append(code[op])
+        off[k + 1] = len(spins)
+    return (coef, block, off, np.asarray(spins, dtype=np.int32), np.asarray(ops, dtype=np.uint8))
+
+
+def replica_start(seed, L: int, chi: int) -> np.ndarray:
+    """A random starting TT, padded cores [L][2][chi][chi] (row = left bond):
+    Gaussian entries / sqrt(2 chi) on ranks min(chi, 2^k, 2^(L-k)), zeros
+    elsewhere (the first core has one row, the last one column)."""
+    rng = np.random.Generator(np.random.PCG64([int(seed), 0x52455043]))
+    r = [min(chi, 2 ** min(k, 62), 2 ** min(L - k, 62)) for k in range(L + 1)]
+    out = np.zeros((L, 2, chi, chi))
+    for k in range(L):
+        out[k, :, :r[k], :r[k + 1]] = rng.standard_normal((2, r[k], r[k + 1])) / np.sqrt(2 * chi)
+    return out
+
+
+def replica_ones(L: int, chi: int) -> np.ndarray:
+    """phi^(0)_i = 1 for every i (the paper's starting TT), padded cores."""
+    out = np.zeros((L, 2, chi, chi))
+    out[:, :, 0, 0] = 1.0
+    return out
+
+
+REPLICA_WORKLOADS = {
+    # the paper's replica-space runs: chi = 2, tau = 0.1, h = 3, path sigma^V+H+D+D'
+    "replica_6x6":   dict(lx=6, ly=6, orderings=("V", "H", "D", "Dp"), chi=2, tau=0.1, h=3.0,
+                          kind="HV", steps=200),
+    "replica_10x10": dict(lx=10, ly=10, orderings=("V", "H", "D", "Dp"), chi=2, tau=0.1, h=3.0,
+                          kind="HV", steps=200),
+    "replica_20x20": dict(lx=20, ly=20, orderings=("V", "H", "D", "Dp"), chi=2, tau=0.1, h=3.0,
+                          kind="HV", steps=50),
+}
