@@ -708,6 +708,163 @@ def run_dual(args):
         h.close()
 
 
+def rounding_flops(L: int, chi: int) -> float:
+    """Dense operation counts of one TT rounding of a two-term sum (rank 2 chi
+    rounded to chi): per site the product with the carried factor, a
+    Householder QR with explicit Q (4 m n^2 - 4 n^3 / 3, m >= n), and a thin SVD
+    with both factors (6 m n^2 + 20 n^3, m >= n) plus the product with U S."""
+    D2 = 2 * chi
+
+    def qr(m, n):
+        m, n = max(m, n), min(m, n)
+        return 4.0 * m * n * n - 4.0 * n ** 3 / 3.0
+
+    def svd(m, n):
+        m, n = max(m, n), min(m, n)
+        return 6.0 * m * n * n + 20.0 * n ** 3
+
+    f = 0.0
+    for k in range(L):
+        rl = min(2 ** min(k, 30), D2)
+        dl = 1 if k == 0 else D2
+        dr = 1 if k == L - 1 else D2
+        f += 2.0 * (2 * rl) * dl * dr
+        if k < L - 1:
+            f += qr(2 * rl, dr)
+        if k >= 1:
+            r1 = min(chi, 2 ** min(L - 1 - k, 30))
+            f += svd(rl, 2 * r1)
+            t = min(chi, rl, 2 * r1)
+            f += 2.0 * (2 * min(2 ** min(k - 1, 30), D2)) * rl * t
+    return f
+
+
+def run_replica(args):
+    """Replica-space optimization (Sec. 3.1, Sec. 4): one step = one application
+    of 1 - tau H-bar to the TT phi -- every term's rank-1 MPO, the tree of
+    two-term sums each rounded to rank chi, phi - tau S rounded and scaled --
+    from phi^(0) = 1.  After the timed steps the RTT psi = C phi is sampled
+    with the library's FP64 sampler for its energy (not timed)."""
+    import torch
+    from paper_2604_22718_gb300 import inputs, rtt
+    name = args.workload
+    w = inputs.REPLICA_WORKLOADS[name]
+    lx, ly, order, chi, tau, h = w["lx"], w["ly"], w["orderings"], w["chi"], w["tau"], w["h"]
+    N = lx * ly
+    path = inputs.path_sum([inputs.ordering(o, lx, ly) for o in order])
+    L = path.shape[0]
+    terms = inputs.hbar_terms(w["kind"], lx, ly, h, orderings=order)
+    eta, ops = rtt.replica_lift(N, path, terms)
+    K_terms = len(eta)
+    levels, n = 0, K_terms
+    while n > 1:
+        n = n // 2 + n % 2
+        levels += 1
+    plan = rtt.TTPlan(L, chi, eta, ops)
+    phi0 = inputs.replica_ones(L, chi)
+    phi = torch.from_numpy(phi0).cuda()
+    K, W = args.steps, args.warmup
+    ln = torch.empty(W + K, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for t in range(W):
+        plan.power(phi, tau, 1, ln[t:t + 1])
+    flush = L2Flush()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    clocks.start()
+    for t in range(K):
+        flush()
+        ev[t][0].record(stream)
+        plan.power(phi, tau, 1, ln[W + t:W + t + 1])
+        ev[t][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(z) for a, z in ev)
+    step_ms = total_ms / K
+    value = K / (total_ms / 1e3)
+    flops_step = K_terms * rounding_flops(L, chi)
+    achieved = flops_step / (step_ms / 1e3) / 1e12
+    peaks, _ = measured_peaks()
+    peak = SM_COUNT * FP64_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    lognorm = ln.cpu().numpy()
+    # end to end: phi from pinned host memory, one step, phi and its log-norm back
+    e2e = None
+    if not args.no_e2e:
+        host_phi = torch.from_numpy(phi.cpu().numpy()).pin_memory()
+        host_ln = torch.empty(1, dtype=torch.float64).pin_memory()
+        dphi = torch.empty_like(phi)
+        dln = torch.empty(1, dtype=torch.float64, device="cuda")
+        ke = min(K, 200)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for t in range(ke):
+            dphi.copy_(host_phi, non_blocking=True)
+            plan.power(dphi, tau, 1, dln)
+            host_phi.copy_(dphi, non_blocking=True)
+            host_ln.copy_(dln, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        nb = phi.numel() * 8
+        e2e = {"value": ke / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb + 8}
+    # the energy of psi = C phi, sampled (FP64, the TT's cores with b_L = b_R = e_0)
+    e0v = np.zeros(chi)
+    e0v[0] = 1.0
+    inst = inputs.RTTInstance(n_spins=N, path=path.astype(np.int32), tensors=phi.cpu().numpy(),
+                              b_left=e0v, b_right=e0v.copy(), bonds=inputs.open_bonds(lx, ly),
+                              J=1.0, h=h, name=name, lx=lx, ly=ly, R=len(order))
+    hh = rtt.RTT(inst, "fp64", seed=22730)
+    B, burn, meas = 4096, 50, 200
+    sp = torch.from_numpy(inputs.initial_spins(22731, B, N)).cuda()
+    st = hh.log_amplitudes(sp)[2]
+    hh.mcmc_sweep(sp, st, 0, burn)
+    tr = torch.empty((meas, B), dtype=torch.float64, device="cuda")
+    hh.mcmc_sweep(sp, st, burn, meas, measure_every=1, trace=tr)
+    obs = hh.observables(tr)
+    hh.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import replica as orp
+        tt = orp.tt_ones(L)
+        t0 = time.perf_counter()
+        nsteps = 0
+        while time.perf_counter() - t0 < 15.0 and nsteps < 1000:
+            tt, _ = orp.power_step(tt, eta, ops, tau, chi)
+            nsteps += 1
+        cpu_s = time.perf_counter() - t0
+        cpu = {"value": nsteps / cpu_s, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{nsteps} steps of the same workload from phi^(0) = 1 (numpy FP64 "
+                         f"oracle, one thread, {cpu_s:.1f} s)"}
+    launches = K * (levels + 1)
+    line = {
+        "metric": "replica-space optimization steps/s (1 - tau H-bar on the TT, rounded to chi)",
+        "value": value, "unit": "steps/s", "n_gpus": 1, "steps": K, "warmup": W,
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{name}: {lx}x{ly} open TFIM h={h}, path "
+                               f"{'+'.join(order)} (L={L}), H-bar_{w['kind']} ({K_terms} terms, "
+                               f"{levels} tree levels), chi={chi}, tau={tau}, phi0 = 1",
+                   "l2": "flushed (256 MiB write + 256 MiB read) between timed steps"},
+        "roundings_per_s": K_terms * value,
+        "launch_ms": step_ms / (levels + 1),
+        "site_step_us": 1e3 * step_ms / (levels + 1) / (2 * L),
+        "log_norm_last": float(lognorm[-1]),
+        "energy": {"E_per_site": obs["mean"] / N, "se_per_site": obs["se"] / N,
+                   "v_score": obs["v_score"], "tau_int": obs["tau_int"], "chains": B,
+                   "sweeps": meas, "sampler": "FP64 SIMT, general path"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_tt_round",
+                     "flops_per_step": flops_step,
+                     "peak_source": "FP64 CUDA-core peak, 152 SMs x 2 FP64 FMA lanes x 2070 MHz",
+                     "note": "latency-bound: each rounding is a chain of 2 L dependent small "
+                             "factorizations on one warp"},
+        "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -722,6 +879,10 @@ def main():
     if args.workload == "learned_16x16":
         if int(os.environ.get("RANK", "0")) == 0:
             run_learned(args)
+        return
+    if args.workload.startswith("replica_"):
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_replica(args)
         return
     if args.workload == "dual_6x6":
         if int(os.environ.get("RANK", "0")) == 0:

@@ -349,6 +349,78 @@ rtt_status rtt_made_sample(rtt_made m, int64_t B, int64_t chain0, int64_t round,
 rtt_status rtt_indep_mh(rtt_handle h, rtt_made m, uint8_t *spins, rtt_chain_state *state,
                         int64_t B, int64_t chain0, int64_t round, int64_t *n_accept, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Replica-space optimization (Sec. 3.1; rules of Sec. 2.2.3)
+ *
+ * phi is a TT over the replica space: L sites i_1..i_L in {0,1},
+ * phi_i = G_1[i_1] G_2[i_2] ... G_L[i_L] with open ends.  Storage ("padded
+ * cores"): device double [L][2][chi][chi], element [k][s][a][b] = G_k[a,s,b];
+ * the first core uses row 0 only, the last core column 0 only, and all other
+ * entries beyond a bond's rank are zero.  The RTT psi = C phi (Eq.
+ * rtt_equal_C_tt) is the handle of rtt_create with these tensors, the same
+ * path and b_L = b_R = e_0.
+ *
+ * A replica-space Pauli string is one code per site: 0 identity, 1 X, 2 Z
+ * (uint8).  Applied to a TT it is a rank-1 MPO: X swaps a core's two
+ * physical slices, Z negates slice 1.
+ * ------------------------------------------------------------------------- */
+
+/* Lift physical Pauli terms to replica-space strings by the commutation rules
+ * of Sec. 2.2.3: Z_j is sent to one replica of spin j (the term's block), X_j
+ * becomes X on every replica of j.  The path must be a concatenation of
+ * orderings, each a permutation of the n_spins spins (block c = sites
+ * [c n_spins, (c+1) n_spins)).  Term k has coefficient coef[k], block
+ * block[k], and factors offsets[k]..offsets[k+1]-1 of (spins, ops) with ops
+ * 1 = X, 2 = Z (3 = Y is rejected: it would make the TT complex); a term may
+ * not name a spin twice.  Outputs: ops_out [n_terms][length] string codes and
+ * eta_out [n_terms] (= coef).  All pointers host; no device work, callable
+ * without a GPU.  RTT_ERR_INVALID_ARG on a malformed path or term,
+ * RTT_ERR_UNSUPPORTED for Y. */
+rtt_status rtt_replica_lift(int32_t n_spins, int32_t length, const int32_t *path, int32_t n_terms,
+                            const double *coef, const int32_t *block, const int32_t *offsets,
+                            const int32_t *spins, const uint8_t *ops, uint8_t *ops_out,
+                            double *eta_out);
+
+typedef struct rtt_tt_plan_s *rtt_tt_plan;
+
+/* A plan for (1 - tau H-bar) on TTs of `length` sites and rank chi (1..16),
+ * H-bar = sum_k eta[k] P_k with the strings ops [n_terms][length] (host,
+ * codes as above; n_terms >= 1, length >= 2).  Copies the strings to the
+ * device, allocates the tree's node TTs (n_terms - 1 of them) and the
+ * rounding scratch (floor(n_terms/2) * length * 2 * (2 chi)^2 doubles) on
+ * `device`.  *out owned by the caller (rtt_tt_plan_destroy). */
+rtt_status rtt_tt_plan_create(int32_t length, int32_t chi, int32_t n_terms, const uint8_t *ops,
+                              const double *eta, int32_t device, rtt_tt_plan *out);
+rtt_status rtt_tt_plan_destroy(rtt_tt_plan plan);
+
+/* n_steps applications of 1 - tau H-bar to phi in place (device padded
+ * cores), each as Sec. 3.1 orders it: the terms eta_k P_k phi, summed two by
+ * two (items in term order; pairs (0,1), (2,3), ...; an odd last item passes
+ * to the next level unchanged) with every pair sum rounded to rank chi, until
+ * one TT S is left; then phi <- round(phi - tau S) / ||.||_2.  Rounding is
+ * TT rounding: left-to-right Householder QR of each core, then right-to-left
+ * SVD (one-sided Jacobi) keeping the chi largest singular values per bond.
+ * The output's cores 2..L are right-orthonormal and core 1 carries the
+ * replica-space norm, which is scaled to 1; log_norm (device double
+ * [n_steps] or NULL) receives log ||round(phi - tau S)||_2 of every step (a
+ * non-finite entry means the step failed numerically).  One kernel launch
+ * per tree level and one for the final sum per step, plus one
+ * device-to-device copy; ordered on `stream`.  RTT_ERR_INVALID_ARG for a null
+ * phi or n_steps < 0. */
+rtt_status rtt_tt_power(rtt_tt_plan plan, double *phi, double tau, int32_t n_steps,
+                        double *log_norm, void *stream);
+
+/* One rounding of a two-term sum, the operation every tree node performs:
+ * out = round(coef_a P_a a + coef_b P_b b) (device padded cores, each of the
+ * plan's length and chi; ops_a / ops_b device string rows [length] or NULL
+ * for the identity).  If log_norm (device double [1]) is not NULL the result
+ * is scaled to unit norm and the log of its norm stored there.  out must not
+ * alias a or b.  Uses the plan's scratch: calls on one plan are ordered on
+ * their streams by the caller. */
+rtt_status rtt_tt_round_sum(rtt_tt_plan plan, const double *a, const uint8_t *ops_a, double coef_a,
+                            const double *b, const uint8_t *ops_b, double coef_b, double *out,
+                            double *log_norm, void *stream);
+
 /* The local energy of rtt_local_energy (same kernels, same results) from a
  * call that allocates no device memory.  The paper has no counterpart: this
  * is an operational variant for callers that cannot allocate at the time of

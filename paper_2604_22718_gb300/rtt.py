@@ -99,6 +99,14 @@ def lib():
                      "rtt_made_gradients", "rtt_made_train_step", "rtt_made_log_prob",
                      "rtt_made_sample", "rtt_indep_mh"):
             getattr(L, name).restype = ctypes.c_int
+        L.rtt_replica_lift.argtypes = [I32, I32, P, I32, P, P, P, P, P, P, P]
+        L.rtt_tt_plan_create.argtypes = [I32, I32, I32, P, P, I32, ctypes.POINTER(P)]
+        L.rtt_tt_plan_destroy.argtypes = [P]
+        L.rtt_tt_power.argtypes = [P, P, ctypes.c_double, I32, P, P]
+        L.rtt_tt_round_sum.argtypes = [P, P, P, ctypes.c_double, P, P, ctypes.c_double, P, P, P]
+        for name in ("rtt_replica_lift", "rtt_tt_plan_create", "rtt_tt_plan_destroy",
+                     "rtt_tt_power", "rtt_tt_round_sum"):
+            getattr(L, name).restype = ctypes.c_int
         L.rtt_status_string.argtypes = [I32]
         L.rtt_status_string.restype = ctypes.c_char_p
         L.rtt_last_error.restype = ctypes.c_char_p
@@ -533,3 +541,86 @@ def indep_mh(model: RTT, made: MADE, spins, state, round: int, n_accept=None, ch
         _dev_check(n_accept, torch.int64, (B,), "n_accept")
     _check(lib().rtt_indep_mh(model.handle, made.handle, _ptr(spins), _ptr(state), B, int(chain0),
                               int(round), _ptr(n_accept), _stream(stream)), "rtt_indep_mh")
+
+
+# ---------------------------------------------------------------- replica space
+
+def replica_lift(n_spins: int, path, terms):
+    """rtt_replica_lift: physical Pauli terms [(coef, [(spin, 'X'|'Z'), ...], block)]
+    -> (eta [K] float64, ops [K][L] uint8 string codes: 0 I, 1 X, 2 Z)."""
+    code = {"X": 1, "Z": 2, "Y": 3}
+    path = np.ascontiguousarray(path, dtype=np.int32)
+    L = path.shape[0]
+    K = len(terms)
+    coef = np.ascontiguousarray([t[0] for t in terms], dtype=np.float64)
+    block = np.ascontiguousarray([t[2] for t in terms], dtype=np.int32)
+    off = np.zeros(K + 1, dtype=np.int32)
+    spins, ops = [], []
+    for k, (_, factors, _) in enumerate(terms):
+        for j, op in factors:
+            spins.append(int(j))
+            ops.append(code[op])
+        off[k + 1] = len(spins)
+    spins = np.ascontiguousarray(spins if spins else [0], dtype=np.int32)
+    ops = np.ascontiguousarray(ops if ops else [0], dtype=np.uint8)
+    out = np.zeros((max(K, 1), L), dtype=np.uint8)
+    eta = np.zeros(max(K, 1), dtype=np.float64)
+    _check(lib().rtt_replica_lift(int(n_spins), L, path.ctypes.data, K, coef.ctypes.data,
+                                  block.ctypes.data, off.ctypes.data, spins.ctypes.data,
+                                  ops.ctypes.data, out.ctypes.data, eta.ctypes.data),
+           "rtt_replica_lift")
+    return eta[:K], out[:K]
+
+
+class TTPlan:
+    """rtt_tt_plan: (1 - tau H-bar) steps and two-term roundings on TTs of
+    `length` sites and rank chi; H-bar = sum_k eta[k] P_k (ops [K][length])."""
+
+    def __init__(self, length: int, chi: int, eta, ops, device: int = 0):
+        eta = np.ascontiguousarray(eta, dtype=np.float64)
+        ops = np.ascontiguousarray(ops, dtype=np.uint8)
+        if ops.ndim != 2 or ops.shape != (eta.shape[0], length):
+            raise ValueError("ops must have shape [len(eta)][length]")
+        self.length, self.chi = int(length), int(chi)
+        self._p = ctypes.c_void_p()
+        _check(lib().rtt_tt_plan_create(self.length, self.chi, eta.shape[0], ops.ctypes.data,
+                                        eta.ctypes.data, int(device), ctypes.byref(self._p)),
+               "rtt_tt_plan_create")
+
+    def close(self):
+        if getattr(self, "_p", None) is not None and self._p.value:
+            lib().rtt_tt_plan_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _cores(self, t, name):
+        _dev_check(t, torch.float64, (self.length, 2, self.chi, self.chi), name)
+
+    def power(self, phi: torch.Tensor, tau: float, steps: int, log_norm: torch.Tensor = None,
+              stream=None):
+        """phi (device float64 [L][2][chi][chi]) <- (1 - tau H-bar)^steps phi, each
+        step rounded and scaled to unit norm; log_norm (device float64 [steps])."""
+        self._cores(phi, "phi")
+        if log_norm is not None:
+            _dev_check(log_norm, torch.float64, (steps,), "log_norm")
+        _check(lib().rtt_tt_power(self._p, _ptr(phi), float(tau), int(steps), _ptr(log_norm),
+                                  _stream(stream)), "rtt_tt_power")
+
+    def round_sum(self, a, b, out, coef_a: float = 1.0, coef_b: float = 1.0, ops_a=None,
+                  ops_b=None, log_norm=None, stream=None):
+        """out <- round(coef_a P_a a + coef_b P_b b); ops_* device uint8 [L] or None."""
+        for t, nm in ((a, "a"), (b, "b"), (out, "out")):
+            self._cores(t, nm)
+        for t, nm in ((ops_a, "ops_a"), (ops_b, "ops_b")):
+            if t is not None:
+                _dev_check(t, torch.uint8, (self.length,), nm)
+        if log_norm is not None:
+            _dev_check(log_norm, torch.float64, (1,), "log_norm")
+        _check(lib().rtt_tt_round_sum(self._p, _ptr(a), _ptr(ops_a), float(coef_a), _ptr(b),
+                                      _ptr(ops_b), float(coef_b), _ptr(out), _ptr(log_norm),
+                                      _stream(stream)), "rtt_tt_round_sum")
