@@ -1,4 +1,4 @@
-"""Replica-space optimization of Sec. 3.1 in plain FP64 -- TEST INFRASTRUCTURE ONLY.
+"""Replica- and physical-space optimization (Sec. 3.1, 3.2) in plain FP64 -- TEST INFRASTRUCTURE ONLY.
 
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this module.  The product path (the CUDA library and
@@ -29,6 +29,17 @@ What it computes:
     every sum (an odd last item passes to the next level unchanged) until one
     TT S is left; then phi' = compress(phi - tau S), scaled to unit replica-space
     2-norm (RTTs are not normalised; the scale keeps the numbers finite).
+
+Physical-space optimization (Sec. 3.2, Sec. 4):
+  * ``apply_operator``: phi^alpha = O-bar_alpha phi, the terms summed two by two
+    with a rounding after every sum, the root rounded once more, scaled to unit
+    norm (psi^alpha = O_alpha psi built "as in the replica-space optimization");
+  * ``combine``: phi' = sum_alpha c_alpha phi^alpha (Eq. lin_comb) the same way.
+  Pinned in ``tests/test_oracle_physical.py``: without truncation they are the
+  dense operator and the dense linear combination; with H~, S~ enumerated
+  exactly, the combination's energy is the lowest generalized eigenvalue, at
+  most the starting energy (the identity is one of the operators) and at least
+  the ground-state energy.
 
 Parity status: pinned in ``tests/test_oracle_replica.py`` against the paper's
 worked lifting example (``tests/golden/lift_example_hv.txt``), the identity
@@ -247,3 +258,36 @@ def unpadded(cores):
             G = G[:, :, :1]
         out.append(np.ascontiguousarray(G))
     return out
+
+
+# ---------------------------------------------------------------- physical-space optimization
+
+def tree_round(items, chi):
+    """Sum of TTs, two by two with a rounding after every sum (an odd last item
+    passes up unchanged), as in the replica-space step; the root is rounded
+    once more so that every result has the same canonical form."""
+    items = list(items)
+    while len(items) > 1:
+        nxt = [tt_round(tt_sum(items[i], items[i + 1]), chi) for i in range(0, len(items) - 1, 2)]
+        if len(items) % 2:
+            nxt.append(items[-1])
+        items = nxt
+    return tt_round(items[0], chi)
+
+
+def normalised(tt):
+    nrm = tt_norm(tt)
+    return tt_scale(tt, 1.0 / nrm), nrm
+
+
+def apply_operator(phi, eta, ops, chi):
+    """phi^alpha = O-bar_alpha phi (Sec. 3.2: psi^alpha = O_alpha psi built with
+    O-bar_alpha as in the replica-space optimization), rounded to chi and scaled
+    to unit replica-space norm.  Returns (phi^alpha, norm before scaling)."""
+    return normalised(tree_round([apply_string(phi, ops[k], eta[k]) for k in range(len(eta))], chi))
+
+
+def combine(phis, coef, chi):
+    """phi' = sum_alpha c_alpha phi^alpha (Eq. lin_comb, the TTs summed back into
+    one), rounded to chi and scaled to unit norm."""
+    return normalised(tree_round([tt_scale(p, float(c)) for p, c in zip(phis, coef)], chi))
