@@ -364,12 +364,11 @@ size_t q_site_doubles(int chi) {
     return (size_t)2 * (2 * cm) * (2 * cm);
 }
 
-// The tree over items 0..K-1 (term k = phi with string k and coefficient
-// eta_k), node outputs numbered in creation order, then the final pair.
-void build_pairs(rtt_tt_plan_s *p, const double *phi, double tau, std::vector<TTPair> &pairs) {
+// Pairs of the tree over `items` (two by two, an odd last item passes up),
+// level by level, node outputs in the plan's node buffers in creation order;
+// appends to `pairs`, sets the plan's level offsets and returns the root.
+TTItem build_tree(rtt_tt_plan_s *p, std::vector<TTItem> items, std::vector<TTPair> &pairs) {
     const size_t tt = (size_t)p->L * 2 * p->chi * p->chi;
-    std::vector<TTItem> items(p->K);
-    for (int k = 0; k < p->K; ++k) items[k] = TTItem{phi, p->d_ops + (size_t)k * p->L, p->eta[k]};
     pairs.clear();
     p->level_off.assign(1, 0);
     int node = 0;
@@ -384,9 +383,39 @@ void build_pairs(rtt_tt_plan_s *p, const double *phi, double tau, std::vector<TT
         items.swap(nxt);
         p->level_off.push_back((int)pairs.size());
     }
-    TTItem s = items[0];
+    return items[0];
+}
+
+std::vector<TTItem> term_items(rtt_tt_plan_s *p, const double *phi) {
+    std::vector<TTItem> items(p->K);
+    for (int k = 0; k < p->K; ++k) items[k] = TTItem{phi, p->d_ops + (size_t)k * p->L, p->eta[k]};
+    return items;
+}
+
+// (1 - tau H-bar): the tree's root S, then phi - tau S into the plan's next buffer.
+void build_pairs(rtt_tt_plan_s *p, const double *phi, double tau, std::vector<TTPair> &pairs) {
+    TTItem s = build_tree(p, term_items(p, phi), pairs);
     s.coef *= -tau;
     pairs.push_back(TTPair{TTItem{phi, nullptr, 1.0}, s, p->d_next});
+}
+
+// Upload a pair table (pageable source: staged before the call returns, copied
+// in stream order after earlier work that read the old table) and run it:
+// every tree level, then the final pair, which is scaled to unit norm.
+cudaError_t run_pairs(rtt_tt_plan_s *p, const std::vector<TTPair> &pairs, double *log_norm,
+                      cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(p->d_pairs, pairs.data(), pairs.size() * sizeof(TTPair),
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    const int nlev = (int)p->level_off.size() - 1;
+    for (int l = 0; l < nlev; ++l) {
+        const int n = p->level_off[l + 1] - p->level_off[l];
+        if ((e = launch_round_any(p->d_pairs + p->level_off[l], n, p->L, p->chi, p->d_scratch, 0,
+                                  nullptr, st)) != cudaSuccess)
+            return e;
+    }
+    return launch_round_any(p->d_pairs + p->level_off.back(), 1, p->L, p->chi, p->d_scratch, 1,
+                            log_norm, st);
 }
 
 }  // namespace
@@ -539,6 +568,48 @@ rtt_status rtt_tt_power(rtt_tt_plan p, double *phi, double tau, int32_t n_steps,
         if ((e = cudaMemcpyAsync(phi, p->d_next, tt * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
             return rp_fail(RTT_ERR_CUDA, std::string("rtt_tt_power: ") + cudaGetErrorString(e));
     }
+    return RTT_OK;
+}
+
+rtt_status rtt_tt_apply(rtt_tt_plan p, const double *phi, double *out, double *log_norm,
+                        void *stream) {
+    if (!p || !phi || !out) return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_apply: null pointer");
+    if (out == phi) return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_apply: out aliases phi");
+    cudaError_t e = cudaSetDevice(p->device);
+    if (e != cudaSuccess) return rp_fail(RTT_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    std::vector<TTPair> pairs;
+    TTItem root = build_tree(p, term_items(p, phi), pairs);
+    TTItem zero = root;
+    zero.coef = 0.0;
+    pairs.push_back(TTPair{root, zero, out});
+    p->pairs_valid = false;
+    if ((e = run_pairs(p, pairs, log_norm, (cudaStream_t)stream)) != cudaSuccess)
+        return rp_fail(RTT_ERR_CUDA, std::string("rtt_tt_apply: ") + cudaGetErrorString(e));
+    return RTT_OK;
+}
+
+rtt_status rtt_tt_sum_round(rtt_tt_plan p, int32_t n, const double *const *tts, const double *coef,
+                            double *out, double *log_norm, void *stream) {
+    if (!p || !tts || !coef || !out || n < 1)
+        return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_sum_round: null pointer or n < 1");
+    if (n > p->K)
+        return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_sum_round: n exceeds the plan's term count");
+    std::vector<TTItem> items(n);
+    for (int m = 0; m < n; ++m) {
+        if (!tts[m] || tts[m] == out)
+            return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_sum_round: null input or out aliases one");
+        items[m] = TTItem{tts[m], nullptr, coef[m]};
+    }
+    cudaError_t e = cudaSetDevice(p->device);
+    if (e != cudaSuccess) return rp_fail(RTT_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    std::vector<TTPair> pairs;
+    TTItem root = build_tree(p, items, pairs);
+    TTItem zero = root;
+    zero.coef = 0.0;
+    pairs.push_back(TTPair{root, zero, out});
+    p->pairs_valid = false;
+    if ((e = run_pairs(p, pairs, log_norm, (cudaStream_t)stream)) != cudaSuccess)
+        return rp_fail(RTT_ERR_CUDA, std::string("rtt_tt_sum_round: ") + cudaGetErrorString(e));
     return RTT_OK;
 }
 

@@ -104,8 +104,10 @@ def lib():
         L.rtt_tt_plan_destroy.argtypes = [P]
         L.rtt_tt_power.argtypes = [P, P, ctypes.c_double, I32, P, P]
         L.rtt_tt_round_sum.argtypes = [P, P, P, ctypes.c_double, P, P, ctypes.c_double, P, P, P]
+        L.rtt_tt_apply.argtypes = [P, P, P, P, P]
+        L.rtt_tt_sum_round.argtypes = [P, I32, P, P, P, P, P]
         for name in ("rtt_replica_lift", "rtt_tt_plan_create", "rtt_tt_plan_destroy",
-                     "rtt_tt_power", "rtt_tt_round_sum"):
+                     "rtt_tt_power", "rtt_tt_round_sum", "rtt_tt_apply", "rtt_tt_sum_round"):
             getattr(L, name).restype = ctypes.c_int
         L.rtt_status_string.argtypes = [I32]
         L.rtt_status_string.restype = ctypes.c_char_p
@@ -624,3 +626,28 @@ class TTPlan:
         _check(lib().rtt_tt_round_sum(self._p, _ptr(a), _ptr(ops_a), float(coef_a), _ptr(b),
                                       _ptr(ops_b), float(coef_b), _ptr(out), _ptr(log_norm),
                                       _stream(stream)), "rtt_tt_round_sum")
+
+    def apply(self, phi: torch.Tensor, out: torch.Tensor, log_norm: torch.Tensor = None,
+              stream=None):
+        """out <- round(H-bar phi) / norm for the plan's operator (rtt_tt_apply)."""
+        self._cores(phi, "phi")
+        self._cores(out, "out")
+        if log_norm is not None:
+            _dev_check(log_norm, torch.float64, (1,), "log_norm")
+        _check(lib().rtt_tt_apply(self._p, _ptr(phi), _ptr(out), _ptr(log_norm), _stream(stream)),
+               "rtt_tt_apply")
+
+    def sum_round(self, tts, coef, out: torch.Tensor, log_norm: torch.Tensor = None, stream=None):
+        """out <- round(sum_m coef[m] tts[m]) / norm (rtt_tt_sum_round)."""
+        for m, t in enumerate(tts):
+            self._cores(t, f"tts[{m}]")
+        self._cores(out, "out")
+        if log_norm is not None:
+            _dev_check(log_norm, torch.float64, (1,), "log_norm")
+        n = len(tts)
+        ptrs = (ctypes.c_void_p * n)(*[t.data_ptr() for t in tts])
+        c = np.ascontiguousarray(coef, dtype=np.float64)
+        if c.shape != (n,):
+            raise ValueError("coef must have one entry per TT")
+        _check(lib().rtt_tt_sum_round(self._p, n, ptrs, c.ctypes.data, _ptr(out), _ptr(log_norm),
+                                      _stream(stream)), "rtt_tt_sum_round")

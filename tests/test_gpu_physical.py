@@ -1,0 +1,125 @@
+"""Physical-space optimization through the library against the oracle (Sec. 3.2).
+
+Deterministic parts (operator application, the TT of a combination) are
+compared on amplitudes from random starts (unique truncations, as in
+test_gpu_replica.py: 1e-9 of the largest amplitude per rounding chain).  The
+sampled parts (H~, S~ by dual Monte Carlo) are compared with their exact
+enumeration within a multiple of the reported standard errors.
+"""
+import numpy as np
+import pytest
+
+from paper_2604_22718_gb300 import inputs
+from oracle import dual
+from oracle import replica as rp
+
+torch = pytest.importorskip("torch")
+
+LX, LY, ORDER = 3, 2, ("H", "V")
+
+
+def _operators():
+    return [("1", []),
+            ("X", inputs.replica_terms(LX, LY, ORDER, [], 1.0)),
+            ("ZZ_HV", inputs.replica_terms(LX, LY, ORDER, [("H", 1.0, "H"), ("V", 1.0, "V")], 0.0))]
+
+
+def _path():
+    return inputs.path_sum([inputs.ordering(o, LX, LY) for o in ORDER])
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _opt(chi):
+    from paper_2604_22718_gb300.physical import PhysicalOptimizer
+    return PhysicalOptimizer(LX * LY, _path(), inputs.open_bonds(LX, LY), 1.0, 3.0, chi, _operators())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("chi", [2, 3])
+def test_operator_states_match_oracle(chi):
+    opt = _opt(chi)
+    phi0 = inputs.replica_start(40 + chi, 12, chi)
+    phis, logn = opt.operator_states(_dev(phi0))
+    torch.cuda.synchronize()
+    for a, (_, eta, ops) in enumerate(opt.ops):
+        ref, nrm = rp.apply_operator(rp.unpadded(phi0), eta, ops, chi)
+        got = rp.unpadded(phis[a].cpu().numpy())
+        x, y = rp.tt_dense(got), rp.tt_dense(ref)
+        assert np.abs(x - y).max() <= 1e-9 * np.abs(y).max()
+        assert float(logn[a]) == pytest.approx(np.log(nrm), rel=1e-10, abs=1e-10)
+    opt.close()
+
+
+@pytest.mark.gpu
+def test_sum_round_matches_oracle_combine():
+    rtt = pytest.importorskip("paper_2604_22718_gb300.rtt")
+    L, chi = 30, 2
+    phis = [inputs.replica_start(70 + m, L, chi) for m in range(5)]
+    c = np.array([0.5, -1.5, 2.0, 0.25, -0.75])
+    plan = rtt.TTPlan(L, chi, np.ones(5), np.zeros((5, L), dtype=np.uint8))
+    out = torch.empty((L, 2, chi, chi), dtype=torch.float64, device="cuda")
+    ln = torch.empty(1, dtype=torch.float64, device="cuda")
+    plan.sum_round([_dev(p) for p in phis], c, out, ln)
+    torch.cuda.synchronize()
+    ref, nrm = rp.combine([rp.unpadded(p) for p in phis], c, chi)
+    rng = np.random.default_rng(1)
+    idx = rng.integers(0, 2, size=(512, L))
+    x, y = rp.tt_eval(rp.unpadded(out.cpu().numpy()), idx), rp.tt_eval(ref, idx)
+    assert np.abs(x - y).max() <= 1e-9 * np.abs(y).max()
+    assert float(ln.item()) == pytest.approx(np.log(nrm), rel=1e-10)
+    with pytest.raises(rtt.RTTError, match="n exceeds"):
+        plan.sum_round([_dev(p) for p in phis] + [_dev(phis[0])], np.ones(6), out)
+
+
+@pytest.mark.gpu
+def test_physical_step_against_exact_enumeration():
+    """One iteration on 3x2 (four sites per spin pair, N = 6): sampled H~, S~
+    within 6 standard errors (plus 1e-9) of their enumeration over the GPU's own
+    operator states; the combination's TT equals the oracle's combination with
+    the same coefficients; lambda_0 lies between the ground-state energy and
+    the starting energy."""
+    opt = _opt(2)
+    phi0 = inputs.replica_start(77, 12, 2)
+    spins0 = inputs.initial_spins(5, 4096, 6)
+    res = opt.step(_dev(phi0), spins0, chains=4096, sweeps=200, burn=20, seed=31)
+    torch.cuda.synchronize()
+    path = _path()
+    e0v = np.zeros(2)
+    e0v[0] = 1.0
+    states = [inputs.RTTInstance(n_spins=6, path=path.astype(np.int32), tensors=p.cpu().numpy(),
+                                 b_left=e0v, b_right=e0v.copy(), bonds=inputs.open_bonds(LX, LY),
+                                 J=1.0, h=3.0) for p in res["phis"]]
+    Ht, St = dual.exact_tilde_matrices(states)
+    assert np.all(np.abs(res["Ht"] - Ht) <= 6 * res["Ht_se"] + 1e-9), (res["Ht"], Ht, res["Ht_se"])
+    assert np.all(np.abs(res["St"] - St) <= 6 * res["St_se"] + 1e-9), (res["St"], St, res["St_se"])
+    ref, _ = rp.combine([rp.unpadded(p.cpu().numpy()) for p in res["phis"]], res["c"], 2)
+    got = rp.unpadded(res["phi"].cpu().numpy())
+    x, y = rp.tt_dense(got), rp.tt_dense(ref)
+    assert np.abs(x - y).max() <= 1e-9 * np.abs(y).max()
+    w, _ = dual.solve(Ht, St)
+    lam = res["lambda"][0].real
+    assert lam == pytest.approx(w[0].real, abs=0.02 * abs(w[0].real))
+    # exact bounds: ground state <= lambda_0 (exact) <= energy of the start (identity included)
+    H = _dense_tfim(6, inputs.open_bonds(LX, LY), 1.0, 3.0)
+    psi1 = rp.constrained_amplitudes(rp.unpadded(phi0), path, 6)
+    assert np.linalg.eigvalsh(H)[0] - 1e-9 <= w[0].real <= psi1 @ H @ psi1 / (psi1 @ psi1) + 1e-9
+    opt.close()
+
+
+def _dense_tfim(n, bonds, J, h):
+    I2, Z, X = np.eye(2), np.diag([1.0, -1.0]), np.array([[0.0, 1.0], [1.0, 0.0]])
+
+    def op(site_ops):
+        m = np.array([[1.0]])
+        for i in range(n):
+            m = np.kron(m, site_ops.get(i, I2))
+        return m
+    H = np.zeros((1 << n, 1 << n))
+    for i, j in bonds:
+        H += J * op({int(i): Z, int(j): Z})
+    for i in range(n):
+        H -= h * op({i: X})
+    return H
