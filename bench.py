@@ -760,7 +760,8 @@ def run_replica(args):
     while n > 1:
         n = n // 2 + n % 2
         levels += 1
-    plan = rtt.TTPlan(L, chi, eta, ops)
+    tt_prec = "fp64" if args.precision == "fp64" else "fp32"
+    plan = rtt.TTPlan(L, chi, eta, ops, precision=tt_prec)
     phi0 = inputs.replica_ones(L, chi)
     phi = torch.from_numpy(phi0).cuda()
     K, W = args.steps, args.warmup
@@ -786,7 +787,8 @@ def run_replica(args):
     flops_step = K_terms * rounding_flops(L, chi)
     achieved = flops_step / (step_ms / 1e3) / 1e12
     peaks, _ = measured_peaks()
-    peak = SM_COUNT * FP64_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    lanes = FP64_LANES_PER_SM if tt_prec == "fp64" else FP32_LANES_PER_SM
+    peak = SM_COUNT * lanes * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     lognorm = ln.cpu().numpy()
     # end to end: phi from pinned host memory, one step, phi and its log-norm back
     e2e = None
@@ -841,7 +843,7 @@ def run_replica(args):
         "metric": "replica-space optimization steps/s (1 - tau H-bar on the TT, rounded to chi)",
         "value": value, "unit": "steps/s", "n_gpus": 1, "steps": K, "warmup": W,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": {"fp64": "f64", "fp32": "f32"}[tt_prec], "data": "synthetic",
         "config": {"workload": f"{name}: {lx}x{ly} open TFIM h={h}, path "
                                f"{'+'.join(order)} (L={L}), H-bar_{w['kind']} ({K_terms} terms, "
                                f"{levels} tree levels), chi={chi}, tau={tau}, phi0 = 1",
@@ -856,7 +858,9 @@ def run_replica(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "k_tt_round",
                      "flops_per_step": flops_step,
-                     "peak_source": "FP64 CUDA-core peak, 152 SMs x 2 FP64 FMA lanes x 2070 MHz",
+                     "peak_source": ("FP64 CUDA-core peak, 152 SMs x 2 FP64 FMA lanes x 2070 MHz"
+                                     if tt_prec == "fp64" else
+                                     "FP32 CUDA-core peak, 152 SMs x 128 FP32 FMA lanes x 2070 MHz"),
                      "note": "latency-bound: each rounding is a chain of 2 L dependent small "
                              "factorizations on one warp"},
         "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
@@ -886,10 +890,12 @@ def run_physical(args):
            ("ZZ_HV", inputs.replica_terms(lx, ly, order, [("H", 1.0, "H"), ("V", 1.0, "V")], 0.0)),
            ("ZZ_DDp", inputs.replica_terms(lx, ly, order, [("D", 1.0, "D"), ("Dp", 1.0, "Dp")], 0.0))]
     eta, hops = rtt.replica_lift(N, path, inputs.hbar_terms("HV", lx, ly, h, orderings=order))
-    plan = rtt.TTPlan(L, chi, eta, hops)
+    prec = "fp64" if args.precision == "fp64" else "fp32"
+    plan = rtt.TTPlan(L, chi, eta, hops, precision=prec)
     phi = torch.from_numpy(inputs.replica_ones(L, chi)).cuda()
     plan.power(phi, tau, 30)
-    opt = PhysicalOptimizer(N, path, inputs.open_bonds(lx, ly), 1.0, h, chi, ops)
+    opt = PhysicalOptimizer(N, path, inputs.open_bonds(lx, ly), 1.0, h, chi, ops, precision=prec,
+                            tt_precision=prec)
     B, S, burn = args.chains or 4096, 100, 20
     spins0 = inputs.initial_spins(22741, B, N)
     e_start = opt.energy(phi, B, 200, 50, 22742)
@@ -954,11 +960,11 @@ def run_physical(args):
                   "eigenproblem, combined TT)",
         "value": value, "unit": "iterations/s", "n_gpus": 1, "steps": K, "warmup": W,
         "ms_per_step": 1e3 * total / K, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32"}[prec], "data": "synthetic",
         "config": {"workload": f"physical_6x6: 6x6 open TFIM h={h}, path V+H+D+Dp (L={L}), chi={chi}, "
                                f"operators 1, O_X, O_ZZ,HV, O_ZZ,DD' ({M} states), start = 30 steps of "
                                f"H-bar_HV from phi0 = 1; dual Monte Carlo {B} chains x {S} sweeps "
-                               f"(+{burn} burn-in) per state, FP64 sampler",
+                               f"(+{burn} burn-in) per state, {prec.upper()} sampler and TT arithmetic",
                    "timing": "host wall clock around each iteration (synchronized), includes "
                              "handle creation and the host eigen-solver"},
         "dual_samples_per_s": dual_samples * value,

@@ -385,12 +385,16 @@ typedef struct rtt_tt_plan_s *rtt_tt_plan;
 
 /* A plan for (1 - tau H-bar) on TTs of `length` sites and rank chi (1..16),
  * H-bar = sum_k eta[k] P_k with the strings ops [n_terms][length] (host,
- * codes as above; n_terms >= 1, length >= 2).  Copies the strings to the
- * device, allocates the tree's node TTs (n_terms - 1 of them) and the
- * rounding scratch (floor(n_terms/2) * length * 2 * (2 chi)^2 doubles) on
- * `device`.  *out owned by the caller (rtt_tt_plan_destroy). */
-rtt_status rtt_tt_plan_create(int32_t length, int32_t chi, int32_t n_terms, const uint8_t *ops,
-                              const double *eta, int32_t device, rtt_tt_plan *out);
+ * codes as above; n_terms >= 1, length >= 2).  precision: RTT_FP64 or
+ * RTT_FP32, the arithmetic of the roundings (cores are FP64 in memory either
+ * way; FP32 runs the factorizations at the FP32 rate, with correspondingly
+ * larger rounding errors).  Copies the strings to the device, allocates the
+ * tree's node TTs (n_terms - 1 of them) and the rounding scratch
+ * (floor(n_terms/2) * length * 2 * (2 c)^2 values, c = chi rounded up to 4, 8
+ * or 16) on `device`.  *out owned by the caller (rtt_tt_plan_destroy). */
+rtt_status rtt_tt_plan_create(int32_t length, int32_t chi, int32_t precision, int32_t n_terms,
+                              const uint8_t *ops, const double *eta, int32_t device,
+                              rtt_tt_plan *out);
 rtt_status rtt_tt_plan_destroy(rtt_tt_plan plan);
 
 /* n_steps applications of 1 - tau H-bar to phi in place (device padded

@@ -44,25 +44,60 @@ rtt_status rp_fail(rtt_status s, const std::string &msg) {
     return s;
 }
 
-// Per-warp shared memory (doubles), CM = compile-time bound on chi.
-template <int CM>
+// Per-warp shared memory, T = arithmetic type, CM = compile-time bound on chi:
+// the Householder vectors of the current site and the R factor carried to the
+// next one.  Everything else lives in registers, one matrix column per lane.
+template <typename T, int CM>
 struct WarpSmem {
     static constexpr int D2 = 2 * CM, MR = 4 * CM;
-    double m[D2][MR];        // sweep 1: columns of the matrix being factored (then Q)
-    double v[D2][MR];        // sweep 1: Householder vectors
-    double beta[D2];
-    double r[D2][D2];        // R factor carried to the next site (row-major)
-    double x[2][D2][D2];     // sweep 2: columns being rotated (double-buffered)
-    double vv[2][D2][D2];    // sweep 2: accumulated rotations, columns
-    double w[D2][CM];        // sweep 2: U S carried to the left, [row][kept column]
-    double sig[D2];
-    int sel[CM];
+    T v[D2][MR];        // sweep 1: Householder vectors (zero above their pivot)
+    T beta[D2];
+    T r[D2][D2];        // R factor carried to the next site (row-major)
 };
+
+template <typename T> struct Arith;
+// eps: unit roundoff x 2, times the column length the Jacobi threshold; big: the
+// largest zeta whose square is finite; tiny: a column whose squared norm is
+// below it counts as zero in the QR (v^T v >= 2 |x|^2, so 2 / v^T v stays
+// finite; at the O(1) scale of these matrices such a column is far below the
+// type's resolution).
+template <> struct Arith<double> {
+    static constexpr double eps = 2.220446049250313e-16;
+    static constexpr double big = 1e150;
+    static constexpr double tiny = 1e-290;
+};
+template <> struct Arith<float> {
+    static constexpr float eps = 1.1920929e-7f;
+    static constexpr float big = 1e18f;
+    static constexpr float tiny = 1e-30f;
+};
+
+// floor(log2 x) of a finite x > 0 from its exponent field, clamped so that
+// pow2<T>(-e) stays a normal number; pow2<T>(e) = 2^e exactly.
+__device__ __forceinline__ int exp2_of(float x) {
+    const int e = (int)((__float_as_uint(x) >> 23) & 0xffu) - 127;
+    return max(-125, min(125, e));
+}
+__device__ __forceinline__ int exp2_of(double x) {
+    const int e = (int)((unsigned long long)(__double_as_longlong(x) >> 52) & 0x7ffull) - 1023;
+    return max(-1021, min(1021, e));
+}
+template <typename T> __device__ __forceinline__ T pow2(int e);
+template <> __device__ __forceinline__ float pow2<float>(int e) {
+    return __uint_as_float((unsigned)(127 + e) << 23);
+}
+template <> __device__ __forceinline__ double pow2<double>(int e) {
+    return __longlong_as_double((long long)(1023 + e) << 52);
+}
 
 // Element (b, s, c) of the sum core at site k: block diagonal in the middle,
 // [a | b] at the first site, [a ; b] stacked at the last; strings applied.
-__device__ __forceinline__ double item_core(const TTItem &it, int L, int chi, int k, int s,
-                                            int b, int c) {
+// The first cores are scaled by s0 (an exact power of two) in FP64 before the
+// conversion to T, so that a TT whose norm sits in its first core cannot
+// overflow the arithmetic type.
+template <typename T>
+__device__ __forceinline__ T item_core(const TTItem &it, int L, int chi, int k, int s, int b, int c,
+                                       double s0) {
     int so = s;
     double sg = 1.0;
     if (it.ops) {
@@ -70,270 +105,383 @@ __device__ __forceinline__ double item_core(const TTItem &it, int L, int chi, in
         if (op == 1) so = 1 - s;
         else if (op == 2 && s == 1) sg = -1.0;
     }
-    if (k == 0) sg *= it.coef;
-    return sg * it.tt[(((size_t)k * 2 + so) * chi + b) * chi + c];
+    if (k == 0) sg *= it.coef * s0;
+    return (T)(sg * it.tt[(((size_t)k * 2 + so) * chi + b) * chi + c]);
 }
 
-__device__ __forceinline__ double sum_core(const TTItem &A, const TTItem &B, int L, int chi, int k,
-                                           int s, int b, int c) {
+template <typename T>
+__device__ __forceinline__ T sum_core(const TTItem &A, const TTItem &B, int L, int chi, int k, int s,
+                                      int b, int c, double s0) {
     if (k == 0) {                         // left rank 1
-        return c < chi ? item_core(A, L, chi, k, s, 0, c) : item_core(B, L, chi, k, s, 0, c - chi);
+        return c < chi ? item_core<T>(A, L, chi, k, s, 0, c, s0)
+                       : item_core<T>(B, L, chi, k, s, 0, c - chi, s0);
     }
     if (k == L - 1) {                     // right rank 1
-        return b < chi ? item_core(A, L, chi, k, s, b, 0) : item_core(B, L, chi, k, s, b - chi, 0);
+        return b < chi ? item_core<T>(A, L, chi, k, s, b, 0, s0)
+                       : item_core<T>(B, L, chi, k, s, b - chi, 0, s0);
     }
-    if (b < chi && c < chi) return item_core(A, L, chi, k, s, b, c);
-    if (b >= chi && c >= chi) return item_core(B, L, chi, k, s, b - chi, c - chi);
-    return 0.0;
+    if (b < chi && c < chi) return item_core<T>(A, L, chi, k, s, b, c, s0);
+    if (b >= chi && c >= chi) return item_core<T>(B, L, chi, k, s, b - chi, c - chi, s0);
+    return T(0);
 }
 
-template <int CM>
+template <typename T, int CM>
 __global__ void __launch_bounds__(128) k_tt_round(const TTPair *__restrict__ pairs, int npairs,
-                                                  int L, int chi, double *__restrict__ scratch,
+                                                  int L, int chi, T *__restrict__ scratch,
                                                   int normalize, double *__restrict__ log_norm) {
-    constexpr int D2M = 2 * CM;
+    constexpr int D2M = 2 * CM, MR = 4 * CM;
+    constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int w = blockIdx.x * (blockDim.x >> 5) + wib;
     if (w >= npairs) return;
-    WarpSmem<CM> &S = reinterpret_cast<WarpSmem<CM> *>(smem_raw)[wib];
+    WarpSmem<T, CM> &S = reinterpret_cast<WarpSmem<T, CM> *>(smem_raw)[wib];
     const TTPair P = pairs[w];
     const int D2 = 2 * chi;
     const size_t qstride = (size_t)2 * D2M * D2M;            // one site's Q, [row (a,s)][col]
-    double *Q = scratch + (size_t)w * L * qstride;
+    T *Q = scratch + (size_t)w * L * qstride;
+
+    // Power-of-two bookkeeping: the TT's scale is carried as an integer
+    // exponent E (a TT of ones on 144 sites has norm 2^72, whose square
+    // exceeds the FP32 range).  First the first cores, scaled on load ...
+    int E = 0;
+    double s0 = 1.0;
+    {
+        double mx = 0.0;
+        for (int e = lane; e < 2 * chi; e += 32) {
+            const int s = e / chi, c = e % chi;
+            mx = fmax(mx, fabs(P.a.coef * P.a.tt[(s * chi + 0) * chi + c]));
+            mx = fmax(mx, fabs(P.b.coef * P.b.tt[(s * chi + 0) * chi + c]));
+        }
+        for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, off));
+        if (mx > 0.0 && isfinite(mx)) {
+            E = exp2_of(mx);
+            s0 = pow2<double>(-E);
+        }
+    }
 
     // ---------------- sweep 1: left to right, Householder QR -----------------
+    // Lane c holds column c of M = R x_1 G_k in col[], rows (a, s) -> a * 2 + s.
     // R starts as the 1 x 1 identity (left rank 1 at the first site).
-    if (lane == 0) S.r[0][0] = 1.0;
+    if (lane == 0) S.r[0][0] = T(1);
     __syncwarp();
     int rl = 1;                                  // rows of R = left rank of M
+    T col[MR];
     for (int k = 0; k < L; ++k) {
         const int dl = (k == 0) ? 1 : D2;        // left bond of the sum core
         const int dr = (k == L - 1) ? 1 : D2;    // right bond
-        const int mr = 2 * rl;                   // rows of M, (a, s) -> a * 2 + s
-        // M = R x_1 G_k, lanes own columns c < dr
+        const int mr = 2 * rl;
+#pragma unroll
+        for (int i = 0; i < MR; ++i) col[i] = T(0);
         if (lane < dr) {
-            for (int a = 0; a < rl; ++a)
-                for (int s = 0; s < 2; ++s) {
-                    double acc = 0.0;
-                    for (int b = 0; b < dl; ++b) {
-                        const double g = sum_core(P.a, P.b, L, chi, k, s, b, lane);
-                        acc = fma(S.r[a][b], g, acc);
+            for (int b = 0; b < dl; ++b) {
+                const T g0 = sum_core<T>(P.a, P.b, L, chi, k, 0, b, lane, s0);
+                const T g1 = sum_core<T>(P.a, P.b, L, chi, k, 1, b, lane, s0);
+#pragma unroll
+                for (int a = 0; a < D2M; ++a)
+                    if (a < rl) {
+                        const T rab = S.r[a][b];
+                        col[2 * a] = fma(rab, g0, col[2 * a]);
+                        col[2 * a + 1] = fma(rab, g1, col[2 * a + 1]);
                     }
-                    S.m[lane][a * 2 + s] = acc;
-                }
+            }
         }
-        __syncwarp();
-        double *Qk = Q + (size_t)k * qstride;
+        // ... then M at every site: its largest entry brought into [1, 2)
+        {
+            T mx = T(0);
+#pragma unroll
+            for (int i = 0; i < MR; ++i)
+                if (i < mr) mx = fmax(mx, fabs(col[i]));
+            for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, off));
+            if (mx > T(0) && isfinite(mx)) {
+                const int e = exp2_of(mx);
+                if (e != 0) {
+                    const T f = pow2<T>(-e);
+#pragma unroll
+                    for (int i = 0; i < MR; ++i) col[i] *= f;
+                    E += e;
+                }
+            }
+        }
+        __syncwarp();                            // S.r is rewritten below
+        T *Qk = Q + (size_t)k * qstride;
         if (k == L - 1) {                        // the last core keeps R absorbed
-            for (int i = lane; i < mr; i += 32) Qk[(size_t)i * D2M] = S.m[0][i];
-            __syncwarp();
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < MR; ++i)
+                    if (i < mr) Qk[(size_t)i * D2M] = col[i];
+            }
+            __syncwarp();                        // lane 1 reads this core in sweep 2
             break;
         }
         const int m = min(mr, dr);
         for (int j = 0; j < m; ++j) {
             if (lane == j) {
-                double n2 = 0.0;
-                for (int i = j; i < mr; ++i) n2 = fma(S.m[j][i], S.m[j][i], n2);
-                const double x0 = S.m[j][j];
-                double beta = 0.0, alpha = 0.0;
-                if (n2 > 0.0) {
-                    alpha = x0 >= 0.0 ? -sqrt(n2) : sqrt(n2);
-                    const double v0 = x0 - alpha;
-                    const double vtv = n2 - x0 * x0 + v0 * v0;
-                    beta = vtv > 0.0 ? 2.0 / vtv : 0.0;
-                    S.v[j][j] = v0;
-                    for (int i = j + 1; i < mr; ++i) S.v[j][i] = S.m[j][i];
-                } else {
-                    for (int i = j; i < mr; ++i) S.v[j][i] = 0.0;
-                    alpha = 0.0;
+                T n2 = T(0), x0 = T(0);
+#pragma unroll
+                for (int i = 0; i < MR; ++i) {
+                    if (i >= j && i < mr) n2 = fma(col[i], col[i], n2);
+                    if (i == j) x0 = col[i];
+                }
+                T beta = T(0), alpha = T(0), v0 = T(0);
+                const bool live = n2 > Arith<T>::tiny;
+                if (live) {
+                    alpha = x0 >= T(0) ? -sqrt(n2) : sqrt(n2);
+                    v0 = x0 - alpha;
+                    const T vtv = n2 - x0 * x0 + v0 * v0;
+                    beta = vtv > T(0) ? T(2) / vtv : T(0);
+                }
+#pragma unroll
+                for (int i = 0; i < MR; ++i) {
+                    T vi = T(0);
+                    if (live && i > j && i < mr) vi = col[i];
+                    if (live && i == j) vi = v0;
+                    S.v[j][i] = vi;
+                    if (i == j) col[i] = live ? alpha : x0;
+                    else if (i > j && live) col[i] = T(0);
                 }
                 S.beta[j] = beta;
-                S.m[j][j] = alpha;
-                for (int i = j + 1; i < mr; ++i) S.m[j][i] = 0.0;
             }
             __syncwarp();
             if (lane > j && lane < dr) {
-                const double beta = S.beta[j];
-                double d = 0.0;
-                for (int i = j; i < mr; ++i) d = fma(S.v[j][i], S.m[lane][i], d);
+                const T beta = S.beta[j];
+                T d = T(0);
+#pragma unroll
+                for (int i = 0; i < MR; ++i)
+                    if (i < mr) d = fma(S.v[j][i], col[i], d);
                 d *= beta;
-                for (int i = j; i < mr; ++i) S.m[lane][i] = fma(-d, S.v[j][i], S.m[lane][i]);
+#pragma unroll
+                for (int i = 0; i < MR; ++i)
+                    if (i < mr) col[i] = fma(-d, S.v[j][i], col[i]);
             }
-            __syncwarp();
         }
-        // R (m x dr, upper trapezoidal) for the next site
-        if (lane < dr)
-            for (int j = 0; j < m; ++j) S.r[j][lane] = (j <= lane) ? S.m[lane][j] : 0.0;
-        __syncwarp();
-        // Q = H_0 ... H_{m-1} I[:, :m], lanes own columns c < m
+        // R (m x dr, upper trapezoidal) for the next site: rows j < m of the columns
+        if (lane < dr) {
+#pragma unroll
+            for (int j = 0; j < D2M; ++j)
+                if (j < m) S.r[j][lane] = col[j];
+        }
+        // Q = H_0 ... H_{m-1} I[:, :m], lane c < m builds column c
         if (lane < m) {
-            for (int i = 0; i < mr; ++i) S.m[lane][i] = (i == lane) ? 1.0 : 0.0;
+#pragma unroll
+            for (int i = 0; i < MR; ++i) col[i] = (i == lane) ? T(1) : T(0);
             for (int j = m - 1; j >= 0; --j) {
-                const double beta = S.beta[j];
-                double d = 0.0;
-                for (int i = j; i < mr; ++i) d = fma(S.v[j][i], S.m[lane][i], d);
+                const T beta = S.beta[j];
+                T d = T(0);
+#pragma unroll
+                for (int i = 0; i < MR; ++i)
+                    if (i < mr) d = fma(S.v[j][i], col[i], d);
                 d *= beta;
-                for (int i = j; i < mr; ++i) S.m[lane][i] = fma(-d, S.v[j][i], S.m[lane][i]);
+#pragma unroll
+                for (int i = 0; i < MR; ++i)
+                    if (i < mr) col[i] = fma(-d, S.v[j][i], col[i]);
             }
-            for (int i = 0; i < mr; ++i) Qk[(size_t)i * D2M + lane] = S.m[lane][i];
+#pragma unroll
+            for (int i = 0; i < MR; ++i)
+                if (i < mr) Qk[(size_t)i * D2M + lane] = col[i];
         }
-        __syncwarp();
+        __syncwarp();                            // S.v, S.beta, S.r complete
         rl = m;
     }
 
     // ---------------- sweep 2: right to left, truncated SVD ------------------
-    // rank to the left of site k after sweep 1: min(2^k, 2 chi)
+    // Lane j holds column j of the unfolding N (rows: left bond a < r0; columns
+    // (s, c) -> s * r1 + c) in x[] and column j of the accumulated rotation V
+    // in vc[]; the partner's columns come by shuffle.
     auto rank_left = [&](int k) { return k >= 5 ? D2 : min(1 << k, D2); };
     double *out = P.out;
-    // N for site L-1: rows a < r0, columns s (right rank 1)
     int r1 = 1;
-    int cur = 0;
+    T x[D2M], vc[D2M];
     {
         const int r0 = rank_left(L - 1);
-        const double *Qk = Q + (size_t)(L - 1) * qstride;
-        if (lane < 2)
-            for (int a = 0; a < r0; ++a) S.x[0][lane][a] = Qk[(size_t)(a * 2 + lane) * D2M];
-        __syncwarp();
+        const T *Qk = Q + (size_t)(L - 1) * qstride;
+#pragma unroll
+        for (int a = 0; a < D2M; ++a)
+            x[a] = (lane < 2 && a < r0) ? Qk[(size_t)(a * 2 + lane) * D2M] : T(0);
     }
     for (int k = L - 1; k >= 1; --k) {
         const int r0 = rank_left(k);
-        const int n2 = 2 * r1;                   // columns (s, c) -> s * r1 + c
-        // V = I
-        if (lane < n2)
-            for (int i = 0; i < n2; ++i) S.vv[cur][lane][i] = (i == lane) ? 1.0 : 0.0;
-        __syncwarp();
-        // Hestenes sweeps with a round-robin tournament (n2 even)
-        for (int sweep = 0; sweep < 60; ++sweep) {
+        const int n2 = 2 * r1;
+#pragma unroll
+        for (int i = 0; i < D2M; ++i) vc[i] = (i == lane) ? T(1) : T(0);
+        // Hestenes sweeps with a round-robin tournament (n2 even): player 0
+        // fixed, players 1..n2-1 rotate by one position per round
+        for (int sweep = 0; sweep < 30; ++sweep) {
             int rotated = 0;
             for (int rnd = 0; rnd < n2 - 1; ++rnd) {
-                const int nxt = cur ^ 1;
+                int partner = lane;
                 if (lane < n2) {
-                    // circle method: player 0 fixed, the others rotate
-                    const int pos = (lane == 0) ? 0 : ((lane - 1 - rnd + 2 * (n2 - 1)) % (n2 - 1)) + 1;
-                    const int ppos = n2 - 1 - pos;
-                    const int partner = (ppos == 0) ? 0 : ((ppos - 1 + rnd) % (n2 - 1)) + 1;
-                    const int lo = min(lane, partner), hi = max(lane, partner);
-                    double a = 0.0, b = 0.0, g = 0.0;
-                    for (int i = 0; i < r0; ++i) {
-                        const double xl = S.x[cur][lo][i], xh = S.x[cur][hi][i];
-                        a = fma(xl, xl, a);
-                        b = fma(xh, xh, b);
-                        g = fma(xl, xh, g);
+                    int pos = 0;
+                    if (lane > 0) {
+                        pos = lane - 1 - rnd;
+                        if (pos < 0) pos += n2 - 1;
+                        pos += 1;
                     }
-                    double c = 1.0, sn = 0.0;
-                    if (g != 0.0 && fabs(g) > 2.220446049250313e-16 * sqrt(a * b)) {
-                        const double zeta = (b - a) / (2.0 * g);
+                    const int ppos = n2 - 1 - pos;
+                    if (ppos == 0) {
+                        partner = 0;
+                    } else {
+                        int q = ppos - 1 + rnd;
+                        if (q >= n2 - 1) q -= n2 - 1;
+                        partner = q + 1;
+                    }
+                }
+                T px[D2M], pv[D2M];
+#pragma unroll
+                for (int i = 0; i < D2M; ++i) {
+                    px[i] = __shfl_sync(FULL, x[i], partner);
+                    pv[i] = __shfl_sync(FULL, vc[i], partner);
+                }
+                if (lane < n2) {
+                    const bool am_lo = lane < partner;
+                    T a = T(0), b = T(0), g = T(0);
+#pragma unroll
+                    for (int i = 0; i < D2M; ++i)
+                        if (i < r0) {
+                            const T xl = am_lo ? x[i] : px[i], xh = am_lo ? px[i] : x[i];
+                            a = fma(xl, xl, a);
+                            b = fma(xh, xh, b);
+                            g = fma(xl, xh, g);
+                        }
+                    // rotate while the columns are not orthogonal to the working
+                    // precision: the computed g carries about r0 roundings of its own
+                    T c = T(1), sn = T(0);
+                    const T tol = Arith<T>::eps * T(r0);
+                    if (g != T(0) && g * g > tol * tol * a * b) {
+                        const T zeta = (b - a) / (T(2) * g);
                         // smaller root of t^2 + 2 zeta t - 1 = 0; 1/(2 zeta) once zeta^2 would overflow
-                        const double t = fabs(zeta) > 1e150
-                                             ? 0.5 / zeta
-                                             : (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                        c = 1.0 / sqrt(1.0 + t * t);
+                        const T t = fabs(zeta) > Arith<T>::big
+                                        ? T(0.5) / zeta
+                                        : (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                        c = T(1) / sqrt(T(1) + t * t);
                         sn = c * t;
                         rotated = 1;
                     }
                     // lo' = c lo - s hi, hi' = s lo + c hi
-                    const bool am_lo = (lane == lo);
-                    for (int i = 0; i < r0; ++i) {
-                        const double xl = S.x[cur][lo][i], xh = S.x[cur][hi][i];
-                        S.x[nxt][lane][i] = am_lo ? (c * xl - sn * xh) : (sn * xl + c * xh);
-                    }
-                    for (int i = 0; i < n2; ++i) {
-                        const double vl = S.vv[cur][lo][i], vh = S.vv[cur][hi][i];
-                        S.vv[nxt][lane][i] = am_lo ? (c * vl - sn * vh) : (sn * vl + c * vh);
+#pragma unroll
+                    for (int i = 0; i < D2M; ++i) {
+                        const T xl = am_lo ? x[i] : px[i], xh = am_lo ? px[i] : x[i];
+                        x[i] = am_lo ? (c * xl - sn * xh) : (sn * xl + c * xh);
+                        const T vl = am_lo ? vc[i] : pv[i], vh = am_lo ? pv[i] : vc[i];
+                        vc[i] = am_lo ? (c * vl - sn * vh) : (sn * vl + c * vh);
                     }
                 }
-                __syncwarp();
-                cur ^= 1;
             }
-            if (!__any_sync(0xffffffffu, rotated)) break;
+            if (!__any_sync(FULL, rotated)) break;
         }
-        // singular values and the kept columns, largest first (ties by index)
-        if (lane < n2) {
-            double s2 = 0.0;
-            for (int i = 0; i < r0; ++i) s2 = fma(S.x[cur][lane][i], S.x[cur][lane][i], s2);
-            S.sig[lane] = sqrt(s2);
+        // singular values and ranks (largest first, ties by index)
+        T s2 = T(0);
+#pragma unroll
+        for (int i = 0; i < D2M; ++i)
+            if (i < r0) s2 = fma(x[i], x[i], s2);
+        const T sig = lane < n2 ? sqrt(s2) : T(-1);
+        int rank = 0;
+        for (int j = 0; j < n2; ++j) {
+            const T sj = __shfl_sync(FULL, sig, j);
+            rank += (sj > sig) || (sj == sig && j < lane);
         }
-        __syncwarp();
         const int t = min(chi, min(r0, n2));
-        if (lane < n2) {
-            int rank = 0;
-            for (int j = 0; j < n2; ++j)
-                rank += (S.sig[j] > S.sig[lane]) || (S.sig[j] == S.sig[lane] && j < lane);
-            if (rank < t) S.sel[rank] = lane;
+        // output core k: row i < t is the V column of the lane ranked i; rows t..chi-1 zero
+        double *ok = out + (size_t)k * 2 * chi * chi;
+        if (lane < n2 && rank < t) {
+#pragma unroll
+            for (int e = 0; e < D2M; ++e)
+                if (e < n2) {
+                    const int s = e >= r1 ? 1 : 0, c = e - s * r1;
+                    ok[(s * chi + rank) * chi + c] = (double)vc[e];
+                }
+            for (int s = 0; s < 2; ++s)
+                for (int c = r1; c < chi; ++c) ok[(s * chi + rank) * chi + c] = 0.0;
         }
-        __syncwarp();
-        // output core k: rows i < t are columns sel[i] of V, reshaped (s, c)
-        for (int e = lane; e < 2 * chi * chi; e += 32) {
-            const int s = e / (chi * chi), i = (e / chi) % chi, c = e % chi;
-            double val = 0.0;
-            if (i < t && c < r1) val = S.vv[cur][S.sel[i]][s * r1 + c];
-            out[(size_t)k * 2 * chi * chi + e] = val;
-        }
-        // U S for the site to the left: w[row][i] = rotated column sel[i]
-        for (int e = lane; e < r0 * t; e += 32) {
-            const int row = e / t, i = e % t;
-            S.w[row][i] = S.x[cur][S.sel[i]][row];
-        }
-        __syncwarp();
-        // next N: Q_{k-1} (r0' x 2 x r0) x_3 w (r0 x t), columns (s, i) -> s * t + i
-        const int rp = rank_left(k - 1);
-        const double *Qp = Q + (size_t)(k - 1) * qstride;
+        if (lane >= t && lane < chi)
+            for (int s = 0; s < 2; ++s)
+                for (int c = 0; c < chi; ++c) ok[(s * chi + lane) * chi + c] = 0.0;
+        // next N = Q_{k-1} (r0' x 2 x r0) x_3 (U S)(r0 x t), column (s, i) -> s * t + i,
+        // U S column i = rotated column of the lane ranked i
         const int nn = 2 * t;
-        if (lane < nn) {
-            const int s = lane / t, i = lane % t;
-            for (int a = 0; a < rp; ++a) {
-                double acc = 0.0;
-                for (int b = 0; b < r0; ++b) acc = fma(Qp[(size_t)(a * 2 + s) * D2M + b], S.w[b][i], acc);
-                S.x[cur][lane][a] = acc;
-            }
+        const int my_i = lane < nn ? (lane >= t ? lane - t : lane) : 0;
+        const int my_s = lane < nn && lane >= t ? 1 : 0;
+        int my_sel = 0;
+        for (int i = 0; i < t; ++i) {
+            const unsigned m = __ballot_sync(FULL, lane < n2 && rank == i);
+            if (i == my_i) my_sel = __ffs(m) - 1;
         }
-        __syncwarp();
+        T wcol[D2M];
+#pragma unroll
+        for (int b = 0; b < D2M; ++b) wcol[b] = __shfl_sync(FULL, x[b], my_sel);
+        const int rp = rank_left(k - 1);
+        const T *Qp = Q + (size_t)(k - 1) * qstride;
+#pragma unroll
+        for (int a = 0; a < D2M; ++a) {
+            T acc = T(0);
+            if (lane < nn && a < rp) {
+#pragma unroll
+                for (int b = 0; b < D2M; ++b)
+                    if (b < r0) acc = fma(Qp[(size_t)(a * 2 + my_s) * D2M + b], wcol[b], acc);
+            }
+            x[a] = acc;
+        }
         r1 = t;
     }
-    // first core: 1 x 2 x r1, optionally scaled to unit norm
-    double scale = 1.0;
+    // first core: 1 x 2 x r1 in x[0] of lanes < 2 r1, times 2^E; or scaled to
+    // unit norm (the norm's log then takes E ln 2)
+    double scale = pow2<double>(E);
     if (normalize) {
-        double s2 = 0.0;
-        for (int j = 0; j < 2 * r1; ++j) s2 = fma(S.x[cur][j][0], S.x[cur][j][0], s2);
-        const double nrm = sqrt(s2);
-        scale = 1.0 / nrm;
-        if (lane == 0 && log_norm) log_norm[w] = log(nrm);
+        T s2 = T(0);
+        for (int j = 0; j < 2 * r1; ++j) {
+            const T v = __shfl_sync(FULL, x[0], j);
+            s2 = fma(v, v, s2);
+        }
+        const T nrm = sqrt(s2);
+        scale = 1.0 / (double)nrm;
+        if (lane == 0 && log_norm) log_norm[w] = log((double)nrm) + (double)E * 0.6931471805599453;
     }
+    if (lane < 2 * r1) {
+        const int s = lane >= r1 ? 1 : 0, c = lane - s * r1;
+        out[(s * chi + 0) * chi + c] = (double)x[0] * scale;
+    }
+    // the rest of core 0 is zero: rows 1.., and columns r1.. of row 0
     for (int e = lane; e < 2 * chi * chi; e += 32) {
-        const int s = e / (chi * chi), i = (e / chi) % chi, c = e % chi;
-        double val = 0.0;
-        if (i == 0 && c < r1) val = S.x[cur][s * r1 + c][0] * scale;
-        out[e] = val;
+        const int i = (e / chi) % chi, c = e % chi;
+        if (i != 0 || c >= r1) out[e] = 0.0;
     }
 }
 
 template <int CM>
 constexpr int warps_per_cta() {
-    return CM <= 4 ? 4 : (CM <= 8 ? 2 : 1);
+    return CM <= 8 ? 4 : 2;
 }
 
-template <int CM>
-cudaError_t launch_round(const TTPair *pairs, int npairs, int L, int chi, double *scratch,
+template <typename T, int CM>
+cudaError_t launch_round(const TTPair *pairs, int npairs, int L, int chi, void *scratch,
                          int normalize, double *log_norm, cudaStream_t st) {
     constexpr int wpc = warps_per_cta<CM>();
-    const size_t smem = sizeof(WarpSmem<CM>) * wpc;
+    const size_t smem = sizeof(WarpSmem<T, CM>) * wpc;
     // per device and cheap: set on every launch
-    cudaError_t e = cudaFuncSetAttribute(k_tt_round<CM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_tt_round<T, CM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int blocks = (npairs + wpc - 1) / wpc;
-    k_tt_round<CM><<<blocks, 32 * wpc, smem, st>>>(pairs, npairs, L, chi, scratch, normalize,
-                                                   log_norm);
+    k_tt_round<T, CM><<<blocks, 32 * wpc, smem, st>>>(pairs, npairs, L, chi, (T *)scratch,
+                                                      normalize, log_norm);
     return cudaGetLastError();
 }
 
-cudaError_t launch_round_any(const TTPair *pairs, int npairs, int L, int chi, double *scratch,
-                             int normalize, double *log_norm, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_round_t(const TTPair *pairs, int npairs, int L, int chi, void *scratch,
+                           int normalize, double *log_norm, cudaStream_t st) {
+    if (chi <= 2) return launch_round<T, 2>(pairs, npairs, L, chi, scratch, normalize, log_norm, st);
+    if (chi <= 4) return launch_round<T, 4>(pairs, npairs, L, chi, scratch, normalize, log_norm, st);
+    if (chi <= 8) return launch_round<T, 8>(pairs, npairs, L, chi, scratch, normalize, log_norm, st);
+    return launch_round<T, 16>(pairs, npairs, L, chi, scratch, normalize, log_norm, st);
+}
+
+cudaError_t launch_round_any(const TTPair *pairs, int npairs, int L, int chi, int precision,
+                             void *scratch, int normalize, double *log_norm, cudaStream_t st) {
     if (npairs <= 0) return cudaSuccess;
-    if (chi <= 4) return launch_round<4>(pairs, npairs, L, chi, scratch, normalize, log_norm, st);
-    if (chi <= 8) return launch_round<8>(pairs, npairs, L, chi, scratch, normalize, log_norm, st);
-    return launch_round<16>(pairs, npairs, L, chi, scratch, normalize, log_norm, st);
+    if (precision == RTT_FP32)
+        return launch_round_t<float>(pairs, npairs, L, chi, scratch, normalize, log_norm, st);
+    return launch_round_t<double>(pairs, npairs, L, chi, scratch, normalize, log_norm, st);
 }
 
 }  // namespace
@@ -342,16 +490,17 @@ cudaError_t launch_round_any(const TTPair *pairs, int npairs, int L, int chi, do
 // Plan
 // ----------------------------------------------------------------------------
 struct rtt_tt_plan_s {
-    int device = 0, L = 0, chi = 0, K = 0;
+    int device = 0, L = 0, chi = 0, K = 0, precision = RTT_FP64;
     std::vector<double> eta;
     uint8_t *d_ops = nullptr;     // [K][L]
     double *d_nodes = nullptr;    // [K-1][L][2][chi][chi] tree node TTs
     double *d_next = nullptr;     // [L][2][chi][chi]
-    double *d_scratch = nullptr;  // [max pairs][L][2 (2chi)^2] (padded to the kernel's bound)
+    void *d_scratch = nullptr;    // [max pairs][L][2 (2chi)^2] of the arithmetic type (padded
+                                  // to the kernel's bound on chi)
     TTPair *d_pairs = nullptr;    // the tree's pairs, level by level, then the final pair
     std::vector<int> level_off;   // pairs of level l: [level_off[l], level_off[l+1])
     int max_pairs = 1;
-    size_t qsite = 0;             // doubles of one site's Q in the scratch
+    size_t qsite = 0;             // elements of one site's Q in the scratch
     const double *pairs_phi = nullptr;  // phi and tau the device pairs were built for
     double pairs_tau = 0.0;
     bool pairs_valid = false;
@@ -360,7 +509,7 @@ struct rtt_tt_plan_s {
 namespace {
 
 size_t q_site_doubles(int chi) {
-    const int cm = chi <= 4 ? 4 : (chi <= 8 ? 8 : 16);
+    const int cm = chi <= 2 ? 2 : (chi <= 4 ? 4 : (chi <= 8 ? 8 : 16));
     return (size_t)2 * (2 * cm) * (2 * cm);
 }
 
@@ -410,11 +559,11 @@ cudaError_t run_pairs(rtt_tt_plan_s *p, const std::vector<TTPair> &pairs, double
     const int nlev = (int)p->level_off.size() - 1;
     for (int l = 0; l < nlev; ++l) {
         const int n = p->level_off[l + 1] - p->level_off[l];
-        if ((e = launch_round_any(p->d_pairs + p->level_off[l], n, p->L, p->chi, p->d_scratch, 0,
+        if ((e = launch_round_any(p->d_pairs + p->level_off[l], n, p->L, p->chi, p->precision, p->d_scratch, 0,
                                   nullptr, st)) != cudaSuccess)
             return e;
     }
-    return launch_round_any(p->d_pairs + p->level_off.back(), 1, p->L, p->chi, p->d_scratch, 1,
+    return launch_round_any(p->d_pairs + p->level_off.back(), 1, p->L, p->chi, p->precision, p->d_scratch, 1,
                             log_norm, st);
 }
 
@@ -480,14 +629,17 @@ rtt_status rtt_replica_lift(int32_t n_spins, int32_t length, const int32_t *path
     return RTT_OK;
 }
 
-rtt_status rtt_tt_plan_create(int32_t length, int32_t chi, int32_t n_terms, const uint8_t *ops,
-                              const double *eta, int32_t device, rtt_tt_plan *out) {
+rtt_status rtt_tt_plan_create(int32_t length, int32_t chi, int32_t precision, int32_t n_terms,
+                              const uint8_t *ops, const double *eta, int32_t device,
+                              rtt_tt_plan *out) {
     if (!out) return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_plan_create: out is null");
     *out = nullptr;
     if (length < 2 || chi < 1 || n_terms < 1 || !ops || !eta)
         return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_plan_create: need length >= 2, chi >= 1, "
                                             "n_terms >= 1 and non-null ops, eta");
     if (chi > kMaxChi) return rp_fail(RTT_ERR_UNSUPPORTED, "rtt_tt_plan_create: chi > 16");
+    if (precision != RTT_FP64 && precision != RTT_FP32)
+        return rp_fail(RTT_ERR_UNSUPPORTED, "rtt_tt_plan_create: precision must be FP64 or FP32");
     for (size_t i = 0; i < (size_t)n_terms * length; ++i)
         if (ops[i] > 2) return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_plan_create: string code > 2");
     cudaError_t e = cudaSetDevice(device);
@@ -497,6 +649,7 @@ rtt_status rtt_tt_plan_create(int32_t length, int32_t chi, int32_t n_terms, cons
     p->L = length;
     p->chi = chi;
     p->K = n_terms;
+    p->precision = precision;
     p->eta.assign(eta, eta + n_terms);
     p->max_pairs = std::max(1, n_terms / 2);
     p->qsite = q_site_doubles(chi);
@@ -513,7 +666,8 @@ rtt_status rtt_tt_plan_create(int32_t length, int32_t chi, int32_t n_terms, cons
     if (n_terms > 1 && (e = cudaMalloc(&p->d_nodes, (size_t)(n_terms - 1) * tt * 8)) != cudaSuccess)
         return cleanup(e);
     if ((e = cudaMalloc(&p->d_next, tt * 8)) != cudaSuccess) return cleanup(e);
-    if ((e = cudaMalloc(&p->d_scratch, (size_t)p->max_pairs * length * p->qsite * 8)) != cudaSuccess)
+    const size_t esz = precision == RTT_FP32 ? 4 : 8;
+    if ((e = cudaMalloc(&p->d_scratch, (size_t)p->max_pairs * length * p->qsite * esz)) != cudaSuccess)
         return cleanup(e);
     if ((e = cudaMalloc(&p->d_pairs, (size_t)n_pairs_total * sizeof(TTPair))) != cudaSuccess)
         return cleanup(e);
@@ -558,11 +712,11 @@ rtt_status rtt_tt_power(rtt_tt_plan p, double *phi, double tau, int32_t n_steps,
     for (int step = 0; step < n_steps; ++step) {
         for (int l = 0; l < nlev; ++l) {
             const int n = p->level_off[l + 1] - p->level_off[l];
-            if ((e = launch_round_any(p->d_pairs + p->level_off[l], n, p->L, p->chi, p->d_scratch,
-                                      0, nullptr, st)) != cudaSuccess)
+            if ((e = launch_round_any(p->d_pairs + p->level_off[l], n, p->L, p->chi, p->precision,
+                                      p->d_scratch, 0, nullptr, st)) != cudaSuccess)
                 return rp_fail(RTT_ERR_CUDA, std::string("k_tt_round: ") + cudaGetErrorString(e));
         }
-        if ((e = launch_round_any(p->d_pairs + final_idx, 1, p->L, p->chi, p->d_scratch, 1,
+        if ((e = launch_round_any(p->d_pairs + final_idx, 1, p->L, p->chi, p->precision, p->d_scratch, 1,
                                   log_norm ? log_norm + step : nullptr, st)) != cudaSuccess)
             return rp_fail(RTT_ERR_CUDA, std::string("k_tt_round: ") + cudaGetErrorString(e));
         if ((e = cudaMemcpyAsync(phi, p->d_next, tt * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
@@ -627,7 +781,8 @@ rtt_status rtt_tt_round_sum(rtt_tt_plan p, const double *a, const uint8_t *ops_a
     p->pairs_valid = false;
     if ((e = cudaMemcpyAsync(p->d_pairs, &pr, sizeof(TTPair), cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return rp_fail(RTT_ERR_CUDA, std::string("rtt_tt_round_sum: ") + cudaGetErrorString(e));
-    if ((e = launch_round_any(p->d_pairs, 1, p->L, p->chi, p->d_scratch, log_norm ? 1 : 0, log_norm,
+    if ((e = launch_round_any(p->d_pairs, 1, p->L, p->chi, p->precision, p->d_scratch, log_norm ? 1 : 0,
+                              log_norm,
                               st)) != cudaSuccess)
         return rp_fail(RTT_ERR_CUDA, std::string("k_tt_round: ") + cudaGetErrorString(e));
     return RTT_OK;

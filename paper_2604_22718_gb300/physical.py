@@ -34,10 +34,12 @@ def lift_operators(n_spins: int, path, operators):
 
 
 class PhysicalOptimizer:
-    """Operators O_alpha (lifted), chi and the lattice of the states."""
+    """Operators O_alpha (lifted), chi and the lattice of the states; precision
+    is the sampler's (the operator states' handles), tt_precision the TT
+    roundings' arithmetic (FP64 or FP32)."""
 
     def __init__(self, n_spins: int, path, bonds, J: float, h: float, chi: int, operators,
-                 precision: str = "fp64", device: int = 0):
+                 precision: str = "fp64", device: int = 0, tt_precision: str = "fp64"):
         self.n, self.path = int(n_spins), np.ascontiguousarray(path, dtype=np.int32)
         self.L = self.path.shape[0]
         self.bonds = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
@@ -45,9 +47,10 @@ class PhysicalOptimizer:
         self.precision, self.device = precision, device
         self.ops = lift_operators(self.n, self.path, operators)
         self.M = len(self.ops)
-        self.plans = [rtt.TTPlan(self.L, self.chi, eta, ops, device) for _, eta, ops in self.ops]
+        self.plans = [rtt.TTPlan(self.L, self.chi, eta, ops, device, tt_precision)
+                      for _, eta, ops in self.ops]
         self.comb = rtt.TTPlan(self.L, self.chi, np.ones(self.M),
-                               np.zeros((self.M, self.L), dtype=np.uint8), device)
+                               np.zeros((self.M, self.L), dtype=np.uint8), device, tt_precision)
 
     def close(self):
         for p in self.plans:

@@ -280,3 +280,154 @@ def test_plan_rejects_bad_arguments():
     a = torch.zeros((8, 2, 2, 2), dtype=torch.float64, device="cuda")
     with pytest.raises(rtt.RTTError, match="alias"):
         plan.round_sum(a, a, a)
+
+
+# ---------------------------------------------------------------- FP32 arithmetic
+
+def _min_gap(tt, chi):
+    """Smallest relative gap (sigma_chi - sigma_chi+1) / sigma_chi over the
+    truncated bonds of the oracle's own rounding of tt."""
+    L = len(tt)
+    cores = [G.copy() for G in tt]
+    for k in range(L - 1):
+        r0, _, r1 = cores[k].shape
+        Q, R = np.linalg.qr(cores[k].reshape(r0 * 2, r1))
+        cores[k] = Q.reshape(r0, 2, -1)
+        cores[k + 1] = np.einsum("ab,bsc->asc", R, cores[k + 1])
+    gap = 1.0
+    for k in range(L - 1, 0, -1):
+        r0, _, r1 = cores[k].shape
+        U, S, Vt = np.linalg.svd(cores[k].reshape(r0, 2 * r1), full_matrices=False)
+        if len(S) > chi and S[chi - 1] > 1e-12 * S[0]:
+            gap = min(gap, (S[chi - 1] - S[chi]) / S[chi - 1])
+        t = min(chi, len(S))
+        cores[k] = Vt[:t].reshape(t, 2, r1)
+        cores[k - 1] = np.einsum("asb,bc->asc", cores[k - 1], U[:, :t] * S[:t])
+    return gap
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("L,chi", [(2, 1), (3, 2), (12, 2), (37, 2), (37, 8), (64, 16), (144, 2)])
+def test_round_sum_fp32_within_derived_tolerance(L, chi):
+    """FP32 roundings: 2L factorizations, each backward stable to a small
+    multiple of u = 2^-24 relative, the truncations amplifying by 1/gap:
+    tolerance 16 u 2L / gap of the largest amplitude (gap from the oracle)."""
+    rtt = _rtt()
+    rng = np.random.default_rng(2000 + 7 * L + chi)
+    a = inputs.replica_start(11 + L, L, chi)
+    b = inputs.replica_start(12 + L, L, chi)
+    ops_a = rng.integers(0, 3, size=L).astype(np.uint8)
+    ops_b = rng.integers(0, 3, size=L).astype(np.uint8)
+    s = rp.tt_sum(rp.apply_string(rp.unpadded(a), ops_a, 0.8),
+                  rp.apply_string(rp.unpadded(b), ops_b, -1.3))
+    ref = rp.tt_round(s, chi)
+    tol = 16 * 2.0 ** -24 * 2 * L / _min_gap(s, chi)
+    plan = rtt.TTPlan(L, chi, np.ones(1), np.zeros((1, L), dtype=np.uint8), precision="fp32")
+    out = torch.empty((L, 2, chi, chi), dtype=torch.float64, device="cuda")
+    plan.round_sum(_dev(a), _dev(b), out, 0.8, -1.3, _dev(ops_a, torch.uint8), _dev(ops_b, torch.uint8))
+    torch.cuda.synchronize()
+    _compare(_host_tt(out), ref, L, tol, rng)
+
+
+def _oracle_power_with_gaps(phi, eta, ops, tau, chi, steps):
+    """The oracle's steps (same tree, same roundings) and the smallest
+    truncation gap met by any rounding on the way."""
+    gap = 1.0
+    for _ in range(steps):
+        items = [rp.apply_string(phi, ops[k], eta[k]) for k in range(len(eta))]
+        while len(items) > 1:
+            nxt = []
+            for i in range(0, len(items) - 1, 2):
+                s = rp.tt_sum(items[i], items[i + 1])
+                gap = min(gap, _min_gap(s, chi))
+                nxt.append(rp.tt_round(s, chi))
+            if len(items) % 2:
+                nxt.append(items[-1])
+            items = nxt
+        s = rp.tt_sum(phi, rp.tt_scale(items[0], -tau))
+        gap = min(gap, _min_gap(s, chi))
+        phi = rp.tt_scale(rp.tt_round(s, chi), 1.0)
+        phi = rp.tt_scale(phi, 1.0 / rp.tt_norm(phi))
+    return phi, gap
+
+
+@pytest.mark.gpu
+def test_power_fp32_amplitudes_within_derived_tolerance():
+    """One FP32 (1 - tau H-bar) step from a random start on 3x3 (path
+    V+H+D+D', chi = 2, 21 terms: 5 tree levels + the final rounding): each of
+    the 6 roundings in sequence contributes at most 16 u 2L / gap of the
+    largest amplitude (u = 2^-24, gap = the smallest truncation gap the
+    oracle's own run meets, 0.015 here).  Longer runs meet near-degenerate
+    truncations (gap 4e-5 in the second step) where any two correct
+    implementations may part; they are checked on the energy instead."""
+    rtt = _rtt()
+    lx = ly = 3
+    order = ("V", "H", "D", "Dp")
+    path = inputs.path_sum([inputs.ordering(o, lx, ly) for o in order])
+    L = path.shape[0]
+    eta, ops = rtt.replica_lift(9, path, inputs.hbar_terms("HV", lx, ly, 3.0, orderings=order))
+    phi0 = inputs.replica_start(91, L, 2)
+    plan = rtt.TTPlan(L, 2, eta, ops, precision="fp32")
+    phi = _dev(phi0)
+    steps = 1
+    plan.power(phi, 0.1, steps)
+    torch.cuda.synchronize()
+    ref, gap = _oracle_power_with_gaps(rp.unpadded(phi0), eta, ops, 0.1, 2, steps)
+    tol = 16 * 2.0 ** -24 * 2 * L * steps * 6 / gap
+    _compare(_host_tt(phi), ref, L, tol, np.random.default_rng(12))
+
+
+@pytest.mark.gpu
+def test_power_fp32_symmetric_start_energy_is_valid():
+    """From phi^(0) = 1 (degenerate truncations, R23): the FP32 run's exact
+    energy is variational and within a quarter of the oracle run's error."""
+    rtt = _rtt()
+    lx = ly = 3
+    order = ("V", "H", "D", "Dp")
+    path = inputs.path_sum([inputs.ordering(o, lx, ly) for o in order])
+    L = path.shape[0]
+    eta, ops = rtt.replica_lift(9, path, inputs.hbar_terms("HV", lx, ly, 3.0, orderings=order))
+    phi0 = inputs.replica_ones(L, 2)
+    plan = rtt.TTPlan(L, 2, eta, ops, precision="fp32")
+    phi = _dev(phi0)
+    plan.power(phi, 0.1, 6)
+    torch.cuda.synchronize()
+    ref, _ = rp.power(rp.unpadded(phi0), eta, ops, 0.1, 2, 6)
+    H = _dense_tfim(9, inputs.open_bonds(lx, ly), 1.0, 3.0)
+    e0 = np.linalg.eigvalsh(H)[0]
+
+    def energy(tt):
+        psi = rp.constrained_amplitudes(tt, path, 9)
+        return psi @ H @ psi / (psi @ psi)
+    eg, eo = energy(_host_tt(phi)), energy(ref)
+    assert eg >= e0 - 1e-9 and abs((eg - e0) - (eo - e0)) <= 0.25 * (eo - e0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_round_sum_beyond_fp32_range(precision):
+    """A TT whose norm overflows FP32 (every core of a random TT doubled on 144
+    sites: 2^144 more) and whose first core is 2^100 larger still: the kernel
+    carries the scale as a power-of-two exponent, so the rounding is finite,
+    agrees with the oracle within the derived tolerance, and the log-norm
+    carries the scale."""
+    rtt = _rtt()
+    L, chi = 144, 2
+    rng = np.random.default_rng(31)
+    a = inputs.replica_start(501, L, chi) * 2.0
+    b = inputs.replica_start(502, L, chi) * 2.0
+    a[0] *= 2.0 ** 100
+    b[0] *= 2.0 ** 100
+    s = rp.tt_sum(rp.unpadded(a), rp.unpadded(b))
+    ref = rp.tt_round(s, chi)
+    tol = 1e-9 if precision == "fp64" else 16 * 2.0 ** -24 * 2 * L / _min_gap(s, chi)
+    plan = rtt.TTPlan(L, chi, np.ones(1), np.zeros((1, L), dtype=np.uint8), precision=precision)
+    out = torch.empty((L, 2, chi, chi), dtype=torch.float64, device="cuda")
+    ln = torch.empty(1, dtype=torch.float64, device="cuda")
+    plan.round_sum(_dev(a), _dev(b), out, 1.0, 1.0, log_norm=ln)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    nrm = rp.tt_norm(ref)
+    assert float(ln.item()) == pytest.approx(np.log(nrm), rel=1e-6 if precision == "fp32" else 1e-12)
+    _compare(rp.tt_scale(rp.unpadded(got), nrm), ref, L, tol, rng)
