@@ -362,7 +362,10 @@ rtt_status rtt_create(const rtt_desc *d, rtt_handle *out) {
     rtt_status s;
     API_CUDA_CLEANUP(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking),
                      "rtt_create: second stream");
+    API_CUDA_CLEANUP(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking),
+                     "rtt_create: third stream");
     API_CUDA_CLEANUP(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "rtt_create: events");
+    API_CUDA_CLEANUP(cudaEventCreateWithFlags(&h->ev_aux, cudaEventDisableTiming), "rtt_create: events");
     for (int i = 0; i < 2; ++i)
         API_CUDA_CLEANUP(cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming),
                          "rtt_create: events");
@@ -413,7 +416,9 @@ rtt_status rtt_destroy(rtt_handle h) {
     cudaDeviceSynchronize();
     free_scratch(h);
     if (h->side) cudaStreamDestroy(h->side);
+    if (h->aux) cudaStreamDestroy(h->aux);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_aux) cudaEventDestroy(h->ev_aux);
     for (int i = 0; i < 2; ++i)
         if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
     tc_plan_destroy(h);
@@ -554,10 +559,12 @@ rtt_status rtt_dual_step(const rtt_handle *handles, int32_t M, uint8_t *const *s
     for (int a = 0; a < M; ++a) {
         rtt_s *ha = handles[a];
         // measurements of a's entering configurations, on h0's second stream
-        if (e_mixed || ratio) {
+        // (the pairs (a, b) share b's energy scratch, so they stay in one stream)
+        if (e_mixed || ratio)
             API_CUDA(cudaMemcpyAsync(ha->d_snap[0], spins[a], nv, cudaMemcpyDeviceToDevice, st),
                      "rtt_dual_step: spin snapshot");
-            API_CUDA(cudaEventRecord(ha->ev_fork, st), "rtt_dual_step: fork");
+        API_CUDA(cudaEventRecord(ha->ev_fork, st), "rtt_dual_step: fork");
+        if (e_mixed || ratio) {
             API_CUDA(cudaStreamWaitEvent(h0->side, ha->ev_fork, 0), "rtt_dual_step: fork");
             if ((s = mixed_amplitudes(ha, ha->d_snap[0], B, h0->side)) != RTT_OK) return s;
             for (int b = 0; b < M; ++b) {
@@ -568,25 +575,35 @@ rtt_status rtt_dual_step(const rtt_handle *handles, int32_t M, uint8_t *const *s
                     return s;
             }
         }
-        // one sweep of a's chains on the caller's stream
+        // one sweep of a's chains, after the snapshot.  A SIMT sweep holds few
+        // SMs (one thread group per chain), so it runs on a's third stream beside
+        // the other states' sweeps (each uses its own sweep scratch); a
+        // tensor-core sweep fills 64 SMs per 4096 chains and stays in the
+        // caller's stream, leaving the other SMs to the measurements
+        cudaStream_t sa_st = ha->precision >= RTT_BF16X3 ? st : ha->aux;
+        API_CUDA(cudaStreamWaitEvent(sa_st, ha->ev_fork, 0), "rtt_dual_step: fork");
         if (ha->precision >= RTT_BF16X3) {
             if ((s = tc_sweep(ha, spins[a], state[a], B, chain0, sweep, 1,
-                              n_accept ? n_accept[a] : nullptr, st)) != RTT_OK)
+                              n_accept ? n_accept[a] : nullptr, sa_st)) != RTT_OK)
                 return s;
         } else {
             const SimtArgs sa = simt_args(ha);
-            prof_begin(ha, KID_SWEEP, st);
+            prof_begin(ha, KID_SWEEP, sa_st);
             API_CUDA(ha->precision == RTT_FP64
                          ? simt_sweep_f64(sa, spins[a], state[a], B, chain0, sweep, 1, ha->seed,
                                           ha->d_sw_rstack, ha->d_sw_rexp, nullptr, nullptr,
-                                          n_accept ? n_accept[a] : nullptr, st)
+                                          n_accept ? n_accept[a] : nullptr, sa_st)
                          : simt_sweep_f32(sa, spins[a], state[a], B, chain0, sweep, 1, ha->seed,
                                           ha->d_sw_rstack, ha->d_sw_rexp, nullptr, nullptr,
-                                          n_accept ? n_accept[a] : nullptr, st),
+                                          n_accept ? n_accept[a] : nullptr, sa_st),
                      "rtt_dual_step: sweep kernel");
-            prof_end(ha, KID_SWEEP, st);
+            prof_end(ha, KID_SWEEP, sa_st);
         }
+        API_CUDA(cudaEventRecord(ha->ev_aux, sa_st), "rtt_dual_step: join");
     }
+    // the caller's stream waits for every sweep and the measurements
+    for (int a = 0; a < M; ++a)
+        API_CUDA(cudaStreamWaitEvent(st, handles[a]->ev_aux, 0), "rtt_dual_step: join");
     if (e_mixed || ratio) {
         API_CUDA(cudaEventRecord(h0->ev_done[0], h0->side), "rtt_dual_step: join");
         API_CUDA(cudaStreamWaitEvent(st, h0->ev_done[0], 0), "rtt_dual_step: join");

@@ -60,6 +60,10 @@ struct rtt_s {
     // sweeps, and its events (created with the handle)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_done[2] = {nullptr, nullptr};
+    // third stream: the handle's sweep inside a dual step, so that the sweeps
+    // of several states run side by side (each uses only its own sweep scratch)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_aux = nullptr;
 
     void *prof = nullptr;         // per-kernel event profiler (rtt_api.cu)
 
