@@ -343,6 +343,20 @@ rtt_status rtt_made_gradients(rtt_made m, const uint8_t *spins, int64_t B, float
 /* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean NLL of a batch */
 rtt_status rtt_made_train_step(rtt_made m, const uint8_t *spins, int64_t B, float lr, double *nll,
                                void *stream);
+/* Inference arithmetic of the H x H layer (sampling, log q, the independence
+ * step): bf16 = 1 runs it on the tensor cores -- ReLU(first layer) and the
+ * masked W2 rounded to BF16, FP32 accumulation, the same kernel for sampling
+ * and for evaluation, so the density a proposal is drawn from is exactly the
+ * one the acceptance test evaluates; bf16 = 0 runs it in FP32 on the CUDA
+ * cores.  Training is FP32 either way.  BF16 needs H in {64, 128, 192, 256,
+ * 512} (RTT_ERR_UNSUPPORTED otherwise) and is the default for those. */
+rtt_status rtt_made_set_inference(rtt_made m, int32_t bf16);
+/* Device-side error flags of the model's tensor-core layer since the last
+ * call (bit 0: a bounded wait ran out of its clock budget; that CTA recorded
+ * the flag, drained its own copies, freed its tensor memory and returned
+ * without writing its rows).  SYNCHRONOUS; RTT_ERR_TIMEOUT if bit 0 is set;
+ * clears the flags.  flags: host int32 or NULL. */
+rtt_status rtt_made_device_status(rtt_made m, int32_t *flags);
 /* log q(s) for B configurations: logq device double [B] */
 rtt_status rtt_made_log_prob(rtt_made m, const uint8_t *spins, int64_t B, double *logq, void *stream);
 /* B samples s' ~ q (device [B][N]) with their log q (device [B]) */

@@ -151,6 +151,8 @@ rtt_status tc_chain_init(rtt_s *h, const uint8_t *spins, int64_t B, double *log_
 rtt_status tc_sweep(rtt_s *h, uint8_t *spins, rtt_chain_state *state, int64_t B, int64_t chain0,
                     int64_t sweep0, int32_t n_sweeps, int64_t *n_accept, cudaStream_t st);
 bool tc_supported_chi(int chi);
+// cuTensorMapEncodeTiled from the driver (null if unavailable); cast to its signature
+void *tc_encode_tiled_fn();
 int *tc_error_word(rtt_s *h);   // device error flags of the tensor-core kernels (or null)
 
 // ----------------------------------------------------------------------------

@@ -15,13 +15,25 @@
 // the conditionals it samples from, and the log q it reports, are bit for
 // bit those of the full forward pass: the acceptance test uses exactly the
 // density the proposal was drawn from.
+//
+// Inference (sampling, log q for the acceptance test) can run its H x H layer
+// on the tensor cores: h1 = ReLU(first layer) rounded to BF16, W2 (masked)
+// in BF16, FP32 accumulation in tensor memory (tcgen05.mma kind::f16), bias
+// and ReLU in the epilogue.  Sampling and evaluation run the same kernel on
+// bit-identical BF16 inputs, so the density the proposal is drawn from is
+// still exactly the one the acceptance test evaluates; training stays FP32.
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cuda_bf16.h>
+
 #include "rtt_internal.cuh"
+#include "rtt_tcgen05.cuh"
 
 struct rtt_made_s {
     int device = 0, N = 0, H = 0;
@@ -40,6 +52,12 @@ struct rtt_made_s {
     rtt_chain_state *d_pstate = nullptr;
     double *d_plogq = nullptr;
     size_t off_W1 = 0, off_b1 = 0, off_W2 = 0, off_b2 = 0, off_W3 = 0, off_b3 = 0;
+    // BF16 tensor-core inference of the H x H layer (when H allows it)
+    int infer_bf16 = 0;
+    __nv_bfloat16 *d_w2b = nullptr;    // [H][H] masked W2, row n = output unit, K-major
+    __nv_bfloat16 *d_h1b = nullptr;    // [cap][H] ReLU(first layer) in BF16
+    int *d_err = nullptr;              // bit 0: a bounded wait of the layer kernel expired
+    CUtensorMap map_w2;
 };
 
 namespace mk {
@@ -240,6 +258,153 @@ __global__ void k_indep_decide(int64_t B, int N, uint8_t *__restrict__ spins,
     if (n_accept) n_accept[b] += 1;
 }
 
+// BF16 (round to nearest) of ReLU(x), and of the masked second-layer weights
+__global__ void k_relu_bf16(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = __float2bfloat16_rn(fmaxf(x[i], 0.f));
+}
+__global__ void k_w2_bf16(const float *__restrict__ w, const float *__restrict__ mask,
+                          __nv_bfloat16 *__restrict__ y, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = __float2bfloat16_rn(w[i] * mask[i]);
+}
+
+// h2[m][n] = ReLU(b2[n] + sum_k h1[m][k] W2[n][k]) for one 128-row tile and all
+// H columns: A (h1, 128 x 64 per K chunk) and B (W2, H x 64 per chunk) by TMA
+// into a two-stage ring (128-byte swizzle, K-major), thread 0 issues the MMAs
+// (M = 128, N = min(H, 256), K = 16 each) into an H-column FP32 accumulator in
+// tensor memory; the epilogue (thread = row = TMEM lane) adds the bias, applies
+// ReLU and stores the row.  Every wait is bounded: on expiry the CTA sets bit 0
+// of err, drains its own copies, frees its tensor memory and returns.
+constexpr int L2_THREADS = 128;
+__global__ void __launch_bounds__(L2_THREADS, 1)
+    k_l2_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+            const float *__restrict__ bias, float *__restrict__ out, int64_t B, int H, int tcols,
+            int *__restrict__ err, long long wait_limit) {
+    using namespace tcd;
+    extern __shared__ __align__(1024) uint8_t l2_smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t base = (sa(l2_smem) + 1023u) & ~1023u;
+    const uint32_t A_BYTES = 128u * 128u, B_BYTES = (uint32_t)H * 128u, STAGE = A_BYTES + B_BYTES;
+    const uint32_t ctrl = base + 2u * STAGE;
+    auto full_bar = [&](int st) { return ctrl + 8u * (uint32_t)st; };
+    auto empty_bar = [&](int st) { return ctrl + 16u + 8u * (uint32_t)st; };
+    const uint32_t done_bar = ctrl + 32u;
+    uint32_t *tmem_slot = (uint32_t *)(l2_smem + (ctrl + 40u - sa(l2_smem)));
+    volatile int *abort_flag = (volatile int *)(l2_smem + (ctrl + 44u - sa(l2_smem)));
+    const int64_t m0 = (int64_t)blockIdx.x * 128;
+    const int nmma = H > 256 ? 256 : H;           // N of one MMA
+    const int nsub = H / nmma;
+    const int brows = H > 256 ? 256 : H;          // rows of one B box
+    const int nbox = H / brows;
+    const int nK = H / 64;
+    const uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nmma >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    if (tid == 0) {
+        for (int st = 0; st < 2; ++st) {
+            mbar_init(full_bar(st), 1);
+            mbar_init(empty_bar(st), 1);
+        }
+        mbar_init(done_bar, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(sa(tmem_slot), (uint32_t)tcols);
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int issued = 0, waited = 0;
+    auto issue = [&](int c) {
+        const int st = c & 1;
+        const uint32_t a_dst = base + (uint32_t)st * STAGE, b_dst = a_dst + A_BYTES;
+        mbar_expect_tx(full_bar(st), STAGE);
+        tma_load_2d(a_dst, &map_a, c * 64, (int)m0, full_bar(st));
+        for (int r = 0; r < nbox; ++r)
+            tma_load_2d(b_dst + (uint32_t)r * (uint32_t)brows * 128u, &map_b, c * 64, r * brows,
+                        full_bar(st));
+        ++issued;
+    };
+    if (tid == 0) {
+        issue(0);
+        if (nK > 1) issue(1);
+        for (int c = 0; c < nK; ++c) {
+            const int st = c & 1;
+            if (!mbar_wait(full_bar(st), (uint32_t)((c >> 1) & 1), wait_limit)) {
+                atomicOr(err, 1);
+                *abort_flag = 1;
+                break;
+            }
+            waited = c + 1;
+            tc_after();
+            const uint32_t a_src = base + (uint32_t)st * STAGE, b_src = a_src + A_BYTES;
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb) {
+                const uint64_t adesc = sdesc(a_src + (uint32_t)kb * 32u);
+                for (int ns = 0; ns < nsub; ++ns) {
+                    const uint64_t bdesc = sdesc(b_src + (uint32_t)ns * (uint32_t)nmma * 128u +
+                                                 (uint32_t)kb * 32u);
+                    mma_bf16(tmem + (uint32_t)(ns * nmma), adesc, bdesc, IDESC,
+                             (c | kb) != 0 ? 1u : 0u);
+                }
+            }
+            mma_commit(empty_bar(st));
+            if (c + 2 < nK) {
+                if (!mbar_wait(empty_bar(st), (uint32_t)((c >> 1) & 1), wait_limit)) {
+                    atomicOr(err, 1);
+                    *abort_flag = 1;
+                    break;
+                }
+                issue(c + 2);
+            }
+        }
+        mma_commit(done_bar);       // arrives once every MMA issued so far is done
+    }
+    if (!mbar_wait(done_bar, 0u, wait_limit)) {
+        atomicOr(err, 1);
+        *abort_flag = 1;
+    }
+    tc_after();
+    __syncthreads();
+    if (!*abort_flag) {
+        const int64_t row = m0 + warp * 32 + lane;
+        const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
+        float *orow = out + (row < B ? row : 0) * (int64_t)H;
+        for (int c0 = 0; c0 < H; c0 += 64) {
+            uint32_t x[32], y[32];
+            tmem_ld_2x32(tw + (uint32_t)c0, tw + (uint32_t)c0 + 32u, x, y);
+            if (row < B) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float4 v;
+                    v.x = fmaxf(__uint_as_float(x[4 * q + 0]) + bias[c0 + 4 * q + 0], 0.f);
+                    v.y = fmaxf(__uint_as_float(x[4 * q + 1]) + bias[c0 + 4 * q + 1], 0.f);
+                    v.z = fmaxf(__uint_as_float(x[4 * q + 2]) + bias[c0 + 4 * q + 2], 0.f);
+                    v.w = fmaxf(__uint_as_float(x[4 * q + 3]) + bias[c0 + 4 * q + 3], 0.f);
+                    *reinterpret_cast<float4 *>(orow + c0 + 4 * q) = v;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float4 v;
+                    v.x = fmaxf(__uint_as_float(y[4 * q + 0]) + bias[c0 + 32 + 4 * q + 0], 0.f);
+                    v.y = fmaxf(__uint_as_float(y[4 * q + 1]) + bias[c0 + 32 + 4 * q + 1], 0.f);
+                    v.z = fmaxf(__uint_as_float(y[4 * q + 2]) + bias[c0 + 32 + 4 * q + 2], 0.f);
+                    v.w = fmaxf(__uint_as_float(y[4 * q + 3]) + bias[c0 + 32 + 4 * q + 3], 0.f);
+                    *reinterpret_cast<float4 *>(orow + c0 + 32 + 4 * q) = v;
+                }
+            }
+        }
+    } else if (tid == 0) {
+        // drain this CTA's own copies before the shared memory goes away
+        for (int c = waited; c < issued; ++c)
+            mbar_wait(full_bar(c & 1), (uint32_t)((c >> 1) & 1), wait_limit);
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, (uint32_t)tcols);
+}
+
 // masks in parameter layout (1 on biases)
 __global__ void k_masks(float *__restrict__ mask, int N, int H, size_t oW1, size_t oW2, size_t oW3,
                         int64_t P) {
@@ -311,12 +476,13 @@ struct MGuard {
 
 void free_ws(rtt_made_s *m) {
     void *bufs[] = {m->d_x, m->d_h1, m->d_h2, m->d_lg, m->d_d3, m->d_dh2, m->d_dh1,
-                    m->d_logq, m->d_nll_parts, m->d_prop, m->d_pstate, m->d_plogq};
+                    m->d_logq, m->d_nll_parts, m->d_prop, m->d_pstate, m->d_plogq, m->d_h1b};
     for (void *b : bufs) cudaFree(b);
     m->d_x = m->d_h1 = m->d_h2 = m->d_lg = m->d_d3 = m->d_dh2 = m->d_dh1 = nullptr;
     m->d_logq = m->d_nll_parts = m->d_plogq = nullptr;
     m->d_prop = nullptr;
     m->d_pstate = nullptr;
+    m->d_h1b = nullptr;
     m->cap = 0;
 }
 
@@ -328,6 +494,7 @@ rtt_status ensure_ws(rtt_made_s *m, int64_t B) {
     MC(cudaMalloc((void **)&m->d_x, B * N * 4), "made ws");
     MC(cudaMalloc((void **)&m->d_h1, B * H * 4), "made ws");
     MC(cudaMalloc((void **)&m->d_h2, B * H * 4), "made ws");
+    MC(cudaMalloc((void **)&m->d_h1b, B * H * 2), "made ws");
     MC(cudaMalloc((void **)&m->d_lg, B * N * 4), "made ws");
     MC(cudaMalloc((void **)&m->d_d3, B * N * 4), "made ws");
     MC(cudaMalloc((void **)&m->d_dh2, B * H * 4), "made ws");
@@ -351,6 +518,86 @@ rtt_status forward(rtt_made_s *m, const uint8_t *spins, int64_t B, cudaStream_t 
                               p + m->off_b1, 1, nullptr, nullptr, st)), "made layer 1");
     MC((mk::gemm<false, true>((int)B, H, H, m->d_h1, H, p + m->off_W2, H, m->d_h2, H,
                               p + m->off_b2, 1, nullptr, nullptr, st)), "made layer 2");
+    MC((mk::gemm<false, true>((int)B, N, H, m->d_h2, H, p + m->off_W3, H, m->d_lg, N,
+                              p + m->off_b3, 0, nullptr, nullptr, st)), "made output");
+    return RTT_OK;
+}
+
+// H values the tensor-core layer takes: multiples of 64 up to 512 that are
+// one or two MMA widths (N <= 256)
+bool l2_tc_supported(int H) {
+    if (H < 64 || H > 512 || H % 64) return false;
+    const int nmma = H > 256 ? 256 : H;
+    return H % nmma == 0;
+}
+int l2_tcols(int H) {
+    int c = 32;
+    while (c < H) c <<= 1;
+    return c;
+}
+size_t l2_smem(int H) {
+    const size_t stage = (size_t)128 * 128 + (size_t)H * 128;
+    // at least 164 KB, so that no other tensor-memory kernel shares the SM
+    return std::max((size_t)1024 + 2 * stage + 64, (size_t)164 * 1024);
+}
+
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// row-major bf16 matrix [rows][cols] (cols = K, a multiple of 64), boxes of
+// 64 K-elements x box_rows rows, 128-byte swizzle, rows past the end read as 0
+bool encode_bf16(CUtensorMap *map, const void *ptr, int64_t rows, int cols, int box_rows) {
+    EncodeTiled enc = (EncodeTiled)tc_encode_tiled_fn();
+    if (!enc) return false;
+    const cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t gstride[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    const cuuint32_t estride[2] = {1u, 1u};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), gdim, gstride, box,
+               estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the masked W2 in BF16 (before every inference call: parameters may have changed)
+rtt_status refresh_w2(rtt_made_s *m, cudaStream_t st) {
+    const int64_t n = (int64_t)m->H * m->H;
+    mk::k_w2_bf16<<<mk::nb(n, 256), 256, 0, st>>>(m->d_p + m->off_W2, m->d_mask + m->off_W2,
+                                                   m->d_w2b, n);
+    MC(cudaGetLastError(), "made W2 to BF16");
+    return RTT_OK;
+}
+
+// h2 = ReLU(b2 + h1b W2b^T) on the tensor cores, h1b already filled
+rtt_status layer2_tc(rtt_made_s *m, int64_t B, cudaStream_t st) {
+    const int H = m->H;
+    CUtensorMap map_a;
+    if (!encode_bf16(&map_a, m->d_h1b, B, H, 128))
+        return mfail(RTT_ERR_CUDA, "made layer 2: cuTensorMapEncodeTiled failed");
+    const size_t smem = l2_smem(H);
+    MC(cudaFuncSetAttribute(mk::k_l2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+       "made layer 2 attributes");
+    mk::k_l2_tc<<<(unsigned)((B + 127) / 128), mk::L2_THREADS, smem, st>>>(
+        map_a, m->map_w2, m->d_p + m->off_b2, m->d_h2, B, H, l2_tcols(H), m->d_err, 4000000000LL);
+    MC(cudaGetLastError(), "made layer 2 (tensor cores)");
+    return RTT_OK;
+}
+
+// the inference forward pass: as forward(), with the H x H layer on the
+// tensor cores when inference runs in BF16
+rtt_status forward_infer(rtt_made_s *m, const uint8_t *spins, int64_t B, cudaStream_t st) {
+    if (!m->infer_bf16) return forward(m, spins, B, st);
+    const int N = m->N, H = m->H;
+    const float *p = m->d_p;
+    mk::k_inputs<<<mk::nb(B * N, 256), 256, 0, st>>>(spins, B, N, m->d_order, m->d_x);
+    MC(cudaGetLastError(), "made inputs");
+    MC((mk::gemm<false, true>((int)B, H, N, m->d_x, N, p + m->off_W1, N, m->d_h1, H,
+                              p + m->off_b1, 1, nullptr, nullptr, st)), "made layer 1");
+    mk::k_relu_bf16<<<mk::nb(B * H, 256), 256, 0, st>>>(m->d_h1, m->d_h1b, B * H);
+    MC(cudaGetLastError(), "made layer 1 to BF16");
+    rtt_status s = layer2_tc(m, B, st);
+    if (s != RTT_OK) return s;
     MC((mk::gemm<false, true>((int)B, N, H, m->d_h2, H, p + m->off_W3, H, m->d_lg, N,
                               p + m->off_b3, 0, nullptr, nullptr, st)), "made output");
     return RTT_OK;
@@ -443,6 +690,15 @@ rtt_status rtt_made_create(int32_t n_spins, int32_t hidden, const int32_t *order
                                              m->off_W3, m->P);
     mk::k_mul<<<mk::nb(m->P, 256), 256>>>(m->d_p, m->d_mask, m->P);
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cleanup(mcuda(e, "made masks"));
+    if ((e = cudaMalloc((void **)&m->d_err, sizeof(int))) != cudaSuccess) return cleanup(mcuda(e, "made"));
+    cudaMemset(m->d_err, 0, sizeof(int));
+    if (l2_tc_supported((int)H)) {
+        if ((e = cudaMalloc((void **)&m->d_w2b, H * H * 2)) != cudaSuccess)
+            return cleanup(mcuda(e, "made BF16 weights"));
+        if (!encode_bf16(&m->map_w2, m->d_w2b, (int64_t)H, (int)H, H > 256 ? 256 : (int)H))
+            return cleanup(mfail(RTT_ERR_CUDA, "rtt_made_create: cuTensorMapEncodeTiled failed"));
+        m->infer_bf16 = 1;
+    }
     *out = m;
     return RTT_OK;
 }
@@ -458,7 +714,30 @@ rtt_status rtt_made_destroy(rtt_made m) {
     cudaFree(m->d_m);
     cudaFree(m->d_v);
     cudaFree(m->d_mask);
+    cudaFree(m->d_w2b);
+    cudaFree(m->d_err);
     delete m;
+    return RTT_OK;
+}
+
+rtt_status rtt_made_set_inference(rtt_made m, int32_t bf16) {
+    if (!m) return mfail(RTT_ERR_INVALID_ARG, "rtt_made_set_inference: null model");
+    if (bf16 && !m->d_w2b)
+        return mfail(RTT_ERR_UNSUPPORTED, "rtt_made_set_inference: BF16 needs H in {64, 128, 192, "
+                                          "256, 512}");
+    m->infer_bf16 = bf16 ? 1 : 0;
+    return RTT_OK;
+}
+
+rtt_status rtt_made_device_status(rtt_made m, int32_t *flags) {
+    if (!m) return mfail(RTT_ERR_INVALID_ARG, "rtt_made_device_status: null model");
+    MGuard guard(m->device);
+    int v = 0;
+    MC(cudaDeviceSynchronize(), "rtt_made_device_status");
+    MC(cudaMemcpy(&v, m->d_err, sizeof(int), cudaMemcpyDeviceToHost), "rtt_made_device_status");
+    MC(cudaMemset(m->d_err, 0, sizeof(int)), "rtt_made_device_status");
+    if (flags) *flags = v;
+    if (v & 1) return mfail(RTT_ERR_TIMEOUT, "a bounded wait in the BF16 layer kernel expired");
     return RTT_OK;
 }
 
@@ -508,7 +787,8 @@ rtt_status rtt_made_log_prob(rtt_made m, const uint8_t *spins, int64_t B, double
     cudaStream_t st = (cudaStream_t)stream;
     rtt_status s = ensure_ws(m, B);
     if (s != RTT_OK) return s;
-    if ((s = forward(m, spins, B, st)) != RTT_OK) return s;
+    if (m->infer_bf16 && (s = refresh_w2(m, st)) != RTT_OK) return s;
+    if ((s = forward_infer(m, spins, B, st)) != RTT_OK) return s;
     mk::k_loss<<<mk::nb(B, 128), 128, 0, st>>>(m->d_lg, spins, B, m->N, m->d_order, logq, nullptr);
     MC(cudaGetLastError(), "made log prob");
     return RTT_OK;
@@ -522,9 +802,16 @@ static rtt_status made_sample_into(rtt_made m, int64_t B, int64_t chain0, int64_
     mk::k_fill_rows<<<mk::nb(B * H, 256), 256, 0, st>>>(m->d_dh1, B, H, p + m->off_b1);
     MC(cudaGetLastError(), "made sample init");
     for (int d = 0; d < N; ++d) {
-        mk::k_relu<<<mk::nb(B * H, 256), 256, 0, st>>>(m->d_dh1, m->d_h1, B * H);
-        MC((mk::gemm<false, true>((int)B, H, H, m->d_h1, H, p + m->off_W2, H, m->d_h2, H,
-                                  p + m->off_b2, 1, nullptr, nullptr, st)), "made sample layer 2");
+        if (m->infer_bf16) {
+            mk::k_relu_bf16<<<mk::nb(B * H, 256), 256, 0, st>>>(m->d_dh1, m->d_h1b, B * H);
+            MC(cudaGetLastError(), "made sample layer 1 to BF16");
+            rtt_status s = layer2_tc(m, B, st);
+            if (s != RTT_OK) return s;
+        } else {
+            mk::k_relu<<<mk::nb(B * H, 256), 256, 0, st>>>(m->d_dh1, m->d_h1, B * H);
+            MC((mk::gemm<false, true>((int)B, H, H, m->d_h1, H, p + m->off_W2, H, m->d_h2, H,
+                                      p + m->off_b2, 1, nullptr, nullptr, st)), "made sample layer 2");
+        }
         mk::k_sample_pos<<<mk::nb(B, 128), 128, 0, st>>>(d, B, N, H, p + m->off_W1, p + m->off_W3,
                                                           p + m->off_b3, m->d_h2, m->d_dh1,
                                                           m->d_order, spins, logq, m->seed, chain0,
@@ -542,6 +829,7 @@ rtt_status rtt_made_sample(rtt_made m, int64_t B, int64_t chain0, int64_t round,
     MGuard guard(m->device);
     rtt_status s = ensure_ws(m, B);
     if (s != RTT_OK) return s;
+    if (m->infer_bf16 && (s = refresh_w2(m, (cudaStream_t)stream)) != RTT_OK) return s;
     return made_sample_into(m, B, chain0, round, spins, logq, (cudaStream_t)stream);
 }
 
@@ -556,7 +844,8 @@ rtt_status rtt_indep_mh(rtt_handle h, rtt_made m, uint8_t *spins, rtt_chain_stat
     rtt_status s = ensure_ws(m, B);
     if (s != RTT_OK) return s;
     // log q(s) of the current configurations
-    if ((s = forward(m, spins, B, st)) != RTT_OK) return s;
+    if (m->infer_bf16 && (s = refresh_w2(m, st)) != RTT_OK) return s;
+    if ((s = forward_infer(m, spins, B, st)) != RTT_OK) return s;
     mk::k_loss<<<mk::nb(B, 128), 128, 0, st>>>(m->d_lg, spins, B, m->N, m->d_order, m->d_logq, nullptr);
     MC(cudaGetLastError(), "indep log q");
     // proposals s' ~ q with log q(s'), and psi(s')

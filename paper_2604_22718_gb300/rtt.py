@@ -95,6 +95,10 @@ def lib():
         L.rtt_made_log_prob.argtypes = [P, P, I64, P, P]
         L.rtt_made_sample.argtypes = [P, I64, I64, I64, P, P, P]
         L.rtt_indep_mh.argtypes = [P, P, P, P, I64, I64, I64, P, P]
+        L.rtt_made_set_inference.argtypes = [P, I32]
+        L.rtt_made_device_status.argtypes = [P, ctypes.POINTER(I32)]
+        L.rtt_made_set_inference.restype = ctypes.c_int
+        L.rtt_made_device_status.restype = ctypes.c_int
         for name in ("rtt_made_create", "rtt_made_destroy", "rtt_made_get_params",
                      "rtt_made_gradients", "rtt_made_train_step", "rtt_made_log_prob",
                      "rtt_made_sample", "rtt_indep_mh"):
@@ -479,6 +483,19 @@ class MADE:
     @property
     def handle(self):
         return self._m
+
+    def set_inference(self, bf16: bool):
+        """Tensor-core BF16 (True) or FP32 (False) arithmetic for the H x H layer
+        of sampling and evaluation (rtt_made_set_inference)."""
+        _check(lib().rtt_made_set_inference(self._m, 1 if bf16 else 0), "rtt_made_set_inference")
+
+    def device_status(self) -> int:
+        """Error flags of the tensor-core layer since the last call (0 = none)."""
+        f = ctypes.c_int32()
+        st = lib().rtt_made_device_status(self._m, ctypes.byref(f))
+        if st not in (0, 5):
+            _check(st, "rtt_made_device_status")
+        return int(f.value)
 
     def params(self) -> np.ndarray:
         out = np.empty(self.P, dtype=np.float32)

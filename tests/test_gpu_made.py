@@ -182,3 +182,81 @@ def test_learned_proposal_beats_local_flips_on_a_slowly_mixing_state():
     assert acc_rate > 0.3
     # local flips: populations frozen at their start -- biased or slowly mixing
     assert (abs(s_l["mean"] - e_exact) > 3.5 * s_l["se"]) or (s_m["tau_int"] < 0.5 * s_l["tau_int"])
+
+
+# ---------------------------------------------------------------- BF16 tensor-core inference
+
+def _bf16_bound(p, spins, order, K):
+    """Per configuration, a bound on |log q_bf16 - log q|: the H x H layer's
+    products h1_k W2_nk carry at most 2u + u^2 (u = 2^-9, both factors rounded
+    to BF16) plus K 2^-24 (FP32 accumulation) of |h1_k W2_nk|; ReLU and
+    log-sigmoid are 1-Lipschitz, so the logit error is at most
+    sum_n |W3_dn| |da2_n| and the log q error at most the sum over positions.
+    A 1e-4 per position allowance covers the FP32 arithmetic of the other
+    layers (the FP32 path meets the oracle to 1e-5)."""
+    x, _ = made.inputs_of(spins, order)
+    a1, h1, a2, h2, lg = made.forward(p, x)
+    u = 2.0 ** -9
+    rel = 2 * u + u * u + K * 2.0 ** -24
+    da2 = rel * (np.abs(h1) @ np.abs(p["W2"]).T)
+    dlg = da2 @ np.abs(p["W3"]).T
+    return dlg.sum(axis=1) + 1e-4 * x.shape[1]
+
+
+@pytest.mark.parametrize("N,H", [(16, 64), (12, 256), (10, 512)])
+def test_bf16_sampler_reports_its_own_log_prob_and_meets_the_bound(N, H):
+    """Tensor-core inference: the sampler's log q is bit for bit the
+    evaluation's (same kernel on identical BF16 inputs), and both stay within
+    the BF16 bound of the FP64 oracle's log q of the same configurations."""
+    rtt = _rtt()
+    B = 1000
+    w, order = _setup(N, H, seed=N + H)
+    p = made.masked_params(w, N, H)
+    with rtt.MADE(N, H, order, w, seed=41) as m:
+        sp, lq = m.sample(B, chain0=3, round=2)
+        lq_fwd = m.log_prob(sp)
+        assert m.device_status() == 0
+        sp, lq, lq_fwd = sp.cpu().numpy(), lq.cpu().numpy(), lq_fwd.cpu().numpy()
+        m.set_inference(False)
+        lq32 = m.log_prob(torch.from_numpy(sp).cuda()).cpu().numpy()
+    assert np.array_equal(lq, lq_fwd)
+    ref = made.log_prob(p, sp, order)
+    bound = _bf16_bound(p, sp, order, H)
+    assert np.all(np.abs(lq - ref) <= bound), float(np.max(np.abs(lq - ref) - bound))
+    np.testing.assert_allclose(lq32, ref, rtol=1e-5, atol=1e-5)
+    # the bound is not vacuous: BF16 differs from FP32, by less than the bound
+    assert np.any(lq != lq32)
+
+
+def test_bf16_needs_a_supported_hidden_width():
+    rtt = _rtt()
+    N, H = 8, 24
+    w, order = _setup(N, H)
+    with rtt.MADE(N, H, order, w) as m:
+        with pytest.raises(rtt.RTTError, match="UNSUPPORTED"):
+            m.set_inference(True)
+        m.set_inference(False)
+
+
+def test_bf16_sampler_distribution_chi2():
+    """Samples of the BF16 sampler against its own exact density: the
+    evaluation kernel's q over all 2^N configurations (N = 10, H = 64)."""
+    rtt = _rtt()
+    N, H, B = 10, 64, 1 << 16
+    w, order = _setup(N, H, seed=3)
+    allc = ((np.arange(1 << N)[:, None] >> (N - 1 - np.arange(N))[None, :]) & 1).astype(np.uint8)
+    with rtt.MADE(N, H, order, w, seed=5) as m:
+        sp, _ = m.sample(B)
+        q = np.exp(m.log_prob(torch.from_numpy(allc).cuda()).cpu().numpy())
+        sp = sp.cpu().numpy()
+    assert abs(q.sum() - 1.0) < 1e-5
+    idx = (sp.astype(np.int64) * (1 << (N - 1 - np.arange(N)))[None, :]).sum(axis=1)
+    obs = np.bincount(idx, minlength=1 << N).astype(np.float64)
+    exp_ = q * B
+    keep = exp_ >= 5
+    o, e = obs[keep], exp_[keep]
+    if np.any(~keep):                      # bins with few expected counts merged into one
+        o, e = np.append(o, obs[~keep].sum()), np.append(e, exp_[~keep].sum())
+    chi2 = float(np.sum((o - e) ** 2 / e))
+    from scipy.stats import chi2 as c2
+    assert c2.sf(chi2, len(o) - 1) > 1e-3
