@@ -280,6 +280,7 @@ constexpr int L2_THREADS = 128;
 __global__ void __launch_bounds__(L2_THREADS, 1)
     k_l2_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
             const float *__restrict__ bias, float *__restrict__ out, int64_t B, int H, int tcols,
+            const float *__restrict__ w3row, const float *__restrict__ b3d, float *__restrict__ lg_out,
             int *__restrict__ err, long long wait_limit) {
     using namespace tcd;
     extern __shared__ __align__(1024) uint8_t l2_smem[];
@@ -370,11 +371,20 @@ __global__ void __launch_bounds__(L2_THREADS, 1)
     if (!*abort_flag) {
         const int64_t row = m0 + warp * 32 + lane;
         const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);
-        float *orow = out + (row < B ? row : 0) * (int64_t)H;
+        float *orow = out ? out + (row < B ? row : 0) * (int64_t)H : nullptr;
+        float lg = lg_out ? *b3d : 0.f;  // logit mode: b3[d] + sum_n h2[n] W3[d][n], increasing n
         for (int c0 = 0; c0 < H; c0 += 64) {
             uint32_t x[32], y[32];
             tmem_ld_2x32(tw + (uint32_t)c0, tw + (uint32_t)c0 + 32u, x, y);
-            if (row < B) {
+            if (lg_out) {
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    lg = fmaf(fmaxf(__uint_as_float(x[q]) + bias[c0 + q], 0.f), w3row[c0 + q], lg);
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    lg = fmaf(fmaxf(__uint_as_float(y[q]) + bias[c0 + 32 + q], 0.f), w3row[c0 + 32 + q],
+                              lg);
+            } else if (row < B) {
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     float4 v;
@@ -395,6 +405,7 @@ __global__ void __launch_bounds__(L2_THREADS, 1)
                 }
             }
         }
+        if (lg_out && row < B) lg_out[row] = lg;
     } else if (tid == 0) {
         // drain this CTA's own copies before the shared memory goes away
         for (int c = waited; c < issued; ++c)
@@ -403,6 +414,79 @@ __global__ void __launch_bounds__(L2_THREADS, 1)
     tc_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, (uint32_t)tcols);
+}
+
+// Feature-major forms for BF16 sampling ([H][B], thread = chain, so that a
+// warp touches consecutive chains of one feature): the same arithmetic per
+// element as the row-major kernels above.
+__global__ void k_fill_T(float *__restrict__ xT, int64_t B, int H, const float *__restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B * H) xT[i] = b[i / B];
+}
+// y[b][k] = bf16(ReLU(xT[k][b])) through a 32 x 32 shared-memory tile
+__global__ void k_relu_bf16_T(const float *__restrict__ xT, __nv_bfloat16 *__restrict__ y,
+                              int64_t B, int H) {
+    __shared__ float t[32][33];
+    const int64_t b0 = (int64_t)blockIdx.x * 32;
+    const int k0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int k = k0 + r;
+        const int64_t b = b0 + threadIdx.x;
+        t[r][threadIdx.x] = (k < H && b < B) ? xT[(int64_t)k * B + b] : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t b = b0 + r;
+        const int k = k0 + threadIdx.x;
+        if (b < B && k < H) y[b * H + k] = __float2bfloat16_rn(fmaxf(t[threadIdx.x][r], 0.f));
+    }
+}
+// Position d of BF16 sampling, one thread per chain: the logit comes from the
+// layer kernel's epilogue (bias, then increasing n, as the output product);
+// draw the bit, add its log-probability, keep x_d = 1 - 2 s for the update.
+__global__ void k_sample_bit(int d, int64_t B, int N, const float *__restrict__ lg,
+                             const int32_t *__restrict__ order, uint8_t *__restrict__ spins,
+                             double *__restrict__ logq, float *__restrict__ xs, uint64_t seed,
+                             int64_t chain0, int64_t round) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const double y = (double)lg[b];
+    uint64_t r[4];
+    rttd::philox4x64_10((uint64_t)(chain0 + b), (uint64_t)round, (uint64_t)d, 0ull, seed,
+                        MADE_STREAM, r);
+    const double u = (double)(r[0] >> 11) * 0x1.0p-53;
+    const double pr = 1.0 / (1.0 + exp(-y));
+    const int t = u < pr ? 1 : 0;
+    logq[b] = (d == 0 ? 0.0 : logq[b]) + log_sigmoid(t ? y : -y);
+    spins[b * N + order[d]] = (uint8_t)t;
+    xs[b] = t ? -1.f : 1.f;
+}
+// add input d to the feature-major pre-activations, h1preT[k][b] += x_b W1[k][d]
+// (the forward product's next fma), and write bf16(ReLU) of the result to the
+// row-major h1b[b][k] through a 32 x 32 shared-memory tile
+__global__ void k_h1_update_bf16_T(int d, int64_t B, int N, int H, const float *__restrict__ W1,
+                                   const float *__restrict__ xs, float *__restrict__ h1preT,
+                                   __nv_bfloat16 *__restrict__ y) {
+    __shared__ float t[32][33];
+    const int64_t b0 = (int64_t)blockIdx.x * 32;
+    const int k0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int k = k0 + r;
+        const int64_t b = b0 + threadIdx.x;
+        float v = 0.f;
+        if (k < H && b < B) {
+            float *h = h1preT + (int64_t)k * B + b;
+            v = fmaf(xs[b], W1[(size_t)k * N + d], *h);
+            *h = v;
+        }
+        t[r][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t b = b0 + r;
+        const int k = k0 + threadIdx.x;
+        if (b < B && k < H) y[b * H + k] = __float2bfloat16_rn(fmaxf(t[threadIdx.x][r], 0.f));
+    }
 }
 
 // masks in parameter layout (1 on biases)
@@ -569,8 +653,9 @@ rtt_status refresh_w2(rtt_made_s *m, cudaStream_t st) {
     return RTT_OK;
 }
 
-// h2 = ReLU(b2 + h1b W2b^T) on the tensor cores, h1b already filled
-rtt_status layer2_tc(rtt_made_s *m, int64_t B, cudaStream_t st) {
+// h2 = ReLU(b2 + h1b W2b^T) on the tensor cores, h1b already filled; with
+// d >= 0 only the logit of position d per row goes to m->d_lg (h2 is not stored)
+rtt_status layer2_tc(rtt_made_s *m, int64_t B, cudaStream_t st, int d = -1) {
     const int H = m->H;
     CUtensorMap map_a;
     if (!encode_bf16(&map_a, m->d_h1b, B, H, 128))
@@ -579,7 +664,10 @@ rtt_status layer2_tc(rtt_made_s *m, int64_t B, cudaStream_t st) {
     MC(cudaFuncSetAttribute(mk::k_l2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
        "made layer 2 attributes");
     mk::k_l2_tc<<<(unsigned)((B + 127) / 128), mk::L2_THREADS, smem, st>>>(
-        map_a, m->map_w2, m->d_p + m->off_b2, m->d_h2, B, H, l2_tcols(H), m->d_err, 4000000000LL);
+        map_a, m->map_w2, m->d_p + m->off_b2, d >= 0 ? nullptr : m->d_h2, B, H, l2_tcols(H),
+        d >= 0 ? m->d_p + m->off_W3 + (size_t)d * H : nullptr,
+        d >= 0 ? m->d_p + m->off_b3 + d : nullptr,
+        d >= 0 ? m->d_lg : nullptr, m->d_err, 4000000000LL);
     MC(cudaGetLastError(), "made layer 2 (tensor cores)");
     return RTT_OK;
 }
@@ -798,16 +886,35 @@ static rtt_status made_sample_into(rtt_made m, int64_t B, int64_t chain0, int64_
                                    uint8_t *spins, double *logq, cudaStream_t st) {
     const int N = m->N, H = m->H;
     const float *p = m->d_p;
-    // first-layer pre-activations start at the bias; x is not used here
+    // first-layer pre-activations start at the bias; x is not used here.  The
+    // BF16 path keeps them and h2 feature-major ([H][B]) for coalesced access
+    if (m->infer_bf16) {
+        // per position: the layer on the tensor cores with the logit of position
+        // d in its epilogue, the draw, then input d added to the feature-major
+        // pre-activations together with the next BF16 operand
+        mk::k_fill_T<<<mk::nb(B * H, 256), 256, 0, st>>>(m->d_dh1, B, H, p + m->off_b1);
+        MC(cudaGetLastError(), "made sample init");
+        const dim3 tb(32, 8), tg((unsigned)((B + 31) / 32), (unsigned)((H + 31) / 32));
+        mk::k_relu_bf16_T<<<tg, tb, 0, st>>>(m->d_dh1, m->d_h1b, B, H);
+        MC(cudaGetLastError(), "made sample layer 1 to BF16");
+        for (int d = 0; d < N; ++d) {
+            rtt_status s = layer2_tc(m, B, st, d);
+            if (s != RTT_OK) return s;
+            mk::k_sample_bit<<<mk::nb(B, 128), 128, 0, st>>>(d, B, N, m->d_lg, m->d_order, spins,
+                                                              logq, m->d_x, m->seed, chain0, round);
+            MC(cudaGetLastError(), "made sample position");
+            if (d + 1 < N) {
+                mk::k_h1_update_bf16_T<<<tg, tb, 0, st>>>(d, B, N, H, p + m->off_W1, m->d_x, m->d_dh1,
+                                                          m->d_h1b);
+                MC(cudaGetLastError(), "made sample update");
+            }
+        }
+        return RTT_OK;
+    }
     mk::k_fill_rows<<<mk::nb(B * H, 256), 256, 0, st>>>(m->d_dh1, B, H, p + m->off_b1);
     MC(cudaGetLastError(), "made sample init");
     for (int d = 0; d < N; ++d) {
-        if (m->infer_bf16) {
-            mk::k_relu_bf16<<<mk::nb(B * H, 256), 256, 0, st>>>(m->d_dh1, m->d_h1b, B * H);
-            MC(cudaGetLastError(), "made sample layer 1 to BF16");
-            rtt_status s = layer2_tc(m, B, st);
-            if (s != RTT_OK) return s;
-        } else {
+        {
             mk::k_relu<<<mk::nb(B * H, 256), 256, 0, st>>>(m->d_dh1, m->d_h1, B * H);
             MC((mk::gemm<false, true>((int)B, H, H, m->d_h1, H, p + m->off_W2, H, m->d_h2, H,
                                       p + m->off_b2, 1, nullptr, nullptr, st)), "made sample layer 2");
