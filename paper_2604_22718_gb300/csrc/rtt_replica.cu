@@ -14,10 +14,13 @@
 //     columns are rotated pairwise until orthogonal, so the rotated columns
 //     are U S and the accumulated rotations V.  The chi largest singular
 //     values are kept: rows of V^T become the output core, U S is carried on.
-// Lanes own matrix columns (at most 2 chi <= 32 of them), so a reflector or a
-// rotation is one sequential loop per lane and no cross-lane reduction.  All
-// arithmetic is FP64: a rounding is a chain of L small dependent
-// factorizations, bound by latency rather than arithmetic throughput.
+// Lanes own matrix columns (at most 2 chi <= 32 of them) in registers: a
+// reflector or a rotation is one unrolled loop per lane, the reflectors pass
+// through shared memory and a Jacobi partner's column comes by shuffle.  The
+// arithmetic is FP64 or FP32 (the cores stay FP64 in memory); the TT's scale
+// travels as an integer power-of-two exponent, so FP32 cannot overflow on long
+// trains.  A rounding is a chain of 2 L small dependent factorizations, bound
+// by latency rather than arithmetic throughput.
 #include <algorithm>
 #include <cmath>
 #include <string>

@@ -5,7 +5,6 @@ stream per chain), whatever tile shape the autotuner picks and whether the
 launch goes through the CUDA graph or not; sampled chains are checked against
 the FP64 oracle."""
 import json
-import os
 
 import numpy as np
 import pytest

@@ -3,7 +3,6 @@ oracle/made.py: forward log-probabilities, gradients, Adam, the sampler
 (same Philox stream), exact self-consistency of the sampled log q, and the
 gain of the trained proposal over local flips on a slowly mixing state."""
 import itertools
-import math
 
 import numpy as np
 import pytest

@@ -10,7 +10,6 @@ eps_site = 3 u_b^2 + chi u_32, i.e. a relative error <= eps_site kappa_k in
 norm, and the closing contraction <= eps_site kappa_fin.  Hence
 |d log|psi|| <= eps_site (sum_k kappa_k + kappa_fin), with the kappas computed
 per configuration by the oracle in FP64."""
-import math
 
 import numpy as np
 import pytest

@@ -1,7 +1,6 @@
 """The oracle on general paths (the replicas visit the spins in different
 orders, Sec. 2.2.1 path sums; orderings of Sec. 4): pinned against brute
 force and a dense TFIM matrix."""
-import itertools
 
 import numpy as np
 import pytest

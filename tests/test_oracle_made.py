@@ -4,7 +4,6 @@ differences, Adam against torch.optim.Adam, sampling against the enumerated
 distribution, and the independence Metropolis-Hastings rule against an exact
 proposal (acceptance identically one)."""
 import itertools
-import math
 
 import numpy as np
 import pytest

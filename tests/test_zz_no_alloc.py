@@ -8,7 +8,6 @@ This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test."""
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
