@@ -123,3 +123,20 @@ def _dense_tfim(n, bonds, J, h):
     for i in range(n):
         H -= h * op({i: X})
     return H
+
+
+@pytest.mark.gpu
+def test_identity_only_iteration_keeps_the_state():
+    """M = 1 (the identity): H~ = <E_loc>, S~ = 1, c = (1); the combined TT is
+    the start itself (up to the unit-norm scaling)."""
+    from paper_2604_22718_gb300.physical import PhysicalOptimizer
+    opt = PhysicalOptimizer(LX * LY, _path(), inputs.open_bonds(LX, LY), 1.0, 3.0, 2, [("1", [])])
+    phi0 = inputs.replica_start(78, 12, 2)
+    res = opt.step(_dev(phi0), inputs.initial_spins(6, 1024, 6), chains=1024, sweeps=20, burn=5, seed=3)
+    torch.cuda.synchronize()
+    assert res["c"].shape == (1,) and res["c"][0] == pytest.approx(1.0)
+    assert res["St"][0, 0] == pytest.approx(1.0, abs=1e-12)
+    want = rp.tt_dense(rp.unpadded(phi0))
+    got = rp.tt_dense(rp.unpadded(res["phi"].cpu().numpy()))
+    np.testing.assert_allclose(got * np.linalg.norm(want), want, atol=1e-10 * np.abs(want).max())
+    opt.close()

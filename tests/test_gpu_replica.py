@@ -276,10 +276,18 @@ def test_plan_rejects_bad_arguments():
         rtt.TTPlan(1, 2, np.ones(1), np.zeros((1, 1), dtype=np.uint8))
     with pytest.raises(rtt.RTTError, match="INVALID_ARG"):
         rtt.TTPlan(8, 2, np.ones(1), np.full((1, 8), 3, dtype=np.uint8))
+    with pytest.raises(rtt.RTTError, match="INVALID_ARG"):
+        rtt.TTPlan(8, 2, np.ones(0), np.zeros((0, 8), dtype=np.uint8))
     plan = rtt.TTPlan(8, 2, np.ones(1), np.zeros((1, 8), dtype=np.uint8))
     a = torch.zeros((8, 2, 2, 2), dtype=torch.float64, device="cuda")
     with pytest.raises(rtt.RTTError, match="alias"):
         plan.round_sum(a, a, a)
+    # zero steps leave phi untouched
+    phi = _dev(inputs.replica_start(3, 8, 2))
+    before = phi.clone()
+    plan.power(phi, 0.1, 0)
+    torch.cuda.synchronize()
+    assert torch.equal(phi, before)
 
 
 # ---------------------------------------------------------------- FP32 arithmetic
