@@ -208,14 +208,15 @@ rtt_status rtt_mixed_local_energy(rtt_handle a, rtt_handle b, const uint8_t *spi
  * mixed local energies E^{ab} and ratios r^{ab} (all b) of the configurations
  * a's chains enter the iteration with (as rtt_mixed_local_energy), then one
  * systematic sweep of a's chains on P^a (as rtt_mcmc_sweep with chain0 and
- * sweep0 = sweep).  The measurements run on the first handle's second stream
- * from copies of the spins; with FP64/FP32 handles each state's sweep runs on
- * its own handle's third stream, so the M sweeps and the measurements proceed
- * side by side (tensor-core sweeps, which fill 64 SMs per 4096 chains, run one
- * after another on `stream`); all work is ordered after earlier and before
- * later work on `stream`.  Calls on one
- * set of handles must not overlap (they share the handles' streams and
- * scratch).
+ * sweep0 = sweep).  The measurements run from copies of the spins on the
+ * handles' second streams, in M waves: wave w evaluates the pairs (a, (a+w)
+ * mod M), so that no two concurrent pairs share a handle's energy scratch;
+ * with FP64/FP32 handles each state's sweep runs on its own handle's third
+ * stream, so the M sweeps and the measurements proceed side by side
+ * (tensor-core sweeps, which fill 64 SMs per 4096 chains, run one after
+ * another on `stream`); all work is ordered after earlier and before later
+ * work on `stream`.  The M handles must be distinct; calls on one set of
+ * handles must not overlap (they share the handles' streams and scratch).
  *   handles   host [M] (M >= 1), one lattice as for rtt_mixed_local_energy
  *   spins     host [M] of device [B][N]; state host [M] of device [B]
  *   e_mixed   device [M][M][B] (a-major, then b) or NULL; ratio likewise

@@ -366,6 +366,8 @@ rtt_status rtt_create(const rtt_desc *d, rtt_handle *out) {
                      "rtt_create: third stream");
     API_CUDA_CLEANUP(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "rtt_create: events");
     API_CUDA_CLEANUP(cudaEventCreateWithFlags(&h->ev_aux, cudaEventDisableTiming), "rtt_create: events");
+    API_CUDA_CLEANUP(cudaEventCreateWithFlags(&h->ev_amp, cudaEventDisableTiming), "rtt_create: events");
+    API_CUDA_CLEANUP(cudaEventCreateWithFlags(&h->ev_meas, cudaEventDisableTiming), "rtt_create: events");
     for (int i = 0; i < 2; ++i)
         API_CUDA_CLEANUP(cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming),
                          "rtt_create: events");
@@ -419,6 +421,8 @@ rtt_status rtt_destroy(rtt_handle h) {
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_aux) cudaEventDestroy(h->ev_aux);
+    if (h->ev_amp) cudaEventDestroy(h->ev_amp);
+    if (h->ev_meas) cudaEventDestroy(h->ev_meas);
     for (int i = 0; i < 2; ++i)
         if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
     tc_plan_destroy(h);
@@ -542,6 +546,9 @@ rtt_status rtt_dual_step(const rtt_handle *handles, int32_t M, uint8_t *const *s
         return fail(RTT_ERR_INVALID_ARG, "rtt_dual_step: negative B, chain0 or sweep");
     for (int m = 0; m < M; ++m) {
         if (!handles[m]) return fail(RTT_ERR_INVALID_ARG, "rtt_dual_step: null handle");
+        for (int m2 = 0; m2 < m; ++m2)
+            if (handles[m2] == handles[m])
+                return fail(RTT_ERR_INVALID_ARG, "rtt_dual_step: a handle appears twice");
         rtt_status s = same_lattice(handles[0], handles[m], "rtt_dual_step");
         if (s != RTT_OK) return s;
         if (B > 0 && (!spins[m] || !state[m]))
@@ -556,25 +563,41 @@ rtt_status rtt_dual_step(const rtt_handle *handles, int32_t M, uint8_t *const *s
     for (int m = 0; m < M; ++m)
         if ((s = ensure_scratch(handles[m], B)) != RTT_OK) return s;
     const size_t nv = (size_t)B * h0->N;
+    const bool meas = e_mixed || ratio;
+    // snapshots of the entering configurations, and a's amplitudes of them on
+    // a's second stream
     for (int a = 0; a < M; ++a) {
         rtt_s *ha = handles[a];
-        // measurements of a's entering configurations, on h0's second stream
-        // (the pairs (a, b) share b's energy scratch, so they stay in one stream)
-        if (e_mixed || ratio)
+        if (meas)
             API_CUDA(cudaMemcpyAsync(ha->d_snap[0], spins[a], nv, cudaMemcpyDeviceToDevice, st),
                      "rtt_dual_step: spin snapshot");
         API_CUDA(cudaEventRecord(ha->ev_fork, st), "rtt_dual_step: fork");
-        if (e_mixed || ratio) {
-            API_CUDA(cudaStreamWaitEvent(h0->side, ha->ev_fork, 0), "rtt_dual_step: fork");
-            if ((s = mixed_amplitudes(ha, ha->d_snap[0], B, h0->side)) != RTT_OK) return s;
-            for (int b = 0; b < M; ++b) {
+        if (meas) {
+            API_CUDA(cudaStreamWaitEvent(ha->side, ha->ev_fork, 0), "rtt_dual_step: fork");
+            if ((s = mixed_amplitudes(ha, ha->d_snap[0], B, ha->side)) != RTT_OK) return s;
+            API_CUDA(cudaEventRecord(ha->ev_amp, ha->side), "rtt_dual_step: amplitudes");
+        }
+    }
+    // the pairs (a, b) in M waves: wave w takes b = (a + w) mod M for every a, so
+    // within a wave each b -- whose energy scratch the pair uses -- appears once;
+    // pair (a, b) runs on b's second stream after a's amplitudes
+    if (meas) {
+        for (int w = 0; w < M; ++w)
+            for (int a = 0; a < M; ++a) {
+                const int b = (a + w) % M;
+                rtt_s *ha = handles[a], *hb = handles[b];
+                if (b != a)
+                    API_CUDA(cudaStreamWaitEvent(hb->side, ha->ev_amp, 0), "rtt_dual_step: wave");
                 const size_t off = ((size_t)a * M + b) * B;
-                double *e = e_mixed ? e_mixed + off : nullptr;
-                double *r = ratio ? ratio + off : nullptr;
-                if ((s = mixed_rows(ha, handles[b], ha->d_snap[0], B, e, r, h0->side)) != RTT_OK)
+                if ((s = mixed_rows(ha, hb, ha->d_snap[0], B, e_mixed ? e_mixed + off : nullptr,
+                                    ratio ? ratio + off : nullptr, hb->side)) != RTT_OK)
                     return s;
             }
-        }
+        for (int b = 0; b < M; ++b)
+            API_CUDA(cudaEventRecord(handles[b]->ev_meas, handles[b]->side), "rtt_dual_step: join");
+    }
+    for (int a = 0; a < M; ++a) {
+        rtt_s *ha = handles[a];
         // one sweep of a's chains, after the snapshot.  A SIMT sweep holds few
         // SMs (one thread group per chain), so it runs on a's third stream beside
         // the other states' sweeps (each uses its own sweep scratch); a
@@ -601,12 +624,11 @@ rtt_status rtt_dual_step(const rtt_handle *handles, int32_t M, uint8_t *const *s
         }
         API_CUDA(cudaEventRecord(ha->ev_aux, sa_st), "rtt_dual_step: join");
     }
-    // the caller's stream waits for every sweep and the measurements
-    for (int a = 0; a < M; ++a)
+    // the caller's stream waits for every sweep and every measurement stream
+    for (int a = 0; a < M; ++a) {
         API_CUDA(cudaStreamWaitEvent(st, handles[a]->ev_aux, 0), "rtt_dual_step: join");
-    if (e_mixed || ratio) {
-        API_CUDA(cudaEventRecord(h0->ev_done[0], h0->side), "rtt_dual_step: join");
-        API_CUDA(cudaStreamWaitEvent(st, h0->ev_done[0], 0), "rtt_dual_step: join");
+        if (meas)
+            API_CUDA(cudaStreamWaitEvent(st, handles[a]->ev_meas, 0), "rtt_dual_step: join");
     }
     return RTT_OK;
 }

@@ -64,6 +64,9 @@ struct rtt_s {
     // of several states run side by side (each uses only its own sweep scratch)
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_aux = nullptr;
+    // dual step: this handle's amplitudes of its configurations are ready
+    // (ev_amp), and the measurements run on its second stream are done (ev_meas)
+    cudaEvent_t ev_amp = nullptr, ev_meas = nullptr;
 
     void *prof = nullptr;         // per-kernel event profiler (rtt_api.cu)
 
