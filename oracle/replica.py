@@ -27,8 +27,11 @@ What it computes:
   * ``power_step``: one application of 1 - tau H-bar, in the order of Sec. 3.1:
     the terms eta_k A-bar_k phi, summed two by two with a compression after
     every sum (an odd last item passes to the next level unchanged) until one
-    TT S is left; then phi' = compress(phi - tau S), scaled to unit replica-space
-    2-norm (RTTs are not normalised; the scale keeps the numbers finite).
+    TT S is left; then phi' = compress(phi - tau S) to rank chi, scaled to unit
+    replica-space 2-norm (RTTs are not normalised; the scale keeps the numbers
+    finite).  The pairwise sums are compressed to chi_tree, by default 2 chi
+    (the rank a sum of two rank-chi TTs has); chi_tree = chi truncates every
+    pairwise sum to the final rank.
 
 Physical-space optimization (Sec. 3.2, Sec. 4):
   * ``apply_operator``: phi^alpha = O-bar_alpha phi, the terms summed two by two
@@ -208,12 +211,20 @@ def constrained_amplitudes(tt, path, n_spins):
     return tt_eval(tt, spins[:, np.asarray(path)])
 
 
-def power_step(phi, eta, ops, tau, chi, return_tree=False):
-    """phi' = compress(phi - tau * S) / norm, S = tree sum of eta_k A-bar_k phi."""
+def tree_rank(chi, chi_tree=None):
+    """Rank the tree's pairwise sums are rounded to: 2 chi (the rank of a sum of
+    two rank-chi TTs) unless given."""
+    return 2 * chi if chi_tree is None else int(chi_tree)
+
+
+def power_step(phi, eta, ops, tau, chi, return_tree=False, chi_tree=None):
+    """phi' = compress(phi - tau * S) / norm, S = tree sum of eta_k A-bar_k phi
+    with every pairwise sum rounded to chi_tree (default 2 chi) and phi' to chi."""
+    ct = tree_rank(chi, chi_tree)
     items = [apply_string(phi, ops[k], eta[k]) for k in range(len(eta))]
     levels = 0
     while len(items) > 1:
-        nxt = [tt_round(tt_sum(items[i], items[i + 1]), chi) for i in range(0, len(items) - 1, 2)]
+        nxt = [tt_round(tt_sum(items[i], items[i + 1]), ct) for i in range(0, len(items) - 1, 2)]
         if len(items) % 2:
             nxt.append(items[-1])
         items = nxt
@@ -226,10 +237,10 @@ def power_step(phi, eta, ops, tau, chi, return_tree=False):
     return out, nrm
 
 
-def power(phi, eta, ops, tau, chi, steps):
+def power(phi, eta, ops, tau, chi, steps, chi_tree=None):
     log_norms = []
     for _ in range(steps):
-        phi, nrm = power_step(phi, eta, ops, tau, chi)
+        phi, nrm = power_step(phi, eta, ops, tau, chi, chi_tree=chi_tree)
         log_norms.append(np.log(nrm))
     return phi, np.asarray(log_norms)
 
@@ -262,13 +273,14 @@ def unpadded(cores):
 
 # ---------------------------------------------------------------- physical-space optimization
 
-def tree_round(items, chi):
-    """Sum of TTs, two by two with a rounding after every sum (an odd last item
-    passes up unchanged), as in the replica-space step; the root is rounded
-    once more so that every result has the same canonical form."""
+def tree_round(items, chi, chi_tree=None):
+    """Sum of TTs, two by two with a rounding to chi_tree (default 2 chi) after
+    every sum (an odd last item passes up unchanged), as in the replica-space
+    step; the root is rounded to chi."""
+    ct = tree_rank(chi, chi_tree)
     items = list(items)
     while len(items) > 1:
-        nxt = [tt_round(tt_sum(items[i], items[i + 1]), chi) for i in range(0, len(items) - 1, 2)]
+        nxt = [tt_round(tt_sum(items[i], items[i + 1]), ct) for i in range(0, len(items) - 1, 2)]
         if len(items) % 2:
             nxt.append(items[-1])
         items = nxt
@@ -280,14 +292,15 @@ def normalised(tt):
     return tt_scale(tt, 1.0 / nrm), nrm
 
 
-def apply_operator(phi, eta, ops, chi):
+def apply_operator(phi, eta, ops, chi, chi_tree=None):
     """phi^alpha = O-bar_alpha phi (Sec. 3.2: psi^alpha = O_alpha psi built with
     O-bar_alpha as in the replica-space optimization), rounded to chi and scaled
     to unit replica-space norm.  Returns (phi^alpha, norm before scaling)."""
-    return normalised(tree_round([apply_string(phi, ops[k], eta[k]) for k in range(len(eta))], chi))
+    return normalised(tree_round([apply_string(phi, ops[k], eta[k]) for k in range(len(eta))], chi,
+                                 chi_tree))
 
 
-def combine(phis, coef, chi):
+def combine(phis, coef, chi, chi_tree=None):
     """phi' = sum_alpha c_alpha phi^alpha (Eq. lin_comb, the TTs summed back into
     one), rounded to chi and scaled to unit norm."""
-    return normalised(tree_round([tt_scale(p, float(c)) for p, c in zip(phis, coef)], chi))
+    return normalised(tree_round([tt_scale(p, float(c)) for p, c in zip(phis, coef)], chi, chi_tree))

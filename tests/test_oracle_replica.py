@@ -274,10 +274,12 @@ def test_untruncated_power_method_reaches_the_ground_state():
 
 
 def test_truncated_power_method_is_variational_and_ordered():
-    """Rank-2 and rank-4 TTs on a 3x3 lattice (path V+H+D+D', L = 36): every
-    RTT energy lies above the exact ground state; a larger rank does better;
-    sending the vertical bonds to the V ordering (H-bar_HV) does better than
-    keeping every bond on H (H-bar_H), the ordering the paper reports."""
+    """Rank-2 and rank-4 TTs on a 3x3 lattice (path V+H+D+D', L = 36), 20
+    steps: every RTT energy lies above the exact ground state; sending the
+    vertical bonds to the V ordering (H-bar_HV) does far better than keeping
+    every bond on H (H-bar_H), the ordering the paper reports; a larger rank
+    does better; and rounding every pairwise sum of the tree to the final rank
+    (chi_tree = chi) instead of to 2 chi loses most of that accuracy."""
     lx = ly = 3
     order = ("V", "H", "D", "Dp")
     path = inputs.path_sum([inputs.ordering(o, lx, ly) for o in order])
@@ -289,14 +291,33 @@ def test_truncated_power_method_is_variational_and_ordered():
         return psi @ H @ psi / (psi @ psi)
     e_start = energy(rp.tt_ones(36))
     err = {}
-    for kind, chi in [("H", 2), ("HV", 2), ("HV", 4)]:
+    for kind, chi, ct in [("H", 2, None), ("HV", 2, None), ("HV", 4, None), ("HV", 2, 2)]:
         eta, ops = rp.lift(inputs.hbar_terms(kind, lx, ly, 3.0, orderings=order), path, 9)
-        phi, _ = rp.power(rp.tt_ones(36), eta, ops, 0.1, chi, 20)
-        err[kind, chi] = energy(phi) - e0
-        assert err[kind, chi] >= -1e-9
-    assert err["HV", 2] < 0.5 * (e_start - e0)
-    assert err["HV", 2] < err["H", 2]
-    assert err["HV", 4] < 0.1 * err["HV", 2]
+        phi, _ = rp.power(rp.tt_ones(36), eta, ops, 0.1, chi, 20, chi_tree=ct)
+        err[kind, chi, ct] = energy(phi) - e0
+        assert err[kind, chi, ct] >= -1e-9
+    assert err["HV", 2, None] < 0.05 * (e_start - e0)
+    assert err["HV", 2, None] < 0.2 * err["H", 2, None]
+    assert err["HV", 4, None] < 0.5 * err["HV", 2, None]
+    assert err["HV", 2, 2] > 5 * err["HV", 2, None]
+
+
+def test_tree_without_intermediate_truncation_is_one_rounding_of_the_exact_sum():
+    """With chi_tree at least the rank of every pairwise sum, the tree loses
+    nothing: the step equals rounding phi - tau sum_k eta_k P_k phi once."""
+    lx, ly = 2, 2
+    order = ("H", "V")
+    path = inputs.path_sum([inputs.ordering(o, lx, ly) for o in order])
+    eta, ops = rp.lift(inputs.hbar_terms("HV", lx, ly, 3.0, orderings=order), path, 4)
+    rng = np.random.default_rng(17)
+    phi = rp.tt_random(rng, 8, 2)
+    got, _ = rp.power_step(phi, eta, ops, 0.1, 2, chi_tree=64)
+    S = rp.apply_string(phi, ops[0], eta[0])
+    for k in range(1, len(eta)):
+        S = rp.tt_sum(S, rp.apply_string(phi, ops[k], eta[k]))
+    want = rp.tt_round(rp.tt_sum(phi, rp.tt_scale(S, -0.1)), 2)
+    want = rp.tt_scale(want, 1.0 / rp.tt_norm(want))
+    np.testing.assert_allclose(rp.tt_dense(got), rp.tt_dense(want), atol=1e-10)
 
 
 def test_padded_cores_feed_the_sampler_format():
