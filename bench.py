@@ -707,12 +707,11 @@ def run_dual(args):
         h.close()
 
 
-def rounding_flops(L: int, chi: int) -> float:
-    """Dense operation counts of one TT rounding of a two-term sum (rank 2 chi
+def rounding_flops(L: int, D2: int, chi: int) -> float:
+    """Dense operation counts of one TT rounding of a two-term sum (bond D2
     rounded to chi): per site the product with the carried factor, a
     Householder QR with explicit Q (4 m n^2 - 4 n^3 / 3, m >= n), and a thin SVD
     with both factors (6 m n^2 + 20 n^3, m >= n) plus the product with U S."""
-    D2 = 2 * chi
 
     def qr(m, n):
         m, n = max(m, n), min(m, n)
@@ -783,7 +782,10 @@ def run_replica(args):
     total_ms = sum(a.elapsed_time(z) for a, z in ev)
     step_ms = total_ms / K
     value = K / (total_ms / 1e3)
-    flops_step = K_terms * rounding_flops(L, chi)
+    ct = min(2 * chi, 16)
+    n1 = K_terms // 2                       # first level: sums of two rank-chi terms
+    flops_step = (n1 * rounding_flops(L, 2 * chi, ct) + (K_terms - 1 - n1) * rounding_flops(L, 2 * ct, ct)
+                  + rounding_flops(L, chi + ct, chi))
     achieved = flops_step / (step_ms / 1e3) / 1e12
     peaks, _ = measured_peaks()
     lanes = FP64_LANES_PER_SM if tt_prec == "fp64" else FP32_LANES_PER_SM
@@ -845,7 +847,8 @@ def run_replica(args):
         "dtype": {"fp64": "f64", "fp32": "f32"}[tt_prec], "data": "synthetic",
         "config": {"workload": f"{name}: {lx}x{ly} open TFIM h={h}, path "
                                f"{'+'.join(order)} (L={L}), H-bar_{w['kind']} ({K_terms} terms, "
-                               f"{levels} tree levels), chi={chi}, tau={tau}, phi0 = 1",
+                               f"{levels} tree levels, pairwise sums rounded to rank {min(2 * chi, 16)}), "
+                               f"chi={chi}, tau={tau}, phi0 = 1",
                    "l2": "flushed (256 MiB write + 256 MiB read) between timed steps"},
         "roundings_per_s": K_terms * value,
         "launch_ms": step_ms / (levels + 1),

@@ -405,23 +405,28 @@ typedef struct rtt_tt_plan_s *rtt_tt_plan;
 
 /* A plan for (1 - tau H-bar) on TTs of `length` sites and rank chi (1..16),
  * H-bar = sum_k eta[k] P_k with the strings ops [n_terms][length] (host,
- * codes as above; n_terms >= 1, length >= 2).  precision: RTT_FP64 or
+ * codes as above; n_terms >= 1, length >= 2).  chi_tree: the rank the tree's
+ * pairwise sums are rounded to (chi <= chi_tree <= 16; 0 = min(2 chi, 16),
+ * the rank a sum of two rank-chi TTs has); the final results (phi, operator
+ * states, combinations) are rounded to chi.  precision: RTT_FP64 or
  * RTT_FP32, the arithmetic of the roundings (cores are FP64 in memory either
  * way; FP32 runs the factorizations at the FP32 rate, with correspondingly
  * larger rounding errors).  Copies the strings to the device, allocates the
- * tree's node TTs (n_terms - 1 of them) and the rounding scratch
- * (floor(n_terms/2) * length * 2 * (2 c)^2 values, c = chi rounded up to 4, 8
- * or 16) on `device`.  *out owned by the caller (rtt_tt_plan_destroy). */
-rtt_status rtt_tt_plan_create(int32_t length, int32_t chi, int32_t precision, int32_t n_terms,
-                              const uint8_t *ops, const double *eta, int32_t device,
-                              rtt_tt_plan *out);
+ * tree's node TTs (n_terms - 1 of them, rank chi_tree) and the rounding
+ * scratch (floor(n_terms/2) * length * 2 * (2 c)^2 values, c = max(chi,
+ * chi_tree) rounded up to 2, 4, 8 or 16) on `device`.  *out owned by the
+ * caller (rtt_tt_plan_destroy). */
+rtt_status rtt_tt_plan_create(int32_t length, int32_t chi, int32_t chi_tree, int32_t precision,
+                              int32_t n_terms, const uint8_t *ops, const double *eta,
+                              int32_t device, rtt_tt_plan *out);
 rtt_status rtt_tt_plan_destroy(rtt_tt_plan plan);
 
 /* n_steps applications of 1 - tau H-bar to phi in place (device padded
  * cores), each as Sec. 3.1 orders it: the terms eta_k P_k phi, summed two by
  * two (items in term order; pairs (0,1), (2,3), ...; an odd last item passes
  * to the next level unchanged) with every pair sum rounded to rank chi, until
- * one TT S is left; then phi <- round(phi - tau S) / ||.||_2.  Rounding is
+ * one TT S is left (pairwise sums rounded to chi_tree); then
+ * phi <- round(phi - tau S) / ||.||_2 at rank chi.  Rounding is
  * TT rounding: left-to-right Householder QR of each core, then right-to-left
  * SVD (one-sided Jacobi) keeping the chi largest singular values per bond.
  * The output's cores 2..L are right-orthonormal and core 1 carries the

@@ -36,10 +36,12 @@ struct TTItem {
     const double *tt;     // padded cores [L][2][chi][chi]
     const uint8_t *ops;   // string codes [L] or null (identity)
     double coef;          // multiplies the first core
+    int chi;              // this TT's padded rank (its cores' layout)
 };
 struct TTPair {
     TTItem a, b;
-    double *out;          // padded cores [L][2][chi][chi]
+    double *out;          // padded cores [L][2][chi_out][chi_out]
+    int chi_out;          // rank the sum is rounded to
 };
 
 rtt_status rp_fail(rtt_status s, const std::string &msg) {
@@ -99,8 +101,9 @@ template <> __device__ __forceinline__ double pow2<double>(int e) {
 // conversion to T, so that a TT whose norm sits in its first core cannot
 // overflow the arithmetic type.
 template <typename T>
-__device__ __forceinline__ T item_core(const TTItem &it, int L, int chi, int k, int s, int b, int c,
+__device__ __forceinline__ T item_core(const TTItem &it, int L, int k, int s, int b, int c,
                                        double s0) {
+    const int chi = it.chi;
     int so = s;
     double sg = 1.0;
     if (it.ops) {
@@ -113,24 +116,23 @@ __device__ __forceinline__ T item_core(const TTItem &it, int L, int chi, int k, 
 }
 
 template <typename T>
-__device__ __forceinline__ T sum_core(const TTItem &A, const TTItem &B, int L, int chi, int k, int s,
-                                      int b, int c, double s0) {
+__device__ __forceinline__ T sum_core(const TTItem &A, const TTItem &B, int L, int k, int s, int b,
+                                      int c, double s0) {
+    const int dA = A.chi;                 // A's block comes first
     if (k == 0) {                         // left rank 1
-        return c < chi ? item_core<T>(A, L, chi, k, s, 0, c, s0)
-                       : item_core<T>(B, L, chi, k, s, 0, c - chi, s0);
+        return c < dA ? item_core<T>(A, L, k, s, 0, c, s0) : item_core<T>(B, L, k, s, 0, c - dA, s0);
     }
     if (k == L - 1) {                     // right rank 1
-        return b < chi ? item_core<T>(A, L, chi, k, s, b, 0, s0)
-                       : item_core<T>(B, L, chi, k, s, b - chi, 0, s0);
+        return b < dA ? item_core<T>(A, L, k, s, b, 0, s0) : item_core<T>(B, L, k, s, b - dA, 0, s0);
     }
-    if (b < chi && c < chi) return item_core<T>(A, L, chi, k, s, b, c, s0);
-    if (b >= chi && c >= chi) return item_core<T>(B, L, chi, k, s, b - chi, c - chi, s0);
+    if (b < dA && c < dA) return item_core<T>(A, L, k, s, b, c, s0);
+    if (b >= dA && c >= dA) return item_core<T>(B, L, k, s, b - dA, c - dA, s0);
     return T(0);
 }
 
 template <typename T, int CM>
 __global__ void __launch_bounds__(128) k_tt_round(const TTPair *__restrict__ pairs, int npairs,
-                                                  int L, int chi, T *__restrict__ scratch,
+                                                  int L, T *__restrict__ scratch,
                                                   int normalize, double *__restrict__ log_norm) {
     constexpr int D2M = 2 * CM, MR = 4 * CM;
     constexpr unsigned FULL = 0xffffffffu;
@@ -140,7 +142,8 @@ __global__ void __launch_bounds__(128) k_tt_round(const TTPair *__restrict__ pai
     if (w >= npairs) return;
     WarpSmem<T, CM> &S = reinterpret_cast<WarpSmem<T, CM> *>(smem_raw)[wib];
     const TTPair P = pairs[w];
-    const int D2 = 2 * chi;
+    const int D2 = P.a.chi + P.b.chi;            // bond of the sum
+    const int chi = P.chi_out;                   // rank (and layout) of the result
     const size_t qstride = (size_t)2 * D2M * D2M;            // one site's Q, [row (a,s)][col]
     T *Q = scratch + (size_t)w * L * qstride;
 
@@ -151,10 +154,13 @@ __global__ void __launch_bounds__(128) k_tt_round(const TTPair *__restrict__ pai
     double s0 = 1.0;
     {
         double mx = 0.0;
-        for (int e = lane; e < 2 * chi; e += 32) {
-            const int s = e / chi, c = e % chi;
-            mx = fmax(mx, fabs(P.a.coef * P.a.tt[(s * chi + 0) * chi + c]));
-            mx = fmax(mx, fabs(P.b.coef * P.b.tt[(s * chi + 0) * chi + c]));
+        for (int e = lane; e < 2 * P.a.chi; e += 32) {
+            const int s = e / P.a.chi, c = e % P.a.chi;
+            mx = fmax(mx, fabs(P.a.coef * P.a.tt[(s * P.a.chi + 0) * P.a.chi + c]));
+        }
+        for (int e = lane; e < 2 * P.b.chi; e += 32) {
+            const int s = e / P.b.chi, c = e % P.b.chi;
+            mx = fmax(mx, fabs(P.b.coef * P.b.tt[(s * P.b.chi + 0) * P.b.chi + c]));
         }
         for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, off));
         if (mx > 0.0 && isfinite(mx)) {
@@ -178,8 +184,8 @@ __global__ void __launch_bounds__(128) k_tt_round(const TTPair *__restrict__ pai
         for (int i = 0; i < MR; ++i) col[i] = T(0);
         if (lane < dr) {
             for (int b = 0; b < dl; ++b) {
-                const T g0 = sum_core<T>(P.a, P.b, L, chi, k, 0, b, lane, s0);
-                const T g1 = sum_core<T>(P.a, P.b, L, chi, k, 1, b, lane, s0);
+                const T g0 = sum_core<T>(P.a, P.b, L, k, 0, b, lane, s0);
+                const T g1 = sum_core<T>(P.a, P.b, L, k, 1, b, lane, s0);
 #pragma unroll
                 for (int a = 0; a < D2M; ++a)
                     if (a < rl) {
@@ -455,9 +461,12 @@ constexpr int warps_per_cta() {
     return CM <= 8 ? 4 : 2;
 }
 
+// chi (below): the largest rank among the launch's TTs, which picks the
+// compile-time bound CM (every sum's bond is at most 2 CM)
 template <typename T, int CM>
 cudaError_t launch_round(const TTPair *pairs, int npairs, int L, int chi, void *scratch,
                          int normalize, double *log_norm, cudaStream_t st) {
+    (void)chi;
     constexpr int wpc = warps_per_cta<CM>();
     const size_t smem = sizeof(WarpSmem<T, CM>) * wpc;
     // per device and cheap: set on every launch
@@ -465,8 +474,8 @@ cudaError_t launch_round(const TTPair *pairs, int npairs, int L, int chi, void *
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int blocks = (npairs + wpc - 1) / wpc;
-    k_tt_round<T, CM><<<blocks, 32 * wpc, smem, st>>>(pairs, npairs, L, chi, (T *)scratch,
-                                                      normalize, log_norm);
+    k_tt_round<T, CM><<<blocks, 32 * wpc, smem, st>>>(pairs, npairs, L, (T *)scratch, normalize,
+                                                      log_norm);
     return cudaGetLastError();
 }
 
@@ -494,9 +503,11 @@ cudaError_t launch_round_any(const TTPair *pairs, int npairs, int L, int chi, in
 // ----------------------------------------------------------------------------
 struct rtt_tt_plan_s {
     int device = 0, L = 0, chi = 0, K = 0, precision = RTT_FP64;
+    int chi_tree = 0;             // rank the tree's pairwise sums are rounded to
+    int cm = 0;                   // the largest rank of the plan's TTs, max(chi, chi_tree)
     std::vector<double> eta;
     uint8_t *d_ops = nullptr;     // [K][L]
-    double *d_nodes = nullptr;    // [K-1][L][2][chi][chi] tree node TTs
+    double *d_nodes = nullptr;    // [K-1][L][2][chi_tree][chi_tree] tree node TTs
     double *d_next = nullptr;     // [L][2][chi][chi]
     void *d_scratch = nullptr;    // [max pairs][L][2 (2chi)^2] of the arithmetic type (padded
                                   // to the kernel's bound on chi)
@@ -520,7 +531,7 @@ size_t q_site_doubles(int chi) {
 // level by level, node outputs in the plan's node buffers in creation order;
 // appends to `pairs`, sets the plan's level offsets and returns the root.
 TTItem build_tree(rtt_tt_plan_s *p, std::vector<TTItem> items, std::vector<TTPair> &pairs) {
-    const size_t tt = (size_t)p->L * 2 * p->chi * p->chi;
+    const size_t tt = (size_t)p->L * 2 * p->chi_tree * p->chi_tree;
     pairs.clear();
     p->level_off.assign(1, 0);
     int node = 0;
@@ -528,8 +539,8 @@ TTItem build_tree(rtt_tt_plan_s *p, std::vector<TTItem> items, std::vector<TTPai
         std::vector<TTItem> nxt;
         for (size_t i = 0; i + 1 < items.size(); i += 2) {
             double *o = p->d_nodes + (size_t)node++ * tt;
-            pairs.push_back(TTPair{items[i], items[i + 1], o});
-            nxt.push_back(TTItem{o, nullptr, 1.0});
+            pairs.push_back(TTPair{items[i], items[i + 1], o, p->chi_tree});
+            nxt.push_back(TTItem{o, nullptr, 1.0, p->chi_tree});
         }
         if (items.size() % 2) nxt.push_back(items.back());
         items.swap(nxt);
@@ -540,7 +551,7 @@ TTItem build_tree(rtt_tt_plan_s *p, std::vector<TTItem> items, std::vector<TTPai
 
 std::vector<TTItem> term_items(rtt_tt_plan_s *p, const double *phi) {
     std::vector<TTItem> items(p->K);
-    for (int k = 0; k < p->K; ++k) items[k] = TTItem{phi, p->d_ops + (size_t)k * p->L, p->eta[k]};
+    for (int k = 0; k < p->K; ++k) items[k] = TTItem{phi, p->d_ops + (size_t)k * p->L, p->eta[k], p->chi};
     return items;
 }
 
@@ -548,7 +559,7 @@ std::vector<TTItem> term_items(rtt_tt_plan_s *p, const double *phi) {
 void build_pairs(rtt_tt_plan_s *p, const double *phi, double tau, std::vector<TTPair> &pairs) {
     TTItem s = build_tree(p, term_items(p, phi), pairs);
     s.coef *= -tau;
-    pairs.push_back(TTPair{TTItem{phi, nullptr, 1.0}, s, p->d_next});
+    pairs.push_back(TTPair{TTItem{phi, nullptr, 1.0, p->chi}, s, p->d_next, p->chi});
 }
 
 // Upload a pair table (pageable source: staged before the call returns, copied
@@ -562,11 +573,11 @@ cudaError_t run_pairs(rtt_tt_plan_s *p, const std::vector<TTPair> &pairs, double
     const int nlev = (int)p->level_off.size() - 1;
     for (int l = 0; l < nlev; ++l) {
         const int n = p->level_off[l + 1] - p->level_off[l];
-        if ((e = launch_round_any(p->d_pairs + p->level_off[l], n, p->L, p->chi, p->precision, p->d_scratch, 0,
+        if ((e = launch_round_any(p->d_pairs + p->level_off[l], n, p->L, p->cm, p->precision, p->d_scratch, 0,
                                   nullptr, st)) != cudaSuccess)
             return e;
     }
-    return launch_round_any(p->d_pairs + p->level_off.back(), 1, p->L, p->chi, p->precision, p->d_scratch, 1,
+    return launch_round_any(p->d_pairs + p->level_off.back(), 1, p->L, p->cm, p->precision, p->d_scratch, 1,
                             log_norm, st);
 }
 
@@ -632,9 +643,9 @@ rtt_status rtt_replica_lift(int32_t n_spins, int32_t length, const int32_t *path
     return RTT_OK;
 }
 
-rtt_status rtt_tt_plan_create(int32_t length, int32_t chi, int32_t precision, int32_t n_terms,
-                              const uint8_t *ops, const double *eta, int32_t device,
-                              rtt_tt_plan *out) {
+rtt_status rtt_tt_plan_create(int32_t length, int32_t chi, int32_t chi_tree, int32_t precision,
+                              int32_t n_terms, const uint8_t *ops, const double *eta,
+                              int32_t device, rtt_tt_plan *out) {
     if (!out) return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_plan_create: out is null");
     *out = nullptr;
     if (length < 2 || chi < 1 || n_terms < 1 || !ops || !eta)
@@ -643,6 +654,9 @@ rtt_status rtt_tt_plan_create(int32_t length, int32_t chi, int32_t precision, in
     if (chi > kMaxChi) return rp_fail(RTT_ERR_UNSUPPORTED, "rtt_tt_plan_create: chi > 16");
     if (precision != RTT_FP64 && precision != RTT_FP32)
         return rp_fail(RTT_ERR_UNSUPPORTED, "rtt_tt_plan_create: precision must be FP64 or FP32");
+    if (chi_tree == 0) chi_tree = std::min(2 * chi, kMaxChi);
+    if (chi_tree < chi || chi_tree > kMaxChi)
+        return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_plan_create: need chi <= chi_tree <= 16");
     for (size_t i = 0; i < (size_t)n_terms * length; ++i)
         if (ops[i] > 2) return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_plan_create: string code > 2");
     cudaError_t e = cudaSetDevice(device);
@@ -653,10 +667,13 @@ rtt_status rtt_tt_plan_create(int32_t length, int32_t chi, int32_t precision, in
     p->chi = chi;
     p->K = n_terms;
     p->precision = precision;
+    p->chi_tree = chi_tree;
+    p->cm = std::max(chi, chi_tree);
     p->eta.assign(eta, eta + n_terms);
     p->max_pairs = std::max(1, n_terms / 2);
-    p->qsite = q_site_doubles(chi);
+    p->qsite = q_site_doubles(p->cm);
     const size_t tt = (size_t)length * 2 * chi * chi;
+    const size_t ttn = (size_t)length * 2 * chi_tree * chi_tree;
     int n_pairs_total = n_terms;                 // K - 1 tree pairs + the final one
     auto cleanup = [&](cudaError_t err) {
         rtt_tt_plan_destroy(p);
@@ -666,7 +683,7 @@ rtt_status rtt_tt_plan_create(int32_t length, int32_t chi, int32_t precision, in
     if ((e = cudaMalloc(&p->d_ops, (size_t)n_terms * length)) != cudaSuccess) return cleanup(e);
     if ((e = cudaMemcpy(p->d_ops, ops, (size_t)n_terms * length, cudaMemcpyHostToDevice)) != cudaSuccess)
         return cleanup(e);
-    if (n_terms > 1 && (e = cudaMalloc(&p->d_nodes, (size_t)(n_terms - 1) * tt * 8)) != cudaSuccess)
+    if (n_terms > 1 && (e = cudaMalloc(&p->d_nodes, (size_t)(n_terms - 1) * ttn * 8)) != cudaSuccess)
         return cleanup(e);
     if ((e = cudaMalloc(&p->d_next, tt * 8)) != cudaSuccess) return cleanup(e);
     const size_t esz = precision == RTT_FP32 ? 4 : 8;
@@ -715,11 +732,11 @@ rtt_status rtt_tt_power(rtt_tt_plan p, double *phi, double tau, int32_t n_steps,
     for (int step = 0; step < n_steps; ++step) {
         for (int l = 0; l < nlev; ++l) {
             const int n = p->level_off[l + 1] - p->level_off[l];
-            if ((e = launch_round_any(p->d_pairs + p->level_off[l], n, p->L, p->chi, p->precision,
+            if ((e = launch_round_any(p->d_pairs + p->level_off[l], n, p->L, p->cm, p->precision,
                                       p->d_scratch, 0, nullptr, st)) != cudaSuccess)
                 return rp_fail(RTT_ERR_CUDA, std::string("k_tt_round: ") + cudaGetErrorString(e));
         }
-        if ((e = launch_round_any(p->d_pairs + final_idx, 1, p->L, p->chi, p->precision, p->d_scratch, 1,
+        if ((e = launch_round_any(p->d_pairs + final_idx, 1, p->L, p->cm, p->precision, p->d_scratch, 1,
                                   log_norm ? log_norm + step : nullptr, st)) != cudaSuccess)
             return rp_fail(RTT_ERR_CUDA, std::string("k_tt_round: ") + cudaGetErrorString(e));
         if ((e = cudaMemcpyAsync(phi, p->d_next, tt * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
@@ -738,7 +755,7 @@ rtt_status rtt_tt_apply(rtt_tt_plan p, const double *phi, double *out, double *l
     TTItem root = build_tree(p, term_items(p, phi), pairs);
     TTItem zero = root;
     zero.coef = 0.0;
-    pairs.push_back(TTPair{root, zero, out});
+    pairs.push_back(TTPair{root, zero, out, p->chi});
     p->pairs_valid = false;
     if ((e = run_pairs(p, pairs, log_norm, (cudaStream_t)stream)) != cudaSuccess)
         return rp_fail(RTT_ERR_CUDA, std::string("rtt_tt_apply: ") + cudaGetErrorString(e));
@@ -755,7 +772,7 @@ rtt_status rtt_tt_sum_round(rtt_tt_plan p, int32_t n, const double *const *tts, 
     for (int m = 0; m < n; ++m) {
         if (!tts[m] || tts[m] == out)
             return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_sum_round: null input or out aliases one");
-        items[m] = TTItem{tts[m], nullptr, coef[m]};
+        items[m] = TTItem{tts[m], nullptr, coef[m], p->chi};
     }
     cudaError_t e = cudaSetDevice(p->device);
     if (e != cudaSuccess) return rp_fail(RTT_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
@@ -763,7 +780,7 @@ rtt_status rtt_tt_sum_round(rtt_tt_plan p, int32_t n, const double *const *tts, 
     TTItem root = build_tree(p, items, pairs);
     TTItem zero = root;
     zero.coef = 0.0;
-    pairs.push_back(TTPair{root, zero, out});
+    pairs.push_back(TTPair{root, zero, out, p->chi});
     p->pairs_valid = false;
     if ((e = run_pairs(p, pairs, log_norm, (cudaStream_t)stream)) != cudaSuccess)
         return rp_fail(RTT_ERR_CUDA, std::string("rtt_tt_sum_round: ") + cudaGetErrorString(e));
@@ -778,13 +795,13 @@ rtt_status rtt_tt_round_sum(rtt_tt_plan p, const double *a, const uint8_t *ops_a
     cudaError_t e = cudaSetDevice(p->device);
     if (e != cudaSuccess) return rp_fail(RTT_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
     cudaStream_t st = (cudaStream_t)stream;
-    TTPair pr{TTItem{a, ops_a, coef_a}, TTItem{b, ops_b, coef_b}, out};
+    TTPair pr{TTItem{a, ops_a, coef_a, p->chi}, TTItem{b, ops_b, coef_b, p->chi}, out, p->chi};
     // the device pair lives in the plan's pair table (slot 0); the power
     // method rebuilds its table on its next call
     p->pairs_valid = false;
     if ((e = cudaMemcpyAsync(p->d_pairs, &pr, sizeof(TTPair), cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return rp_fail(RTT_ERR_CUDA, std::string("rtt_tt_round_sum: ") + cudaGetErrorString(e));
-    if ((e = launch_round_any(p->d_pairs, 1, p->L, p->chi, p->precision, p->d_scratch, log_norm ? 1 : 0,
+    if ((e = launch_round_any(p->d_pairs, 1, p->L, p->cm, p->precision, p->d_scratch, log_norm ? 1 : 0,
                               log_norm,
                               st)) != cudaSuccess)
         return rp_fail(RTT_ERR_CUDA, std::string("k_tt_round: ") + cudaGetErrorString(e));

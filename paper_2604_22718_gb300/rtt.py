@@ -104,7 +104,7 @@ def lib():
                      "rtt_made_sample", "rtt_indep_mh"):
             getattr(L, name).restype = ctypes.c_int
         L.rtt_replica_lift.argtypes = [I32, I32, P, I32, P, P, P, P, P, P, P]
-        L.rtt_tt_plan_create.argtypes = [I32, I32, I32, I32, P, P, I32, ctypes.POINTER(P)]
+        L.rtt_tt_plan_create.argtypes = [I32, I32, I32, I32, I32, P, P, I32, ctypes.POINTER(P)]
         L.rtt_tt_plan_destroy.argtypes = [P]
         L.rtt_tt_power.argtypes = [P, P, ctypes.c_double, I32, P, P]
         L.rtt_tt_round_sum.argtypes = [P, P, P, ctypes.c_double, P, P, ctypes.c_double, P, P, P]
@@ -593,9 +593,11 @@ def replica_lift(n_spins: int, path, terms):
 
 class TTPlan:
     """rtt_tt_plan: (1 - tau H-bar) steps and two-term roundings on TTs of
-    `length` sites and rank chi; H-bar = sum_k eta[k] P_k (ops [K][length])."""
+    `length` sites and rank chi; H-bar = sum_k eta[k] P_k (ops [K][length]);
+    the tree's pairwise sums are rounded to chi_tree (0: 2 chi, at most 16)."""
 
-    def __init__(self, length: int, chi: int, eta, ops, device: int = 0, precision: str = "fp64"):
+    def __init__(self, length: int, chi: int, eta, ops, device: int = 0, precision: str = "fp64",
+                 chi_tree: int = 0):
         eta = np.ascontiguousarray(eta, dtype=np.float64)
         ops = np.ascontiguousarray(ops, dtype=np.uint8)
         if ops.ndim != 2 or ops.shape != (eta.shape[0], length):
@@ -603,8 +605,9 @@ class TTPlan:
         self.length, self.chi = int(length), int(chi)
         self._p = ctypes.c_void_p()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        _check(lib().rtt_tt_plan_create(self.length, self.chi, prec, eta.shape[0], ops.ctypes.data,
-                                        eta.ctypes.data, int(device), ctypes.byref(self._p)),
+        _check(lib().rtt_tt_plan_create(self.length, self.chi, int(chi_tree), prec, eta.shape[0],
+                                        ops.ctypes.data, eta.ctypes.data, int(device),
+                                        ctypes.byref(self._p)),
                "rtt_tt_plan_create")
 
     def close(self):

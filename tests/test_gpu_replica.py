@@ -163,18 +163,19 @@ def test_round_sum_of_a_tt_with_itself_and_of_zero():
 
 # ---------------------------------------------------------------- (1 - tau H-bar) steps
 
-def _power_case(lx, ly, order, kind, chi, steps, start, tau=0.1, h=3.0, seed=0):
+def _power_case(lx, ly, order, kind, chi, steps, start, tau=0.1, h=3.0, seed=0, chi_tree=None):
     rtt = _rtt()
     path = inputs.path_sum([inputs.ordering(o, lx, ly) for o in order])
     L = path.shape[0]
     eta, ops = rtt.replica_lift(lx * ly, path, inputs.hbar_terms(kind, lx, ly, h, orderings=order))
     phi0 = inputs.replica_ones(L, chi) if start == "ones" else inputs.replica_start(seed, L, chi)
-    plan = rtt.TTPlan(L, chi, eta, ops)
+    ct = min(rp.tree_rank(chi, chi_tree), 16)
+    plan = rtt.TTPlan(L, chi, eta, ops, chi_tree=ct)
     phi = _dev(phi0)
     ln = torch.empty(steps, dtype=torch.float64, device="cuda")
     plan.power(phi, tau, steps, log_norm=ln)
     torch.cuda.synchronize()
-    ref, ref_ln = rp.power(rp.unpadded(phi0), eta, ops, tau, chi, steps)
+    ref, ref_ln = rp.power(rp.unpadded(phi0), eta, ops, tau, chi, steps, chi_tree=ct)
     return path, _host_tt(phi), ref, ln.cpu().numpy(), ref_ln
 
 
@@ -191,6 +192,17 @@ def test_power_steps_match_oracle(lx, ly, order, kind, chi, steps, start):
     _compare(got, ref, len(path), 1e-7, rng)
     np.testing.assert_allclose(ln, ref_ln, rtol=1e-9, atol=1e-9)
     assert rp.tt_norm(got) == pytest.approx(1.0, rel=1e-10)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("chi,chi_tree", [(2, 2), (2, 3), (3, 6)])
+def test_power_steps_with_other_tree_ranks(chi, chi_tree):
+    """The tree's pairwise sums rounded to chi_tree (chi itself: every sum
+    truncated to the final rank; between chi and 2 chi)."""
+    path, got, ref, ln, ref_ln = _power_case(3, 2, ("H", "V"), "HV", chi, 4, "random", seed=90 + chi,
+                                            chi_tree=chi_tree)
+    _compare(got, ref, len(path), 1e-7, np.random.default_rng(4))
+    np.testing.assert_allclose(ln, ref_ln, rtol=1e-9, atol=1e-9)
 
 
 @pytest.mark.gpu
@@ -278,6 +290,8 @@ def test_plan_rejects_bad_arguments():
         rtt.TTPlan(8, 2, np.ones(1), np.full((1, 8), 3, dtype=np.uint8))
     with pytest.raises(rtt.RTTError, match="INVALID_ARG"):
         rtt.TTPlan(8, 2, np.ones(0), np.zeros((0, 8), dtype=np.uint8))
+    with pytest.raises(rtt.RTTError, match="chi_tree"):
+        rtt.TTPlan(8, 4, np.ones(1), np.zeros((1, 8), dtype=np.uint8), chi_tree=3)
     plan = rtt.TTPlan(8, 2, np.ones(1), np.zeros((1, 8), dtype=np.uint8))
     a = torch.zeros((8, 2, 2, 2), dtype=torch.float64, device="cuda")
     with pytest.raises(rtt.RTTError, match="alias"):
@@ -341,14 +355,15 @@ def _oracle_power_with_gaps(phi, eta, ops, tau, chi, steps):
     """The oracle's steps (same tree, same roundings) and the smallest
     truncation gap met by any rounding on the way."""
     gap = 1.0
+    ct = rp.tree_rank(chi)
     for _ in range(steps):
         items = [rp.apply_string(phi, ops[k], eta[k]) for k in range(len(eta))]
         while len(items) > 1:
             nxt = []
             for i in range(0, len(items) - 1, 2):
                 s = rp.tt_sum(items[i], items[i + 1])
-                gap = min(gap, _min_gap(s, chi))
-                nxt.append(rp.tt_round(s, chi))
+                gap = min(gap, _min_gap(s, ct))
+                nxt.append(rp.tt_round(s, ct))
             if len(items) % 2:
                 nxt.append(items[-1])
             items = nxt
