@@ -872,8 +872,9 @@ def run_replica(args):
 
 
 def run_physical(args):
-    """Physical-space optimization (Sec. 3.2; Sec. 4, Table 1): from the
-    replica-space result (H-bar_HV, 30 steps from phi^(0) = 1), iterations with
+    """Physical-space optimization (Sec. 3.2; Sec. 4, Table 1) on 6x6 or 10x10:
+    from the replica-space result (H-bar_HV, 30 or 60 steps from phi^(0) = 1),
+    iterations with
     the operators {1, O_X, O_ZZ,HV, O_ZZ,DD'}: operator states, dual Monte Carlo
     (4096 chains per state), the generalized eigenproblem and the combined TT.
     One step = one iteration; the sampled energy of each result (not timed) is
@@ -881,7 +882,8 @@ def run_physical(args):
     import torch
     from paper_2604_22718_gb300 import inputs, rtt
     from paper_2604_22718_gb300.physical import PhysicalOptimizer
-    lx = ly = 6
+    lx = ly = int(args.workload.split("_")[1].split("x")[0])
+    start_steps = 30 if lx <= 6 else 60
     order = ("V", "H", "D", "Dp")
     chi, tau, h = 2, 0.1, 3.0
     N = lx * ly
@@ -895,7 +897,7 @@ def run_physical(args):
     prec = "fp64" if args.precision == "fp64" else "fp32"
     plan = rtt.TTPlan(L, chi, eta, hops, precision=prec)
     phi = torch.from_numpy(inputs.replica_ones(L, chi)).cuda()
-    plan.power(phi, tau, 30)
+    plan.power(phi, tau, start_steps)
     opt = PhysicalOptimizer(N, path, inputs.open_bonds(lx, ly), 1.0, h, chi, ops, precision=prec,
                             tt_precision=prec)
     B, S, burn = args.chains or 4096, 100, 20
@@ -963,8 +965,9 @@ def run_physical(args):
         "value": value, "unit": "iterations/s", "n_gpus": 1, "steps": K, "warmup": W,
         "ms_per_step": 1e3 * total / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32"}[prec], "data": "synthetic",
-        "config": {"workload": f"physical_6x6: 6x6 open TFIM h={h}, path V+H+D+Dp (L={L}), chi={chi}, "
-                               f"operators 1, O_X, O_ZZ,HV, O_ZZ,DD' ({M} states), start = 30 steps of "
+        "config": {"workload": f"{args.workload}: {lx}x{ly} open TFIM h={h}, path V+H+D+Dp (L={L}), "
+                               f"chi={chi}, operators 1, O_X, O_ZZ,HV, O_ZZ,DD' ({M} states), start = "
+                               f"{start_steps} steps of "
                                f"H-bar_HV from phi0 = 1; dual Monte Carlo {B} chains x {S} sweeps "
                                f"(+{burn} burn-in) per state, {prec.upper()} sampler and TT arithmetic",
                    "timing": "host wall clock around each iteration (synchronized), includes "
@@ -997,7 +1000,7 @@ def main():
         if int(os.environ.get("RANK", "0")) == 0:
             run_learned(args)
         return
-    if args.workload == "physical_6x6":
+    if args.workload in ("physical_6x6", "physical_10x10"):
         if int(os.environ.get("RANK", "0")) == 0:
             run_physical(args)
         return
