@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--chains", type=int, default=0, help="override the workload's chain count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--gram-schmidt", default="first", choices=["none", "first", "all"],
+                    help="physical-space workloads: the basis of the dual Monte Carlo")
     return ap.parse_args()
 
 
@@ -901,11 +903,13 @@ def run_physical(args):
     opt = PhysicalOptimizer(N, path, inputs.open_bonds(lx, ly), 1.0, h, chi, ops, precision=prec,
                             tt_precision=prec)
     B, S, burn = args.chains or 4096, 100, 20
+    gs = "" if args.gram_schmidt == "none" else args.gram_schmidt
+    pilot = max(S // 5, 10) if gs else 0
     spins0 = inputs.initial_spins(22741, B, N)
     e_start = opt.energy(phi, B, 200, 50, 22742)
     K, W = args.steps, args.warmup
     for t in range(W):
-        opt.step(phi.clone(), spins0, B, S, burn, 22750 + t)
+        opt.step(phi.clone(), spins0, B, S, burn, 22750 + t, gram_schmidt=gs)
     clocks = ClockSampler(torch.cuda.current_device())
     torch.cuda.synchronize()
     clocks.start()
@@ -913,7 +917,7 @@ def run_physical(args):
     for t in range(K):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = opt.step(phi, spins0, B, S, burn, 22760 + t)
+        res = opt.step(phi, spins0, B, S, burn, 22760 + t, gram_schmidt=gs)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         total += dt
@@ -925,7 +929,7 @@ def run_physical(args):
     clk = clocks.stop()
     value = K / total
     M = len(ops)
-    dual_samples = M * B * S
+    dual_samples = M * B * (S + pilot)
     cpu = None
     if not args.no_cpu_baseline:
         from oracle import replica as orp
@@ -934,14 +938,19 @@ def run_physical(args):
         t0 = time.perf_counter()
         tt = orp.unpadded(phi.cpu().numpy())
         lifted = [(e, o) for _, e, o in opt.ops]
-        phis = [orp.apply_operator(tt, e, o, chi)[0] for e, o in lifted]
+        phis = [orp.apply_operator(tt, e, o, opt.chi_s, chi_tree=min(2 * opt.chi_s, 16))[0]
+                for e, o in lifted]
         t_tt = time.perf_counter() - t0
-        e0v = np.zeros(chi)
+        e0v = np.zeros(opt.chi_s)
         e0v[0] = 1.0
-        insts = [inputs.RTTInstance(n_spins=N, path=path.astype(np.int32), tensors=orp.padded(p, chi),
+        insts = [inputs.RTTInstance(n_spins=N, path=path.astype(np.int32),
+                                    tensors=orp.padded(p, opt.chi_s),
                                     b_left=e0v, b_right=e0v.copy(), bonds=inputs.open_bonds(lx, ly),
                                     J=1.0, h=h) for p in phis]
-        orcs = [orc.Oracle(i) for i in insts]
+        T = res["T"]
+        main = [insts[0]] + [odual.direct_sum([insts[a] for a in range(M) if T[m, a] != 0.0],
+                                              T[m][T[m] != 0.0]) for m in range(1, M)]
+        orcs = [orc.Oracle(i) for i in main]
         nb = 64
         cores = os.cpu_count() or 1
         sp = inputs.initial_spins(22743, nb, N)
@@ -953,12 +962,15 @@ def run_physical(args):
             for b in range(M):
                 odual.mixed_local_energies(orcs[a], orcs[b], x, threads=cores)
         t_mc = (time.perf_counter() - t1) * (B * (S + burn)) / nb
+        if pilot:       # the pilot pass on the states psi^alpha, timed at the main pass's rate
+            t_mc *= 1.0 + (pilot + burn) / (S + burn)
         cpu_it = t_tt * 2 + t_mc
         cpu = {"value": 1.0 / cpu_it, "unit": "iterations/s", "cores": cores, "kind": "oracle",
                "sample": f"operator TTs timed in full ({t_tt:.1f} s, counted twice for the "
                          f"combination), dual Monte Carlo timed on {nb} chains x 1 sweep with "
                          f"{M}x{M} mixed energies and scaled to {B} chains x {S + burn} sweeps "
-                         f"(FP64 oracle, {cores} threads)"}
+                         + (f"plus the {pilot + burn}-sweep pilot " if pilot else "")
+                         + f"(FP64 oracle, {cores} threads)"}
     line = {
         "metric": "physical-space optimization iterations/s (operator TTs, dual Monte Carlo, "
                   "eigenproblem, combined TT)",
@@ -966,10 +978,15 @@ def run_physical(args):
         "ms_per_step": 1e3 * total / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32"}[prec], "data": "synthetic",
         "config": {"workload": f"{args.workload}: {lx}x{ly} open TFIM h={h}, path V+H+D+Dp (L={L}), "
-                               f"chi={chi}, operators 1, O_X, O_ZZ,HV, O_ZZ,DD' ({M} states), start = "
+                               f"chi={chi}, operators 1, O_X, O_ZZ,HV, O_ZZ,DD' ({M} states of rank "
+                               f"{opt.chi_s}), start = "
                                f"{start_steps} steps of "
                                f"H-bar_HV from phi0 = 1; dual Monte Carlo {B} chains x {S} sweeps "
-                               f"(+{burn} burn-in) per state, {prec.upper()} sampler and TT arithmetic",
+                               f"(+{burn} burn-in) per state"
+                               + (f" on the Gram-Schmidt states (against psi^1 only)" if gs == "first"
+                                  else " on the Gram-Schmidt states" if gs else "")
+                               + (f" after a {pilot}-sweep pilot" if gs else "")
+                               + f", {prec.upper()} sampler and TT arithmetic",
                    "timing": "host wall clock around each iteration (synchronized), includes "
                              "handle creation and the host eigen-solver"},
         "dual_samples_per_s": dual_samples * value,

@@ -442,20 +442,23 @@ rtt_status rtt_tt_power(rtt_tt_plan plan, double *phi, double tau, int32_t n_ste
 /* phi^alpha = O-bar phi for the plan's operator O-bar = sum_k eta[k] P_k
  * (Sec. 3.2: psi^alpha = O_alpha psi built with the lifted operator as in the
  * replica-space optimization): the terms eta_k P_k phi summed two by two with
- * a rounding to chi after every sum, the root rounded once more and scaled to
- * unit norm; log_norm (device double [1] or NULL) receives the log of the norm
- * before scaling.  phi, out: device padded cores; out must not alias phi.
- * Uses the plan's node buffers and scratch (calls on one plan are ordered by
- * the caller).  One launch per tree level plus one. */
-rtt_status rtt_tt_apply(rtt_tt_plan plan, const double *phi, double *out, double *log_norm,
-                        void *stream);
+ * a rounding to chi_tree after every sum, the root rounded to the plan's chi
+ * and scaled to unit norm; log_norm (device double [1] or NULL) receives the
+ * log of the norm before scaling.  phi: device padded cores of rank chi_phi
+ * (0 = the plan's chi; at most max(chi, chi_tree)); out: the plan's chi; out
+ * must not alias phi.  Uses the plan's node buffers and scratch (calls on one
+ * plan are ordered by the caller).  One launch per tree level plus one. */
+rtt_status rtt_tt_apply(rtt_tt_plan plan, const double *phi, int32_t chi_phi, double *out,
+                        double *log_norm, void *stream);
 
 /* out = round(sum_m coef[m] tts[m]) scaled to unit norm (Eq. lin_comb: the
  * optimal combination turned back into one TT), the sum taken two by two with
- * a rounding after every sum like rtt_tt_apply.  n <= the plan's n_terms (the
- * plan's node buffers hold the tree); tts: host array of n device padded-core
- * pointers of the plan's length and chi; coef: host [n]; log_norm as above. */
-rtt_status rtt_tt_sum_round(rtt_tt_plan plan, int32_t n, const double *const *tts,
+ * a rounding to chi_tree after every sum and the root rounded to chi, like
+ * rtt_tt_apply.  n <= the plan's n_terms (the plan's node buffers hold the
+ * tree); tts: host array of n device padded-core pointers of the plan's
+ * length and rank chi_in (0 = chi; at most max(chi, chi_tree)); coef: host
+ * [n]; out: the plan's chi; log_norm as above. */
+rtt_status rtt_tt_sum_round(rtt_tt_plan plan, int32_t n, const double *const *tts, int32_t chi_in,
                             const double *coef, double *out, double *log_norm, void *stream);
 
 /* One rounding of a two-term sum, the operation every tree node performs:

@@ -549,15 +549,15 @@ TTItem build_tree(rtt_tt_plan_s *p, std::vector<TTItem> items, std::vector<TTPai
     return items[0];
 }
 
-std::vector<TTItem> term_items(rtt_tt_plan_s *p, const double *phi) {
+std::vector<TTItem> term_items(rtt_tt_plan_s *p, const double *phi, int chi_phi) {
     std::vector<TTItem> items(p->K);
-    for (int k = 0; k < p->K; ++k) items[k] = TTItem{phi, p->d_ops + (size_t)k * p->L, p->eta[k], p->chi};
+    for (int k = 0; k < p->K; ++k) items[k] = TTItem{phi, p->d_ops + (size_t)k * p->L, p->eta[k], chi_phi};
     return items;
 }
 
 // (1 - tau H-bar): the tree's root S, then phi - tau S into the plan's next buffer.
 void build_pairs(rtt_tt_plan_s *p, const double *phi, double tau, std::vector<TTPair> &pairs) {
-    TTItem s = build_tree(p, term_items(p, phi), pairs);
+    TTItem s = build_tree(p, term_items(p, phi, p->chi), pairs);
     s.coef *= -tau;
     pairs.push_back(TTPair{TTItem{phi, nullptr, 1.0, p->chi}, s, p->d_next, p->chi});
 }
@@ -745,14 +745,17 @@ rtt_status rtt_tt_power(rtt_tt_plan p, double *phi, double tau, int32_t n_steps,
     return RTT_OK;
 }
 
-rtt_status rtt_tt_apply(rtt_tt_plan p, const double *phi, double *out, double *log_norm,
-                        void *stream) {
+rtt_status rtt_tt_apply(rtt_tt_plan p, const double *phi, int32_t chi_phi, double *out,
+                        double *log_norm, void *stream) {
     if (!p || !phi || !out) return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_apply: null pointer");
     if (out == phi) return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_apply: out aliases phi");
+    if (chi_phi == 0) chi_phi = p->chi;
+    if (chi_phi < 1 || chi_phi > p->cm)
+        return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_apply: chi_phi must be in [1, max(chi, chi_tree)]");
     cudaError_t e = cudaSetDevice(p->device);
     if (e != cudaSuccess) return rp_fail(RTT_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
     std::vector<TTPair> pairs;
-    TTItem root = build_tree(p, term_items(p, phi), pairs);
+    TTItem root = build_tree(p, term_items(p, phi, chi_phi), pairs);
     TTItem zero = root;
     zero.coef = 0.0;
     pairs.push_back(TTPair{root, zero, out, p->chi});
@@ -762,17 +765,20 @@ rtt_status rtt_tt_apply(rtt_tt_plan p, const double *phi, double *out, double *l
     return RTT_OK;
 }
 
-rtt_status rtt_tt_sum_round(rtt_tt_plan p, int32_t n, const double *const *tts, const double *coef,
-                            double *out, double *log_norm, void *stream) {
+rtt_status rtt_tt_sum_round(rtt_tt_plan p, int32_t n, const double *const *tts, int32_t chi_in,
+                            const double *coef, double *out, double *log_norm, void *stream) {
     if (!p || !tts || !coef || !out || n < 1)
         return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_sum_round: null pointer or n < 1");
+    if (chi_in == 0) chi_in = p->chi;
+    if (chi_in < 1 || chi_in > p->cm)
+        return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_sum_round: chi_in must be in [1, max(chi, chi_tree)]");
     if (n > p->K)
         return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_sum_round: n exceeds the plan's term count");
     std::vector<TTItem> items(n);
     for (int m = 0; m < n; ++m) {
         if (!tts[m] || tts[m] == out)
             return rp_fail(RTT_ERR_INVALID_ARG, "rtt_tt_sum_round: null input or out aliases one");
-        items[m] = TTItem{tts[m], nullptr, coef[m], p->chi};
+        items[m] = TTItem{tts[m], nullptr, coef[m], chi_in};
     }
     cudaError_t e = cudaSetDevice(p->device);
     if (e != cudaSuccess) return rp_fail(RTT_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));

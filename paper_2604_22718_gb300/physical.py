@@ -2,14 +2,24 @@
 library's calls: every arithmetic step runs in librtt (kernels, or its host
 solver for the small eigenproblem); this module only sequences them.
 
-One iteration from the TT phi (psi = C phi):
+One iteration from the TT phi of rank chi (psi = C phi):
   1. phi^alpha = O-bar_alpha phi for each operator (rtt_tt_apply: terms summed
-     two by two, rounded to chi, scaled to unit norm);
+     two by two, kept at the state rank chi_s, scaled to unit norm);
   2. each phi^alpha becomes an RTT handle (b_L = b_R = e_0, the path of phi);
   3. dual Monte Carlo over the M states (rtt_dual_step): mixed local energies
      E^{ab} and ratios r^{ab} on samples of |psi^a|^2, averaged into H~, S~;
   4. H~ c = lambda S~ c (rtt_dual_solve), lowest eigenvalue;
-  5. phi' = sum_alpha c_alpha phi^alpha rounded to chi (rtt_tt_sum_round).
+  5. phi' = sum_alpha c_alpha phi^alpha compressed back to chi
+     (rtt_tt_sum_round).
+With gram_schmidt set (Sec. 3.3, Eq. Gram-Schmid), a short pilot pass of step
+3 gives S~ on the states psi^alpha; the dual Monte Carlo of step 3 then runs on
+psi'^m = psi^m - sum_{a<m} S~_{am} psi^a (or a = 1 only), each an exact
+direct-sum RTT (rtt_create_sum), so that the overlap matrix the eigenproblem
+sees is close to diagonal; step 4 gives c' in that basis and step 5 combines
+the phi^alpha with c = T^T c' (psi' = T psi).
+Sec. 3.2 compresses only the final combination; the operator states keep the
+rank chi_s = 2 chi (the rank of a sum of two rank-chi TTs) by default, so the
+eigenproblem sees O_alpha psi rather than its rank-chi truncation.
 """
 from __future__ import annotations
 
@@ -36,10 +46,13 @@ def lift_operators(n_spins: int, path, operators):
 class PhysicalOptimizer:
     """Operators O_alpha (lifted), chi and the lattice of the states; precision
     is the sampler's (the operator states' handles), tt_precision the TT
-    roundings' arithmetic (FP64 or FP32)."""
+    roundings' arithmetic (FP64 or FP32); chi_states the operator states' rank
+    (0: min(2 chi, 16)), the tree sums inside each O-bar_alpha phi rounded to
+    min(2 chi_states, 16)."""
 
     def __init__(self, n_spins: int, path, bonds, J: float, h: float, chi: int, operators,
-                 precision: str = "fp64", device: int = 0, tt_precision: str = "fp64"):
+                 precision: str = "fp64", device: int = 0, tt_precision: str = "fp64",
+                 chi_states: int = 0):
         self.n, self.path = int(n_spins), np.ascontiguousarray(path, dtype=np.int32)
         self.L = self.path.shape[0]
         self.bonds = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
@@ -47,63 +60,121 @@ class PhysicalOptimizer:
         self.precision, self.device = precision, device
         self.ops = lift_operators(self.n, self.path, operators)
         self.M = len(self.ops)
-        self.plans = [rtt.TTPlan(self.L, self.chi, eta, ops, device, tt_precision)
-                      for _, eta, ops in self.ops]
+        self.chi_s = int(chi_states) or min(2 * self.chi, 16)
+        if not self.chi <= self.chi_s <= 16:
+            raise ValueError("chi_states must be in [chi, 16]")
+        self.plans = [rtt.TTPlan(self.L, self.chi_s, eta, ops, device, tt_precision,
+                                 chi_tree=min(2 * self.chi_s, 16)) for _, eta, ops in self.ops]
         self.comb = rtt.TTPlan(self.L, self.chi, np.ones(self.M),
-                               np.zeros((self.M, self.L), dtype=np.uint8), device, tt_precision)
+                               np.zeros((self.M, self.L), dtype=np.uint8), device, tt_precision,
+                               chi_tree=self.chi_s)
 
     def close(self):
         for p in self.plans:
             p.close()
         self.comb.close()
 
-    def handle(self, cores: torch.Tensor, seed: int):
-        """An RTT handle of psi = C phi for padded cores (device or host)."""
+    def instance(self, cores: torch.Tensor):
+        """The RTT description of psi = C phi for padded cores [L][2][c][c]
+        (device or host): b_L = b_R = e_0 on the path of phi."""
         from .inputs import RTTInstance
-        e0 = np.zeros(self.chi)
+        e0 = np.zeros(int(cores.shape[2]))
         e0[0] = 1.0
-        inst = RTTInstance(n_spins=self.n, path=self.path, tensors=cores.detach().cpu().numpy(),
+        return RTTInstance(n_spins=self.n, path=self.path, tensors=cores.detach().cpu().numpy(),
                            b_left=e0, b_right=e0.copy(), bonds=self.bonds, J=self.J, h=self.h)
-        return rtt.RTT(inst, self.precision, device=self.device, seed=seed)
+
+    def handle(self, cores: torch.Tensor, seed: int):
+        """An RTT handle of psi = C phi for padded cores [L][2][c][c] (device or host)."""
+        return rtt.RTT(self.instance(cores), self.precision, device=self.device, seed=seed)
 
     def operator_states(self, phi: torch.Tensor):
-        """phi^alpha (device padded cores, unit norm) and log ||O-bar_alpha phi||."""
+        """phi^alpha (device padded cores of rank chi_s, unit norm) and
+        log ||O-bar_alpha phi||."""
         phis, logn = [], torch.empty(self.M, dtype=torch.float64, device=phi.device)
+        shape = (self.L, 2, self.chi_s, self.chi_s)
         for a, plan in enumerate(self.plans):
-            out = torch.empty_like(phi)
+            out = torch.empty(shape, dtype=torch.float64, device=phi.device)
             plan.apply(phi, out, logn[a:a + 1])
             phis.append(out)
         return phis, logn
 
-    def step(self, phi: torch.Tensor, spins0, chains: int, sweeps: int, burn: int, seed: int):
-        """One iteration.  spins0: host uint8 [chains][N] starting configurations
-        (the same for every state).  Returns a dict with the new cores 'phi',
-        'lambda' (eigenvalues), 'c', 'Ht', 'St' and their standard errors."""
-        phis, logn = self.operator_states(phi)
-        hs = [self.handle(p, seed + 101 * a) for a, p in enumerate(phis)]
-        M, B = self.M, chains
-        sp = [torch.from_numpy(np.ascontiguousarray(spins0)).to(phi.device) for _ in range(M)]
+    def _dual(self, hs, spins0, sweeps: int, burn: int, device, sweep0: int = 0):
+        """Dual Monte Carlo over the handles: burn-in sweeps, then one dual step
+        per sweep (the sweeps numbered from sweep0 for the random streams);
+        H~, S~ and their standard errors."""
+        M = len(hs)
+        B = int(np.asarray(spins0).shape[0])
+        sp = [torch.from_numpy(np.ascontiguousarray(spins0)).to(device) for _ in range(M)]
         st = [h.log_amplitudes(x)[2] for h, x in zip(hs, sp)]
         for h, x, s in zip(hs, sp, st):
-            h.mcmc_sweep(x, s, 0, burn)
-        e = torch.empty((sweeps, M, M, B), dtype=torch.float64, device=phi.device)
+            h.mcmc_sweep(x, s, sweep0, burn)
+        e = torch.empty((sweeps, M, M, B), dtype=torch.float64, device=device)
         r = torch.empty_like(e)
         for t in range(sweeps):
-            rtt.dual_step(hs, sp, st, burn + t, e[t], r[t])
+            rtt.dual_step(hs, sp, st, sweep0 + burn + t, e[t], r[t])
         Ht, St, Hse, Sse = (np.zeros((M, M)) for _ in range(4))
         for a in range(M):
             for b in range(M):
                 so = hs[a].observables(e[:, a, b, :].contiguous())
                 sr = hs[a].observables(r[:, a, b, :].contiguous())
                 Ht[a, b], Hse[a, b], St[a, b], Sse[a, b] = so["mean"], so["se"], sr["mean"], sr["se"]
-        eig, c = rtt.dual_solve(Ht, St)
-        new = torch.empty_like(phi)
+        return Ht, St, Hse, Sse
+
+    @staticmethod
+    def gram_schmidt_matrix(St, first_only: bool):
+        """T of psi' = T psi for Eq. Gram-Schmid: row m holds 1 at m and
+        -<psi^m / psi^a>_{P^a} = -S~_{am} at every a < m (a = 0 only when
+        first_only)."""
+        St = np.asarray(St, dtype=np.float64)
+        M = St.shape[0]
+        T = np.eye(M)
+        for m in range(1, M):
+            for a in range(1 if first_only else m):
+                T[m, a] = -St[a, m]
+        return T
+
+    def step(self, phi: torch.Tensor, spins0, chains: int, sweeps: int, burn: int, seed: int,
+             gram_schmidt: str = "", pilot_sweeps: int = 0):
+        """One iteration.  spins0: host uint8 [chains][N] starting configurations
+        (the same for every state).  gram_schmidt: "" (none), "first" or "all"
+        (Eq. Gram-Schmid against psi^1 only, or against every earlier state),
+        its S~ from a pilot pass of pilot_sweeps (0: max(sweeps // 5, 10))
+        sweeps.  Returns a dict with the new cores 'phi', 'lambda'
+        (eigenvalues), 'c' (on the phi^alpha), 'Ht', 'St' and their standard
+        errors (in the basis the dual Monte Carlo ran on), 'T' (that basis:
+        psi' = T psi; the identity without Gram-Schmidt)."""
+        if gram_schmidt not in ("", "first", "all"):
+            raise ValueError("gram_schmidt must be '', 'first' or 'all'")
+        phis, logn = self.operator_states(phi)
+        hs = [self.handle(p, seed + 101 * a) for a, p in enumerate(phis)]
+        M = self.M
+        T = np.eye(M)
+        pilot = None
+        if gram_schmidt and M > 1:
+            ps = int(pilot_sweeps) or max(sweeps // 5, 10)
+            pilot = self._dual(hs, spins0, ps, burn, phi.device)
+            T = self.gram_schmidt_matrix(pilot[1], gram_schmidt == "first")
+            insts = [self.instance(p) for p in phis]
+            for m in range(1, M):
+                used = [a for a in range(M) if T[m, a] != 0.0]
+                gs = rtt.RTT.from_sum([insts[a] for a in used], T[m, used], self.precision,
+                                      device=self.device, seed=seed + 101 * m + 7)
+                hs[m].close()
+                hs[m] = gs
+        Ht, St, Hse, Sse = self._dual(hs, spins0, sweeps, burn, phi.device,
+                                      0 if pilot is None else burn + ps)
+        eig, cp = rtt.dual_solve(Ht, St)
+        c = T.T @ cp
+        new = torch.empty((self.L, 2, self.chi, self.chi), dtype=torch.float64, device=phi.device)
         ln = torch.empty(1, dtype=torch.float64, device=phi.device)
         self.comb.sum_round(phis, c, new, ln)
         for h in hs:
             h.close()
-        return {"phi": new, "lambda": eig, "c": c, "Ht": Ht, "St": St, "Ht_se": Hse, "St_se": Sse,
-                "phis": phis, "log_norms": logn.cpu().numpy()}
+        out = {"phi": new, "lambda": eig, "c": c, "Ht": Ht, "St": St, "Ht_se": Hse, "St_se": Sse,
+               "T": T, "phis": phis, "log_norms": logn.cpu().numpy()}
+        if pilot is not None:
+            out["pilot_St"] = pilot[1]
+        return out
 
     def energy(self, phi: torch.Tensor, chains: int, sweeps: int, burn: int, seed: int):
         """Sampled energy of psi = C phi: observables of E_loc (mean, se, v_score, ...)."""

@@ -108,8 +108,8 @@ def lib():
         L.rtt_tt_plan_destroy.argtypes = [P]
         L.rtt_tt_power.argtypes = [P, P, ctypes.c_double, I32, P, P]
         L.rtt_tt_round_sum.argtypes = [P, P, P, ctypes.c_double, P, P, ctypes.c_double, P, P, P]
-        L.rtt_tt_apply.argtypes = [P, P, P, P, P]
-        L.rtt_tt_sum_round.argtypes = [P, I32, P, P, P, P, P]
+        L.rtt_tt_apply.argtypes = [P, P, I32, P, P, P]
+        L.rtt_tt_sum_round.argtypes = [P, I32, P, I32, P, P, P, P]
         for name in ("rtt_replica_lift", "rtt_tt_plan_create", "rtt_tt_plan_destroy",
                      "rtt_tt_power", "rtt_tt_round_sum", "rtt_tt_apply", "rtt_tt_sum_round"):
             getattr(L, name).restype = ctypes.c_int
@@ -650,25 +650,29 @@ class TTPlan:
 
     def apply(self, phi: torch.Tensor, out: torch.Tensor, log_norm: torch.Tensor = None,
               stream=None):
-        """out <- round(H-bar phi) / norm for the plan's operator (rtt_tt_apply)."""
-        self._cores(phi, "phi")
+        """out <- round(H-bar phi) / norm for the plan's operator (rtt_tt_apply);
+        phi may have a smaller rank (padded cores [L][2][c][c]) than the plan's."""
+        c = int(phi.shape[2]) if phi.dim() == 4 else 0
+        _dev_check(phi, torch.float64, (self.length, 2, c, c), "phi")
         self._cores(out, "out")
         if log_norm is not None:
             _dev_check(log_norm, torch.float64, (1,), "log_norm")
-        _check(lib().rtt_tt_apply(self._p, _ptr(phi), _ptr(out), _ptr(log_norm), _stream(stream)),
+        _check(lib().rtt_tt_apply(self._p, _ptr(phi), c, _ptr(out), _ptr(log_norm), _stream(stream)),
                "rtt_tt_apply")
 
     def sum_round(self, tts, coef, out: torch.Tensor, log_norm: torch.Tensor = None, stream=None):
         """out <- round(sum_m coef[m] tts[m]) / norm (rtt_tt_sum_round)."""
+        c = int(tts[0].shape[2]) if tts and tts[0].dim() == 4 else 0
         for m, t in enumerate(tts):
-            self._cores(t, f"tts[{m}]")
+            _dev_check(t, torch.float64, (self.length, 2, c, c), f"tts[{m}]")
         self._cores(out, "out")
         if log_norm is not None:
             _dev_check(log_norm, torch.float64, (1,), "log_norm")
         n = len(tts)
+        c_in = c
         ptrs = (ctypes.c_void_p * n)(*[t.data_ptr() for t in tts])
-        c = np.ascontiguousarray(coef, dtype=np.float64)
-        if c.shape != (n,):
+        cf = np.ascontiguousarray(coef, dtype=np.float64)
+        if cf.shape != (n,):
             raise ValueError("coef must have one entry per TT")
-        _check(lib().rtt_tt_sum_round(self._p, n, ptrs, c.ctypes.data, _ptr(out), _ptr(log_norm),
-                                      _stream(stream)), "rtt_tt_sum_round")
+        _check(lib().rtt_tt_sum_round(self._p, n, ptrs, c_in, cf.ctypes.data, _ptr(out),
+                                      _ptr(log_norm), _stream(stream)), "rtt_tt_sum_round")

@@ -44,8 +44,10 @@ def test_operator_states_match_oracle(chi):
     phi0 = inputs.replica_start(40 + chi, 12, chi)
     phis, logn = opt.operator_states(_dev(phi0))
     torch.cuda.synchronize()
+    assert opt.chi_s == 2 * chi
     for a, (_, eta, ops) in enumerate(opt.ops):
-        ref, nrm = rp.apply_operator(rp.unpadded(phi0), eta, ops, chi)
+        assert tuple(phis[a].shape) == (12, 2, 2 * chi, 2 * chi)
+        ref, nrm = rp.apply_operator(rp.unpadded(phi0), eta, ops, 2 * chi, chi_tree=4 * chi)
         got = rp.unpadded(phis[a].cpu().numpy())
         x, y = rp.tt_dense(got), rp.tt_dense(ref)
         assert np.abs(x - y).max() <= 1e-9 * np.abs(y).max()
@@ -75,6 +77,48 @@ def test_sum_round_matches_oracle_combine():
 
 
 @pytest.mark.gpu
+def test_sum_round_and_apply_across_ranks():
+    """Inputs of another rank than the plan's chi: rank-4 TTs summed with the
+    tree at rank 4 and compressed to 2 (the physical-space combination), and a
+    rank-2 TT put through a rank-4 plan (the operator states); a rank above
+    max(chi, chi_tree) is rejected."""
+    rtt = pytest.importorskip("paper_2604_22718_gb300.rtt")
+    L = 24
+    phis = [inputs.replica_start(90 + m, L, 4) for m in range(3)]
+    c = np.array([1.0, -0.5, 0.75])
+    plan = rtt.TTPlan(L, 2, np.ones(3), np.zeros((3, L), dtype=np.uint8), chi_tree=4)
+    out = torch.empty((L, 2, 2, 2), dtype=torch.float64, device="cuda")
+    ln = torch.empty(1, dtype=torch.float64, device="cuda")
+    plan.sum_round([_dev(p) for p in phis], c, out, ln)
+    torch.cuda.synchronize()
+    ref, nrm = rp.combine([rp.unpadded(p) for p in phis], c, 2, chi_tree=4)
+    idx = np.random.default_rng(2).integers(0, 2, size=(512, L))
+    x, y = rp.tt_eval(rp.unpadded(out.cpu().numpy()), idx), rp.tt_eval(ref, idx)
+    assert np.abs(x - y).max() <= 1e-9 * np.abs(y).max()
+    assert float(ln.item()) == pytest.approx(np.log(nrm), rel=1e-10)
+    with pytest.raises(rtt.RTTError, match="chi_in"):
+        plan.sum_round([_dev(inputs.replica_start(95, L, 8))] * 2, np.ones(2), out)
+
+    terms = inputs.replica_terms(LX, LY, ORDER, [("H", 0.7, "H"), ("V", -1.1, "V")], 2.0)
+    path = _path()
+    eta, ops = rp.lift(terms, path, LX * LY)
+    up = rtt.TTPlan(12, 4, eta, ops, chi_tree=8)
+    phi2 = inputs.replica_start(96, 12, 2)
+    o4 = torch.empty((12, 2, 4, 4), dtype=torch.float64, device="cuda")
+    ln4 = torch.empty(1, dtype=torch.float64, device="cuda")
+    up.apply(_dev(phi2), o4, ln4)
+    torch.cuda.synchronize()
+    ref, nrm = rp.apply_operator(rp.unpadded(phi2), eta, ops, 4, chi_tree=8)
+    x, y = rp.tt_dense(rp.unpadded(o4.cpu().numpy())), rp.tt_dense(ref)
+    assert np.abs(x - y).max() <= 1e-9 * np.abs(y).max()
+    assert float(ln4.item()) == pytest.approx(np.log(nrm), rel=1e-10)
+    with pytest.raises(rtt.RTTError, match="chi_phi"):
+        up.apply(_dev(inputs.replica_start(97, 12, 16)), o4)
+    plan.close()
+    up.close()
+
+
+@pytest.mark.gpu
 def test_physical_step_against_exact_enumeration():
     """One iteration on 3x2 (four sites per spin pair, N = 6): sampled H~, S~
     within 6 standard errors (plus 1e-9) of their enumeration over the GPU's own
@@ -87,7 +131,7 @@ def test_physical_step_against_exact_enumeration():
     res = opt.step(_dev(phi0), spins0, chains=4096, sweeps=200, burn=20, seed=31)
     torch.cuda.synchronize()
     path = _path()
-    e0v = np.zeros(2)
+    e0v = np.zeros(opt.chi_s)
     e0v[0] = 1.0
     states = [inputs.RTTInstance(n_spins=6, path=path.astype(np.int32), tensors=p.cpu().numpy(),
                                  b_left=e0v, b_right=e0v.copy(), bonds=inputs.open_bonds(LX, LY),
@@ -106,6 +150,56 @@ def test_physical_step_against_exact_enumeration():
     H = _dense_tfim(6, inputs.open_bonds(LX, LY), 1.0, 3.0)
     psi1 = rp.constrained_amplitudes(rp.unpadded(phi0), path, 6)
     assert np.linalg.eigvalsh(H)[0] - 1e-9 <= w[0].real <= psi1 @ H @ psi1 / (psi1 @ psi1) + 1e-9
+    opt.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("mode", ["first", "all"])
+def test_gram_schmidt_step_against_exact_enumeration(mode):
+    """The iteration with Eq. Gram-Schmid: T from the pilot S~ (1 on the
+    diagonal, -S~_am below it, column 0 only for 'first'); the sampled H~, S~
+    of the direct-sum states psi' = T psi within 6 standard errors of their
+    enumeration; the S~ entries against psi^1 close to zero; lambda_0 the
+    eigenvalue of the untransformed problem; c = T^T c' on the phi^alpha."""
+    opt = _opt(2)
+    phi0 = inputs.replica_start(77, 12, 2)
+    res = opt.step(_dev(phi0), inputs.initial_spins(5, 4096, 6), chains=4096, sweeps=200, burn=20,
+                   seed=31, gram_schmidt=mode)
+    torch.cuda.synchronize()
+    T = res["T"]
+    M = T.shape[0]
+    for m in range(M):
+        for a in range(M):
+            want = 1.0 if a == m else (-res["pilot_St"][a, m] if a < m and (mode == "all" or a == 0)
+                                       else 0.0)
+            assert T[m, a] == want
+    path = _path()
+    e0v = np.zeros(opt.chi_s)
+    e0v[0] = 1.0
+    raw = [inputs.RTTInstance(n_spins=6, path=path.astype(np.int32), tensors=p.cpu().numpy(),
+                              b_left=e0v, b_right=e0v.copy(), bonds=inputs.open_bonds(LX, LY),
+                              J=1.0, h=3.0) for p in res["phis"]]
+    gs = [raw[0]] + [dual.direct_sum(raw, T[m]) for m in range(1, M)]
+    Ht, St = dual.exact_tilde_matrices(gs)
+    assert np.all(np.abs(res["Ht"] - Ht) <= 6 * res["Ht_se"] + 1e-9), (res["Ht"], Ht, res["Ht_se"])
+    assert np.all(np.abs(res["St"] - St) <= 6 * res["St_se"] + 1e-9), (res["St"], St, res["St_se"])
+    # against psi^1 only: orthogonal to it up to the pilot's noise (the 'all'
+    # form projects on the original states, which brings psi^1 back in)
+    Ht_raw, St_raw = dual.exact_tilde_matrices(raw)
+    if mode == "first":
+        for m in range(1, M):
+            assert abs(St[0, m]) <= 0.2 * abs(St_raw[0, m]) + 15 * res["St_se"][0, m]
+    w_raw, _ = dual.solve(Ht_raw, St_raw)
+    w, _ = dual.solve(Ht, St)
+    assert w[0].real == pytest.approx(w_raw[0].real, rel=1e-9)
+    _, cp = dual.solve(res["Ht"], res["St"])
+    np.testing.assert_allclose(res["c"], T.T @ cp, rtol=1e-6, atol=1e-9)
+    ref, _ = rp.combine([rp.unpadded(p.cpu().numpy()) for p in res["phis"]], res["c"], 2)
+    x, y = rp.tt_dense(rp.unpadded(res["phi"].cpu().numpy())), rp.tt_dense(ref)
+    assert np.abs(x - y).max() <= 1e-9 * np.abs(y).max()
+    with pytest.raises(ValueError):
+        opt.step(_dev(phi0), inputs.initial_spins(5, 64, 6), chains=64, sweeps=2, burn=1, seed=1,
+                 gram_schmidt="second")
     opt.close()
 
 
