@@ -925,7 +925,8 @@ def run_physical(args):
         obs = opt.energy(phi, B, 200, 50, 22770 + t)
         rows.append({"lambda0_per_site": float(res["lambda"][0].real) / N,
                      "E_per_site": obs["mean"] / N, "se_per_site": obs["se"] / N,
-                     "v_score": obs["v_score"], "c": [float(x) for x in res["c"]], "s": dt})
+                     "v_score": obs["v_score"], "c": [float(x) for x in res["c"]], "s": dt,
+                     "phases_s": {k: round(v, 4) for k, v in res["timing"].items()}})
     clk = clocks.stop()
     value = K / total
     M = len(ops)

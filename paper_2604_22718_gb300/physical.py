@@ -23,10 +23,29 @@ eigenproblem sees O_alpha psi rather than its rank-chi truncation.
 """
 from __future__ import annotations
 
+import time
+
 import numpy as np
 import torch
 
 from . import rtt
+
+
+class _PhaseClock:
+    """Host wall time of each phase of an iteration, the device synchronized
+    at every mark (the phases are sequential anyway: each one's results go
+    through the host)."""
+
+    def __init__(self):
+        torch.cuda.synchronize()
+        self.t = time.perf_counter()
+        self.phases = {}
+
+    def mark(self, name):
+        torch.cuda.synchronize()
+        now = time.perf_counter()
+        self.phases[name] = now - self.t
+        self.t = now
 
 
 def lift_operators(n_spins: int, path, operators):
@@ -145,14 +164,18 @@ class PhysicalOptimizer:
         psi' = T psi; the identity without Gram-Schmidt)."""
         if gram_schmidt not in ("", "first", "all"):
             raise ValueError("gram_schmidt must be '', 'first' or 'all'")
+        clock = _PhaseClock()
         phis, logn = self.operator_states(phi)
+        clock.mark("operator_states")
         hs = [self.handle(p, seed + 101 * a) for a, p in enumerate(phis)]
+        clock.mark("handles")
         M = self.M
         T = np.eye(M)
         pilot = None
         if gram_schmidt and M > 1:
             ps = int(pilot_sweeps) or max(sweeps // 5, 10)
             pilot = self._dual(hs, spins0, ps, burn, phi.device)
+            clock.mark("pilot")
             T = self.gram_schmidt_matrix(pilot[1], gram_schmidt == "first")
             insts = [self.instance(p) for p in phis]
             for m in range(1, M):
@@ -161,17 +184,20 @@ class PhysicalOptimizer:
                                       device=self.device, seed=seed + 101 * m + 7)
                 hs[m].close()
                 hs[m] = gs
+            clock.mark("gram_schmidt_handles")
         Ht, St, Hse, Sse = self._dual(hs, spins0, sweeps, burn, phi.device,
                                       0 if pilot is None else burn + ps)
+        clock.mark("dual_monte_carlo")
         eig, cp = rtt.dual_solve(Ht, St)
         c = T.T @ cp
         new = torch.empty((self.L, 2, self.chi, self.chi), dtype=torch.float64, device=phi.device)
         ln = torch.empty(1, dtype=torch.float64, device=phi.device)
         self.comb.sum_round(phis, c, new, ln)
+        clock.mark("solve_and_combine")
         for h in hs:
             h.close()
         out = {"phi": new, "lambda": eig, "c": c, "Ht": Ht, "St": St, "Ht_se": Hse, "St_se": Sse,
-               "T": T, "phis": phis, "log_norms": logn.cpu().numpy()}
+               "T": T, "phis": phis, "log_norms": logn.cpu().numpy(), "timing": clock.phases}
         if pilot is not None:
             out["pilot_St"] = pilot[1]
         return out
