@@ -68,3 +68,23 @@ def test_dual_entry_points_reject_null_arguments(rtt):
     assert lib.rtt_mixed_local_energy(None, None, None, 4, None, None, None) == 1
     out = ctypes.c_void_p()
     assert lib.rtt_create_sum(None, 2, None, ctypes.byref(out)) == 1
+
+
+@pytest.mark.parametrize("first_only", [True, False])
+def test_gram_schmidt_basis_matches_oracle_and_keeps_the_pencil(rtt, first_only):
+    """The physical step's Gram-Schmidt basis T (Eq. Gram-Schmid) equals the
+    oracle's; the eigenvalues of the pencil in that basis, (T H T^T, T S T^T)
+    on the symmetric matrices H = Z H~, S = Z S~, are those of the original,
+    and c = T^T c' maps its lowest eigenvector back."""
+    from paper_2604_22718_gb300.physical import PhysicalOptimizer
+    Ht, St = dual.exact_tilde_matrices(_states(4))
+    T = PhysicalOptimizer.gram_schmidt_matrix(St, first_only)
+    np.testing.assert_array_equal(T, dual.gram_schmidt(St, first_only=first_only))
+    # Z_a from S~ (S_ab = Z_a S~_ab symmetric): Z_a / Z_0 = S~_0a / S~_a0
+    Z = np.array([St[0, a] / St[a, 0] for a in range(4)])
+    H, S = Z[:, None] * Ht, Z[:, None] * St
+    w, _ = rtt.dual_solve(H, S)
+    wp, cp = rtt.dual_solve(T @ H @ T.T, T @ S @ T.T)
+    np.testing.assert_allclose(wp.real, w.real, rtol=1e-9, atol=1e-12)
+    c = T.T @ cp
+    np.testing.assert_allclose(H @ c, wp[0].real * (S @ c), atol=1e-9 * np.abs(H @ c).max())
