@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--chains", type=int, default=0, help="override the workload's chain count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sweeps", type=int, default=0,
+                    help="physical-space workloads: dual Monte Carlo sweeps per state (default 100)")
     ap.add_argument("--gram-schmidt", default="first", choices=["none", "first", "all"],
                     help="physical-space workloads: the basis of the dual Monte Carlo")
     return ap.parse_args()
@@ -876,9 +878,9 @@ def run_replica(args):
 def run_physical(args):
     """Physical-space optimization (Sec. 3.2; Sec. 4, Table 1) on 6x6 or 10x10:
     from the replica-space result (H-bar_HV, 30 or 60 steps from phi^(0) = 1),
-    iterations with
-    the operators {1, O_X, O_ZZ,HV, O_ZZ,DD'}: operator states, dual Monte Carlo
-    (4096 chains per state), the generalized eigenproblem and the combined TT.
+    iterations with the operators {1, O_X, O_ZZ,HV, O_ZZ,DD'}: operator states,
+    dual Monte Carlo (4096 chains x 100 sweeps per state unless --chains /
+    --sweeps say otherwise), the generalized eigenproblem and the combined TT.
     One step = one iteration; the sampled energy of each result (not timed) is
     reported beside lambda_0."""
     import torch
@@ -902,11 +904,12 @@ def run_physical(args):
     plan.power(phi, tau, start_steps)
     opt = PhysicalOptimizer(N, path, inputs.open_bonds(lx, ly), 1.0, h, chi, ops, precision=prec,
                             tt_precision=prec)
-    B, S, burn = args.chains or 4096, 100, 20
+    B, S, burn = args.chains or 4096, args.sweeps or 100, 20
+    BE = 4096           # chains of the (untimed) energy of each result
     gs = "" if args.gram_schmidt == "none" else args.gram_schmidt
     pilot = max(S // 5, 10) if gs else 0
     spins0 = inputs.initial_spins(22741, B, N)
-    e_start = opt.energy(phi, B, 200, 50, 22742)
+    e_start = opt.energy(phi, BE, 200, 50, 22742)
     K, W = args.steps, args.warmup
     for t in range(W):
         opt.step(phi.clone(), spins0, B, S, burn, 22750 + t, gram_schmidt=gs)
@@ -922,7 +925,7 @@ def run_physical(args):
         dt = time.perf_counter() - t0
         total += dt
         phi = res["phi"]
-        obs = opt.energy(phi, B, 200, 50, 22770 + t)
+        obs = opt.energy(phi, BE, 200, 50, 22770 + t)
         rows.append({"lambda0_per_site": float(res["lambda"][0].real) / N,
                      "E_per_site": obs["mean"] / N, "se_per_site": obs["se"] / N,
                      "v_score": obs["v_score"], "c": [float(x) for x in res["c"]], "s": dt,

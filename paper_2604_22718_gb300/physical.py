@@ -84,6 +84,7 @@ class PhysicalOptimizer:
             raise ValueError("chi_states must be in [chi, 16]")
         self.plans = [rtt.TTPlan(self.L, self.chi_s, eta, ops, device, tt_precision,
                                  chi_tree=min(2 * self.chi_s, 16)) for _, eta, ops in self.ops]
+        self._streams = []
         self.comb = rtt.TTPlan(self.L, self.chi, np.ones(self.M),
                                np.zeros((self.M, self.L), dtype=np.uint8), device, tt_precision,
                                chi_tree=self.chi_s)
@@ -111,10 +112,19 @@ class PhysicalOptimizer:
         log ||O-bar_alpha phi||."""
         phis, logn = [], torch.empty(self.M, dtype=torch.float64, device=phi.device)
         shape = (self.L, 2, self.chi_s, self.chi_s)
+        # the operators are independent (own plans, node buffers and scratch):
+        # each tree runs on its own stream, a few warps per level each
+        cur = torch.cuda.current_stream(phi.device)
+        if len(self._streams) < self.M:
+            self._streams = [torch.cuda.Stream(phi.device) for _ in range(self.M)]
         for a, plan in enumerate(self.plans):
             out = torch.empty(shape, dtype=torch.float64, device=phi.device)
-            plan.apply(phi, out, logn[a:a + 1])
+            st = self._streams[a]
+            st.wait_stream(cur)
+            plan.apply(phi, out, logn[a:a + 1], stream=st)
             phis.append(out)
+        for a in range(self.M):
+            cur.wait_stream(self._streams[a])
         return phis, logn
 
     def _dual(self, hs, spins0, sweeps: int, burn: int, device, sweep0: int = 0):
