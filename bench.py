@@ -954,27 +954,43 @@ def run_physical(args):
         T = res["T"]
         main = [insts[0]] + [odual.direct_sum([insts[a] for a in range(M) if T[m, a] != 0.0],
                                               T[m][T[m] != 0.0]) for m in range(1, M)]
-        orcs = [orc.Oracle(i) for i in main]
         nb = 64
         cores = os.cpu_count() or 1
         sp = inputs.initial_spins(22743, nb, N)
-        t1 = time.perf_counter()
-        for a in range(M):
-            x = sp.copy()
-            mant, ex = orcs[a].init_chains(x)
-            orcs[a].mcmc(22744, x, mant, ex, 0, 1, record=False, threads=cores)
-            for b in range(M):
-                odual.mixed_local_energies(orcs[a], orcs[b], x, threads=cores)
-        t_mc = (time.perf_counter() - t1) * (B * (S + burn)) / nb
-        if pilot:       # the pilot pass on the states psi^alpha, timed at the main pass's rate
-            t_mc *= 1.0 + (pilot + burn) / (S + burn)
+
+        def unit(states, pairs, swept):
+            """Oracle seconds for one sweep of each state in swept and the mixed
+            energies of the (a, b) pairs, on nb chains."""
+            oc = [orc.Oracle(i) for i in states]
+            xs = [sp.copy() for _ in oc]
+            t_sw = t_mx = 0.0
+            for a in swept:
+                mant, ex = oc[a].init_chains(xs[a])
+                t = time.perf_counter()
+                oc[a].mcmc(22744, xs[a], mant, ex, 0, 1, record=False, threads=cores)
+                t_sw += time.perf_counter() - t
+            for a, b in pairs:
+                t = time.perf_counter()
+                odual.mixed_local_energies(oc[a], oc[b], xs[a], threads=cores)
+                t_mx += time.perf_counter() - t
+            return t_sw, t_mx
+
+        all_pairs = [(a, b) for a in range(M) for b in range(M)]
+        t_sw, t_mx = unit(main, all_pairs, range(M))
+        t_mc = ((S + burn) * t_sw + S * t_mx) * B / nb
+        if gs:              # the pilot on the raw states: psi^1 alone for "first"
+            p_sw, p_mx = (unit(insts, [(0, b) for b in range(1, M)], [0]) if gs == "first"
+                          else unit(insts, all_pairs, range(M)))
+            t_mc += ((pilot + burn) * p_sw + pilot * p_mx) * B / nb
         cpu_it = t_tt * 2 + t_mc
         cpu = {"value": 1.0 / cpu_it, "unit": "iterations/s", "cores": cores, "kind": "oracle",
                "sample": f"operator TTs timed in full ({t_tt:.1f} s, counted twice for the "
-                         f"combination), dual Monte Carlo timed on {nb} chains x 1 sweep with "
-                         f"{M}x{M} mixed energies and scaled to {B} chains x {S + burn} sweeps "
-                         + (f"plus the {pilot + burn}-sweep pilot " if pilot else "")
-                         + f"(FP64 oracle, {cores} threads)"}
+                         f"combination), dual Monte Carlo timed on {nb} chains x 1 sweep and "
+                         f"{M}x{M} mixed energies of the states it runs on, scaled to {B} chains x "
+                         f"{S + burn} sweeps with {S} measured"
+                         + (f", plus the pilot ({pilot + burn} sweeps, {pilot} measured)" if pilot
+                            else "")
+                         + f" (FP64 oracle, {cores} threads)"}
     line = {
         "metric": "physical-space optimization iterations/s (operator TTs, dual Monte Carlo, "
                   "eigenproblem, combined TT)",

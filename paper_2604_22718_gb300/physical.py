@@ -11,8 +11,9 @@ One iteration from the TT phi of rank chi (psi = C phi):
   4. H~ c = lambda S~ c (rtt_dual_solve), lowest eigenvalue;
   5. phi' = sum_alpha c_alpha phi^alpha compressed back to chi
      (rtt_tt_sum_round).
-With gram_schmidt set (Sec. 3.3, Eq. Gram-Schmid), a short pilot pass of step
-3 gives S~ on the states psi^alpha; the dual Monte Carlo of step 3 then runs on
+With gram_schmidt set (Sec. 3.3, Eq. Gram-Schmid), a short pilot pass gives S~
+on the states psi^alpha (against psi^1 only: chains of psi^1 alone and their
+ratios to the others; otherwise a pilot of step 3); step 3 then runs on
 psi'^m = psi^m - sum_{a<m} S~_{am} psi^a (or a = 1 only), each an exact
 direct-sum RTT (rtt_create_sum), so that the overlap matrix the eigenproblem
 sees is close to diagonal; step 4 gives c' in that basis and step 5 combines
@@ -149,6 +150,27 @@ class PhysicalOptimizer:
                 Ht[a, b], Hse[a, b], St[a, b], Sse[a, b] = so["mean"], so["se"], sr["mean"], sr["se"]
         return Ht, St, Hse, Sse
 
+    def _pilot_first(self, hs, spins0, sweeps: int, burn: int, device):
+        """S~_{0m} = <psi^m / psi^1>_{P^1} (the only overlaps the Gram-Schmidt
+        against psi^1 needs) from chains of psi^1 alone: burn-in, then per sweep
+        the ratios psi^m / psi^1 at its configurations.  Row 0 of S~; the other
+        rows are NaN."""
+        M = len(hs)
+        h0 = hs[0]
+        sp = torch.from_numpy(np.ascontiguousarray(spins0)).to(device)
+        st = h0.log_amplitudes(sp)[2]
+        h0.mcmc_sweep(sp, st, 0, burn)
+        r = torch.empty((M, sweeps, sp.shape[0]), dtype=torch.float64, device=device)
+        for t in range(sweeps):
+            h0.mcmc_sweep(sp, st, burn + t, 1)
+            for m in range(1, M):
+                r[m, t] = h0.mixed_local_energy(hs[m], sp)[1]
+        St = np.full((M, M), np.nan)
+        St[0, 0] = 1.0
+        for m in range(1, M):
+            St[0, m] = h0.observables(r[m])["mean"]
+        return St
+
     @staticmethod
     def gram_schmidt_matrix(St, first_only: bool):
         """T of psi' = T psi for Eq. Gram-Schmid: row m holds 1 at m and
@@ -171,7 +193,8 @@ class PhysicalOptimizer:
         sweeps.  Returns a dict with the new cores 'phi', 'lambda'
         (eigenvalues), 'c' (on the phi^alpha), 'Ht', 'St' and their standard
         errors (in the basis the dual Monte Carlo ran on), 'T' (that basis:
-        psi' = T psi; the identity without Gram-Schmidt)."""
+        psi' = T psi; the identity without Gram-Schmidt) and, with
+        Gram-Schmidt, 'pilot_St' (only row 0 for "first")."""
         if gram_schmidt not in ("", "first", "all"):
             raise ValueError("gram_schmidt must be '', 'first' or 'all'")
         clock = _PhaseClock()
@@ -184,9 +207,13 @@ class PhysicalOptimizer:
         pilot = None
         if gram_schmidt and M > 1:
             ps = int(pilot_sweeps) or max(sweeps // 5, 10)
-            pilot = self._dual(hs, spins0, ps, burn, phi.device)
+            if gram_schmidt == "first":
+                pilot_St = self._pilot_first(hs, spins0, ps, burn, phi.device)
+            else:
+                pilot_St = self._dual(hs, spins0, ps, burn, phi.device)[1]
+            pilot = pilot_St
             clock.mark("pilot")
-            T = self.gram_schmidt_matrix(pilot[1], gram_schmidt == "first")
+            T = self.gram_schmidt_matrix(pilot_St, gram_schmidt == "first")
             insts = [self.instance(p) for p in phis]
             for m in range(1, M):
                 used = [a for a in range(M) if T[m, a] != 0.0]
@@ -209,7 +236,7 @@ class PhysicalOptimizer:
         out = {"phi": new, "lambda": eig, "c": c, "Ht": Ht, "St": St, "Ht_se": Hse, "St_se": Sse,
                "T": T, "phis": phis, "log_norms": logn.cpu().numpy(), "timing": clock.phases}
         if pilot is not None:
-            out["pilot_St"] = pilot[1]
+            out["pilot_St"] = pilot
         return out
 
     def energy(self, phi: torch.Tensor, chains: int, sweeps: int, burn: int, seed: int):
