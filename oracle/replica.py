@@ -295,7 +295,10 @@ def normalised(tt):
 def apply_operator(phi, eta, ops, chi, chi_tree=None):
     """phi^alpha = O-bar_alpha phi (Sec. 3.2: psi^alpha = O_alpha psi built with
     O-bar_alpha as in the replica-space optimization), rounded to chi and scaled
-    to unit replica-space norm.  Returns (phi^alpha, norm before scaling)."""
+    to unit replica-space norm.  Returns (phi^alpha, norm before scaling).  The
+    physical-space step keeps the states at twice the rank of phi (Sec. 3.2
+    compresses only the final combination) and calls this with chi = 2 chi_phi,
+    chi_tree = 4 chi_phi."""
     return normalised(tree_round([apply_string(phi, ops[k], eta[k]) for k in range(len(eta))], chi,
                                  chi_tree))
 
