@@ -110,3 +110,47 @@ def test_optimal_combination_energy_is_lambda_and_never_above_the_start():
     psi1 = rp.constrained_amplitudes(phis[0], path, N)
     assert lam <= psi1 @ H @ psi1 / (psi1 @ psi1) + 1e-10
     assert lam >= np.linalg.eigvalsh(H)[0] - 1e-9
+
+
+def test_states_at_twice_the_rank_give_table1_pattern():
+    """The reading of Sec. 3.2 the physical step takes (operator states kept at
+    rank 2 chi, only the combination compressed to chi), on 3x3 with the
+    Sec. 4 path and operators, exact H~ and S~: the step gains an order of
+    magnitude over the start, and only with O_ZZ,DD' among the operators; the
+    compression then costs little, as Table 1 and Sec. 4.3 find.  With the
+    states themselves compressed to chi the gain is lost."""
+    lx = ly = 3
+    N = lx * ly
+    order = ("V", "H", "D", "Dp")
+    path = inputs.path_sum([inputs.ordering(o, lx, ly) for o in order])
+    H = _dense_tfim(N, inputs.open_bonds(lx, ly), 1.0, 3.0)
+    e0 = np.linalg.eigvalsh(H)[0]
+
+    def err(tt):
+        p = rp.constrained_amplitudes(tt, path, N)
+        return (p @ H @ p / (p @ p) - e0) / abs(e0)
+
+    eta, ops = rp.lift(inputs.hbar_terms("HV", lx, ly, 3.0, orderings=order), path, N)
+    phi, _ = rp.power(rp.tt_ones(len(path)), eta, ops, 0.1, 2, 20)
+    start = err(phi)
+    operators = [
+        [],
+        inputs.replica_terms(lx, ly, order, [], 1.0),
+        inputs.replica_terms(lx, ly, order, [("H", 1.0, "H"), ("V", 1.0, "V")], 0.0),
+        inputs.replica_terms(lx, ly, order, [("D", 1.0, "D"), ("Dp", 1.0, "Dp")], 0.0),
+    ]
+
+    def step(ops_list, rank):
+        phis = [rp.normalised(phi)[0] if not t else rp.apply_operator(phi, *rp.lift(t, path, N), rank)[0]
+                for t in ops_list]
+        P = np.stack([rp.constrained_amplitudes(p, path, N) for p in phis], axis=1)
+        Z = np.sum(P * P, axis=0)
+        w, c = dual.solve((P.T @ H @ P) / Z[:, None], (P.T @ P) / Z[:, None])
+        return (w.real[0] - e0) / abs(e0), err(rp.combine(phis, c, 2)[0])
+
+    lam4, new4 = step(operators, 4)
+    assert new4 < 0.15 * start and new4 < 1.5 * lam4
+    _, new2 = step(operators, 2)
+    assert new2 > 0.5 * start
+    _, nodd4 = step(operators[:3], 4)
+    assert nodd4 > 0.5 * start
