@@ -128,6 +128,14 @@ class PhysicalOptimizer:
             cur.wait_stream(self._streams[a])
         return phis, logn
 
+    def combine(self, phis, coef):
+        """phi' = sum_alpha coef[alpha] phi^alpha compressed to chi and scaled to
+        unit norm (Eq. lin_comb; rtt_tt_sum_round), phis of rank chi_s."""
+        new = torch.empty((self.L, 2, self.chi, self.chi), dtype=torch.float64,
+                          device=phis[0].device)
+        self.comb.sum_round(phis, coef, new)
+        return new
+
     def _dual(self, hs, spins0, sweeps: int, burn: int, device, sweep0: int = 0):
         """Dual Monte Carlo over the handles: burn-in sweeps, then one dual step
         per sweep (the sweeps numbered from sweep0 for the random streams);
@@ -153,8 +161,8 @@ class PhysicalOptimizer:
     def _pilot_first(self, hs, spins0, sweeps: int, burn: int, device):
         """S~_{0m} = <psi^m / psi^1>_{P^1} (the only overlaps the Gram-Schmidt
         against psi^1 needs) from chains of psi^1 alone: burn-in, then per sweep
-        the ratios psi^m / psi^1 at its configurations.  Row 0 of S~; the other
-        rows are NaN."""
+        the ratios psi^m / psi^1 at its configurations.  Row 0 of S~ and its
+        standard errors; the other rows are NaN."""
         M = len(hs)
         h0 = hs[0]
         sp = torch.from_numpy(np.ascontiguousarray(spins0)).to(device)
@@ -165,11 +173,12 @@ class PhysicalOptimizer:
             h0.mcmc_sweep(sp, st, burn + t, 1)
             for m in range(1, M):
                 r[m, t] = h0.mixed_local_energy(hs[m], sp)[1]
-        St = np.full((M, M), np.nan)
-        St[0, 0] = 1.0
+        St, Sse = np.full((M, M), np.nan), np.full((M, M), np.nan)
+        St[0, 0], Sse[0, 0] = 1.0, 0.0
         for m in range(1, M):
-            St[0, m] = h0.observables(r[m])["mean"]
-        return St
+            o = h0.observables(r[m])
+            St[0, m], Sse[0, m] = o["mean"], o["se"]
+        return St, Sse
 
     @staticmethod
     def gram_schmidt_matrix(St, first_only: bool):
@@ -194,7 +203,7 @@ class PhysicalOptimizer:
         (eigenvalues), 'c' (on the phi^alpha), 'Ht', 'St' and their standard
         errors (in the basis the dual Monte Carlo ran on), 'T' (that basis:
         psi' = T psi; the identity without Gram-Schmidt) and, with
-        Gram-Schmidt, 'pilot_St' (only row 0 for "first")."""
+        Gram-Schmidt, 'pilot_St' and 'pilot_St_se' (only row 0 for "first")."""
         if gram_schmidt not in ("", "first", "all"):
             raise ValueError("gram_schmidt must be '', 'first' or 'all'")
         clock = _PhaseClock()
@@ -208,10 +217,10 @@ class PhysicalOptimizer:
         if gram_schmidt and M > 1:
             ps = int(pilot_sweeps) or max(sweeps // 5, 10)
             if gram_schmidt == "first":
-                pilot_St = self._pilot_first(hs, spins0, ps, burn, phi.device)
+                pilot_St, pilot_se = self._pilot_first(hs, spins0, ps, burn, phi.device)
             else:
-                pilot_St = self._dual(hs, spins0, ps, burn, phi.device)[1]
-            pilot = pilot_St
+                _, pilot_St, _, pilot_se = self._dual(hs, spins0, ps, burn, phi.device)
+            pilot = (pilot_St, pilot_se)
             clock.mark("pilot")
             T = self.gram_schmidt_matrix(pilot_St, gram_schmidt == "first")
             insts = [self.instance(p) for p in phis]
@@ -227,16 +236,14 @@ class PhysicalOptimizer:
         clock.mark("dual_monte_carlo")
         eig, cp = rtt.dual_solve(Ht, St)
         c = T.T @ cp
-        new = torch.empty((self.L, 2, self.chi, self.chi), dtype=torch.float64, device=phi.device)
-        ln = torch.empty(1, dtype=torch.float64, device=phi.device)
-        self.comb.sum_round(phis, c, new, ln)
+        new = self.combine(phis, c)
         clock.mark("solve_and_combine")
         for h in hs:
             h.close()
         out = {"phi": new, "lambda": eig, "c": c, "Ht": Ht, "St": St, "Ht_se": Hse, "St_se": Sse,
                "T": T, "phis": phis, "log_norms": logn.cpu().numpy(), "timing": clock.phases}
         if pilot is not None:
-            out["pilot_St"] = pilot
+            out["pilot_St"], out["pilot_St_se"] = pilot
         return out
 
     def energy(self, phi: torch.Tensor, chains: int, sweeps: int, burn: int, seed: int):

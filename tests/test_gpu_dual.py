@@ -204,10 +204,10 @@ def test_gram_schmidt_states_on_gpu():
             r_tr[t] = r
         sr = base.observables(r_tr)
         assert abs(sr["mean"]) <= 4.5 * sr["se"], sr
-        spins = sp[:64].cpu().numpy()
+        spins = inputs.initial_spins(92 + k, 64, 9)       # seeded, the same on both sides
         e_o, r_o = dual.mixed_local_energies(orc.Oracle(states[0]),
                                              orc.Oracle(dual.direct_sum(states, T_gs[k + 1])), spins)
-        e, r = base.mixed_local_energy(mn, sp[:64].contiguous())
+        e, r = base.mixed_local_energy(mn, torch.from_numpy(spins).cuda())
         assert np.array_equal(e.cpu().numpy(), e_o) and np.array_equal(r.cpu().numpy(), r_o)
     base.close()
     for mn in news:

@@ -45,7 +45,12 @@ def test_operator_states_match_oracle(chi):
     phis, logn = opt.operator_states(_dev(phi0))
     torch.cuda.synchronize()
     assert opt.chi_s == 2 * chi
-    for a, (_, eta, ops) in enumerate(opt.ops):
+    path = _path()
+    for a, (_, terms) in enumerate(_operators()):
+        if terms:
+            eta, ops = rp.lift(terms, path, LX * LY)
+        else:
+            eta, ops = np.ones(1), np.zeros((1, path.shape[0]), dtype=np.uint8)
         assert tuple(phis[a].shape) == (12, 2, 2 * chi, 2 * chi)
         ref, nrm = rp.apply_operator(rp.unpadded(phi0), eta, ops, 2 * chi, chi_tree=4 * chi)
         got = rp.unpadded(phis[a].cpu().numpy())
@@ -118,85 +123,97 @@ def test_sum_round_and_apply_across_ranks():
     up.close()
 
 
+def _oracle_states(phi0, chi_s):
+    """The operator states by the oracle alone, from the seeded start: its own
+    lifting and apply_operator at rank chi_s (tree rank 2 chi_s), as RTT
+    descriptions with b_L = b_R = e_0."""
+    path = _path()
+    e0v = np.zeros(chi_s)
+    e0v[0] = 1.0
+    out = []
+    for _, terms in _operators():
+        if terms:
+            eta, ops = rp.lift(terms, path, LX * LY)
+        else:
+            eta, ops = np.ones(1), np.zeros((1, path.shape[0]), dtype=np.uint8)
+        phi, _ = rp.apply_operator(rp.unpadded(phi0), eta, ops, chi_s, chi_tree=2 * chi_s)
+        out.append(inputs.RTTInstance(n_spins=LX * LY, path=path.astype(np.int32),
+                                      tensors=rp.padded(phi, chi_s), b_left=e0v, b_right=e0v.copy(),
+                                      bonds=inputs.open_bonds(LX, LY), J=1.0, h=3.0))
+    return out
+
+
 @pytest.mark.gpu
 def test_physical_step_against_exact_enumeration():
     """One iteration on 3x2 (four sites per spin pair, N = 6): sampled H~, S~
-    within 6 standard errors (plus 1e-9) of their enumeration over the GPU's own
-    operator states; the combination's TT equals the oracle's combination with
-    the same coefficients; lambda_0 lies between the ground-state energy and
-    the starting energy."""
+    within 6 standard errors (plus 1e-9) of their enumeration over the oracle's
+    own operator states (built from the same seeded start); lambda_0 close to
+    the exact one, which lies between the ground-state energy and the starting
+    energy; the optimizer's combination of its states with fixed coefficients
+    equal to the oracle's combination of its states; the step's TT that
+    combination taken with the step's own c."""
     opt = _opt(2)
     phi0 = inputs.replica_start(77, 12, 2)
     spins0 = inputs.initial_spins(5, 4096, 6)
     res = opt.step(_dev(phi0), spins0, chains=4096, sweeps=200, burn=20, seed=31)
     torch.cuda.synchronize()
-    path = _path()
-    e0v = np.zeros(opt.chi_s)
-    e0v[0] = 1.0
-    states = [inputs.RTTInstance(n_spins=6, path=path.astype(np.int32), tensors=p.cpu().numpy(),
-                                 b_left=e0v, b_right=e0v.copy(), bonds=inputs.open_bonds(LX, LY),
-                                 J=1.0, h=3.0) for p in res["phis"]]
+    states = _oracle_states(phi0, opt.chi_s)
     Ht, St = dual.exact_tilde_matrices(states)
     assert np.all(np.abs(res["Ht"] - Ht) <= 6 * res["Ht_se"] + 1e-9), (res["Ht"], Ht, res["Ht_se"])
     assert np.all(np.abs(res["St"] - St) <= 6 * res["St_se"] + 1e-9), (res["St"], St, res["St_se"])
-    ref, _ = rp.combine([rp.unpadded(p.cpu().numpy()) for p in res["phis"]], res["c"], 2)
-    got = rp.unpadded(res["phi"].cpu().numpy())
-    x, y = rp.tt_dense(got), rp.tt_dense(ref)
-    assert np.abs(x - y).max() <= 1e-9 * np.abs(y).max()
     w, _ = dual.solve(Ht, St)
     lam = res["lambda"][0].real
     assert lam == pytest.approx(w[0].real, abs=0.02 * abs(w[0].real))
     # exact bounds: ground state <= lambda_0 (exact) <= energy of the start (identity included)
     H = _dense_tfim(6, inputs.open_bonds(LX, LY), 1.0, 3.0)
+    path = _path()
     psi1 = rp.constrained_amplitudes(rp.unpadded(phi0), path, 6)
     assert np.linalg.eigvalsh(H)[0] - 1e-9 <= w[0].real <= psi1 @ H @ psi1 / (psi1 @ psi1) + 1e-9
+    # the combination: fixed coefficients on both sides
+    c = np.array([1.0, -0.35, 0.6])
+    got = opt.combine(res["phis"], c)
+    ref, _ = rp.combine([rp.unpadded(st.tensors) for st in states], c, 2)
+    x, y = rp.tt_dense(rp.unpadded(got.cpu().numpy())), rp.tt_dense(ref)
+    assert np.abs(x - y).max() <= 1e-9 * np.abs(y).max()
+    again = opt.combine(res["phis"], res["c"])
+    assert torch.equal(again, res["phi"])
     opt.close()
 
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("mode", ["first", "all"])
 def test_gram_schmidt_step_against_exact_enumeration(mode):
-    """The iteration with Eq. Gram-Schmid: T from the pilot S~ (1 on the
-    diagonal, -S~_am below it, column 0 only for 'first'); the sampled H~, S~
-    of the direct-sum states psi' = T psi within 6 standard errors of their
-    enumeration; the S~ entries against psi^1 close to zero; lambda_0 the
-    eigenvalue of the untransformed problem; c = T^T c' on the phi^alpha."""
+    """The iteration with Eq. Gram-Schmid: the pilot's S~ entries within 6
+    standard errors of their enumeration over the oracle's states; T built from
+    them (1 on the diagonal, -S~_am below it, column 0 only for 'first');
+    lambda_0 from the Gram-Schmidt basis close to the exact one of the original
+    basis (the basis does not change the eigenvalues); for 'first' the main
+    pass's S~ against psi^1 near zero; c = T^T c' with c' from the library's
+    solver."""
+    rtt = pytest.importorskip("paper_2604_22718_gb300.rtt")
     opt = _opt(2)
     phi0 = inputs.replica_start(77, 12, 2)
     res = opt.step(_dev(phi0), inputs.initial_spins(5, 4096, 6), chains=4096, sweeps=200, burn=20,
                    seed=31, gram_schmidt=mode)
     torch.cuda.synchronize()
-    T = res["T"]
+    T, P, Pse = res["T"], res["pilot_St"], res["pilot_St_se"]
     M = T.shape[0]
+    Ht_x, St_x = dual.exact_tilde_matrices(_oracle_states(phi0, opt.chi_s))
+    rows = [0] if mode == "first" else range(M)
+    for a in rows:
+        for m in range(M):
+            assert abs(P[a, m] - St_x[a, m]) <= 6 * Pse[a, m] + 1e-9, (a, m, P, St_x, Pse)
     for m in range(M):
         for a in range(M):
-            want = 1.0 if a == m else (-res["pilot_St"][a, m] if a < m and (mode == "all" or a == 0)
-                                       else 0.0)
+            want = 1.0 if a == m else (-P[a, m] if a < m and (mode == "all" or a == 0) else 0.0)
             assert T[m, a] == want
-    path = _path()
-    e0v = np.zeros(opt.chi_s)
-    e0v[0] = 1.0
-    raw = [inputs.RTTInstance(n_spins=6, path=path.astype(np.int32), tensors=p.cpu().numpy(),
-                              b_left=e0v, b_right=e0v.copy(), bonds=inputs.open_bonds(LX, LY),
-                              J=1.0, h=3.0) for p in res["phis"]]
-    gs = [raw[0]] + [dual.direct_sum(raw, T[m]) for m in range(1, M)]
-    Ht, St = dual.exact_tilde_matrices(gs)
-    assert np.all(np.abs(res["Ht"] - Ht) <= 6 * res["Ht_se"] + 1e-9), (res["Ht"], Ht, res["Ht_se"])
-    assert np.all(np.abs(res["St"] - St) <= 6 * res["St_se"] + 1e-9), (res["St"], St, res["St_se"])
-    # against psi^1 only: orthogonal to it up to the pilot's noise (the 'all'
-    # form projects on the original states, which brings psi^1 back in)
-    Ht_raw, St_raw = dual.exact_tilde_matrices(raw)
+    w_x, _ = dual.solve(Ht_x, St_x)
+    assert res["lambda"][0].real == pytest.approx(w_x[0].real, abs=0.02 * abs(w_x[0].real))
     if mode == "first":
         for m in range(1, M):
-            assert abs(St[0, m]) <= 0.2 * abs(St_raw[0, m]) + 15 * res["St_se"][0, m]
-    w_raw, _ = dual.solve(Ht_raw, St_raw)
-    w, _ = dual.solve(Ht, St)
-    assert w[0].real == pytest.approx(w_raw[0].real, rel=1e-9)
-    _, cp = dual.solve(res["Ht"], res["St"])
-    np.testing.assert_allclose(res["c"], T.T @ cp, rtol=1e-6, atol=1e-9)
-    ref, _ = rp.combine([rp.unpadded(p.cpu().numpy()) for p in res["phis"]], res["c"], 2)
-    x, y = rp.tt_dense(rp.unpadded(res["phi"].cpu().numpy())), rp.tt_dense(ref)
-    assert np.abs(x - y).max() <= 1e-9 * np.abs(y).max()
+            assert abs(res["St"][0, m]) <= 0.2 * abs(St_x[0, m]) + 15 * res["St_se"][0, m]
+    _, cp = rtt.dual_solve(res["Ht"], res["St"])
+    np.testing.assert_array_equal(res["c"], T.T @ cp)
     with pytest.raises(ValueError):
         opt.step(_dev(phi0), inputs.initial_spins(5, 64, 6), chains=64, sweeps=2, burn=1, seed=1,
                  gram_schmidt="second")
