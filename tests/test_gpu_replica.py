@@ -167,7 +167,9 @@ def _power_case(lx, ly, order, kind, chi, steps, start, tau=0.1, h=3.0, seed=0, 
     rtt = _rtt()
     path = inputs.path_sum([inputs.ordering(o, lx, ly) for o in order])
     L = path.shape[0]
-    eta, ops = rtt.replica_lift(lx * ly, path, inputs.hbar_terms(kind, lx, ly, h, orderings=order))
+    terms = inputs.hbar_terms(kind, lx, ly, h, orderings=order)
+    eta, ops = rtt.replica_lift(lx * ly, path, terms)
+    eta_o, ops_o = rp.lift(terms, path, lx * ly)          # the oracle lifts on its own
     phi0 = inputs.replica_ones(L, chi) if start == "ones" else inputs.replica_start(seed, L, chi)
     ct = min(rp.tree_rank(chi, chi_tree), 16)
     plan = rtt.TTPlan(L, chi, eta, ops, chi_tree=ct)
@@ -175,7 +177,7 @@ def _power_case(lx, ly, order, kind, chi, steps, start, tau=0.1, h=3.0, seed=0, 
     ln = torch.empty(steps, dtype=torch.float64, device="cuda")
     plan.power(phi, tau, steps, log_norm=ln)
     torch.cuda.synchronize()
-    ref, ref_ln = rp.power(rp.unpadded(phi0), eta, ops, tau, chi, steps, chi_tree=ct)
+    ref, ref_ln = rp.power(rp.unpadded(phi0), eta_o, ops_o, tau, chi, steps, chi_tree=ct)
     return path, _host_tt(phi), ref, ln.cpu().numpy(), ref_ln
 
 
@@ -237,11 +239,12 @@ def test_power_single_term_and_two_terms():
 @pytest.mark.gpu
 def test_power_result_feeds_the_sampler():
     """phi^(P) as an RTT handle (b_L = b_R = e_0, same path): the sampler's
-    amplitudes are C phi^(P) of the same cores."""
+    amplitudes are C phi^(P) of the same cores (the oracle's phi^(P), so that
+    the expected amplitudes come from the oracle alone)."""
     rtt = _rtt()
     lx, ly, chi = 3, 3, 2
     order = ("V", "H", "D", "Dp")
-    path, got, _, _, _ = _power_case(lx, ly, order, "HV", chi, 6, "random", seed=8)
+    path, _, got, _, _ = _power_case(lx, ly, order, "HV", chi, 6, "random", seed=8)
     e0 = np.zeros(chi)
     e0[0] = 1.0
     inst = inputs.RTTInstance(n_spins=9, path=path.astype(np.int32), tensors=rp.padded(got, chi),
@@ -388,14 +391,16 @@ def test_power_fp32_amplitudes_within_derived_tolerance():
     order = ("V", "H", "D", "Dp")
     path = inputs.path_sum([inputs.ordering(o, lx, ly) for o in order])
     L = path.shape[0]
-    eta, ops = rtt.replica_lift(9, path, inputs.hbar_terms("HV", lx, ly, 3.0, orderings=order))
+    terms = inputs.hbar_terms("HV", lx, ly, 3.0, orderings=order)
+    eta, ops = rtt.replica_lift(9, path, terms)
+    eta_o, ops_o = rp.lift(terms, path, 9)
     phi0 = inputs.replica_start(91, L, 2)
     plan = rtt.TTPlan(L, 2, eta, ops, precision="fp32")
     phi = _dev(phi0)
     steps = 1
     plan.power(phi, 0.1, steps)
     torch.cuda.synchronize()
-    ref, gap = _oracle_power_with_gaps(rp.unpadded(phi0), eta, ops, 0.1, 2, steps)
+    ref, gap = _oracle_power_with_gaps(rp.unpadded(phi0), eta_o, ops_o, 0.1, 2, steps)
     tol = 16 * 2.0 ** -24 * 2 * L * steps * 6 / gap
     _compare(_host_tt(phi), ref, L, tol, np.random.default_rng(12))
 
@@ -409,13 +414,15 @@ def test_power_fp32_symmetric_start_energy_is_valid():
     order = ("V", "H", "D", "Dp")
     path = inputs.path_sum([inputs.ordering(o, lx, ly) for o in order])
     L = path.shape[0]
-    eta, ops = rtt.replica_lift(9, path, inputs.hbar_terms("HV", lx, ly, 3.0, orderings=order))
+    terms = inputs.hbar_terms("HV", lx, ly, 3.0, orderings=order)
+    eta, ops = rtt.replica_lift(9, path, terms)
+    eta_o, ops_o = rp.lift(terms, path, 9)
     phi0 = inputs.replica_ones(L, 2)
     plan = rtt.TTPlan(L, 2, eta, ops, precision="fp32")
     phi = _dev(phi0)
     plan.power(phi, 0.1, 6)
     torch.cuda.synchronize()
-    ref, _ = rp.power(rp.unpadded(phi0), eta, ops, 0.1, 2, 6)
+    ref, _ = rp.power(rp.unpadded(phi0), eta_o, ops_o, 0.1, 2, 6)
     H = _dense_tfim(9, inputs.open_bonds(lx, ly), 1.0, 3.0)
     e0 = np.linalg.eigvalsh(H)[0]
 
