@@ -939,9 +939,13 @@ def run_physical(args):
         from oracle import replica as orp
         from oracle import oracle as orc
         from oracle import dual as odual
+        # the oracle's own inputs of the same shapes: a seeded rank-chi TT, its
+        # own lifting, a Gram-Schmidt basis of the same pattern (the cost does
+        # not depend on the values)
+        tt = orp.unpadded(inputs.replica_start(22744, L, chi))
+        lifted = [orp.lift(terms, path, N) if terms
+                  else (np.ones(1), np.zeros((1, L), dtype=np.uint8)) for _, terms in ops]
         t0 = time.perf_counter()
-        tt = orp.unpadded(phi.cpu().numpy())
-        lifted = [(e, o) for _, e, o in opt.ops]
         phis = [orp.apply_operator(tt, e, o, opt.chi_s, chi_tree=min(2 * opt.chi_s, 16))[0]
                 for e, o in lifted]
         t_tt = time.perf_counter() - t0
@@ -951,7 +955,10 @@ def run_physical(args):
                                     tensors=orp.padded(p, opt.chi_s),
                                     b_left=e0v, b_right=e0v.copy(), bonds=inputs.open_bonds(lx, ly),
                                     J=1.0, h=h) for p in phis]
-        T = res["T"]
+        T = np.eye(M)
+        if gs:
+            for m in range(1, M):
+                T[m, :1 if gs == "first" else m] = -0.5
         main = [insts[0]] + [odual.direct_sum([insts[a] for a in range(M) if T[m, a] != 0.0],
                                               T[m][T[m] != 0.0]) for m in range(1, M)]
         nb = 64
@@ -984,7 +991,8 @@ def run_physical(args):
             t_mc += ((pilot + burn) * p_sw + pilot * p_mx) * B / nb
         cpu_it = t_tt * 2 + t_mc
         cpu = {"value": 1.0 / cpu_it, "unit": "iterations/s", "cores": cores, "kind": "oracle",
-               "sample": f"operator TTs timed in full ({t_tt:.1f} s, counted twice for the "
+               "sample": f"on a seeded rank-{chi} TT of the same shape: "
+                         f"operator TTs timed in full ({t_tt:.1f} s, counted twice for the "
                          f"combination), dual Monte Carlo timed on {nb} chains x 1 sweep and "
                          f"{M}x{M} mixed energies of the states it runs on, scaled to {B} chains x "
                          f"{S + burn} sweeps with {S} measured"
