@@ -88,3 +88,14 @@ def test_gram_schmidt_basis_matches_oracle_and_keeps_the_pencil(rtt, first_only)
     np.testing.assert_allclose(wp.real, w.real, rtol=1e-9, atol=1e-12)
     c = T.T @ cp
     np.testing.assert_allclose(H @ c, wp[0].real * (S @ c), atol=1e-9 * np.abs(H @ c).max())
+
+
+def test_physical_optimizer_rejects_state_ranks_outside_chi_to_16(rtt):
+    """The operator states' rank must lie in [chi, 16] (host check, before any
+    device allocation)."""
+    from paper_2604_22718_gb300.physical import PhysicalOptimizer
+    path = inputs.path_sum([inputs.ordering(o, 3, 2) for o in ("H", "V")])
+    ops = [("1", []), ("X", inputs.replica_terms(3, 2, ("H", "V"), [], 1.0))]
+    for bad in (1, 17):
+        with pytest.raises(ValueError, match="chi_states"):
+            PhysicalOptimizer(6, path, inputs.open_bonds(3, 2), 1.0, 3.0, 2, ops, chi_states=bad)
