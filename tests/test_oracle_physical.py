@@ -154,3 +154,49 @@ def test_states_at_twice_the_rank_give_table1_pattern():
     assert new2 > 0.5 * start
     _, nodd4 = step(operators[:3], 4)
     assert nodd4 > 0.5 * start
+
+
+def test_exact_gram_schmidt_states_beat_compressed_ones():
+    """The reading of Sec. 3.3 the physical step takes: the Gram-Schmidt
+    states psi'^m = psi^m - S~_1m psi^1 enter the eigenproblem exactly (as
+    direct sums) rather than compressed to chi.  On 3x3 with exact H~, S~ one
+    iteration then gains an order of magnitude; compressing the new states to
+    chi first keeps well under half of that gain."""
+    lx = ly = 3
+    N = lx * ly
+    order = ("V", "H", "D", "Dp")
+    path = inputs.path_sum([inputs.ordering(o, lx, ly) for o in order])
+    H = _dense_tfim(N, inputs.open_bonds(lx, ly), 1.0, 3.0)
+    e0 = np.linalg.eigvalsh(H)[0]
+
+    def amp(tt):
+        return rp.constrained_amplitudes(tt, path, N)
+
+    def err(p):
+        return (p @ H @ p / (p @ p) - e0) / abs(e0)
+
+    eta, ops = rp.lift(inputs.hbar_terms("HV", lx, ly, 3.0, orderings=order), path, N)
+    phi, _ = rp.power(rp.tt_ones(len(path)), eta, ops, 0.1, 2, 20)
+    terms = [[], inputs.replica_terms(lx, ly, order, [], 1.0),
+             inputs.replica_terms(lx, ly, order, [("H", 1.0, "H"), ("V", 1.0, "V")], 0.0),
+             inputs.replica_terms(lx, ly, order, [("D", 1.0, "D"), ("Dp", 1.0, "Dp")], 0.0)]
+    phis = [rp.normalised(rp.tt_round(phi, 4))[0] if not t
+            else rp.apply_operator(phi, *rp.lift(t, path, N), 4, chi_tree=8)[0] for t in terms]
+    P = np.stack([amp(p) for p in phis], axis=1)
+    Z = np.sum(P * P, axis=0)
+    St = (P.T @ P) / Z[:, None]
+    T = dual.gram_schmidt(St, first_only=True)
+    Q = P @ T.T                                      # the exact direct sums psi' = T psi
+    Zq = np.sum(Q * Q, axis=0)
+    _, cq = dual.solve((Q.T @ H @ Q) / Zq[:, None], (Q.T @ Q) / Zq[:, None])
+    exact = err(amp(rp.combine(phis, T.T @ cq, 2)[0]))
+    gs = [rp.normalised(rp.tt_round(phis[0], 2))[0]] + [
+        rp.normalised(rp.tt_round(rp.tt_sum(phis[m], rp.tt_scale(phis[0], -St[0, m])), 2))[0]
+        for m in range(1, 4)]
+    G = np.stack([amp(p) for p in gs], axis=1)
+    Zg = np.sum(G * G, axis=0)
+    _, cg = dual.solve((G.T @ H @ G) / Zg[:, None], (G.T @ G) / Zg[:, None])
+    compressed = err(amp(rp.combine(gs, cg, 2)[0]))
+    start = err(amp(phi))
+    assert exact < 0.15 * start
+    assert compressed > 0.3 * start and compressed > 3 * exact
