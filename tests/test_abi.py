@@ -108,3 +108,32 @@ def test_null_handle_is_an_argument_error(lib):
 def test_uniforms_empty_request_needs_no_gpu(lib):
     assert lib.rtt_mcmc_uniforms(1, 0, None, None, None) == 0
     assert lib.rtt_mcmc_uniforms(1, -1, None, None, None) == 1
+
+
+def test_replica_plan_calls_reject_bad_arguments_before_any_cuda_call(lib):
+    """rtt_tt_plan_create validates sizes, ranks, precision and string codes
+    before it selects a device; the plan calls reject a null plan."""
+    P = ctypes.c_void_p
+    ops = np.zeros((2, 8), dtype=np.uint8)
+    eta = np.ones(2)
+    out = P()
+
+    def create(length=8, chi=2, chi_tree=0, precision=0, n_terms=2, o=ops):
+        return lib.rtt_tt_plan_create(ctypes.c_int32(length), ctypes.c_int32(chi),
+                                      ctypes.c_int32(chi_tree), ctypes.c_int32(precision),
+                                      ctypes.c_int32(n_terms), o.ctypes.data_as(P),
+                                      eta.ctypes.data_as(P), ctypes.c_int32(0), ctypes.byref(out))
+    assert create(length=1) == 1                         # RTT_ERR_INVALID_ARG
+    assert create(n_terms=0) == 1
+    assert create(chi=17) == 6                           # RTT_ERR_UNSUPPORTED
+    assert create(precision=2) == 6                      # only FP64 and FP32
+    assert create(chi=4, chi_tree=3) == 1                # chi <= chi_tree <= 16
+    assert create(chi_tree=17) == 1
+    bad = ops.copy()
+    bad[1, 3] = 3                                        # string codes are 0, 1, 2
+    assert create(o=bad) == 1
+    assert out.value is None
+    assert lib.rtt_tt_power(None, None, 0.1, 1, None, None) == 1
+    assert lib.rtt_tt_apply(None, None, 0, None, None, None) == 1
+    assert lib.rtt_tt_sum_round(None, 1, None, 0, None, None, None, None) == 1
+    assert lib.rtt_tt_plan_destroy(None) == 0
