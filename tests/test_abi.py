@@ -137,3 +137,29 @@ def test_replica_plan_calls_reject_bad_arguments_before_any_cuda_call(lib):
     assert lib.rtt_tt_apply(None, None, 0, None, None, None) == 1
     assert lib.rtt_tt_sum_round(None, 1, None, 0, None, None, None, None) == 1
     assert lib.rtt_tt_plan_destroy(None) == 0
+
+
+def test_made_and_batch_calls_reject_bad_arguments_before_any_cuda_call(lib):
+    """The learned-proposal and batched entry points: null handles, a
+    non-permutation order and missing inputs are argument errors that
+    need no GPU; destroying a null handle is a no-op."""
+    P = ctypes.c_void_p
+    out = P()
+    order = np.array([0, 1, 1, 3], dtype=np.int32)           # not a permutation
+    w = np.zeros(1000)
+    assert lib.rtt_made_create(4, 8, order.ctypes.data, w.ctypes.data, 1, 0, ctypes.byref(out)) == 1
+    good = np.arange(4, dtype=np.int32)
+    assert lib.rtt_made_create(0, 8, good.ctypes.data, w.ctypes.data, 1, 0, ctypes.byref(out)) == 1
+    assert lib.rtt_made_create(4, 8, good.ctypes.data, None, 1, 0, ctypes.byref(out)) == 1
+    assert out.value is None
+    assert lib.rtt_made_log_prob(None, None, 4, None, None) == 1
+    assert lib.rtt_made_sample(None, 4, 0, 0, None, None, None) == 1
+    assert lib.rtt_made_train_step(None, None, 4, 1e-3, None, None) == 1
+    assert lib.rtt_made_set_inference(None, 1) == 1
+    assert lib.rtt_indep_mh(None, None, None, None, 4, 0, 0, None, None) == 1
+    assert lib.rtt_made_destroy(None) == 0
+    chains = np.array([16], dtype=np.int64)
+    assert lib.rtt_batch_create(None, 1, chains.ctypes.data, ctypes.byref(out)) == 1
+    assert lib.rtt_batch_step(None, None, None, 0, None, None, 0, None) == 1
+    assert lib.rtt_batch_layout(None, None, None, None, None) == 1
+    assert lib.rtt_batch_destroy(None) == 0
