@@ -252,6 +252,20 @@ rtt_status rtt_create_sum(const rtt_desc *descs, int32_t M, const double *coef, 
 rtt_status rtt_dual_solve(int32_t M, const double *Ht, const double *St, double *eig_re,
                           double *eig_im, double *c0);
 
+/* The stochastic Gram-Schmidt basis of Sec. 3.3 (Eq. Gram-Schmid):
+ * psi'^m = psi^m - sum_a <psi^m / psi^a>_{P^a} psi^a over a < m (a = 0 only
+ * when first_only != 0), <psi^m / psi^a>_{P^a} = S~_am.  Writes T (host
+ * [M][M] row-major) with psi' = T psi: T[m][m] = 1, T[m][a] = -S~[a][m].
+ * St: host [M][M]; 1 <= M <= 8; RTT_ERR_NUMERIC on a non-finite entry used.
+ * Host computation only. */
+rtt_status rtt_dual_gram_schmidt(int32_t M, const double *St, int32_t first_only, double *T);
+
+/* Coefficients on the original states from those on psi' = T psi:
+ * c = T^T c' (sum over m in increasing order).  T: host [M][M] row-major;
+ * c_prime, c: host [M], c must not alias c_prime; 1 <= M <= 8.  Host
+ * computation only. */
+rtt_status rtt_dual_back_transform(int32_t M, const double *T, const double *c_prime, double *c);
+
 /* The Metropolis uniforms themselves, for checking the device generator:
  * counters: device uint64 [n][3] = (chain, sweep, proposal); out: device [n]. */
 rtt_status rtt_mcmc_uniforms(uint64_t seed, int64_t n, const uint64_t *counters, double *out,

@@ -265,3 +265,35 @@ extern "C" rtt_status rtt_dual_solve(int32_t M, const double *Ht, const double *
     for (int i = 0; i < n; ++i) c0[i] = sgn * x[i];
     return RTT_OK;
 }
+
+// Eq. Gram-Schmid: row m of T holds 1 at m and -<psi^m / psi^a>_{P^a} =
+// -S~[a][m] at every a < m (a = 0 only when first_only), so psi' = T psi.
+extern "C" rtt_status rtt_dual_gram_schmidt(int32_t M, const double *St, int32_t first_only,
+                                            double *T) {
+    rtt_set_error("");
+    if (M < 1 || M > 8 || !St || !T)
+        return dual_fail(RTT_ERR_INVALID_ARG, "rtt_dual_gram_schmidt: bad arguments (1 <= M <= 8)");
+    for (int m = 0; m < M; ++m)
+        for (int a = 0; a < M; ++a) {
+            double v = a == m ? 1.0 : 0.0;
+            if (a < m && (!first_only || a == 0)) v = -St[a * M + m];
+            if (!std::isfinite(v)) return dual_fail(RTT_ERR_NUMERIC, "rtt_dual_gram_schmidt: non-finite S~");
+            T[m * M + a] = v;
+        }
+    return RTT_OK;
+}
+
+// psi' = T psi and sum_m c'_m psi'^m = sum_a c_a psi^a give c = T^T c',
+// summed over m in increasing order.
+extern "C" rtt_status rtt_dual_back_transform(int32_t M, const double *T, const double *c_prime,
+                                              double *c) {
+    rtt_set_error("");
+    if (M < 1 || M > 8 || !T || !c_prime || !c || c == c_prime)
+        return dual_fail(RTT_ERR_INVALID_ARG, "rtt_dual_back_transform: bad arguments (1 <= M <= 8)");
+    for (int a = 0; a < M; ++a) {
+        double acc = 0.0;
+        for (int m = 0; m < M; ++m) acc += T[m * M + a] * c_prime[m];
+        c[a] = acc;
+    }
+    return RTT_OK;
+}

@@ -182,16 +182,10 @@ class PhysicalOptimizer:
 
     @staticmethod
     def gram_schmidt_matrix(St, first_only: bool):
-        """T of psi' = T psi for Eq. Gram-Schmid: row m holds 1 at m and
-        -<psi^m / psi^a>_{P^a} = -S~_{am} at every a < m (a = 0 only when
-        first_only)."""
-        St = np.asarray(St, dtype=np.float64)
-        M = St.shape[0]
-        T = np.eye(M)
-        for m in range(1, M):
-            for a in range(1 if first_only else m):
-                T[m, a] = -St[a, m]
-        return T
+        """T of psi' = T psi for Eq. Gram-Schmid (rtt_dual_gram_schmidt): row m
+        holds 1 at m and -<psi^m / psi^a>_{P^a} = -S~_{am} at every a < m
+        (a = 0 only when first_only)."""
+        return rtt.dual_gram_schmidt(St, first_only)
 
     def step(self, phi: torch.Tensor, spins0, chains: int, sweeps: int, burn: int, seed: int,
              gram_schmidt: str = "", pilot_sweeps: int = 0):
@@ -235,7 +229,7 @@ class PhysicalOptimizer:
                                       0 if pilot is None else burn + ps)
         clock.mark("dual_monte_carlo")
         eig, cp = rtt.dual_solve(Ht, St)
-        c = T.T @ cp
+        c = rtt.dual_back_transform(T, cp) if pilot is not None else cp
         new = self.combine(phis, c)
         clock.mark("solve_and_combine")
         for h in hs:

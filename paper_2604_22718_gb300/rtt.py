@@ -71,6 +71,8 @@ def lib():
         L.rtt_mixed_local_energy.argtypes = [P, P, P, I64, P, P, P]
         L.rtt_create_sum.argtypes = [ctypes.POINTER(_Desc), I32, P, ctypes.POINTER(P)]
         L.rtt_dual_solve.argtypes = [I32, P, P, P, P, P]
+        L.rtt_dual_gram_schmidt.argtypes = [I32, P, I32, P]
+        L.rtt_dual_back_transform.argtypes = [I32, P, P, P]
         L.rtt_dual_step.argtypes = [P, I32, P, P, I64, I64, I64, P, P, P, P]
         L.rtt_mcmc_sweep.argtypes = [P, P, P, I64, I64, I64, I32, I32, P, P, P]
         L.rtt_observables.argtypes = [P, P, I32, I64, P, I64, ctypes.POINTER(_Stats), P]
@@ -149,6 +151,29 @@ def dual_solve(Ht, St):
     _check(lib().rtt_dual_solve(M, Ht.ctypes.data, St.ctypes.data, re.ctypes.data, im.ctypes.data,
                                 c.ctypes.data), "rtt_dual_solve")
     return re + 1j * im, c
+
+
+def dual_gram_schmidt(St, first_only: bool):
+    """rtt_dual_gram_schmidt: T with psi' = T psi (Eq. Gram-Schmid)."""
+    St = np.ascontiguousarray(St, dtype=np.float64)
+    M = St.shape[0]
+    assert St.shape == (M, M)
+    T = np.empty((M, M))
+    _check(lib().rtt_dual_gram_schmidt(M, St.ctypes.data, int(bool(first_only)), T.ctypes.data),
+           "rtt_dual_gram_schmidt")
+    return T
+
+
+def dual_back_transform(T, c_prime):
+    """rtt_dual_back_transform: c = T^T c' on the original states."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    cp = np.ascontiguousarray(c_prime, dtype=np.float64)
+    M = cp.shape[0]
+    assert T.shape == (M, M)
+    c = np.empty(M)
+    _check(lib().rtt_dual_back_transform(M, T.ctypes.data, cp.ctypes.data, c.ctypes.data),
+           "rtt_dual_back_transform")
+    return c
 
 
 def dual_step(handles, spins, states, sweep: int, e_mixed=None, ratio=None, n_accept=None,

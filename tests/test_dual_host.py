@@ -99,3 +99,29 @@ def test_physical_optimizer_rejects_state_ranks_outside_chi_to_16(rtt):
     for bad in (1, 17):
         with pytest.raises(ValueError, match="chi_states"):
             PhysicalOptimizer(6, path, inputs.open_bonds(3, 2), 1.0, 3.0, 2, ops, chi_states=bad)
+
+
+def test_gram_schmidt_and_back_transform_host_calls(rtt):
+    """rtt_dual_gram_schmidt writes the oracle's T bit for bit (only the S~
+    entries it uses must be finite: row 0 for the first-only form);
+    rtt_dual_back_transform is T^T c'; both reject bad sizes, null pointers
+    and an aliased output."""
+    Ht, St = dual.exact_tilde_matrices(_states(4))
+    for first_only in (True, False):
+        T = rtt.dual_gram_schmidt(St, first_only)
+        np.testing.assert_array_equal(T, dual.gram_schmidt(St, first_only=first_only))
+        cp = np.array([0.3, -1.1, 2.5, 0.75])
+        np.testing.assert_allclose(rtt.dual_back_transform(T, cp), T.T @ cp, rtol=1e-15, atol=1e-15)
+    row0 = np.full((4, 4), np.nan)
+    row0[0] = St[0]
+    np.testing.assert_array_equal(rtt.dual_gram_schmidt(row0, True), dual.gram_schmidt(St, True))
+    with pytest.raises(rtt.RTTError):
+        rtt.dual_gram_schmidt(row0, False)          # rows 1.. are used and not finite
+    lib = rtt.lib()
+    buf = np.zeros(81)
+    assert lib.rtt_dual_gram_schmidt(0, buf.ctypes.data, 1, buf.ctypes.data) == 1
+    assert lib.rtt_dual_gram_schmidt(9, buf.ctypes.data, 1, buf.ctypes.data) == 1
+    assert lib.rtt_dual_gram_schmidt(2, None, 1, buf.ctypes.data) == 1
+    v = np.ones(4)
+    assert lib.rtt_dual_back_transform(4, buf.ctypes.data, v.ctypes.data, v.ctypes.data) == 1
+    assert lib.rtt_dual_back_transform(4, None, v.ctypes.data, buf.ctypes.data) == 1

@@ -213,7 +213,8 @@ def test_gram_schmidt_step_against_exact_enumeration(mode):
         for m in range(1, M):
             assert abs(res["St"][0, m]) <= 0.2 * abs(St_x[0, m]) + 15 * res["St_se"][0, m]
     _, cp = rtt.dual_solve(res["Ht"], res["St"])
-    np.testing.assert_array_equal(res["c"], T.T @ cp)
+    np.testing.assert_array_equal(res["c"], rtt.dual_back_transform(T, cp))
+    np.testing.assert_allclose(res["c"], T.T @ cp, rtol=1e-13, atol=1e-13 * np.abs(cp).max())
     with pytest.raises(ValueError):
         opt.step(_dev(phi0), inputs.initial_spins(5, 64, 6), chains=64, sweeps=2, burn=1, seed=1,
                  gram_schmidt="second")
