@@ -50,10 +50,11 @@ FP64_LANES_PER_SM = 2
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: a per-workload count that runs for seconds)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="plain_6x6")
+    ap.add_argument("--workload", default="learned_16x16")
     ap.add_argument("--precision", default="fp16x3", choices=["fp32", "fp64", "bf16x3", "fp16x3"])
     ap.add_argument("--chains", type=int, default=0, help="override the workload's chain count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -62,7 +63,20 @@ def parse():
                     help="physical-space workloads: dual Monte Carlo sweeps per state (default 100)")
     ap.add_argument("--gram-schmidt", default="first", choices=["none", "first", "all"],
                     help="physical-space workloads: the basis of the dual Monte Carlo")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = DEFAULT_STEPS.get(args.workload, 20)
+    return args
+
+
+# timed steps when --steps is not given: each runs for seconds
+DEFAULT_STEPS = {"learned_16x16": 20, "plain_6x6": 1000, "vhdd_6x6": 500, "prec_10x10": 50,
+                 "tiny_fp64": 1000, "batched64": 3, "dual_6x6": 500, "physical_6x6": 3,
+                 "physical_10x10": 2}
+
+# executed tensor flops per algorithmic flop of the split-precision site
+# products: both spin slices per MMA (x2) and three hi/lo products (x3)
+EXECUTED_PER_ALG = 6.0
 
 
 def measured_peaks():
@@ -149,13 +163,10 @@ class L2Flush:
 
 
 # ---------------------------------------------------------------- DRAM traffic
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from an ncu capture
-# of the same command on this kernel build (profiles/ names the capture); None
-# where no capture of the current kernel exists.
-MEASURED_TRAFFIC = {
-    # profiles/tc_sweep_split_plain6x6_fp16x3.md: 3 847 680 B read + 66 560 B written
-    ("plain_6x6", "fp16x3", "tc_sweep", 4096): 3847680 + 66560,
-}
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of a kernel, from
+# an ncu capture of that kernel as it is built now, keyed by (workload,
+# precision, kernel, chains); a kernel with no current capture reports None.
+MEASURED_TRAFFIC = {}
 
 
 def measured_traffic(args, kernel, B):
@@ -199,25 +210,58 @@ def site_steps(N: int, R: int, kernel: str, path=None) -> int:
 
 # ---------------------------------------------------------------- reference arm (oracle)
 def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on this host's cores,
+    each step a bounded sample of the workload's step (one chain per core for
+    the learned-proposal workload, two per core otherwise)."""
+    from concurrent.futures import ThreadPoolExecutor
     from oracle import oracle as orc
     from paper_2604_22718_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]
     inst = inputs.workload(args.workload)
     o = orc.Oracle(inst)
     cores = os.cpu_count() or 1
-    # two chains per thread: the binding splits a batch across threads only when
-    # it holds at least two chains per thread, else it runs on one core
-    per_step = 2 * cores
-    spins = inputs.initial_spins(w["seed"], per_step, inst.n_spins)
+    N = inst.n_spins
+    learned = args.workload == "learned_16x16"
+    # the binding splits a batch across threads only when it holds at least two
+    # chains per thread; the learned workload's chains run one per thread here
+    per_step = cores if learned else 2 * cores
+    spins = inputs.initial_spins(w["seed"], per_step, N)
     mant, ex = o.init_chains(spins)
+    if learned:
+        from oracle import made as omade
+        H = 512
+        p = omade.masked_params(inputs.made_init_weights(w["seed"], N, H), N, H)
+        order = inst.path[:N].astype(np.int64)
+        exe = ThreadPoolExecutor(cores)
+
+        def step(t):
+            # the learned proposal, then the local sweep with its energy
+            prop, lq_new = omade.sample(p, order, per_step, w["seed"], 0, t, N)
+            lq_cur = omade.log_prob(p, spins, order)
+            la_cur = o.log_amplitudes(spins)[0]
+            la_new, _, m_new, e_new = o.log_amplitudes(prop)
+            for c in range(per_step):
+                if omade.indep_mh_decide(la_cur[c], lq_cur[c], la_new[c], lq_new[c],
+                                         omade.accept_uniform(w["seed"], c, t, N)):
+                    spins[c], mant[c], ex[c] = prop[c], m_new[c], e_new[c]
+
+            def one(c):
+                o.mcmc(w["seed"], spins[c:c + 1], mant[c:c + 1], ex[c:c + 1], t, 1,
+                       measure_every=1, chain0=c)
+            list(exe.map(one, range(per_step)))
+    else:
+        def step(t):
+            o.mcmc(w["seed"], spins, mant, ex, t, 1, measure_every=1, threads=cores)
     t_total = 0.0
     for t in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        o.mcmc(w["seed"], spins, mant, ex, t, 1, measure_every=1, threads=cores)
+        step(t)
         dt = time.perf_counter() - t0
         if t >= args.warmup:
             t_total += dt
     value = per_step * args.steps / t_total
+    what = ("1 local sweep + E_loc (C oracle, one chain per thread) and 1 learned independence "
+            "proposal (numpy FP64)" if learned else "1 sweep + E_loc")
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
@@ -225,7 +269,7 @@ def run_reference(args):
         "data": "synthetic", "impl": "reference",
         "config": {"workload": _workload_desc(args.workload, inst, per_step), "chains": per_step,
                    "sample": f"{per_step} chains per step (bounded sample of the "
-                             f"{w['chains']}-chain workload), 1 sweep + E_loc each"},
+                             f"{w['chains']}-chain workload), {what} each"},
         "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
                          "sample": f"{per_step} chains x {args.steps} steps, {cores} threads"},
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
@@ -286,18 +330,18 @@ def run_ours(args):
     dev = torch.cuda.current_device()
     from paper_2604_22718_gb300 import inputs, rtt
 
+    from paper_2604_22718_gb300 import dist as rdist
     w = inputs.WORKLOADS[args.workload]
     inst = inputs.workload(args.workload)
-    B = args.chains or w["chains"]
+    B_total = (args.chains or w["chains"]) * world
+    chain0, B = rdist.shard(B_total, rank, world)
     N = inst.n_spins
     R = inst.path.shape[0] // N
-    chain0 = rank * B
     m = rtt.RTT(inst, args.precision, seed=w["seed"])
     m.reserve(B)
-    spins = torch.from_numpy(inputs.initial_spins(w["seed"], B, N)).cuda()
-    # chains of other ranks: distinct start configurations, same generator
-    if rank:
-        spins = torch.from_numpy(inputs.initial_spins(w["seed"] + 7919 * rank, B, N)).cuda()
+    # every rank's chains are its block of one seeded start: N ranks run the
+    # chains of one GPU, chain by chain
+    spins = torch.from_numpy(inputs.initial_spins(w["seed"], B_total, N)[chain0:chain0 + B].copy()).cuda()
     _, _, state = m.log_amplitudes(spins)
     K, W = args.steps, args.warmup
     trace = torch.empty((K, B), dtype=torch.float64, device="cuda")
@@ -316,7 +360,6 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    m.profile(True)
     clocks.start()
     t_wall0 = time.perf_counter()
     for t in range(K):
@@ -328,8 +371,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    prof = m.profile_read()
+    # per-kernel times from a separate profiled pass (the event profiler stays
+    # off inside the timed region)
+    n_prof = min(K, 20)
+    sp_p, st_p = spins.clone(), state.clone()
+    torch.cuda.synchronize()
+    m.profile(True)
+    for t in range(n_prof):
+        flush()
+        m.mcmc_sweep(sp_p, st_p, 900000 + t, 1, 1, scratch_row, None, chain0=chain0)
+    torch.cuda.synchronize()
+    prof = {k: (v[0] * K / n_prof, v[1] * K / n_prof) for k, v in m.profile_read().items()}
     m.profile(False)
+    del sp_p, st_p
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
     if dist:
@@ -337,9 +391,9 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = float(tt.item())
         dist.barrier()
-    value = world * B * K / (total_ms / 1e3)
+    value = B_total * K / (total_ms / 1e3)
     stats = m.observables(trace, acc, K * N)
-    ess_per_s = world * stats["ess"] / (total_ms / 1e3)
+    ess_per_s = value / (2.0 * stats["tau_int"])
 
     # dominant kernel roofline
     peaks, peak_kind = measured_peaks()
@@ -350,16 +404,19 @@ def run_ours(args):
         flops = 2.0 * inst.chi * inst.chi * site_steps(N, R, dom, inst.path) * B
         achieved = flops / (ms / launches / 1e3) / 1e12
         if args.precision in ("bf16x3", "fp16x3"):
-            # fp16 and bf16 dense tensor rates are equal on this part
-            peak = peaks["bf16_tflops_sustained"]
-            bound, pk = "tensor", (f"bf16 dense sustained ({peak_kind}); fp16 = bf16 rate; "
-                                   f"executed = 6x algorithmic (both slices x 3 split products)")
+            # fp16 and bf16 dense tensor rates are equal on this part; the
+            # burst peak for a timed region under a second, else the sustained
+            long_region = total_ms / 1e3 > 1.0
+            peak = peaks["bf16_tflops_sustained" if long_region else "bf16_tflops"]
+            bound, pk = "tensor", (f"bf16 dense {'sustained' if long_region else 'burst'} "
+                                   f"({peak_kind}); fp16 = bf16 rate; executed = "
+                                   f"{EXECUTED_PER_ALG:g}x algorithmic")
         else:
             lanes = FP32_LANES_PER_SM if args.precision == "fp32" else FP64_LANES_PER_SM
             peak = SM_COUNT * lanes * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             bound, pk = "alu", (f"{args.precision} CUDA-core fma peak: {SM_COUNT} SMs x {lanes} "
                                 f"lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz")
-        mult = 6.0 if bound == "tensor" else 1.0
+        mult = EXECUTED_PER_ALG if bound == "tensor" else 1.0
         executed = achieved * mult
         step_flops = sum(2.0 * inst.chi * inst.chi * site_steps(N, R, k, inst.path) * B * v[0]
                          for k, v in prof.items()) / K
@@ -372,7 +429,7 @@ def run_ours(args):
                 "kernel_share": ms / sum(v[1] for v in prof.values()),
                 "step_tflops": step_tf, "step_frac": step_tf / peak,
                 "step_executed_frac": step_tf * mult / peak}
-    launches_total = sum(v[0] for v in prof.values())
+    launches_total = int(round(sum(v[0] for v in prof.values())))
 
     # end to end through host buffers
     e2e = None
@@ -403,7 +460,7 @@ def run_ours(args):
             tt = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e2e_ms = float(tt.item())
-        e2e = {"value": world * B * K / (e2e_ms / 1e3), "unit": "samples/s",
+        e2e = {"value": B_total * K / (e2e_ms / 1e3), "unit": "samples/s",
                "h2d_bytes_per_step": B * N + 16 * B,
                "d2h_bytes_per_step": 8 * B + B * N + 16 * B}
 
@@ -514,94 +571,329 @@ def run_batched(args):
     b.close()
 
 
+# launches of one rtt_indep_mh call with tensor-core (BF16) inference, from its
+# host code: log q(s): W2 to BF16, inputs, layer 1, ReLU to BF16, layer 2,
+# output layer, loss (7); sampling: init, ReLU to BF16, per position the
+# tensor-core layer and the draw, and between positions the first-layer
+# update (3N - 1 + 2); psi(s') (1); the decision (1).
+def indep_mh_launches(N: int) -> int:
+    return 7 + (3 * N + 1) + 1 + 1
+
+
 def run_learned(args):
-    """Learned-proposal form: 16x16 TFIM (N = 256, h = 3.044), R = 2 (L = 512),
-    chi = 128, 8192 chains.  A MADE 256 -> 512 -> 512 -> 256 is trained on
-    configurations of the plain local sampler (chains x thinned sweeps), then
-    plain iterations (1 sweep + E_loc) and mixed iterations (1 sweep + 1
-    independence proposal + E_loc) are timed; tau_int and ESS/s of each."""
+    """Learned-proposal form, the metric's configuration: 16x16 open TFIM
+    (N = 256, h = 3.044), R = 2 (L = 512), chi = 128, 8192 chains, FP16X3
+    site products.  A MADE 256 -> 512 -> 512 -> 256 is trained (library
+    call) on 2^20 configurations of the plain local sampler (8192 chains x 128
+    thinned sweeps); then each step is one mixed iteration of every chain: one
+    learned independence proposal (BF16 tensor-core inference) and one local
+    sweep with the local energy of the configuration entering it.
+
+    value     mixed samples/s over exactly K timed steps (CUDA events on the
+              launching stream, L2 flushed between steps outside the events,
+              no profiler)
+    ess_per_s value / (2 tau_int), tau_int (Sokal window) from a trace of
+              max(K, 128) iterations whose first K are the timed steps
+    plain     local flips only, FP16X3, same start, same protocol
+    plain_fp32 the plain FP32 sampler on the CUDA cores (2 timed steps; tau_int
+              of the FP16X3 local-flip trace, the same Markov kernel)
+    gate      FP16X3 against the FP64 oracle on 48 sampled configurations:
+              mean local energy within 1e-4 relative
+    roofline  dominant kernel from a separate profiled pass"""
     import torch
-    from paper_2604_22718_gb300 import inputs, rtt
-    torch.cuda.set_device(0)
-    w = inputs.WORKLOADS["learned_16x16"]
-    inst = inputs.workload("learned_16x16")
+    from paper_2604_22718_gb300 import inputs, rtt, dist as rdist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    tdist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    name = "learned_16x16"
+    w = inputs.WORKLOADS[name]
+    inst = inputs.workload(name)
     N = inst.n_spins
-    B = args.chains or w["chains"]
+    R = inst.path.shape[0] // N
+    B_total = (args.chains or w["chains"]) * world
+    chain0, B = rdist.shard(B_total, rank, world)
     prec = args.precision
     K, W = args.steps, args.warmup
-    n_data_sweeps = int(os.environ.get("RTT_LEARNED_DATA_SWEEPS", "128"))
+    T_tau = max(K, 128)
+    n_data_sweeps = 128
+    epochs = 20
+    stream = torch.cuda.current_stream()
     m = rtt.RTT(inst, prec, seed=w["seed"])
     m.reserve(B)
-    stream = torch.cuda.current_stream()
-    sp = torch.from_numpy(inputs.initial_spins(w["seed"], B, N)).cuda()
+    # every rank's chains are its block of one seeded start
+    sp = torch.from_numpy(inputs.initial_spins(w["seed"], B_total, N)[chain0:chain0 + B].copy()).cuda()
     _, _, st = m.log_amplitudes(sp)
     t0 = time.perf_counter()
-    m.mcmc_sweep(sp, st, 0, 16)                       # burn-in
+    m.mcmc_sweep(sp, st, 0, 16, chain0=chain0)                       # burn-in
     data = torch.empty((n_data_sweeps * B, N), dtype=torch.uint8, device="cuda")
     for r in range(n_data_sweeps):
-        m.mcmc_sweep(sp, st, 16 + r, 1)
+        m.mcmc_sweep(sp, st, 16 + r, 1, chain0=chain0)
         data[r * B:(r + 1) * B].copy_(sp)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     order = inst.path[:N].astype(np.int32)
     made = rtt.MADE(N, 512, order, inputs.made_init_weights(w["seed"], N, 512), seed=w["seed"])
     t0 = time.perf_counter()
-    epochs = int(os.environ.get("RTT_LEARNED_EPOCHS", "20"))
-    hist = made.fit(data, epochs=epochs, batch=1024, lr=1e-3)
+    hist = made.fit(data, epochs=epochs, batch=1024, lr=1e-3, seed=w["seed"])
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del data
+    sp0, st0 = sp.clone(), st.clone()
+    flush = L2Flush()
+    sweep_base = 16 + n_data_sweeps
 
-    def run(mixed, sweep0):
-        s2 = sp.clone()
-        st2 = st.clone()
-        tr = torch.empty((K, B), dtype=torch.float64, device="cuda")
-        acc = torch.zeros(B, dtype=torch.int64, device="cuda")
+    def iterate(spins, state, t, mixed, row=None, acc=None):
+        if mixed:
+            rtt.indep_mh(m, made, spins, state, t, acc, chain0=chain0)
+        m.mcmc_sweep(spins, state, t, 1, 1, row, chain0=chain0)
+
+    def run(mixed):
+        """W warm-up iterations, K timed ones (events), then untimed ones up to
+        T_tau; returns (timed ms, trace [T_tau][B], acceptances, clocks)."""
+        s2, st2 = sp0.clone(), st0.clone()
+        tr = torch.empty((T_tau, B), dtype=torch.float64, device="cuda")
         junk = torch.empty((1, B), dtype=torch.float64, device="cuda")
+        acc = torch.zeros(B, dtype=torch.int64, device="cuda")
+        base = sweep_base + (100000 if mixed else 0)
         for t in range(W):
-            m.mcmc_sweep(s2, st2, sweep0 + t, 1, 1, junk)
-            if mixed:
-                rtt.indep_mh(m, made, s2, st2, sweep0 + t)
+            iterate(s2, st2, base + t, mixed, junk)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        clocks = ClockSampler(dev)
+        torch.cuda.synchronize()
+        if tdist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        for t in range(K):
+            flush()
+            ev[t][0].record(stream)
+            iterate(s2, st2, base + W + t, mixed, tr[t:t + 1], acc)
+            ev[t][1].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        if tdist:
+            tdist.barrier()
+        ms = sum(a.elapsed_time(z) for a, z in ev)
+        for t in range(K, T_tau):
+            iterate(s2, st2, base + W + t, mixed, tr[t:t + 1], acc)
+        torch.cuda.synchronize()
+        return ms, tr, acc, clk, (s2, st2)
+
+    ms_m, tr_m, acc_m, clk, (sp_m, st_m) = run(True)
+    ms_p, tr_p, _, clk_p, _ = run(False)
+    ms_m, ms_p = _max_over_ranks(tdist, ms_m), _max_over_ranks(tdist, ms_p)
+    obs_m = m.observables(tr_m)
+    obs_p = m.observables(tr_p)
+    value = B_total * K / (ms_m / 1e3)
+    value_p = B_total * K / (ms_p / 1e3)
+    ess_m = value / (2.0 * obs_m["tau_int"])
+    ess_p = value_p / (2.0 * obs_p["tau_int"])
+
+    # profiled pass (not timed): per-kernel CUDA-event times of the handle's
+    # kernels over two mixed iterations
+    s3, st3 = sp_m.clone(), st_m.clone()
+    junk = torch.empty((1, B), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    m.profile(True)
+    n_prof = 2
+    t0 = time.perf_counter()
+    for t in range(n_prof):
+        iterate(s3, st3, 500000 + t, True, junk)
+    torch.cuda.synchronize()
+    prof = m.profile_read()
+    m.profile(False)
+    del s3, st3
+    launches_per_step = sum(v[0] for v in prof.values()) / n_prof + indep_mh_launches(N)
+    peaks, peak_kind = measured_peaks()
+    dom = max((k for k in prof if k != "eloc_reduce"), key=lambda k: prof[k][1])
+    launches, kms = prof[dom]
+    flops = 2.0 * inst.chi * inst.chi * site_steps(N, R, dom, inst.path) * B
+    achieved = flops / (kms / launches / 1e3) / 1e12
+    long_region = ms_m / 1e3 > 1.0
+    peak = peaks["bf16_tflops_sustained"] if long_region else peaks["bf16_tflops"]
+    kind_txt = "sustained" if long_region else "burst"
+    step_flops = sum(2.0 * inst.chi * inst.chi * site_steps(N, R, k, inst.path) * B * v[0]
+                     for k, v in prof.items()) / n_prof
+    step_tf = step_flops / (ms_m / K / 1e3) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": measured_traffic(args, dom, B), "kernel": dom,
+            "flops_per_launch": flops, "launch_ms": kms / launches,
+            "peak_source": f"bf16 dense {kind_txt} ({peak_kind}; timed region "
+                           f"{ms_m / 1e3:.1f} s); fp16 = bf16 rate",
+            "frac_of_burst": achieved / peaks["bf16_tflops"],
+            "executed_per_algorithmic": EXECUTED_PER_ALG,
+            "kernel_share": kms / sum(v[1] for v in prof.values()),
+            "step_tflops": step_tf, "step_frac": step_tf / peak}
+
+    # end to end through host buffers: spins and amplitudes from pinned host
+    # memory, one mixed iteration, E_loc, spins and amplitudes back, every step
+    e2e = None
+    if not args.no_e2e:
+        sp_h = sp_m.cpu().pin_memory()
+        st_h = st_m.cpu().pin_memory()
+        el_h = torch.empty((1, B), dtype=torch.float64).pin_memory()
+        sp_d, st_d = torch.empty_like(sp_m), torch.empty_like(st_m)
+        row_d = torch.empty((1, B), dtype=torch.float64, device="cuda")
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(K)]
         torch.cuda.synchronize()
         for t in range(K):
+            flush()
             ev[t][0].record(stream)
-            if mixed:
-                rtt.indep_mh(m, made, s2, st2, sweep0 + W + t, acc)
-            m.mcmc_sweep(s2, st2, sweep0 + W + t, 1, 1, tr[t:t + 1])
+            sp_d.copy_(sp_h, non_blocking=True)
+            st_d.copy_(st_h, non_blocking=True)
+            iterate(sp_d, st_d, 600000 + t, True, row_d)
+            el_h.copy_(row_d, non_blocking=True)
+            sp_h.copy_(sp_d, non_blocking=True)
+            st_h.copy_(st_d, non_blocking=True)
             ev[t][1].record(stream)
         torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(z) for a, z in ev)
-        stats = m.observables(tr)
-        return ms, stats, float(acc.sum()) / (B * K)
+        e2e_ms = _max_over_ranks(tdist, sum(a.elapsed_time(z) for a, z in ev))
+        e2e = {"value": B_total * K / (e2e_ms / 1e3), "unit": "samples/s",
+               "h2d_bytes_per_step": B * N + 16 * B,
+               "d2h_bytes_per_step": 8 * B + B * N + 16 * B}
 
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    ms_p, st_p, _ = run(False, 10000)
-    ms_m, st_m, acc_m = run(True, 20000)
-    clk = clocks.stop()
-    sps_p = B * K / (ms_p / 1e3)
-    sps_m = B * K / (ms_m / 1e3)
-    line = {
-        "metric": METRIC, "value": sps_m, "unit": "samples/s", "n_gpus": 1, "steps": K,
-        "warmup": W, "ms_per_step": ms_m / K, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": prec, "data": "synthetic",
-        "config": {"workload": _workload_desc("learned_16x16", inst, B) +
-                   "; mixed 1:1 with a learned independence proposal (MADE 256-512-512-256, FP32)",
-                   "training_configs": n_data_sweeps * B, "epochs": epochs},
-        "plain": {"samples_per_s": sps_p, "ess_per_s": st_p["ess"] / (ms_p / 1e3),
-                  "tau_int": st_p["tau_int"], "e_mean": st_p["mean"], "e_se": st_p["se"]},
-        "mixed": {"samples_per_s": sps_m, "ess_per_s": st_m["ess"] / (ms_m / 1e3),
-                  "tau_int": st_m["tau_int"], "e_mean": st_m["mean"], "e_se": st_m["se"],
-                  "indep_acceptance": acc_m},
-        "ess_speedup_mixed_vs_plain": (st_m["ess"] / ms_m) / (st_p["ess"] / ms_p),
-        "made_nll_first_last_epoch": [hist[0], hist[-1]] if hist else None,
-        "data_s": t_data, "train_s": t_train, "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
+    # the plain FP32 sampler (CUDA cores) on the same chains: 1 warm-up, 2 timed
+    m32 = rtt.RTT(inst, "fp32", seed=w["seed"])
+    m32.reserve(B)
+    s32 = sp0.clone()
+    _, _, st32 = m32.log_amplitudes(s32)
+    junk = torch.empty((1, B), dtype=torch.float64, device="cuda")
+    m32.mcmc_sweep(s32, st32, sweep_base, 1, 1, junk, chain0=chain0)
+    ev32 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(2)]
+    torch.cuda.synchronize()
+    for t in range(2):
+        flush()
+        ev32[t][0].record(stream)
+        m32.mcmc_sweep(s32, st32, sweep_base + 1 + t, 1, 1, junk, chain0=chain0)
+        ev32[t][1].record(stream)
+    torch.cuda.synchronize()
+    ms32 = _max_over_ranks(tdist, sum(a.elapsed_time(z) for a, z in ev32))
+    m32.close()
+    del s32, st32
+    value32 = B_total * 2 / (ms32 / 1e3)
+    ess32 = value32 / (2.0 * obs_p["tau_int"])
+
+    line = None
+    if rank == 0:
+        gate = precision_gate(m, inst, sp_m[:48].clone())
+        line = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": ms_m / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": _workload_desc(name, inst, B_total) +
+                       "; each step also makes one learned independence proposal per chain "
+                       "(MADE 256-512-512-256 trained on the plain sampler's configurations, "
+                       "BF16 tensor-core inference)",
+                       "chains_per_gpu": B, "precision": prec,
+                       "parallelism": f"replicas over chains x{world} (each rank trains its own "
+                                      "proposal on its own chains)",
+                       "training_configs": n_data_sweeps * B, "epochs": epochs,
+                       "l2": "flushed (256 MiB write + 256 MiB read) between timed steps, "
+                             "outside the events"},
+            "ess_per_s": ess_m, "tau_int": obs_m["tau_int"], "tau_trace_iterations": T_tau,
+            "indep_acceptance": float(acc_m.sum()) / (B * T_tau),
+            "e_mean": obs_m["mean"], "e_se": obs_m["se"], "v_score": obs_m["v_score"],
+            "plain": {"samples_per_s": value_p, "ess_per_s": ess_p, "tau_int": obs_p["tau_int"],
+                      "e_mean": obs_p["mean"], "e_se": obs_p["se"],
+                      "what": "local flips only, same precision and start"},
+            "plain_fp32": {"samples_per_s": value32, "ess_per_s": ess32, "steps": 2,
+                           "what": "the plain sampler on the FP32 CUDA cores; tau_int of the "
+                                   "local-flip trace above (same Markov kernel)"},
+            "ess_speedup_vs_plain_fp32": ess_m / ess32,
+            "ess_speedup_vs_plain_same_precision": ess_m / ess_p,
+            "gate_rel_err": gate["rel_err"], "gate_ok": gate["rel_err"] <= 1e-4,
+            "gate": gate,
+            "roofline": roof, "gpu_launches": int(round(launches_per_step * K)),
+            "kernels_per_step": {k: {"launches": v[0] / n_prof, "ms": v[1] / n_prof}
+                                 for k, v in prof.items()},
+            "made_nll_first_last_epoch": [hist[0], hist[-1]] if hist else None,
+            "data_s": t_data, "train_s": t_train, "clocks": clk, "clocks_plain": clk_p,
+            "e2e": e2e,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_learned(inst, w["seed"], made)
+        print(json.dumps(line), flush=True)
     made.close()
     m.close()
+    if tdist:
+        tdist.destroy_process_group()
+
+
+def _max_over_ranks(tdist, ms):
+    if not tdist:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def precision_gate(m, inst, spins):
+    """Metric gate (R12): the local energies of the same configurations from
+    the split-precision handle and the FP64 oracle; relative error of the mean
+    (relative to the mean, or to the mean |E_loc| when the mean is near zero)."""
+    from oracle import oracle as orc
+    e = m.local_energy(spins).cpu().numpy()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    e_o = orc.Oracle(inst).local_energies(spins.cpu().numpy(), threads=cores)
+    dt = time.perf_counter() - t0
+    scale = max(abs(float(e_o.mean())), float(np.mean(np.abs(e_o))))
+    return {"rel_err": abs(float(e.mean()) - float(e_o.mean())) / scale,
+            "configs": int(spins.shape[0]), "max_abs_err": float(np.max(np.abs(e - e_o))),
+            "e_mean": float(e.mean()), "e_mean_fp64": float(e_o.mean()), "oracle_s": dt}
+
+
+def cpu_baseline_learned(inst, seed, made_gpu):
+    """The FP64 oracle on this host's cores, one mixed iteration (one local
+    sweep with its local energy, and one learned independence proposal with the
+    trained weights) for one chain per core."""
+    from oracle import oracle as orc
+    from oracle import made as omade
+    from paper_2604_22718_gb300 import inputs
+    cores = os.cpu_count() or 1
+    o = orc.Oracle(inst)
+    N = inst.n_spins
+    n = cores
+    spins = inputs.initial_spins(seed + 5, n, N)
+    p = omade.unpack(made_gpu.params().astype(np.float64), N, made_gpu.hidden)
+    order = inst.path[:N].astype(np.int64)
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(c):
+        s = spins[c:c + 1].copy()
+        mant, ex = o.init_chains(s)
+        o.mcmc(seed, s, mant, ex, 0, 1, measure_every=1, chain0=c)
+        return s
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as exe:
+        out = list(exe.map(one, range(n)))
+    # the learned proposal: ancestral sampling, log q of both states, psi(s'),
+    # the decision
+    cur = np.concatenate(out)
+    prop, lq_new = omade.sample(p, order, n, seed, 0, 0, N)
+    lq_cur = omade.log_prob(p, cur, order)
+    la_new = o.log_amplitudes(prop)[0]
+    la_cur = o.log_amplitudes(cur)[0]
+    for c in range(n):
+        omade.indep_mh_decide(la_cur[c], lq_cur[c], la_new[c], lq_new[c],
+                              omade.accept_uniform(seed, c, 0, N))
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} chains x 1 mixed iteration (local sweep + E_loc in the C oracle, "
+                      f"one chain per thread; learned proposal in numpy FP64), {dt:.1f} s wall"}
 
 
 def run_dual(args):

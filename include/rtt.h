@@ -312,7 +312,9 @@ rtt_status rtt_batch_layout(rtt_batch b, int64_t *total_chains, int64_t *total_s
 /* chain states (psi of the current spins) of every instance, Eq. RTT */
 rtt_status rtt_batch_init(rtt_batch b, const uint8_t *spins, rtt_chain_state *state, void *stream);
 /* one iteration (sweep index `sweep`) of every chain; e_loc [sum B_i] receives
- * E_loc after the sweep; n_accept [sum B_i] (or NULL) accumulates acceptances.
+ * E_loc of the configuration the iteration starts from (measured before its
+ * sweep, as rtt_mcmc_sweep measures); n_accept [sum B_i] (or NULL)
+ * accumulates acceptances.
  * use_graph != 0 launches through a CUDA graph built on first use (its kernel
  * node is updated per call). */
 rtt_status rtt_batch_step(rtt_batch b, uint8_t *spins, rtt_chain_state *state, int64_t sweep,
@@ -358,6 +360,23 @@ rtt_status rtt_made_gradients(rtt_made m, const uint8_t *spins, int64_t B, float
 /* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean NLL of a batch */
 rtt_status rtt_made_train_step(rtt_made m, const uint8_t *spins, int64_t B, float lr, double *nll,
                                void *stream);
+/* Minibatch training: `epochs` passes over data (device uint8 [n][N]); each
+ * pass visits the rows in a keyed random order (rtt_made_permutation with
+ * shuffle_seed and the pass number) in n / batch minibatches of `batch`
+ * rows (the last n mod batch rows of each order are skipped), one Adam step
+ * per minibatch as rtt_made_train_step.  The rows are gathered on the device;
+ * data must stay valid until the stream reaches the end of the call's work.
+ * nll_per_epoch: host double [epochs] (mean over the pass's minibatches of
+ * their mean NLL) or NULL; when given, the call waits for the stream before it
+ * returns.  Errors: RTT_ERR_INVALID_ARG for n < 1, batch outside [1, n],
+ * epochs < 0 or lr <= 0 (nothing launched); RTT_ERR_OOM / RTT_ERR_CUDA. */
+rtt_status rtt_made_fit(rtt_made m, const uint8_t *data, int64_t n, int32_t epochs, int32_t batch,
+                        float lr, uint64_t shuffle_seed, double *nll_per_epoch, void *stream);
+/* The training loop's row order for one pass: host_out[i] (host int64 [n]) is
+ * the data row visited i-th.  A permutation of [0, n): a four-round Feistel
+ * network over [0, 4^h), 4^h >= n, keyed by (seed, epoch), restricted to
+ * [0, n) by cycle walking.  Host only; RTT_ERR_INVALID_ARG for n < 1. */
+rtt_status rtt_made_permutation(int64_t n, uint64_t seed, int64_t epoch, int64_t *host_out);
 /* Inference arithmetic of the H x H layer (sampling, log q, the independence
  * step): bf16 = 1 runs it on the tensor cores -- ReLU(first layer) and the
  * masked W2 rounded to BF16, FP32 accumulation, the same kernel for sampling

@@ -51,6 +51,10 @@ struct rtt_made_s {
     uint8_t *d_prop = nullptr;          // proposals [cap][N]
     rtt_chain_state *d_pstate = nullptr;
     double *d_plogq = nullptr;
+    uint8_t *d_batch = nullptr;         // gathered minibatch [batch_cap][N] (training loop)
+    int64_t batch_cap = 0;
+    double *d_fit = nullptr;            // per-epoch NLL sums + one batch NLL [fit_cap + 1]
+    int32_t fit_cap = 0;
     size_t off_W1 = 0, off_b1 = 0, off_W2 = 0, off_b2 = 0, off_W3 = 0, off_b3 = 0;
     // BF16 tensor-core inference of the H x H layer (when H allows it)
     int infer_bf16 = 0;
@@ -517,6 +521,67 @@ __global__ void k_mul(float *__restrict__ x, const float *__restrict__ y, int64_
     if (i < n) x[i] *= y[i];
 }
 
+// Minibatch shuffle of the training loop: a keyed permutation of [0, n)
+// per epoch, computed row by row with no sort.  A balanced Feistel network
+// (four rounds, each half of 2h bits mixed by the 64-bit finaliser of
+// MurmurHash3 keyed by seed, epoch and round) permutes [0, 4^h) with
+// 4^h >= n; values at or beyond n walk the permutation's cycle until they
+// land inside [0, n) (Black and Rogaway, "Ciphers with arbitrary finite
+// domains", 2002), which restricts it to a permutation of [0, n).
+struct Shuffle {
+    uint64_t n = 1, key = 0;
+    int h = 0;
+    uint64_t mask = 0;
+};
+__host__ __device__ inline uint64_t fmix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+__host__ __device__ inline Shuffle shuffle_of(uint64_t n, uint64_t seed, int64_t epoch) {
+    Shuffle s;
+    s.n = n > 0 ? n : 1;
+    s.key = fmix64(seed ^ fmix64((uint64_t)epoch + 0x9e3779b97f4a7c15ull));
+    int h = 1;
+    while (h < 31 && ((uint64_t)1 << (2 * h)) < s.n) ++h;
+    s.h = h;
+    s.mask = ((uint64_t)1 << h) - 1;
+    return s;
+}
+__host__ __device__ inline uint64_t feistel(const Shuffle &s, uint64_t x) {
+    uint64_t l = x >> s.h, r = x & s.mask;
+    for (int k = 0; k < 4; ++k) {
+        const uint64_t f = fmix64(r ^ (s.key + 0x632be59bd9b4e019ull * (uint64_t)(k + 1))) & s.mask;
+        const uint64_t t = l ^ f;
+        l = r;
+        r = t;
+    }
+    return (l << s.h) | r;
+}
+// image of i < n; the walk ends because the cycle through i holds i itself
+__host__ __device__ inline uint64_t shuffle_index(const Shuffle &s, uint64_t i) {
+    uint64_t x = feistel(s, i);
+    while (x >= s.n) x = feistel(s, x);
+    return x;
+}
+
+// out[r][:] = data[shuffle(first + r)][:], r < rows (one block per row)
+__global__ void k_gather_rows(const uint8_t *__restrict__ data, Shuffle sh, int64_t first,
+                              int64_t rows, int N, uint8_t *__restrict__ out) {
+    const int64_t r = blockIdx.x;
+    if (r >= rows) return;
+    const uint64_t src = shuffle_index(sh, (uint64_t)(first + r));
+    for (int i = threadIdx.x; i < N; i += blockDim.x) out[r * N + i] = data[src * N + i];
+}
+
+// acc[e] += x (one thread)
+__global__ void k_accumulate(double *__restrict__ acc, const double *__restrict__ x) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *acc += *x;
+}
+
 inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 template <bool TA, bool TB>
@@ -804,6 +869,8 @@ rtt_status rtt_made_destroy(rtt_made m) {
     cudaFree(m->d_mask);
     cudaFree(m->d_w2b);
     cudaFree(m->d_err);
+    cudaFree(m->d_batch);
+    cudaFree(m->d_fit);
     delete m;
     return RTT_OK;
 }
@@ -849,6 +916,21 @@ rtt_status rtt_made_gradients(rtt_made m, const uint8_t *spins, int64_t B, float
     return RTT_OK;
 }
 
+// gradient of one batch and one Adam step (workspace already sized)
+static rtt_status adam_step(rtt_made m, const uint8_t *spins, int64_t B, float lr, double *nll,
+                            cudaStream_t st) {
+    rtt_status s = gradients(m, spins, B, nll, st);
+    if (s != RTT_OK) return s;
+    m->step += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 - pow(b1, (double)m->step));
+    const float c2 = (float)(1.0 - pow(b2, (double)m->step));
+    mk::k_adam<<<mk::nb(m->P, 256), 256, 0, st>>>(m->d_p, m->d_g, m->d_m, m->d_v, m->P, lr,
+                                                   (float)b1, (float)b2, 1e-8f, c1, c2);
+    MC(cudaGetLastError(), "made adam");
+    return RTT_OK;
+}
+
 rtt_status rtt_made_train_step(rtt_made m, const uint8_t *spins, int64_t B, float lr, double *nll,
                                void *stream) {
     if (!m || !spins || B < 1 || !(lr > 0.f))
@@ -857,14 +939,62 @@ rtt_status rtt_made_train_step(rtt_made m, const uint8_t *spins, int64_t B, floa
     cudaStream_t st = (cudaStream_t)stream;
     rtt_status s = ensure_ws(m, B);
     if (s != RTT_OK) return s;
-    if ((s = gradients(m, spins, B, nll, st)) != RTT_OK) return s;
-    m->step += 1;
-    const double b1 = 0.9, b2 = 0.999;
-    const float c1 = (float)(1.0 - pow(b1, (double)m->step));
-    const float c2 = (float)(1.0 - pow(b2, (double)m->step));
-    mk::k_adam<<<mk::nb(m->P, 256), 256, 0, st>>>(m->d_p, m->d_g, m->d_m, m->d_v, m->P, lr,
-                                                   (float)b1, (float)b2, 1e-8f, c1, c2);
-    MC(cudaGetLastError(), "made adam");
+    return adam_step(m, spins, B, lr, nll, st);
+}
+
+rtt_status rtt_made_permutation(int64_t n, uint64_t seed, int64_t epoch, int64_t *host_out) {
+    if (n < 1 || !host_out) return mfail(RTT_ERR_INVALID_ARG, "rtt_made_permutation: bad arguments");
+    const mk::Shuffle sh = mk::shuffle_of((uint64_t)n, seed, epoch);
+    for (int64_t i = 0; i < n; ++i) host_out[i] = (int64_t)mk::shuffle_index(sh, (uint64_t)i);
+    return RTT_OK;
+}
+
+rtt_status rtt_made_fit(rtt_made m, const uint8_t *data, int64_t n, int32_t epochs, int32_t batch,
+                        float lr, uint64_t shuffle_seed, double *nll_per_epoch, void *stream) {
+    if (!m || !data || n < 1 || epochs < 0 || batch < 1 || batch > n || !(lr > 0.f))
+        return mfail(RTT_ERR_INVALID_ARG, "rtt_made_fit: bad arguments");
+    if (epochs == 0) return RTT_OK;
+    MGuard guard(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    rtt_status s = ensure_ws(m, batch);
+    if (s != RTT_OK) return s;
+    if (batch > m->batch_cap || epochs > m->fit_cap) {
+        MC(cudaStreamSynchronize(st), "made fit workspace");
+        if (batch > m->batch_cap) {
+            cudaFree(m->d_batch);
+            m->d_batch = nullptr;
+            m->batch_cap = 0;
+            MC(cudaMalloc((void **)&m->d_batch, (size_t)batch * m->N), "made fit batch");
+            m->batch_cap = batch;
+        }
+        if (epochs > m->fit_cap) {
+            cudaFree(m->d_fit);
+            m->d_fit = nullptr;
+            m->fit_cap = 0;
+            MC(cudaMalloc((void **)&m->d_fit, (size_t)(epochs + 1) * sizeof(double)), "made fit");
+            m->fit_cap = epochs;
+        }
+    }
+    MC(cudaMemsetAsync(m->d_fit, 0, (size_t)(epochs + 1) * sizeof(double), st), "made fit");
+    double *batch_nll = m->d_fit + m->fit_cap;
+    const int64_t n_batches = n / batch;
+    for (int32_t e = 0; e < epochs; ++e) {
+        const mk::Shuffle sh = mk::shuffle_of((uint64_t)n, shuffle_seed, e);
+        for (int64_t b = 0; b < n_batches; ++b) {
+            mk::k_gather_rows<<<(unsigned)batch, 128, 0, st>>>(data, sh, b * batch, batch, m->N,
+                                                               m->d_batch);
+            MC(cudaGetLastError(), "made fit gather");
+            if ((s = adam_step(m, m->d_batch, batch, lr, batch_nll, st)) != RTT_OK) return s;
+            mk::k_accumulate<<<1, 1, 0, st>>>(m->d_fit + e, batch_nll);
+            MC(cudaGetLastError(), "made fit loss");
+        }
+    }
+    if (nll_per_epoch) {
+        MC(cudaMemcpyAsync(nll_per_epoch, m->d_fit, (size_t)epochs * sizeof(double),
+                           cudaMemcpyDeviceToHost, st), "made fit loss copy");
+        MC(cudaStreamSynchronize(st), "made fit");
+        for (int32_t e = 0; e < epochs; ++e) nll_per_epoch[e] /= (double)n_batches;
+    }
     return RTT_OK;
 }
 

@@ -744,31 +744,12 @@ __global__ void __launch_bounds__(NT, 1)
 // is computed as two half-rows at once: the left tile walks sites j..m from
 // l_{j-1} (left to right), the right tile walks (R-1)N+j..m+1 from the cached
 // right environment (right to left); the halves meet in one dot product and
-// the Metropolis decision.  Roles: warps 0-3 left epilogue, 4-7 right
-// epilogue (same 128 chains, row m = TMEM lane m in both), warp 8 issues the
-// left tile's MMAs, warp 9 the right tile's, warp 10 runs the TMA loads.
-// The rows (A operands) live in TMEM: an epilogue stores its row's 16-bit
-// hi/lo split with tcgen05.st and hands it to its issuer with a named-barrier
-// arrive; the MMAs read A from TMEM and B from shared memory.
-// TMEM columns: [0,128) left accumulator, [128,256) right accumulator,
-// [256,384) the accumulator of the first site of each left half-row (kept
-// until the decision, which reads l_j = l_{j-1} A_j[s_j] from it), [384,416)
-// and [416,448) left A hi / lo (two 16-bit entries per column), [448,512)
-// right A hi / lo.  The finished right half-row reaches the left epilogue
-// through shared memory.  Every mbarrier
-// wait is bounded; after an expired wait every role walks the rest of its
-// program without issuing work (waits return at once), so the named barriers
-// always meet.
-constexpr int SP_THREADS = 352;
-constexpr bool SP_LAZY = true;  // split-row sweep: lazy renormalisation
-constexpr uint32_t SP_TCOLS = 512;
-
+// the Metropolis decision.  The two tiles run on the two CTAs of a cluster
+// (k_tc_sweep_pair below).  On a general path (GEN) proposal j's row covers
+// sites j..L-1 (spin p[j] flipped wherever it sits); the left tile walks the
+// first half from l_{j-1}, the right tile the second half backwards from b_R
+// with the current spins, so no right environment is kept.
 constexpr int SP_HAND = 64 * NT * 4;  // right half-rows, [64][128] floats
-
-inline size_t sweep2_smem(int N, int L) {
-    return 1024 + 2 * (size_t)NS * Cfg<64>::STAGE + SP_HAND + 256 + (size_t)16 * N +
-           (size_t)4 * L + 4 * NT;
-}
 
 __device__ __forceinline__ void named_sync_256() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ void named_arrive(int id, int n) {
@@ -781,339 +762,17 @@ __device__ __forceinline__ void named_sync(int id, int n) {
 // flipped wherever it sits); the left tile walks the first half from l_{j-1},
 // the right tile the second half backwards from b_R with the current spins,
 // so no right environment is kept.
-template <bool F16, bool GEN>
-__global__ void __launch_bounds__(SP_THREADS, 1)
-    k_tc_sweep2(const __grid_constant__ CUtensorMap map, const Args a) {
-    constexpr int CHI = 64;
-    using C = Cfg<CHI, F16>;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const uint32_t ring0 = sa(base);  // ring L: stages 0,1; ring R: stages 2,3
-    float *hand = (float *)(base + 2 * NS * C::STAGE);  // [64][128] right half-rows
-    uint64_t *bars = (uint64_t *)(base + 2 * NS * C::STAGE + SP_HAND);
-    const uint32_t bar0 = sa(bars);
-    // bars: full[4] (L0 L1 R0 R1), empty[4], done[2] (L R)
-    auto full_bar = [&](int X, int s) { return bar0 + 8u * (X * NS + s); };
-    auto empty_bar = [&](int X, int s) { return bar0 + 8u * (4 + X * NS + s); };
-    auto done_bar = [&](int X) { return bar0 + 8u * (8 + X); };
-    uint32_t *tmem_slot = (uint32_t *)(bars + 12);
-    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
-    long long *issued = (long long *)(bars + 14);  // loads issued per tile
-    uint32_t *bits = (uint32_t *)(base + 2 * NS * C::STAGE + SP_HAND + 256);
-    uint32_t *tab = bits + 4 * a.N;
-    int32_t *rexp_s = (int32_t *)(tab + a.L);  // exponent of the handed-over right half-row
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int N = a.N, L = a.L;
-    const int span = (a.R - 1) * N + 1;
-    const int rbase = (a.R - 1) * N + 1;
-    // sites of proposal j's left and right half-rows
-    auto nL_of = [&](int j) -> int { return (GEN ? L - j : span) / 2; };
-    auto nR_of = [&](int j) -> int { return (GEN ? L - j : span) - nL_of(j); };
-    const int m = tid & 127;  // row of the epilogue threads
-    const int64_t c_raw = (int64_t)blockIdx.x * NT + m;
-    const bool active = c_raw < a.B;
-    const int64_t c = active ? c_raw : a.B - 1;
-
-    if (warp == 0) tmem_alloc(sa(tmem_slot), SP_TCOLS);
-    if (tid == 0) {
-        for (int i = 0; i < 10; ++i) mbar_init(bar0 + 8u * i, 1);
-        *abort_flag = 0;
-        issued[0] = issued[1] = 0;
-        fence_barrier_init();
-    }
-    for (int k = tid; k < L; k += SP_THREADS)
-        tab[k] = ((uint32_t)__ldg(GEN ? a.path + k : a.q + (k % N)) & 0xffffu) |
-                 ((uint32_t)(__ldg(a.cexp + k) & 0xffff) << 16);
-    if (warp < 4) {
-        for (int i = 0; i < N; ++i) {
-            const uint32_t w = __ballot_sync(FULL, a.spins_in[c * N + i] != 0);
-            if (lane == 0) bits[i * 4 + warp] = w;
-        }
-    }
-    __syncthreads();
-    const uint32_t tmem = *tmem_slot;
-    auto spin = [&](int i) -> int { return (int)((bits[i * 4 + (warp & 3)] >> lane) & 1u); };
-    auto site_spin = [&](int k) -> int { return (int)(tab[k] & 0xffffu); };
-    auto site_cexp = [&](int k) -> int { return (int)(int16_t)(tab[k] >> 16); };
-    auto bwait = [&](uint32_t bar, uint32_t parity) -> bool {
-        if (*abort_flag) return false;
-        if (!mbar_wait(bar, parity, a.wait_limit)) {
-            atomicOr(a.err, 1);
-            *abort_flag = 1;
-            return false;
-        }
-        return true;
-    };
-    // epilogue of tile X: its A operand is stored in TMEM; hand it to the issuer
-    auto publish = [&](int X) {
-        tc_before();
-        named_arrive(2 + X, NT + 32);
-    };
-
-    if (warp == 8 || warp == 9) {
-        // ---------------------------------------------------------- MMA issuers
-        const int X = warp - 8;
-        long long g = 0;
-        auto issue = [&](uint32_t dcol) {
-            named_sync(2 + X, NT + 32);  // the A operand is in shared memory
-            if (lane == 0) {
-                const int s = (int)(g % NS);
-                if (bwait(full_bar(X, s), (uint32_t)((g / NS) & 1))) {
-                    tc_after();
-                    const uint32_t ahi = tmem + (X ? 448u : 384u), alo = ahi + 32u;
-                    const uint32_t b_hi = ring0 + (uint32_t)(X * NS + s) * C::STAGE;
-                    const uint32_t b_lo = b_hi + C::BOX;
-                    const uint32_t d = tmem + dcol;
-#pragma unroll
-                    for (int kb = 0; kb < 4; ++kb) {
-                        const uint32_t o = (uint32_t)(kb * 32), ka = (uint32_t)(kb * 8);
-                        mma_f16_ts(d, ahi + ka, sdesc(b_hi + o), C::IDESC, kb != 0 ? 1u : 0u);
-                        mma_f16_ts(d, ahi + ka, sdesc(b_lo + o), C::IDESC, 1u);
-                        mma_f16_ts(d, alo + ka, sdesc(b_hi + o), C::IDESC, 1u);
-                    }
-                    mma_commit(empty_bar(X, s));
-                    mma_commit(done_bar(X));
-                }
-            }
-            ++g;
-            __syncwarp();
-        };
-        for (int sw = 0; sw < a.n_sweeps; ++sw) {
-            if (X == 1) {
-                if (!GEN)
-                    for (int u = 0; u < N - 1; ++u) issue(128u);
-                for (int j = 0; j < N; ++j)
-                    for (int t = 0; t < nR_of(j); ++t) issue(128u);
-            } else {
-                for (int j = 0; j < N; ++j)
-                    for (int t = 0; t < nL_of(j); ++t) issue(t == 0 ? 256u : 0u);
-            }
-        }
-    } else if (warp == 10) {
-        // ---------------------------------------------------------- TMA loaders
-        // lane 0 feeds the left ring, lane 1 the right ring
-        if (lane < 2) {
-            const int XX = lane;
-            long long n[2] = {0, 0};
-            auto load = [&](int X, int k) {
-                const long long g = n[X]++;
-                const int s = (int)(g % NS);
-                if (*abort_flag) return;
-                if (g >= NS && !bwait(empty_bar(X, s), (uint32_t)(((g / NS) - 1) & 1))) return;
-                const int y_hi = ((X * 2 + 0) * L + k) * 2 * CHI;
-                const int y_lo = ((X * 2 + 1) * L + k) * 2 * CHI;
-                const uint32_t dst = ring0 + (uint32_t)(X * NS + s) * C::STAGE;
-                mbar_expect_tx(full_bar(X, s), (uint32_t)C::STAGE);
-                tma_load_2d(dst, &map, 0, y_hi, full_bar(X, s));
-                tma_load_2d(dst + C::BOX, &map, 0, y_lo, full_bar(X, s));
-                issued[X] = g + 1;
-            };
-            for (int sw = 0; sw < a.n_sweeps; ++sw) {
-                if (XX == 1 && !GEN)
-                    for (int u = 0; u < N - 1; ++u) load(1, L - 1 - u);
-                for (int j = 0; j < N; ++j) {
-                    if (XX == 0)
-                        for (int t = 0; t < nL_of(j); ++t) load(0, j + t);
-                    else
-                        for (int t = 0; t < nR_of(j); ++t)
-                            load(1, GEN ? L - 1 - t : (a.R - 1) * N + j - t);
-                }
-            }
-        }
-    } else if (warp < 4) {
-        // ---------------------------------------------------------- left epilogue
-        const uint32_t tq = tmem + ((uint32_t)(warp * 32) << 16);
-        const uint32_t tw = tq, tw0 = tq + 256u, ta = tq + 384u;
-        float v[CHI];
-        load_vec<CHI>(a.bl, v);
-        write_A_tmem<CHI, F16>(ta, v);
-        publish(0);
-        double pm = a.state[c].mant;
-        int64_t pe = a.state[c].exp2, acc_count = 0;
-        int64_t El = 0, E = 0;
-        long long nd = 0;
-        for (int sw = 0; sw < a.n_sweeps; ++sw) {
-            for (int j = 0; j < N; ++j) {
-                const int iq = site_spin(j);
-                const int si = spin(iq);
-                const int nL = nL_of(j);
-                double x = 0.0;
-                for (int t = 0; t < nL; ++t) {
-                    const int k = j + t;
-                    bwait(done_bar(0), (uint32_t)(nd++ & 1));
-                    tc_after();
-                    __syncwarp();
-                    const int sk = site_spin(k);
-                    if (t == 0) {
-                        acc_select<CHI>(tw0, si ^ 1, v);
-                        E = El + renorm<CHI, SP_LAZY>(v) - site_cexp(k);
-                    } else {
-                        acc_select<CHI>(tw, spin(sk) ^ (sk == iq ? 1 : 0), v);
-                        E += renorm<CHI, SP_LAZY>(v) - site_cexp(k);
-                    }
-                    if (t + 1 < nL) {
-                        write_A_tmem<CHI, F16>(ta, v);
-                        publish(0);
-                    }
-                    // the uniform is drawn while the next MMA runs
-                    if (t == 0)
-                        x = rttd::mcmc_uniform(a.seed, (uint64_t)(a.chain0 + c),
-                                               (uint64_t)(a.sweep0 + sw), (uint64_t)j);
-                }
-                named_sync_256();  // the right half-row is in shared memory
-                double mm;
-                {
-                    float acc[8];
-#pragma unroll
-                    for (int p = 0; p < 8; ++p) acc[p] = 0.f;
-#pragma unroll
-                    for (int i = 0; i < CHI; ++i) acc[i & 7] = fmaf(v[i], hand[i * NT + m], acc[i & 7]);
-                    mm = 0.0;
-#pragma unroll
-                    for (int p = 0; p < 8; ++p) mm += (double)acc[p];
-                }
-                int64_t Ep = E + rexp_s[m];
-                normalize_scalar(mm, Ep);
-                const double ratio = ldexp(mm / pm, (int)(Ep - pe));
-                const bool accept = active && !*abort_flag && (x < ratio * ratio);
-                if (accept) {
-                    pm = mm;
-                    pe = Ep;
-                    ++acc_count;
-                }
-                const uint32_t flips = __ballot_sync(FULL, accept);
-                if (lane == 0) bits[iq * 4 + warp] ^= flips;
-                tc_before();
-                named_sync_256();  // the decision is published
-                tc_after();
-                // l_j = l_{j-1} A_j[s_j] with the decided spin, from the kept accumulator
-                acc_select<CHI>(tw0, si ^ (accept ? 1 : 0), v);
-                El += renorm<CHI, SP_LAZY>(v) - site_cexp(j);
-                const bool more = (j + 1 < N) || (sw + 1 < a.n_sweeps);
-                if (j + 1 < N) {
-                    write_A_tmem<CHI, F16>(ta, v);
-                    publish(0);
-                }
-                if (j + 1 == N && more) {
-                    load_vec<CHI>(a.bl, v);
-                    El = 0;
-                    write_A_tmem<CHI, F16>(ta, v);
-                    publish(0);
-                }
-            }
-        }
-        if (active && !*abort_flag) {
-            a.state[c].mant = pm;
-            a.state[c].exp2 = pe;
-            if (a.n_accept) a.n_accept[c] += acc_count;
-        }
-    } else {
-        // ---------------------------------------------------------- right epilogue
-        const uint32_t tq = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        const uint32_t tw = tq + 128u, ta = tq + 448u;
-        float v[CHI];
-        load_vec<CHI>(a.br, v);
-        if (active && !GEN) {
-            store_vec<CHI>(a.rstack + ((size_t)c * N + (N - 1)) * CHI, v);
-            a.rexp[(size_t)c * N + (N - 1)] = 0;
-        }
-        write_A_tmem<CHI, F16>(ta, v);
-        publish(1);
-        int64_t E = 0;
-        long long nd = 0;
-        for (int sw = 0; sw < a.n_sweeps; ++sw) {
-            E = 0;
-            for (int u = 0; u < (GEN ? 0 : N - 1); ++u) {  // right environment of the last block
-                const int k = L - 1 - u;
-                bwait(done_bar(1), (uint32_t)(nd++ & 1));
-                tc_after();
-                __syncwarp();
-                acc_select<CHI>(tw, spin(site_spin(k)), v);
-                E += renorm<CHI, SP_LAZY>(v) - site_cexp(k);
-                if (active) {
-                    store_vec<CHI>(a.rstack + ((size_t)c * N + (k - rbase)) * CHI, v);
-                    a.rexp[(size_t)c * N + (k - rbase)] = (int32_t)E;
-                }
-                // next: the next environment step, or (u = N-2) the first right
-                // half-row, which starts from this very vector r_{(R-1)N+1}
-                write_A_tmem<CHI, F16>(ta, v);
-                publish(1);
-            }
-            for (int j = 0; j < N; ++j) {
-                const int iq = site_spin(j);
-                const int nR = nR_of(j);
-                if (GEN)
-                    E = 0;
-                else if (j > 0)
-                    E = a.rexp[(size_t)c * N + j];
-                for (int t = 0; t < nR; ++t) {
-                    const int k = GEN ? L - 1 - t : (a.R - 1) * N + j - t;
-                    bwait(done_bar(1), (uint32_t)(nd++ & 1));
-                    tc_after();
-                    __syncwarp();
-                    const int sk = site_spin(k);
-                    acc_select<CHI>(tw, spin(sk) ^ (sk == iq ? 1 : 0), v);
-                    E += renorm<CHI, SP_LAZY>(v) - site_cexp(k);
-                    if (t + 1 < nR) {
-                        write_A_tmem<CHI, F16>(ta, v);
-                        publish(1);
-                    }
-                }
-                // hand the half-row to the left epilogue (column-major: no bank conflicts)
-#pragma unroll
-                for (int i = 0; i < CHI; ++i) hand[i * NT + m] = v[i];
-                rexp_s[m] = (int32_t)E;
-                tc_before();
-                // the next half-row's start does not depend on this decision
-                const bool more = (j + 1 < N) || (sw + 1 < a.n_sweeps);
-                if (more) {
-                    if (j + 1 < N && !GEN) {
-                        load_vec<CHI>(a.rstack + ((size_t)c * N + (j + 1)) * CHI, v);
-                    } else {
-                        load_vec<CHI>(a.br, v);
-                    }
-                    write_A_tmem<CHI, F16>(ta, v);
-                    publish(1);
-                }
-                named_sync_256();  // publish the right half-row
-                named_sync_256();  // wait for the decision
-            }
-        }
-    }
-    __syncthreads();
-    if (warp < 4 && active && !*abort_flag) {
-        for (int i = 0; i < N; ++i) a.spins_out[c * N + i] = (uint8_t)spin(i);
-    }
-    // teardown: drain this CTA's own copies after an expired wait (bounded)
-    if (tid == 0 && *abort_flag) {
-        for (int X = 0; X < 2; ++X)
-            for (long long g = (issued[X] > NS ? issued[X] - NS : 0); g < issued[X]; ++g)
-                mbar_wait(full_bar(X, (int)(g % NS)), (uint32_t)((g / NS) & 1), a.wait_limit);
-    }
-    tc_before();
-    __syncthreads();
-    tc_after();
-    if (warp == 0) tmem_dealloc(tmem, SP_TCOLS);
-}
 
 
-// ------------------------------------------------------------------ split-row sweep, two warps per row group
-// As k_tc_sweep2, with the epilogue of each tile spread over 8 warps: warp
-// (quadrant q, half h) owns rows 32q..32q+31 (TMEM lanes of quadrant q) and
-// the columns [32h, 32h+32) of every row.  The two warps of a quadrant meet
-// in a 64-thread named barrier (id 4 + 4 tile + q) to combine the row maximum
-// of each site and the partial dot product of each decision, through shared
-// memory slots double-buffered by the exchange count.  Both halves of a row
-// take the same scale: the lazy-rescale vote of a warp covers the same 32
-// rows in both warps.  Roles: warps 0-7 left epilogue, 8-15 right epilogue,
-// 16 left issuer, 17 right issuer, 18 TMA loads.
-constexpr int SP4_THREADS = 608;
-
-inline size_t sweep4_smem(int N, int L) {
-    return 1024 + 2 * (size_t)NS * Cfg<64>::STAGE + SP_HAND + 256 + (size_t)16 * N +
-           (size_t)4 * L + 4 * NT + 16 + (size_t)2 * 2 * 2 * NT * 4 + (size_t)2 * 2 * NT * 8;
-}
+// ------------------------------------------------------------------ two epilogue warps per row group
+// The epilogue of a tile is spread over 8 warps: warp (quadrant q, half h)
+// owns rows 32q..32q+31 (TMEM lanes of quadrant q) and the columns
+// [32h, 32h+32) of every row.  The two warps of a quadrant meet in a
+// 64-thread named barrier to combine the row maximum of each site and the
+// partial dot product of each decision, through shared-memory slots
+// double-buffered by the exchange count.  Both halves of a row take the same
+// scale: the lazy-rescale vote of a warp covers the same 32 rows in both
+// warps.
 
 // Store 16 columns at t0 and 16 at t1 of this warp's 32 TMEM lanes, then wait.
 __device__ __forceinline__ void tmem_st_2x16(uint32_t t0, uint32_t t1, const uint32_t (&x)[16],
@@ -1170,345 +829,12 @@ __device__ __forceinline__ void write_A_half(uint32_t ta, int h, const float (&v
     tmem_st_2x16(ta + (uint32_t)(16 * h), ta + 32u + (uint32_t)(16 * h), hh, ll);
 }
 
-template <bool F16, bool GEN>
-__global__ void __launch_bounds__(SP4_THREADS, 1)
-    k_tc_sweep4(const __grid_constant__ CUtensorMap map, const Args a) {
-    constexpr int CHI = 64;
-    using C = Cfg<CHI, F16>;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const uint32_t ring0 = sa(base);
-    float *hand = (float *)(base + 2 * NS * C::STAGE);
-    uint64_t *bars = (uint64_t *)(base + 2 * NS * C::STAGE + SP_HAND);
-    const uint32_t bar0 = sa(bars);
-    auto full_bar = [&](int X, int s) { return bar0 + 8u * (X * NS + s); };
-    auto empty_bar = [&](int X, int s) { return bar0 + 8u * (4 + X * NS + s); };
-    auto done_bar = [&](int X) { return bar0 + 8u * (8 + X); };
-    uint32_t *tmem_slot = (uint32_t *)(bars + 12);
-    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
-    long long *issued = (long long *)(bars + 14);
-    uint32_t *bits = (uint32_t *)(base + 2 * NS * C::STAGE + SP_HAND + 256);
-    uint32_t *tab = bits + 4 * a.N;
-    int32_t *rexp_s = (int32_t *)(tab + a.L);
-    // exchange slots, 16-byte aligned whatever L is
-    float *xmax = (float *)(((uintptr_t)(rexp_s + NT) + 15) & ~(uintptr_t)15);  // [tile][parity][half][row]
-    double *xdot = (double *)(xmax + 2 * 2 * 2 * NT);                          // [parity][half][row]
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int N = a.N, L = a.L;
-    const int span = (a.R - 1) * N + 1;
-    auto nL_of = [&](int j) -> int { return (GEN ? L - j : span) / 2; };
-    auto nR_of = [&](int j) -> int { return (GEN ? L - j : span) - nL_of(j); };
-    const int q = warp & 3, hf = (warp >> 2) & 1;  // epilogue: quadrant and column half
-    const int m = q * 32 + lane;
-    const int64_t c_raw = (int64_t)blockIdx.x * NT + m;
-    const bool active = c_raw < a.B;
-    const int64_t c = active ? c_raw : a.B - 1;
-
-    if (warp == 0) tmem_alloc(sa(tmem_slot), SP_TCOLS);
-    if (tid == 0) {
-        for (int i = 0; i < 10; ++i) mbar_init(bar0 + 8u * i, 1);
-        *abort_flag = 0;
-        issued[0] = issued[1] = 0;
-        fence_barrier_init();
-    }
-    for (int k = tid; k < L; k += SP4_THREADS)
-        tab[k] = ((uint32_t)__ldg(GEN ? a.path + k : a.q + (k % N)) & 0xffffu) |
-                 ((uint32_t)(__ldg(a.cexp + k) & 0xffff) << 16);
-    if (warp < 4) {
-        for (int i = 0; i < N; ++i) {
-            const uint32_t w = __ballot_sync(FULL, a.spins_in[c * N + i] != 0);
-            if (lane == 0) bits[i * 4 + warp] = w;
-        }
-    }
-    __syncthreads();
-    const uint32_t tmem = *tmem_slot;
-    auto spin = [&](int i) -> int { return (int)((bits[i * 4 + q] >> lane) & 1u); };
-    auto site_spin = [&](int k) -> int { return (int)(tab[k] & 0xffffu); };
-    auto site_cexp = [&](int k) -> int { return (int)(int16_t)(tab[k] >> 16); };
-    auto bwait = [&](uint32_t bar, uint32_t parity) -> bool {
-        if (*abort_flag) return false;
-        if (!mbar_wait(bar, parity, a.wait_limit)) {
-            atomicOr(a.err, 1);
-            *abort_flag = 1;
-            return false;
-        }
-        return true;
-    };
-    auto publish = [&](int X) {
-        tc_before();
-        named_arrive(2 + X, 2 * NT + 32);
-    };
-    // the two warps of a quadrant: whole-row maximum and dot product
-    int xpar = 0;
-    auto pair_max = [&](int X, float mine) -> float {
-        float *slot = xmax + ((X * 2 + xpar) * 2) * NT;
-        slot[hf * NT + m] = mine;
-        named_sync(4 + 4 * X + q, 64);
-        const float other = slot[(hf ^ 1) * NT + m];
-        xpar ^= 1;
-        return fmaxf(mine, other);
-    };
-    int dpar = 0;
-    auto pair_dot = [&](double mine) -> double {
-        double *slot = xdot + (dpar * 2) * NT;
-        slot[hf * NT + m] = mine;
-        named_sync(4 + q, 64);
-        const double d0 = slot[m], d1 = slot[NT + m];
-        dpar ^= 1;
-        return d0 + d1;
-    };
-
-    if (warp == 16 || warp == 17) {
-        // ---------------------------------------------------------- MMA issuers
-        const int X = warp - 16;
-        long long g = 0;
-        auto issue = [&](uint32_t dcol) {
-            named_sync(2 + X, 2 * NT + 32);  // the A operand is in TMEM
-            if (lane == 0) {
-                const int s = (int)(g % NS);
-                if (bwait(full_bar(X, s), (uint32_t)((g / NS) & 1))) {
-                    tc_after();
-                    const uint32_t ahi = tmem + (X ? 448u : 384u), alo = ahi + 32u;
-                    const uint32_t b_hi = ring0 + (uint32_t)(X * NS + s) * C::STAGE;
-                    const uint32_t b_lo = b_hi + C::BOX;
-                    const uint32_t d = tmem + dcol;
-#pragma unroll
-                    for (int kb = 0; kb < 4; ++kb) {
-                        const uint32_t o = (uint32_t)(kb * 32), ka = (uint32_t)(kb * 8);
-                        mma_f16_ts(d, ahi + ka, sdesc(b_hi + o), C::IDESC, kb != 0 ? 1u : 0u);
-                        mma_f16_ts(d, ahi + ka, sdesc(b_lo + o), C::IDESC, 1u);
-                        mma_f16_ts(d, alo + ka, sdesc(b_hi + o), C::IDESC, 1u);
-                    }
-                    mma_commit(empty_bar(X, s));
-                    mma_commit(done_bar(X));
-                }
-            }
-            ++g;
-            __syncwarp();
-        };
-        for (int sw = 0; sw < a.n_sweeps; ++sw) {
-            if (X == 1) {
-                if (!GEN)
-                    for (int u = 0; u < N - 1; ++u) issue(128u);
-                for (int j = 0; j < N; ++j)
-                    for (int t = 0; t < nR_of(j); ++t) issue(128u);
-            } else {
-                for (int j = 0; j < N; ++j)
-                    for (int t = 0; t < nL_of(j); ++t) issue(t == 0 ? 256u : 0u);
-            }
-        }
-    } else if (warp == 18) {
-        // ---------------------------------------------------------- TMA loaders
-        if (lane < 2) {
-            const int XX = lane;
-            long long n[2] = {0, 0};
-            auto load = [&](int X, int k) {
-                const long long g = n[X]++;
-                const int s = (int)(g % NS);
-                if (*abort_flag) return;
-                if (g >= NS && !bwait(empty_bar(X, s), (uint32_t)(((g / NS) - 1) & 1))) return;
-                const int y_hi = ((X * 2 + 0) * L + k) * 2 * CHI;
-                const int y_lo = ((X * 2 + 1) * L + k) * 2 * CHI;
-                const uint32_t dst = ring0 + (uint32_t)(X * NS + s) * C::STAGE;
-                mbar_expect_tx(full_bar(X, s), (uint32_t)C::STAGE);
-                tma_load_2d(dst, &map, 0, y_hi, full_bar(X, s));
-                tma_load_2d(dst + C::BOX, &map, 0, y_lo, full_bar(X, s));
-                issued[X] = g + 1;
-            };
-            for (int sw = 0; sw < a.n_sweeps; ++sw) {
-                if (XX == 1 && !GEN)
-                    for (int u = 0; u < N - 1; ++u) load(1, L - 1 - u);
-                for (int j = 0; j < N; ++j) {
-                    if (XX == 0)
-                        for (int t = 0; t < nL_of(j); ++t) load(0, j + t);
-                    else
-                        for (int t = 0; t < nR_of(j); ++t)
-                            load(1, GEN ? L - 1 - t : (a.R - 1) * N + j - t);
-                }
-            }
-        }
-    } else if (warp < 8) {
-        // ---------------------------------------------------------- left epilogue
-        const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
-        const uint32_t tw = tq, tw0 = tq + 256u, ta = tq + 384u;
-        float v[32];
-        load_vec<32>(a.bl + 32 * hf, v);
-        write_A_half<F16>(ta, hf, v);
-        publish(0);
-        double pm = a.state[c].mant;
-        int64_t pe = a.state[c].exp2, acc_count = 0;
-        int64_t El = 0, E = 0;
-        long long nd = 0;
-        for (int sw = 0; sw < a.n_sweeps; ++sw) {
-            for (int j = 0; j < N; ++j) {
-                const int iq = site_spin(j);
-                const int si = spin(iq);
-                const int nL = nL_of(j);
-                double x = 0.0;
-                float mx_keep = 0.f, mx_flip = 0.f;
-                for (int t = 0; t < nL; ++t) {
-                    const int k = j + t;
-                    bwait(done_bar(0), (uint32_t)(nd++ & 1));
-                    tc_after();
-                    __syncwarp();
-                    const int sk = site_spin(k);
-                    if (t == 0) {
-                        // maxima of both candidates of l_j now, for the decision
-                        float vk[32];
-                        acc_select_half(tw0, hf, si, vk);
-                        acc_select_half(tw0, hf, si ^ 1, v);
-                        const float a0 = half_max(vk), a1 = half_max(v);
-                        mx_keep = pair_max(0, a0);
-                        mx_flip = pair_max(0, a1);
-                        E = El + renorm_half(v, mx_flip) - site_cexp(k);
-                    } else {
-                        acc_select_half(tw, hf, spin(sk) ^ (sk == iq ? 1 : 0), v);
-                        E += renorm_half(v, pair_max(0, half_max(v))) - site_cexp(k);
-                    }
-                    if (t + 1 < nL) {
-                        write_A_half<F16>(ta, hf, v);
-                        publish(0);
-                    }
-                    if (t == 0)
-                        x = rttd::mcmc_uniform(a.seed, (uint64_t)(a.chain0 + c),
-                                               (uint64_t)(a.sweep0 + sw), (uint64_t)j);
-                }
-                named_sync(1, 4 * NT);  // the right half-rows are in shared memory
-                double mm;
-                {
-                    float acc[8];
-#pragma unroll
-                    for (int p = 0; p < 8; ++p) acc[p] = 0.f;
-#pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        acc[i & 7] = fmaf(v[i], hand[(32 * hf + i) * NT + m], acc[i & 7]);
-                    double part = 0.0;
-#pragma unroll
-                    for (int p = 0; p < 8; ++p) part += (double)acc[p];
-                    mm = pair_dot(part);
-                }
-                int64_t Ep = E + rexp_s[m];
-                normalize_scalar(mm, Ep);
-                const double ratio = ldexp(mm / pm, (int)(Ep - pe));
-                const bool accept = active && !*abort_flag && (x < ratio * ratio);
-                if (accept) {
-                    pm = mm;
-                    pe = Ep;
-                    ++acc_count;
-                }
-                const uint32_t flips = __ballot_sync(FULL, accept);
-                if (lane == 0 && hf == 0) bits[iq * 4 + q] ^= flips;
-                tc_before();
-                named_sync(1, 4 * NT);  // the decision is published
-                tc_after();
-                acc_select_half(tw0, hf, si ^ (accept ? 1 : 0), v);
-                El += renorm_half(v, accept ? mx_flip : mx_keep) - site_cexp(j);
-                const bool more = (j + 1 < N) || (sw + 1 < a.n_sweeps);
-                if (j + 1 < N) {
-                    write_A_half<F16>(ta, hf, v);
-                    publish(0);
-                }
-                if (j + 1 == N && more) {
-                    load_vec<32>(a.bl + 32 * hf, v);
-                    El = 0;
-                    write_A_half<F16>(ta, hf, v);
-                    publish(0);
-                }
-            }
-        }
-        if (active && !*abort_flag && hf == 0) {
-            a.state[c].mant = pm;
-            a.state[c].exp2 = pe;
-            if (a.n_accept) a.n_accept[c] += acc_count;
-        }
-    } else if (warp < 16) {
-        // ---------------------------------------------------------- right epilogue
-        const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
-        const uint32_t tw = tq + 128u, ta = tq + 448u;
-        float v[32];
-        load_vec<32>(a.br + 32 * hf, v);
-        if (active && !GEN) {
-            store_vec<32>(a.rstack + ((size_t)c * N + (N - 1)) * CHI + 32 * hf, v);
-            if (hf == 0) a.rexp[(size_t)c * N + (N - 1)] = 0;
-        }
-        write_A_half<F16>(ta, hf, v);
-        publish(1);
-        int64_t E = 0;
-        long long nd = 0;
-        for (int sw = 0; sw < a.n_sweeps; ++sw) {
-            E = 0;
-            for (int u = 0; u < (GEN ? 0 : N - 1); ++u) {
-                const int k = L - 1 - u;
-                bwait(done_bar(1), (uint32_t)(nd++ & 1));
-                tc_after();
-                __syncwarp();
-                acc_select_half(tw, hf, spin(site_spin(k)), v);
-                E += renorm_half(v, pair_max(1, half_max(v))) - site_cexp(k);
-                if (active) {
-                    store_vec<32>(a.rstack + ((size_t)c * N + (k - (a.R - 1) * N - 1)) * CHI + 32 * hf, v);
-                    if (hf == 0) a.rexp[(size_t)c * N + (k - (a.R - 1) * N - 1)] = (int32_t)E;
-                }
-                write_A_half<F16>(ta, hf, v);
-                publish(1);
-            }
-            for (int j = 0; j < N; ++j) {
-                const int iq = site_spin(j);
-                const int nR = nR_of(j);
-                if (GEN)
-                    E = 0;
-                else if (j > 0)
-                    E = a.rexp[(size_t)c * N + j];
-                for (int t = 0; t < nR; ++t) {
-                    const int k = GEN ? L - 1 - t : (a.R - 1) * N + j - t;
-                    bwait(done_bar(1), (uint32_t)(nd++ & 1));
-                    tc_after();
-                    __syncwarp();
-                    const int sk = site_spin(k);
-                    acc_select_half(tw, hf, spin(sk) ^ (sk == iq ? 1 : 0), v);
-                    E += renorm_half(v, pair_max(1, half_max(v))) - site_cexp(k);
-                    if (t + 1 < nR) {
-                        write_A_half<F16>(ta, hf, v);
-                        publish(1);
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 32; ++i) hand[(32 * hf + i) * NT + m] = v[i];
-                if (hf == 0) rexp_s[m] = (int32_t)E;
-                tc_before();
-                const bool more = (j + 1 < N) || (sw + 1 < a.n_sweeps);
-                if (more) {
-                    if (j + 1 < N && !GEN)
-                        load_vec<32>(a.rstack + ((size_t)c * N + (j + 1)) * CHI + 32 * hf, v);
-                    else
-                        load_vec<32>(a.br + 32 * hf, v);
-                    write_A_half<F16>(ta, hf, v);
-                    publish(1);
-                }
-                named_sync(1, 4 * NT);  // publish the right half-rows
-                named_sync(1, 4 * NT);  // wait for the decision
-            }
-        }
-    }
-    __syncthreads();
-    if (warp < 4 && active && !*abort_flag) {
-        for (int i = 0; i < N; ++i) a.spins_out[c * N + i] = (uint8_t)spin(i);
-    }
-    if (tid == 0 && *abort_flag) {
-        for (int X = 0; X < 2; ++X)
-            for (long long g = (issued[X] > NS ? issued[X] - NS : 0); g < issued[X]; ++g)
-                mbar_wait(full_bar(X, (int)(g % NS)), (uint32_t)((g / NS) & 1), a.wait_limit);
-    }
-    tc_before();
-    __syncthreads();
-    tc_after();
-    if (warp == 0) tmem_dealloc(tmem, SP_TCOLS);
-}
 
 
 // ------------------------------------------------------------------ split-row sweep on a CTA pair
-// As k_tc_sweep4, with the two half-row tiles on the two CTAs of a cluster
-// (rank 0 left, rank 1 right), i.e. on two SMs with a tensor pipe each.  Per
+// The two half-row tiles on the two CTAs of a cluster (rank 0 left, rank 1
+// right), i.e. on two SMs with a tensor pipe each, each tile's epilogue on two
+// warps per row group (above).  Per
 // proposal the right CTA stores its finished half-row (and exponent) into the
 // left CTA's shared memory and arrives on the left's `hand` mbarrier; the left
 // decides, stores the flip bits into the right CTA's spin bits and arrives on
@@ -2274,12 +1600,6 @@ rtt_status tc_chain_init(rtt_s *h, const uint8_t *spins, int64_t B, double *log_
     return status_of(e, "tc log amplitudes");
 }
 
-// chi = 64 sweep epilogue: one warp (k_tc_sweep2) or two warps (k_tc_sweep4)
-// per TMEM lane quadrant and tile.
-constexpr int kSweepWarpsPerQuadrant = 2;
-// chi = 64 sweep: the two half-row tiles on the two SMs of a CTA pair (cluster)
-constexpr bool kSweepOnCtaPair = true;
-
 rtt_status tc_sweep(rtt_s *h, uint8_t *spins, rtt_chain_state *state, int64_t B, int64_t chain0,
                     int64_t sweep0, int32_t n_sweeps, int64_t *n_accept, cudaStream_t st) {
     TcPlan *p = h->tc;
@@ -2322,47 +1642,21 @@ rtt_status tc_sweep(rtt_s *h, uint8_t *spins, rtt_chain_state *state, int64_t B,
         return RTT_ERR_UNSUPPORTED;
     }
     if (p->chi == 64 && h->R >= 2 && h->N >= 2) {
-        // split-row sweep: two half-row tiles per CTA
-        const size_t smem = tcd::sweep2_smem(h->N, h->L);
-        auto go = [&](auto kern) {
+        // split-row sweep on CTA pairs.  At least 164 KB of shared memory: no
+        // other CTA that allocates TMEM (a second pair CTA, a 66 KB tile kernel
+        // of the energy) fits beside a pair CTA on one SM, so no tcgen05.alloc
+        // ever waits for a CTA that waits for its cluster peer
+        const size_t smemc = std::max(tcd::sweepc_smem(h->N, h->L), (size_t)164 * 1024);
+        auto goc = [&](auto kern) {
             cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem);
-            if (err == cudaSuccess) kern<<<tiles(B), tcd::SP_THREADS, smem, st>>>(p->map, a);
+                                                   (int)smemc);
+            if (err == cudaSuccess) kern<<<2 * tiles(B), tcd::SPC_THREADS, smemc, st>>>(p->map, a);
             return err;
         };
-        if (kSweepOnCtaPair) {
-            // at least 164 KB: no other CTA that allocates TMEM (a second pair CTA, a
-            // 66 KB tile kernel of the energy) fits beside a pair CTA on one SM, so
-            // no tcgen05.alloc ever waits for a CTA that waits for its cluster peer
-            const size_t smemc = std::max(tcd::sweepc_smem(h->N, h->L), (size_t)164 * 1024);
-            auto goc = [&](auto kern) {
-                cudaError_t err = cudaFuncSetAttribute(
-                    kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemc);
-                if (err == cudaSuccess)
-                    kern<<<2 * tiles(B), tcd::SPC_THREADS, smemc, st>>>(p->map, a);
-                return err;
-            };
-            if (h->periodic)
-                e = p->f16 ? goc(tcd::k_tc_sweep_pair<true, false>) : goc(tcd::k_tc_sweep_pair<false, false>);
-            else
-                e = p->f16 ? goc(tcd::k_tc_sweep_pair<true, true>) : goc(tcd::k_tc_sweep_pair<false, true>);
-        } else if (kSweepWarpsPerQuadrant == 2) {
-            const size_t smem4 = tcd::sweep4_smem(h->N, h->L);
-            auto go4 = [&](auto kern) {
-                cudaError_t err = cudaFuncSetAttribute(
-                    kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
-                if (err == cudaSuccess) kern<<<tiles(B), tcd::SP4_THREADS, smem4, st>>>(p->map, a);
-                return err;
-            };
-            if (h->periodic)
-                e = p->f16 ? go4(tcd::k_tc_sweep4<true, false>) : go4(tcd::k_tc_sweep4<false, false>);
-            else
-                e = p->f16 ? go4(tcd::k_tc_sweep4<true, true>) : go4(tcd::k_tc_sweep4<false, true>);
-        } else if (h->periodic) {
-            e = p->f16 ? go(tcd::k_tc_sweep2<true, false>) : go(tcd::k_tc_sweep2<false, false>);
-        } else {
-            e = p->f16 ? go(tcd::k_tc_sweep2<true, true>) : go(tcd::k_tc_sweep2<false, true>);
-        }
+        if (h->periodic)
+            e = p->f16 ? goc(tcd::k_tc_sweep_pair<true, false>) : goc(tcd::k_tc_sweep_pair<false, false>);
+        else
+            e = p->f16 ? goc(tcd::k_tc_sweep_pair<true, true>) : goc(tcd::k_tc_sweep_pair<false, true>);
         if (e == cudaSuccess) e = cudaGetLastError();
     } else {
         e = launch_chi<tcd::M_SWEEP>(p, a, dim3(tiles(B)), st);

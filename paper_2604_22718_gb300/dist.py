@@ -18,21 +18,30 @@ def shard(total_chains: int, rank: int, world: int) -> tuple[int, int]:
     return chain0, count
 
 
-def local_moments(trace: np.ndarray) -> np.ndarray:
-    """[n, sum x, sum x^2] of a local trace (FP64)."""
-    x = np.asarray(trace, dtype=np.float64)
-    return np.array([float(x.size), float(x.sum()), float((x * x).sum())])
+def local_moments(trace: np.ndarray, center: float = 0.0) -> np.ndarray:
+    """[n, sum (x - center), sum (x - center)^2] of a local trace (FP64)."""
+    d = np.asarray(trace, dtype=np.float64) - center
+    return np.array([float(d.size), float(d.sum()), float((d * d).sum())])
 
 
 def merge_moments(trace: np.ndarray, group=None) -> dict:
-    """Global mean and variance (1/n) of all ranks' traces by an FP64 sum of
-    local moments across the process group (torch.distributed, any backend)."""
-    m = local_moments(trace)
+    """Global mean and variance (1/n) of all ranks' traces, in two passes of
+    FP64 sums across the process group (torch.distributed, any backend): the
+    first gives n and the mean, the second the squared deviations from that
+    mean, so the variance never comes from the difference of two large sums
+    (sum x^2 / n - mean^2 loses every digit the mean has in common with the
+    spread).  The residual sum of deviations corrects the mean's rounding."""
     import torch
     import torch.distributed as dist
-    t = torch.from_numpy(m)
-    if dist.is_available() and dist.is_initialized():
-        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
-    n, s1, s2 = (float(v) for v in t)
+    live = dist.is_available() and dist.is_initialized()
+
+    def allsum(v):
+        t = torch.from_numpy(v)
+        if live:
+            dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        return t.numpy()
+
+    n, s1, _ = allsum(local_moments(trace))
     mean = s1 / n
-    return {"n": n, "mean": mean, "var": s2 / n - mean * mean}
+    _, d1, d2 = allsum(local_moments(trace, mean))
+    return {"n": float(n), "mean": float(mean + d1 / n), "var": float((d2 - d1 * d1 / n) / n)}

@@ -97,13 +97,15 @@ def lib():
         L.rtt_made_log_prob.argtypes = [P, P, I64, P, P]
         L.rtt_made_sample.argtypes = [P, I64, I64, I64, P, P, P]
         L.rtt_indep_mh.argtypes = [P, P, P, P, I64, I64, I64, P, P]
+        L.rtt_made_fit.argtypes = [P, P, I64, I32, I32, ctypes.c_float, U64, P, P]
+        L.rtt_made_permutation.argtypes = [I64, U64, I64, P]
         L.rtt_made_set_inference.argtypes = [P, I32]
         L.rtt_made_device_status.argtypes = [P, ctypes.POINTER(I32)]
         L.rtt_made_set_inference.restype = ctypes.c_int
         L.rtt_made_device_status.restype = ctypes.c_int
         for name in ("rtt_made_create", "rtt_made_destroy", "rtt_made_get_params",
                      "rtt_made_gradients", "rtt_made_train_step", "rtt_made_log_prob",
-                     "rtt_made_sample", "rtt_indep_mh"):
+                     "rtt_made_sample", "rtt_indep_mh", "rtt_made_fit", "rtt_made_permutation"):
             getattr(L, name).restype = ctypes.c_int
         L.rtt_replica_lift.argtypes = [I32, I32, P, I32, P, P, P, P, P, P, P]
         L.rtt_tt_plan_create.argtypes = [I32, I32, I32, I32, I32, P, P, I32, ctypes.POINTER(P)]
@@ -559,20 +561,23 @@ class MADE:
 
     def fit(self, data: torch.Tensor, epochs: int, batch: int = 1024, lr: float = 1e-3,
             seed: int = 0, stream=None):
-        """Minibatch Adam over `data` (device uint8 [n][N]); returns mean NLL per epoch."""
+        """rtt_made_fit: minibatch Adam over `data` (device uint8 [n][N]) in a
+        keyed random row order per epoch; returns the mean NLL of each epoch."""
         n = data.shape[0]
-        g = torch.Generator(device="cpu").manual_seed(seed)
-        nll = torch.zeros(1, dtype=torch.float64, device=data.device)
-        hist = []
-        for _ in range(epochs):
-            perm = torch.randperm(n, generator=g).to(data.device)
-            tot, cnt = torch.zeros((), dtype=torch.float64, device=data.device), 0
-            for s in range(0, n - batch + 1, batch):
-                self.train_step(data[perm[s:s + batch]].contiguous(), lr, nll, stream)
-                tot += nll[0]
-                cnt += 1
-            hist.append(float(tot) / max(cnt, 1))
-        return hist
+        _dev_check(data, torch.uint8, (n, self.n), "data")
+        hist = np.zeros(max(int(epochs), 0), dtype=np.float64)
+        _check(lib().rtt_made_fit(self._m, _ptr(data), n, int(epochs), int(batch), float(lr),
+                                  int(seed), hist.ctypes.data if hist.size else None,
+                                  _stream(stream)), "rtt_made_fit")
+        return [float(x) for x in hist]
+
+
+def made_permutation(n: int, seed: int, epoch: int) -> np.ndarray:
+    """rtt_made_permutation: the training loop's row order for one epoch."""
+    out = np.empty(int(n), dtype=np.int64)
+    _check(lib().rtt_made_permutation(int(n), int(seed), int(epoch), out.ctypes.data),
+           "rtt_made_permutation")
+    return out
 
 
 def indep_mh(model: RTT, made: MADE, spins, state, round: int, n_accept=None, chain0: int = 0,

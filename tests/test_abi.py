@@ -163,3 +163,37 @@ def test_made_and_batch_calls_reject_bad_arguments_before_any_cuda_call(lib):
     assert lib.rtt_batch_step(None, None, None, 0, None, None, 0, None) == 1
     assert lib.rtt_batch_layout(None, None, None, None, None) == 1
     assert lib.rtt_batch_destroy(None) == 0
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 64, 1000, 4097, 1 << 20])
+def test_training_row_order_is_a_permutation(lib, n):
+    """rtt_made_permutation (host only): every row of [0, n) exactly once, a
+    different order for another pass or another seed."""
+    from paper_2604_22718_gb300 import rtt
+    p0 = rtt.made_permutation(n, 7, 0)
+    assert np.array_equal(np.sort(p0), np.arange(n))
+    if n >= 64:
+        p1 = rtt.made_permutation(n, 7, 1)
+        q0 = rtt.made_permutation(n, 8, 0)
+        assert np.array_equal(np.sort(p1), np.arange(n))
+        assert not np.array_equal(p0, p1) and not np.array_equal(p0, q0)
+        # not close to the identity: few fixed points, rows spread over the range
+        assert np.mean(p0 == np.arange(n)) < 0.05
+        assert abs(np.corrcoef(p0, np.arange(n))[0, 1]) < 0.2
+
+
+def test_training_loop_rejects_bad_arguments(lib):
+    from paper_2604_22718_gb300 import rtt
+    dummy = ctypes.c_void_p(1)        # never dereferenced: the checks come first
+    data = ctypes.c_void_p(2)
+    f = lib.rtt_made_fit
+    assert f(None, data, 10, 1, 5, ctypes.c_float(1e-3), 0, None, None) == 1
+    assert f(dummy, None, 10, 1, 5, ctypes.c_float(1e-3), 0, None, None) == 1
+    assert f(dummy, data, 10, 1, 11, ctypes.c_float(1e-3), 0, None, None) == 1     # batch > n
+    assert f(dummy, data, 10, 1, 0, ctypes.c_float(1e-3), 0, None, None) == 1
+    assert f(dummy, data, 10, -1, 5, ctypes.c_float(1e-3), 0, None, None) == 1
+    assert f(dummy, data, 10, 1, 5, ctypes.c_float(0.0), 0, None, None) == 1
+    out = np.zeros(3, dtype=np.int64)
+    assert lib.rtt_made_permutation(0, 1, 0, out.ctypes.data) == 1
+    with pytest.raises(rtt.RTTError, match="INVALID_ARG"):
+        rtt.made_permutation(0, 1, 0)

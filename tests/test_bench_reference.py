@@ -12,8 +12,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_prints_one_json_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "3"], cwd=ROOT, capture_output=True, text=True,
-                         timeout=600, check=True).stdout.strip().splitlines()
+                          "--workload", "plain_6x6", "--steps", "1", "--warmup", "3"], cwd=ROOT,
+                         capture_output=True, text=True, timeout=600,
+                         check=True).stdout.strip().splitlines()
     lines = [l for l in out if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
@@ -24,3 +25,14 @@ def test_reference_arm_prints_one_json_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("plain_6x6")
+
+
+def test_default_workload_is_the_metric_configuration(monkeypatch):
+    """With no flags the bench times the learned-proposal workload (16x16,
+    R = 2, chi = 128, 8192 chains) for a few seconds of steps."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    assert a.workload == "learned_16x16" and a.gpus == 1 and a.impl == "ours"
+    assert a.warmup >= 3 and 1 <= a.steps <= 50

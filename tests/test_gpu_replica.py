@@ -407,8 +407,10 @@ def test_power_fp32_amplitudes_within_derived_tolerance():
 
 @pytest.mark.gpu
 def test_power_fp32_symmetric_start_energy_is_valid():
-    """From phi^(0) = 1 (degenerate truncations, R23): the FP32 run's exact
-    energy is variational and within a quarter of the oracle run's error."""
+    """From phi^(0) = 1 the first truncations are degenerate (equal singular
+    values at the cut, so the kept subspace is not unique): the FP32 run's
+    exact energy is variational and within a quarter of the oracle run's
+    error."""
     rtt = _rtt()
     lx = ly = 3
     order = ("V", "H", "D", "Dp")
