@@ -443,3 +443,78 @@ def test_observables_iid_and_vscore():
     assert st["se_chain"] == pytest.approx(2.0 / math.sqrt(x.size), rel=0.5)
     assert st["v_score"] == pytest.approx(10 * st["var"] / st["mean"] ** 2, rel=1e-12)
     assert st["var"] == pytest.approx(4.0, rel=0.05)
+
+
+# --------------------------------------------------------------------------- conditioning
+# orc_amplitude_cond sets every floating-point tolerance of the FP32 and
+# split-precision parity tests, so it is pinned by values worked out by hand
+# from its definition: per site kappa_k = || |v| |A_k| ||_2 / || v A_k ||_2
+# (v the incoming row after the exact power-of-two renormalisation), and
+# kappa_fin = sum_b |v_b b_R[b]| / |sum_b v_b b_R[b]|.
+
+def _cond(inst, s):
+    return orc.Oracle(inst).amplitude_cond(np.asarray([s], dtype=np.uint8))[0]
+
+
+def _one_site(A0, A1, bl, br):
+    t = np.zeros((1, 2, 2, 2))
+    t[0, 0], t[0, 1] = A0, A1
+    return inputs.RTTInstance(n_spins=1, path=np.zeros(1, np.int32), tensors=t,
+                              b_left=np.asarray(bl, float), b_right=np.asarray(br, float),
+                              bonds=np.zeros((0, 2), np.int32), J=1.0, h=1.0)
+
+
+def test_cond_positive_chi1_is_one_everywhere():
+    """chi = 1 with positive entries: no cancellation anywhere, every kappa is
+    exactly 1 (sum over L sites = L)."""
+    L = 7
+    rng = np.random.default_rng(3)
+    t = rng.uniform(0.5, 2.0, size=(L, 2, 1, 1))
+    inst = inputs.RTTInstance(n_spins=L, path=np.arange(L, dtype=np.int32), tensors=t,
+                              b_left=np.ones(1), b_right=np.ones(1),
+                              bonds=np.zeros((0, 2), np.int32), J=1.0, h=1.0)
+    for s in ([0] * L, [1, 0, 1, 1, 0, 0, 1]):
+        sk, mk, kf = _cond(inst, s)
+        assert (sk, mk, kf) == (float(L), 1.0, 1.0)
+
+
+def test_cond_two_by_two_by_hand():
+    """One site, chi = 2, b_L = (1, 1), b_R = (1, -1).
+    s = 0, A = [[1, -1], [2, 3]]: v A = (3, 2), |v||A| = (3, 4), so kappa =
+    sqrt(25/13); the row renormalised by 2^-1 is (1.5, 1): kappa_fin =
+    (1.5 + 1) / |1.5 - 1| = 5.
+    s = 1, A = [[2, 0], [0, -1]]: v A = (2, -1) = |v||A| up to sign, kappa = 1;
+    the row (1, -0.5) gives kappa_fin = 1.5 / 1.5 = 1."""
+    inst = _one_site([[1.0, -1.0], [2.0, 3.0]], [[2.0, 0.0], [0.0, -1.0]], [1, 1], [1, -1])
+    sk, mk, kf = _cond(inst, [0])
+    assert sk == pytest.approx(math.sqrt(25.0 / 13.0), rel=1e-15)
+    assert mk == sk and kf == 5.0
+    assert tuple(_cond(inst, [1])) == (1.0, 1.0, 1.0)
+
+
+def test_cond_closing_cancellation():
+    """b_R = (1, -1.5 (1 - 2^-20)) against the row (1.5, 1): the closing sum is
+    1.5 2^-20 and the absolute sum 3 - 1.5 2^-20, so kappa_fin = 2^21 - 1
+    exactly."""
+    eps = 2.0 ** -20
+    inst = _one_site([[1.0, -1.0], [2.0, 3.0]], np.eye(2), [1, 1], [1.0, -1.5 * (1.0 - eps)])
+    _, _, kf = _cond(inst, [0])
+    assert kf == 2.0 ** 21 - 1.0
+
+
+def test_cond_invariances_and_lower_bound():
+    """kappa_k >= 1 and kappa_fin >= 1 (triangle inequality); scaling a site
+    tensor by a power of two or negating it (both slices) leaves every kappa
+    unchanged."""
+    inst = inputs.make_instance(3, 3, 2, 6, 3.0, seed=21, mixing=True)
+    spins = inputs.initial_spins(5, 6, 9)
+    o = orc.Oracle(inst)
+    base = o.amplitude_cond(spins)
+    assert np.all(base[:, 1] >= 1.0) and np.all(base[:, 2] >= 1.0)
+    assert np.all(base[:, 0] >= inst.path.shape[0])
+    t = inst.tensors.copy()
+    t[4] *= 8.0
+    t[7] *= -1.0
+    other = inputs.RTTInstance(n_spins=9, path=inst.path, tensors=t, b_left=inst.b_left,
+                               b_right=inst.b_right, bonds=inst.bonds, J=inst.J, h=inst.h)
+    np.testing.assert_allclose(orc.Oracle(other).amplitude_cond(spins), base, rtol=1e-13)
