@@ -175,17 +175,26 @@ class Oracle:
             list(ex.map(run, range(threads)))
         return (e, r) if with_ratios else e
 
-    def amplitude_cond(self, spins):
+    def amplitude_cond(self, spins, threads: int = 0):
         """Per configuration: (sum_k kappa_k, max_k kappa_k, kappa_fin) of the
-        left-to-right evaluation (see orc_amplitude_cond)."""
+        left-to-right evaluation (see orc_amplitude_cond); configurations
+        spread over `threads` host threads (0: all cores)."""
         spins = np.ascontiguousarray(spins, dtype=np.uint8)
         B = spins.shape[0]
         out = np.empty((B, 3))
-        for c in range(B):
+
+        def run(c):
             a, b, k = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
             self.lib.orc_amplitude_cond(self._p, _ptr(spins[c]), ctypes.byref(a),
                                         ctypes.byref(b), ctypes.byref(k))
             out[c] = (a.value, b.value, k.value)
+        nt = min(threads or (os.cpu_count() or 1), B)
+        if nt <= 1 or B * self.L * self.chi * self.chi < (1 << 22):
+            for c in range(B):
+                run(c)
+        else:
+            with ThreadPoolExecutor(nt) as ex:
+                list(ex.map(run, range(B)))
         return out
 
     def all_amplitudes(self):
@@ -240,6 +249,48 @@ class Oracle:
             with ThreadPoolExecutor(len(parts)) as exe:
                 list(exe.map(run, parts))
         return trace, acc
+
+
+    def replay_sweep(self, seed, s_before, s_after, sweep, chain0=0, threads: int = 1):
+        """One systematic sweep (Sec. 3.3: proposal j flips spin path[j], accept
+        iff u < (psi(s')/psi(s))^2) of every chain, taking the decisions that
+        s_after records: a sweep proposes each spin once, so spin path[j]
+        differs between s_before and s_after iff proposal j was accepted.
+        Per proposal, at the state the recorded decisions lead to: r2 =
+        (psi(s')/psi(s))^2 in FP64, the uniform u, the recorded decision and
+        the rule's (u < r2).  Returns (r2, u, taken, rule, states) with arrays
+        [B][N] (proposal order) and states[B][N][N] the configuration each
+        proposal starts from."""
+        s0 = np.ascontiguousarray(s_before, dtype=np.uint8)
+        s1 = np.ascontiguousarray(s_after, dtype=np.uint8)
+        B, N = s0.shape
+        r2 = np.empty((B, N))
+        u = np.empty((B, N))
+        taken = np.zeros((B, N), dtype=bool)
+        states = np.empty((B, N, N), dtype=np.uint8)
+
+        def run(c):
+            s = s0[c].copy()
+            m, e = self.amplitude(s)
+            for j in range(N):
+                i = int(self.path[j])
+                states[c, j] = s
+                mf, ef = self.flip_amplitude(s, i)
+                d = ef - e
+                r = math.ldexp(mf / m, d) if (m != 0.0 and d < 1000) else math.inf
+                r2[c, j] = r * r
+                u[c, j] = mcmc_uniform(seed, chain0 + c, sweep, j)
+                taken[c, j] = s1[c, i] != s0[c, i]
+                if taken[c, j]:
+                    s[i] ^= 1
+                    m, e = mf, ef
+        if threads <= 1 or B < 2:
+            for c in range(B):
+                run(c)
+        else:
+            with ThreadPoolExecutor(min(threads, B)) as ex:
+                list(ex.map(run, range(B)))
+        return r2, u, taken, u < r2, states
 
 
 def philox4x64(counter, key):

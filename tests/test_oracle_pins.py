@@ -518,3 +518,26 @@ def test_cond_invariances_and_lower_bound():
     other = inputs.RTTInstance(n_spins=9, path=inst.path, tensors=t, b_left=inst.b_left,
                                b_right=inst.b_right, bonds=inst.bonds, J=inst.J, h=inst.h)
     np.testing.assert_allclose(orc.Oracle(other).amplitude_cond(spins), base, rtol=1e-13)
+
+
+def test_replayed_sweep_reproduces_the_oracle_chain():
+    """The teacher-forced replay of one sweep (the decisions read from the
+    configuration after it) of the oracle's own chains finds every recorded
+    decision equal to the rule u < r^2 and the uniforms of the Metropolis
+    stream; a planted wrong decision is reported at its proposal."""
+    inst = inputs.workload("tiny_fp64")
+    o = orc.Oracle(inst)
+    s0 = inputs.initial_spins(77, 48, inst.n_spins)
+    s1 = s0.copy()
+    m, e = o.init_chains(s1)
+    o.mcmc(5, s1, m, e, 3, 1, record=False, chain0=10)
+    r2, u, taken, rule, states = o.replay_sweep(5, s0, s1, 3, chain0=10, threads=4)
+    assert np.array_equal(taken, rule)
+    assert np.array_equal(states[:, 0], s0)
+    assert u[2, 4] == orc.mcmc_uniform(5, 12, 3, 4)
+    assert np.array_equal(taken, s1[:, inst.path[:inst.n_spins]] != s0[:, inst.path[:inst.n_spins]])
+    bad = s1.copy()
+    bad[7, inst.path[5]] ^= 1                     # proposal 5 of chain 7 decided the other way
+    _, _, tk, ru, _ = o.replay_sweep(5, s0, bad, 3, chain0=10)
+    first = np.argwhere(tk != ru)
+    assert first[0].tolist() == [7, 5]
