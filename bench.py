@@ -74,9 +74,12 @@ DEFAULT_STEPS = {"learned_16x16": 20, "plain_6x6": 1000, "vhdd_6x6": 500, "prec_
                  "tiny_fp64": 1000, "batched64": 3, "dual_6x6": 500, "physical_6x6": 3,
                  "physical_10x10": 2}
 
-# executed tensor flops per algorithmic flop of the split-precision site
-# products: both spin slices per MMA (x2) and three hi/lo products (x3)
-EXECUTED_PER_ALG = 6.0
+# executed tensor flops (dense-equivalent) per algorithmic flop of the
+# split-precision site products: three hi/lo products (x3); the chi = 64
+# split-row sweep also contracts both spin slices (x2), the other tensor-core
+# kernels take the row's slice through a 2:4-sparse operand
+def executed_per_alg(kernel: str, chi: int) -> float:
+    return 6.0 if (kernel == "tc_sweep" and chi == 64) else 3.0
 
 
 def measured_peaks():
@@ -410,13 +413,13 @@ def run_ours(args):
             peak = peaks["bf16_tflops_sustained" if long_region else "bf16_tflops"]
             bound, pk = "tensor", (f"bf16 dense {'sustained' if long_region else 'burst'} "
                                    f"({peak_kind}); fp16 = bf16 rate; executed = "
-                                   f"{EXECUTED_PER_ALG:g}x algorithmic")
+                                   f"{executed_per_alg(dom, inst.chi):g}x algorithmic")
         else:
             lanes = FP32_LANES_PER_SM if args.precision == "fp32" else FP64_LANES_PER_SM
             peak = SM_COUNT * lanes * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             bound, pk = "alu", (f"{args.precision} CUDA-core fma peak: {SM_COUNT} SMs x {lanes} "
                                 f"lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz")
-        mult = EXECUTED_PER_ALG if bound == "tensor" else 1.0
+        mult = executed_per_alg(dom, inst.chi) if bound == "tensor" else 1.0
         executed = achieved * mult
         step_flops = sum(2.0 * inst.chi * inst.chi * site_steps(N, R, k, inst.path) * B * v[0]
                          for k, v in prof.items()) / K
@@ -730,7 +733,7 @@ def run_learned(args):
             "peak_source": f"bf16 dense {kind_txt} ({peak_kind}; timed region "
                            f"{ms_m / 1e3:.1f} s); fp16 = bf16 rate",
             "frac_of_burst": achieved / peaks["bf16_tflops"],
-            "executed_per_algorithmic": EXECUTED_PER_ALG,
+            "executed_per_algorithmic": executed_per_alg(dom, inst.chi),
             "kernel_share": kms / sum(v[1] for v in prof.values()),
             "step_tflops": step_tf, "step_frac": step_tf / peak}
 
@@ -988,8 +991,8 @@ def run_dual(args):
         "lowest_combination": c0.tolist(),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "kernel": dom,
-                     "executed_frac": 6 * achieved / peak, "step_tflops": step_tf,
-                     "step_executed_frac": 6 * step_tf / peak,
+                     "executed_frac": executed_per_alg(dom, chi) * achieved / peak, "step_tflops": step_tf,
+                     "step_executed_frac": executed_per_alg(dom, chi) * step_tf / peak,
                      "peak_source": f"bf16 dense sustained ({kind}); fp16 = bf16 rate"},
         "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
         "gpu_launches": sum(v[0] for v in prof.values()), "clocks": clk,

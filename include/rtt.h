@@ -508,9 +508,9 @@ rtt_status rtt_tt_round_sum(rtt_tt_plan plan, const double *a, const uint8_t *op
 /* The local energy of rtt_local_energy (same kernels, same results) from a
  * call that allocates no device memory.  The paper has no counterpart: this
  * is an operational variant for callers that cannot allocate at the time of
- * the call -- code recorded into a CUDA graph by stream capture (no cudaMalloc
- * during capture), loops that forbid allocator calls after start-up, or
- * programs whose device memory is owned by an external pool manager.
+ * the call -- loops that forbid allocator calls after start-up, or programs
+ * whose device memory is owned by an external pool manager that must make
+ * every allocation itself.
  *   Scratch comes from one 32 MiB array compiled into the library as a device
  * global (every GPU that loads the library holds it until the process exits);
  * a batch whose scratch -- two stacks of B*N*chi_p values (8 B in FP64, 4 B in
@@ -533,6 +533,18 @@ rtt_status rtt_local_energy_noalloc(rtt_handle h, const uint8_t *spins, int64_t 
  * tensor memory and returned without writing results).  SYNCHRONOUS.
  * Returns RTT_ERR_TIMEOUT if bit 0 is set, and clears the flags. */
 rtt_status rtt_device_status(rtt_handle h, int32_t *flags);
+/* Failure-detection self-test (no counterpart in the paper: it exercises the
+ * path a tensor-core kernel takes when one of its bounded waits runs out).
+ * One warp arms an mbarrier that no copy and no MMA will ever arrive on and
+ * waits on it with a clock budget of budget_cycles; when the budget runs out
+ * it records bit 0 in the handle's device error word, frees the tensor memory
+ * it holds and returns.  Nothing asynchronous is in flight when it gives up,
+ * so the context stays usable: the next rtt_device_status returns
+ * RTT_ERR_TIMEOUT (and clears the flag) and later calls on the handle run
+ * normally.  budget_cycles in [1e3, 4e9] (SM clock cycles; 2e6 is about 1 ms)
+ * else RTT_ERR_INVALID_ARG; BF16X3 / FP16X3 handles only (RTT_ERR_UNSUPPORTED
+ * otherwise).  Asynchronous on `stream`. */
+rtt_status rtt_wait_selftest(rtt_handle h, int64_t budget_cycles, void *stream);
 
 /* Bytes of device scratch a handle holds for batches of B chains. */
 rtt_status rtt_scratch_bytes(rtt_handle h, int64_t B, size_t *bytes);

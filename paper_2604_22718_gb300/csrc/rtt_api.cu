@@ -879,6 +879,17 @@ rtt_status rtt_device_status(rtt_handle h, int32_t *flags) {
     return RTT_OK;
 }
 
+rtt_status rtt_wait_selftest(rtt_handle h, int64_t budget_cycles, void *stream) {
+    rtt_status s = check_handle(h);
+    if (s != RTT_OK) return s;
+    if (!h->tc)
+        return fail(RTT_ERR_UNSUPPORTED, "rtt_wait_selftest: needs a BF16X3 / FP16X3 handle");
+    if (budget_cycles < 1000 || budget_cycles > 4000000000LL)
+        return fail(RTT_ERR_INVALID_ARG, "rtt_wait_selftest: budget outside [1e3, 4e9] cycles");
+    DeviceGuard guard(h->device);
+    return tc_wait_selftest(h, (long long)budget_cycles, (cudaStream_t)stream);
+}
+
 rtt_status rtt_mcmc_uniforms(uint64_t seed, int64_t n, const uint64_t *counters, double *out,
                              void *stream) {
     g_last_error.clear();

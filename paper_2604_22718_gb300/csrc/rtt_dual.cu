@@ -273,11 +273,16 @@ extern "C" rtt_status rtt_dual_gram_schmidt(int32_t M, const double *St, int32_t
     rtt_set_error("");
     if (M < 1 || M > 8 || !St || !T)
         return dual_fail(RTT_ERR_INVALID_ARG, "rtt_dual_gram_schmidt: bad arguments (1 <= M <= 8)");
+    // every entry of S~ that T uses is checked before T is written, so an
+    // error leaves the caller's T untouched
+    for (int m = 0; m < M; ++m)
+        for (int a = 0; a < m; ++a)
+            if ((!first_only || a == 0) && !std::isfinite(St[a * M + m]))
+                return dual_fail(RTT_ERR_NUMERIC, "rtt_dual_gram_schmidt: non-finite S~");
     for (int m = 0; m < M; ++m)
         for (int a = 0; a < M; ++a) {
             double v = a == m ? 1.0 : 0.0;
             if (a < m && (!first_only || a == 0)) v = -St[a * M + m];
-            if (!std::isfinite(v)) return dual_fail(RTT_ERR_NUMERIC, "rtt_dual_gram_schmidt: non-finite S~");
             T[m * M + a] = v;
         }
     return RTT_OK;

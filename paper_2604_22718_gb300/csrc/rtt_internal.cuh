@@ -157,6 +157,7 @@ bool tc_supported_chi(int chi);
 // cuTensorMapEncodeTiled from the driver (null if unavailable); cast to its signature
 void *tc_encode_tiled_fn();
 int *tc_error_word(rtt_s *h);   // device error flags of the tensor-core kernels (or null)
+rtt_status tc_wait_selftest(rtt_s *h, long long budget_cycles, cudaStream_t st);
 
 // ----------------------------------------------------------------------------
 // Device helpers

@@ -1,11 +1,11 @@
 // rtt_noalloc.cu -- local energy that allocates no device memory.
 //
 // Some callers cannot allocate device memory at the moment they need a
-// local-energy evaluation: code recorded into a CUDA graph by stream capture
-// (cudaMalloc is not permitted while a stream is being captured), real-time
-// or embedded loops that forbid allocator calls after start-up, and programs
-// whose device memory is handed out by an external pool manager that must own
-// every allocation.  rtt_local_energy_noalloc serves them: it launches the
+// local-energy evaluation: real-time or embedded loops that forbid allocator
+// calls after start-up, and programs whose device memory is handed out by an
+// external pool manager that must own every allocation (a cudaMalloc behind
+// its back would break its accounting or fail against its reservation).
+// rtt_local_energy_noalloc serves them: it launches the
 // same kernels as rtt_local_energy (left and right environments, flip rows,
 // reduction), but their scratch comes from one fixed array compiled into the
 // library instead of the handle's on-demand scratch, so the call itself
@@ -99,6 +99,18 @@ extern "C" rtt_status rtt_local_energy_noalloc(rtt_handle h, const uint8_t *spin
     if (!h->periodic)
         return noalloc_fail(RTT_ERR_UNSUPPORTED,
                             "rtt_local_energy_noalloc: only periodic paths are supported");
+    // scratch bytes per chain before rounding: two stacks of N chi_p values,
+    // their int32 exponents, and the rows' mantissas and exponents; a batch
+    // beyond the area is rejected before any size is multiplied out, so no
+    // product below can wrap around
+    const size_t per_chain = (size_t)2 * h->N * h->chip * h->elem_bytes() + (size_t)8 * h->N +
+                             (size_t)16 * (h->N + 1);
+    if ((uint64_t)B > RTT_NOALLOC_SCRATCH_BYTES / per_chain)
+        return noalloc_fail(RTT_ERR_INVALID_ARG,
+                            "rtt_local_energy_noalloc: B = " + std::to_string(B) + " needs at least " +
+                                std::to_string(per_chain) + " bytes of scratch per chain; the "
+                                "static area holds " + std::to_string(RTT_NOALLOC_SCRATCH_BYTES) +
+                                " bytes; split the batch");
     const NoallocLayout lay = layout_for(h, B);
     if (lay.total > RTT_NOALLOC_SCRATCH_BYTES) {
         const NoallocLayout one = layout_for(h, 1);

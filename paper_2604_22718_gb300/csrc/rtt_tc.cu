@@ -35,10 +35,17 @@
 struct TcPlan {
     int chi = 0;
     bool f16 = false;              // FP16 operands (else BF16)
-    uint16_t *d_B = nullptr;       // [4][L][2chi][chi]: BT hi, BT lo, B hi, B lo
+    // dense operand (chi = 64 split-row sweep): [4][L][2chi][chi], rows = output
+    // (s, b) of the left-to-right form (planes 0 hi, 1 lo) or (s, a) of the
+    // right-to-left form (planes 2, 3), K = the contracted index
+    uint16_t *d_B = nullptr;
+    CUtensorMap map;
+    // sparse operand (k_tc): [4][L][chi][2chi], rows = output b (planes 0, 1)
+    // or a (planes 2, 3), K = 2 x + s over the contracted index x and slice s
+    uint16_t *d_Bs = nullptr;
+    CUtensorMap map_sp;
     int32_t *d_cexp = nullptr;     // [L] prescale exponents c_k
     float *d_bl = nullptr, *d_br = nullptr;
-    CUtensorMap map;
     float *d_tmp = nullptr;  // [B][chi] sweep scratch (flipped start of a row)
     int32_t *d_tmp_exp = nullptr;
     int64_t tmp_cap = 0;
@@ -58,8 +65,6 @@ enum { M_ROWS = 0, M_LEFT = 1, M_RIGHT = 2, M_INIT = 3, M_SWEEP = 4 };
 template <int CHI, bool F16 = false>
 struct Cfg {
     static constexpr int KA = CHI / 64;            // 64-element K atoms per row
-    static constexpr int A_ATOM = 128 * 128;       // bytes: 128 rows x 128 B
-    static constexpr int A_BYTES = KA * A_ATOM;    // one of hi / lo
     static constexpr int BOX = 2 * CHI * 128;      // bytes: 2chi rows x 128 B
     static constexpr int STAGE = 2 * BOX;          // hi box + lo box
     static constexpr int TCOLS = 2 * CHI;          // accumulator columns
@@ -73,6 +78,63 @@ struct Cfg {
     static constexpr int CTRL = 128;
     static size_t smem_bytes(int N, int L) {
         return 1024 + (size_t)NS * STAGE + CTRL + (size_t)16 * N + (size_t)4 * L;
+    }
+};
+
+// The sparse form of a site product (generic tile kernel k_tc).  A row needs
+// only the slice of its spin, so the two slices are interleaved along K
+// (K index 2a + s, K = 2chi) and the row operand is 2:4 sparse: in every
+// group of four K entries (a, a+1 with both slices) the row keeps the two of
+// its slice.  tcgen05.mma.sp reads the row's chi values as the compressed
+// operand and a per-row metadata word that names the kept positions of each
+// group -- (0,2) for slice 0, (1,3) for slice 1 -- and runs at twice the dense
+// rate: one MMA of N = chi, logical K = 32 per 16 row entries, and the
+// accumulator holds exactly the selected product (no discarded half).
+//
+// Metadata in tensor memory (measured on GB300 with one-row-per-lane words
+// that differ from lane to lane, M = 128, K = 32 per instruction): row m's
+// 32-bit metadata (nibble g = group g: first kept position in bits 0-1,
+// second in bits 2-3) is not lane m's column entry.  Within the row's 32-lane
+// group, with i = m mod 32 = 16u + 8v + w, its low 16 bits are half v of
+// lane 16u + w and its high 16 bits half v of lane 16u + 8 + w.  A slice
+// word has equal halves (0x8888 | 0x8888 << 16 or 0xDDDD | 0xDDDD << 16), so
+// lane l = 16u + 8t + w holds, in half v, the 16-bit pattern of row
+// 16u + 8v + w -- assembled with two shuffles.  The metadata column address
+// must be aligned: every column used here is a multiple of 64.
+template <int CHI, bool F16 = false>
+struct SCfg {
+    // B-operand ring stages of one 64-element K atom (hi and lo boxes): each
+    // atom's stage is refilled with the next site's atom as soon as the MMAs
+    // that read it complete (six stages at chi = 128 measured slower)
+    static constexpr int NSTG = 4;
+    static constexpr int KA = 2 * CHI / 64;        // 64-element K atoms per site
+    static constexpr int BOX = CHI * 128;          // bytes: chi rows x 128 B
+    static constexpr int STAGE = 2 * BOX;          // hi box + lo box
+    static constexpr int ACC2 = CHI;               // second accumulator (sweep: unflipped l_j)
+    static constexpr int A_COL = 2 * CHI;          // row hi at A_COL, lo at A_COL + CHI/2
+    static constexpr int META = 3 * CHI;           // metadata of ACC (a multiple of 64)
+    static constexpr int META2 = META + 64;        // metadata of ACC2 (sweep only)
+    // columns allocated: a power of two covering what the mode uses
+    static constexpr uint32_t TALLOC = META + 1 <= 256 ? 256u : 512u;
+    static constexpr uint32_t TALLOC_SWEEP = META2 + 1 <= 256 ? 256u : 512u;
+    // kind::f16, 2:4 sparse A (bit 2, selector 0), (BF16 or FP16) x same ->
+    // FP32, both K-major, N = chi, M = 128
+    static constexpr uint32_t FMT = F16 ? 0u : 1u;
+    static constexpr uint32_t IDESC = (1u << 2) | (1u << 4) | (FMT << 7) | (FMT << 10) |
+                                      ((uint32_t)(CHI >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    static constexpr uint32_t HALF0 = 0x8888u;  // groups keep positions (0, 2): slice 0
+    static constexpr uint32_t HALF1 = 0xDDDDu;  // positions (1, 3): slice 1
+    static constexpr int CTRL = 128;
+    // epilogue: NH warps per TMEM lane quadrant (one: with a separate producer
+    // warp, two per quadrant would cap the registers below what the sweep
+    // needs), each thread owning CPT 64-column chunks of its row; with NH = 2
+    // the halves of a row exchange the row maximum (two kinds per site) and the
+    // closing dot product
+    static constexpr int NH = 1;
+    static constexpr int CPT = CHI / 64 / NH;
+    static constexpr int XCH = NH * 128 * (2 * 4 + 8);
+    static size_t smem_bytes(int N, int L) {
+        return 1024 + (size_t)NSTG * STAGE + CTRL + (size_t)16 * N + (size_t)4 * L + 16 + XCH;
     }
 };
 
@@ -110,110 +172,101 @@ struct Args {
 };
 
 // PTX wrappers: rtt_tcgen05.cuh
-__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
-                                             uint32_t d) {
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
-                 "r"(d)
-                 : "memory");
-}
-
-// Two 64-column loads (32x32b.x64) -- the same column block of both
-// accumulator halves -- and the wait, in one statement.
-__device__ __forceinline__ void tmem_ld_2x64(uint32_t t0, uint32_t t1, uint32_t (&x)[64],
-                                             uint32_t (&y)[64]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%128];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-        "{%64,%65,%66,%67,%68,%69,%70,%71,%72,%73,%74,%75,%76,%77,%78,%79,"
-        "%80,%81,%82,%83,%84,%85,%86,%87,%88,%89,%90,%91,%92,%93,%94,%95,"
-        "%96,%97,%98,%99,%100,%101,%102,%103,%104,%105,%106,%107,%108,%109,%110,%111,"
-        "%112,%113,%114,%115,%116,%117,%118,%119,%120,%121,%122,%123,%124,%125,%126,%127}, [%129];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]),
-          "=r"(x[7]), "=r"(x[8]), "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]),
-          "=r"(x[13]), "=r"(x[14]), "=r"(x[15]), "=r"(x[16]), "=r"(x[17]), "=r"(x[18]),
-          "=r"(x[19]), "=r"(x[20]), "=r"(x[21]), "=r"(x[22]), "=r"(x[23]), "=r"(x[24]),
-          "=r"(x[25]), "=r"(x[26]), "=r"(x[27]), "=r"(x[28]), "=r"(x[29]), "=r"(x[30]),
-          "=r"(x[31]), "=r"(x[32]), "=r"(x[33]), "=r"(x[34]), "=r"(x[35]), "=r"(x[36]),
-          "=r"(x[37]), "=r"(x[38]), "=r"(x[39]), "=r"(x[40]), "=r"(x[41]), "=r"(x[42]),
-          "=r"(x[43]), "=r"(x[44]), "=r"(x[45]), "=r"(x[46]), "=r"(x[47]), "=r"(x[48]),
-          "=r"(x[49]), "=r"(x[50]), "=r"(x[51]), "=r"(x[52]), "=r"(x[53]), "=r"(x[54]),
-          "=r"(x[55]), "=r"(x[56]), "=r"(x[57]), "=r"(x[58]), "=r"(x[59]), "=r"(x[60]),
-          "=r"(x[61]), "=r"(x[62]), "=r"(x[63]), "=r"(y[0]), "=r"(y[1]), "=r"(y[2]),
-          "=r"(y[3]), "=r"(y[4]), "=r"(y[5]), "=r"(y[6]), "=r"(y[7]), "=r"(y[8]), "=r"(y[9]),
-          "=r"(y[10]), "=r"(y[11]), "=r"(y[12]), "=r"(y[13]), "=r"(y[14]), "=r"(y[15]),
-          "=r"(y[16]), "=r"(y[17]), "=r"(y[18]), "=r"(y[19]), "=r"(y[20]), "=r"(y[21]),
-          "=r"(y[22]), "=r"(y[23]), "=r"(y[24]), "=r"(y[25]), "=r"(y[26]), "=r"(y[27]),
-          "=r"(y[28]), "=r"(y[29]), "=r"(y[30]), "=r"(y[31]), "=r"(y[32]), "=r"(y[33]),
-          "=r"(y[34]), "=r"(y[35]), "=r"(y[36]), "=r"(y[37]), "=r"(y[38]), "=r"(y[39]),
-          "=r"(y[40]), "=r"(y[41]), "=r"(y[42]), "=r"(y[43]), "=r"(y[44]), "=r"(y[45]),
-          "=r"(y[46]), "=r"(y[47]), "=r"(y[48]), "=r"(y[49]), "=r"(y[50]), "=r"(y[51]),
-          "=r"(y[52]), "=r"(y[53]), "=r"(y[54]), "=r"(y[55]), "=r"(y[56]), "=r"(y[57]),
-          "=r"(y[58]), "=r"(y[59]), "=r"(y[60]), "=r"(y[61]), "=r"(y[62]), "=r"(y[63])
-        : "r"(t0), "r"(t1)
-        : "memory");
-}
-
 // ------------------------------------------------------------------ row helpers
-// Accumulator half `sel` (0: columns [0,chi), 1: [chi,2chi)) of this thread's
-// TMEM lane.  The column address of tcgen05.ld is warp-uniform, so both halves
-// are loaded and the row's half is selected in registers.
-template <int CHI>
-__device__ __forceinline__ void acc_select(uint32_t tw, int sel, float (&v)[CHI]) {
-    if constexpr (CHI == 64) {
-        uint32_t x0[64], x1[64];
-        tmem_ld_2x64(tw, tw + CHI, x0, x1);
+// ---- 64-column chunks of a row (the epilogue never holds a whole chi = 128
+// row in registers)
+__device__ __forceinline__ void tmem_ld_64(uint32_t t, float (&y)[64]) {
+    uint32_t x0[32], x1[32];
+    tmem_ld_2x32(t, t + 32, x0, x1);
 #pragma unroll
-        for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(sel ? x1[i] : x0[i]);
-    } else {
-#pragma unroll
-        for (int c = 0; c < CHI; c += 32) {
-            uint32_t x0[32], x1[32];
-            tmem_ld_2x32(tw + c, tw + CHI + c, x0, x1);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[c + i] = __uint_as_float(sel ? x1[i] : x0[i]);
-        }
+    for (int i = 0; i < 32; ++i) {
+        y[i] = __uint_as_float(x0[i]);
+        y[32 + i] = __uint_as_float(x1[i]);
     }
 }
-
-// Rescale by an exact power of two so that max|v| lies in [1,2) (or leave
-// the row alone while max|v| is in [1, 2^8), see below); returns the exponent
-// taken out.  Eight independent partial maxima keep the dependency chain short.
-template <int CHI, bool LAZY = true>
-__device__ __forceinline__ int renorm(float (&v)[CHI]) {
+// The exponent the per-site renormalisation takes out of the row held in the
+// accumulator at t: max|v| brought into [1, 2) by 2^-e, or 0 when every row of
+// the warp keeps its scale (max in [1, 2^8): its 16-bit split stays inside
+// FP16's normal range with full precision relative to the max, and the next
+// site's FP32 accumulator is looked at again).  Eight partial maxima.
+template <int CHI>
+__device__ __forceinline__ int acc_exponent(uint32_t t) {
     float m[8];
 #pragma unroll
-    for (int p = 0; p < 8; ++p) m[p] = fabsf(v[p]);
+    for (int c = 0; c < CHI / 64; ++c) {
+        float y[64];
+        tmem_ld_64(t + 64 * c, y);
 #pragma unroll
-    for (int i = 8; i < CHI; ++i) m[i & 7] = fmaxf(m[i & 7], fabsf(v[i]));
+        for (int i = 0; i < 64; ++i) m[i & 7] = (c == 0 && i < 8) ? fabsf(y[i]) : fmaxf(m[i & 7], fabsf(y[i]));
+    }
     const float mx = fmaxf(fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3])),
                            fmaxf(fmaxf(m[4], m[5]), fmaxf(m[6], m[7])));
     const bool usable = (mx > 0.f) && isfinite(mx);
     const int e = usable ? rttd::exponent_of(mx) : 0;
-    // A row whose max lies in [1, 2^8) can keep its scale: its 16-bit split is
-    // inside FP16's normal range with full precision relative to the max, and
-    // the next site's accumulator (FP32) is rescaled again before its split
-    // unless it too lands in the window.  The warp skips the rescale when all
-    // of its rows can (all lanes of the warp call this together).
-    if (LAZY && __all_sync(FULL, !usable || (e >= 0 && e < 8))) return 0;
-    if (!usable) return 0;
-    if (rttd::pow2_normal(0.f, -e)) {  // one exact multiply per entry
+    if (__all_sync(FULL, !usable || (e >= 0 && e < 8))) return 0;
+    return usable ? e : 0;
+}
+// y <- y 2^-e (exact; e = 0 leaves y)
+__device__ __forceinline__ void scale_chunk(float (&y)[64], int e) {
+    if (e == 0) return;
+    if (rttd::pow2_normal(0.f, -e)) {
         const float sc = rttd::pow2(0.f, -e);
 #pragma unroll
-        for (int i = 0; i < CHI; ++i) v[i] *= sc;
+        for (int i = 0; i < 64; ++i) y[i] *= sc;
     } else {
 #pragma unroll
-        for (int i = 0; i < CHI; ++i) v[i] = rttd::scale2(v[i], -e);
+        for (int i = 0; i < 64; ++i) y[i] = rttd::scale2(y[i], -e);
     }
-    return e;
+}
+__device__ __forceinline__ void load_chunk(const float *__restrict__ p, float (&y)[64]) {
+    const float4 *p4 = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float4 x = p4[i];
+        y[4 * i] = x.x;
+        y[4 * i + 1] = x.y;
+        y[4 * i + 2] = x.z;
+        y[4 * i + 3] = x.w;
+    }
+}
+__device__ __forceinline__ void store_chunk(float *__restrict__ p, const float (&y)[64]) {
+    float4 *p4 = reinterpret_cast<float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) p4[i] = make_float4(y[4 * i], y[4 * i + 1], y[4 * i + 2], y[4 * i + 3]);
+}
+// Chunk c of the closing contraction sum_b v_b r_b into eight FP32 partial
+// sums (r points at entry 64 c); dot_finish combines them in FP64.  The
+// partial a term goes to depends only on its index, so the chunks add up in
+// the order of one pass over the whole row.
+__device__ __forceinline__ void dot_chunk(const float (&y)[64], const float *__restrict__ r,
+                                          float (&acc)[8]) {
+    const float4 *r4 = reinterpret_cast<const float4 *>(r);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float4 x = r4[i];
+        const int p = (2 * i) & 7;
+        acc[p] = fmaf(y[4 * i], x.x, acc[p]);
+        acc[p + 1] = fmaf(y[4 * i + 1], x.y, acc[p + 1]);
+        acc[(p + 2) & 7] = fmaf(y[4 * i + 2], x.z, acc[(p + 2) & 7]);
+        acc[(p + 3) & 7] = fmaf(y[4 * i + 3], x.w, acc[(p + 3) & 7]);
+    }
+}
+__device__ __forceinline__ double dot_finish(const float (&acc)[8]) {
+    double s = 0.0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) s += (double)acc[p];
+    return s;
 }
 
-// Split the row into 16-bit hi/lo and store it as row m of the A operand
-// (K-major, 128-byte swizzle: 16-byte chunk c of row m sits at c ^ (m & 7)).
+// One 32-bit column of this warp's 32 TMEM lanes, then wait.
+__device__ __forceinline__ void tmem_st_1(uint32_t t, uint32_t x) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(t), "r"(x)
+        : "memory");
+}
+
+// Split two entries into 16-bit hi/lo (x = hi + lo + O(u^2 |x|)).
 template <bool F16>
 __device__ __forceinline__ void split2(float x0, float x1, uint32_t &h, uint32_t &l) {
     if (F16) {
@@ -228,24 +281,6 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t &h, uint32_t
         const __nv_bfloat162 lb = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
         h = *reinterpret_cast<const uint32_t *>(&hb);
         l = *reinterpret_cast<const uint32_t *>(&lb);
-    }
-}
-
-template <int CHI, bool F16>
-__device__ __forceinline__ void write_A(uint32_t a_hi, uint32_t a_lo, int m, const float (&v)[CHI]) {
-#pragma unroll
-    for (int at = 0; at < CHI / 64; ++at) {
-#pragma unroll
-        for (int ch = 0; ch < 8; ++ch) {
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-                split2<F16>(v[at * 64 + ch * 8 + 2 * p], v[at * 64 + ch * 8 + 2 * p + 1], h[p], l[p]);
-            const uint32_t off =
-                (uint32_t)(at * Cfg<CHI>::A_ATOM + m * 128 + ((ch ^ (m & 7)) << 4));
-            st_shared_v4(a_hi + off, h[0], h[1], h[2], h[3]);
-            st_shared_v4(a_lo + off, l[0], l[1], l[2], l[3]);
-        }
     }
 }
 
@@ -267,29 +302,6 @@ __device__ __forceinline__ void store_vec(float *__restrict__ p, const float (&v
 #pragma unroll
     for (int i = 0; i < CHI / 4; ++i) p4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
 }
-// Closing contraction sum_b v_b r_b: eight FP32 partial sums (fma), combined
-// in FP64.
-template <int CHI>
-__device__ __forceinline__ double dot(const float (&v)[CHI], const float *__restrict__ r) {
-    float acc[8];
-#pragma unroll
-    for (int p = 0; p < 8; ++p) acc[p] = 0.f;
-    const float4 *r4 = reinterpret_cast<const float4 *>(r);
-#pragma unroll
-    for (int i = 0; i < CHI / 4; ++i) {
-        const float4 x = r4[i];
-        const int p = (2 * i) & 7;
-        acc[p] = fmaf(v[4 * i], x.x, acc[p]);
-        acc[p + 1] = fmaf(v[4 * i + 1], x.y, acc[p + 1]);
-        acc[(p + 2) & 7] = fmaf(v[4 * i + 2], x.z, acc[(p + 2) & 7]);
-        acc[(p + 3) & 7] = fmaf(v[4 * i + 3], x.w, acc[(p + 3) & 7]);
-    }
-    double s = 0.0;
-#pragma unroll
-    for (int p = 0; p < 8; ++p) s += (double)acc[p];
-    return s;
-}
-
 __device__ __forceinline__ void normalize_scalar(double &m, int64_t &e) {
     if (m == 0.0 || !isfinite(m)) return;
     const int k = rttd::exponent_of(m);
@@ -306,19 +318,27 @@ __device__ __forceinline__ void tmem_st_2x32(uint32_t t0, uint32_t t1, const uin
         "tcgen05.wait::st.sync.aligned;" ::"r"(t0), "r"(t1), "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(x[7]), "r"(x[8]), "r"(x[9]), "r"(x[10]), "r"(x[11]), "r"(x[12]), "r"(x[13]), "r"(x[14]), "r"(x[15]), "r"(x[16]), "r"(x[17]), "r"(x[18]), "r"(x[19]), "r"(x[20]), "r"(x[21]), "r"(x[22]), "r"(x[23]), "r"(x[24]), "r"(x[25]), "r"(x[26]), "r"(x[27]), "r"(x[28]), "r"(x[29]), "r"(x[30]), "r"(x[31]), "r"(y[0]), "r"(y[1]), "r"(y[2]), "r"(y[3]), "r"(y[4]), "r"(y[5]), "r"(y[6]), "r"(y[7]), "r"(y[8]), "r"(y[9]), "r"(y[10]), "r"(y[11]), "r"(y[12]), "r"(y[13]), "r"(y[14]), "r"(y[15]), "r"(y[16]), "r"(y[17]), "r"(y[18]), "r"(y[19]), "r"(y[20]), "r"(y[21]), "r"(y[22]), "r"(y[23]), "r"(y[24]), "r"(y[25]), "r"(y[26]), "r"(y[27]), "r"(y[28]), "r"(y[29]), "r"(y[30]), "r"(y[31])
         : "memory");
 }
-// Row m of the A operand in TMEM: the 16-bit hi/lo split of v, entries 2c and
-// 2c+1 in column c (lower index in the low half), hi at t_hi, lo at
-// t_hi + CHI/2.
+// Chunk c (entries 64 c .. 64 c + 63) of the row as the A operand in TMEM,
+// row m in lane m: the 16-bit hi/lo split, entries 2i and 2i+1 in one column
+// (lower index in the low half), hi at t_hi + 32 c, lo at t_hi + CHI/2 + 32 c.
 template <int CHI, bool F16>
-__device__ __forceinline__ void write_A_tmem(uint32_t t_hi, const float (&v)[CHI]) {
+__device__ __forceinline__ void write_A_chunk(uint32_t t_hi, int c, const float (&y)[64]) {
+    uint32_t h[32], l[32];
 #pragma unroll
-    for (int c0 = 0; c0 < CHI; c0 += 64) {
-        uint32_t h[32], l[32];
+    for (int p = 0; p < 32; ++p) split2<F16>(y[2 * p], y[2 * p + 1], h[p], l[p]);
+    tmem_st_2x32(t_hi + (uint32_t)(32 * c), t_hi + (uint32_t)(CHI / 2 + 32 * c), h, l);
+}
+// The A operand from a row in global memory (chunk by chunk).
+template <int CHI, bool F16>
+__device__ __forceinline__ void write_A_from(uint32_t t_hi, const float *__restrict__ p) {
 #pragma unroll
-        for (int p = 0; p < 32; ++p) split2<F16>(v[c0 + 2 * p], v[c0 + 2 * p + 1], h[p], l[p]);
-        tmem_st_2x32(t_hi + (uint32_t)(c0 / 2), t_hi + (uint32_t)(CHI / 2 + c0 / 2), h, l);
+    for (int c = 0; c < CHI / 64; ++c) {
+        float y[64];
+        load_chunk(p + 64 * c, y);
+        write_A_chunk<CHI, F16>(t_hi, c, y);
     }
 }
+
 // D (+)= A . B with A read from TMEM (K-major rows in TMEM lanes) and B from a
 // shared-memory descriptor.
 __device__ __forceinline__ void mma_f16_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc,
@@ -328,6 +348,23 @@ __device__ __forceinline__ void mma_f16_ts(uint32_t d, uint32_t a_tmem, uint64_t
         "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
         "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum)
         : "memory");
+}
+
+// D (+)= A . B with A 2:4 sparse: its compressed entries read from TMEM (row
+// m in lane m), the positions they take from the per-lane metadata column at
+// `meta`, B dense from a shared-memory descriptor.
+__device__ __forceinline__ void mma_sp_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t meta,
+                                          uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %5, 0;\n\t"
+        "tcgen05.mma.sp.cta_group::1.kind::f16 [%0], [%1], %2, [%3], %4, p;\n\t}" ::"r"(d),
+        "r"(a_tmem), "l"(b), "r"(meta), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+// Named barrier over n threads (id 1..15; id 0 is __syncthreads).
+__device__ __forceinline__ void bar_sync_n(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
 // ------------------------------------------------------------------ site program
@@ -413,28 +450,53 @@ __device__ __forceinline__ long long n_steps_of(const Args &a, int j) {
 }
 
 // ------------------------------------------------------------------ kernel
+// One 128-chain tile per CTA (row m = TMEM lane m).  A producer warp (lane 0)
+// streams the site tensors by TMA into a ring of NSTG stages and issues the
+// sparse MMAs of each site, refilling each stage while the epilogue of the
+// site runs; the epilogue runs on NH = chi/64 warps per TMEM lane quadrant, warp
+// (quadrant q, half h) owning rows 32q..32q+31 and columns [64h, 64h+64):
+// each thread loads its 64 accumulator columns once, the two halves of a row
+// agree on the row maximum (renormalisation) and, at a decision, on the
+// closing dot product through shared memory (a 32 NH-thread named barrier
+// per quadrant); then each scales its chunk, writes it into the next A
+// operand and into the stacks.  The h = 0 warps keep the spin bits and write
+// the next site's metadata.  In the sweep, the first site of a proposal row
+// is contracted with both slices (two accumulators): the kept continuation
+// l_j and the flipped start of the row.
 template <int CHI, int MODE, bool F16>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT * SCfg<CHI, F16>::NH + 32, 1)
     k_tc(const __grid_constant__ CUtensorMap map, const Args a) {
-    using C = Cfg<CHI, F16>;
+    using C = SCfg<CHI, F16>;
+    constexpr int NSG = C::NSTG;
+    constexpr int NH = C::NH;
+    constexpr int CPT = C::CPT;
+    constexpr int NTH = NT * NH + 32;  // epilogue warps and the producer warp
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t stage0 = sa(base);
-    uint64_t *bars = (uint64_t *)(base + NS * C::STAGE);
+    uint64_t *bars = (uint64_t *)(base + NSG * C::STAGE);
     const uint32_t bar0 = sa(bars);
-    // bars: full[0..NS), empty[0..NS), mma_done
+    // bars: full[0..NSG), empty[0..NSG), mma_done
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
-    auto empty_bar = [&](int s) { return bar0 + 8u * (NS + s); };
-    const uint32_t done_bar = bar0 + 8u * (2 * NS);
-    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NS + 1);
+    auto empty_bar = [&](int s) { return bar0 + 8u * (NSG + s); };
+    const uint32_t done_bar = bar0 + 8u * (2 * NSG);
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NSG + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
-    uint32_t *bits = (uint32_t *)(base + NS * C::STAGE + C::CTRL);
+    uint32_t *bits = (uint32_t *)(base + NSG * C::STAGE + C::CTRL);
     // site table: low 16 bits spin q[k mod N], high 16 bits the prescale c_k
     uint32_t *tab = bits + 4 * a.N;
+    // exchange slots: row maxima [2 kinds][NH][128], dot products [NH][128]
+    float *xmax = (float *)(((uintptr_t)(tab + a.L) + 15) & ~(uintptr_t)15);
+    double *xdot = (double *)(xmax + 2 * NH * NT);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t c_raw = (int64_t)blockIdx.x * NT + tid;
+    const bool epi = warp < 4 * NH;         // an epilogue warp (else the producer)
+    const bool issuer = warp == 4 * NH && lane == 0;
+    const int q = warp & 3, h = epi ? warp >> 2 : 0;  // TMEM lane quadrant, column half
+    const int m = 32 * q + lane;            // row of the tile
+    const int64_t c_raw = (int64_t)blockIdx.x * NT + m;
     const bool active = c_raw < a.B;
+    const bool lead = epi && active && h == 0;  // the thread that writes the row's scalars
     const int64_t c = active ? c_raw : a.B - 1;
     const int j = (MODE == M_ROWS) ? (int)blockIdx.y : 0;
     const int N = a.N;
@@ -443,9 +505,10 @@ __global__ void __launch_bounds__(NT, 1)
     const long long total_steps = n_steps_of<MODE>(a, j);
     const long long total_atoms = total_steps * C::KA;
 
-    if (warp == 0) tmem_alloc(sa(tmem_slot), C::TALLOC);
-    if (tid == 0) {
-        for (int s = 0; s < NS; ++s) {
+    constexpr uint32_t TALLOC = MODE == M_SWEEP ? C::TALLOC_SWEEP : C::TALLOC;
+    if (warp == 0) tmem_alloc(sa(tmem_slot), TALLOC);
+    if (issuer) {
+        for (int s = 0; s < NSG; ++s) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
@@ -453,54 +516,135 @@ __global__ void __launch_bounds__(NT, 1)
         *abort_flag = 0;
         fence_barrier_init();
     }
-    for (int k = tid; k < a.L; k += NT)
+    for (int k = tid; k < a.L; k += NTH)
         tab[k] = ((uint32_t)__ldg(a.path ? a.path + k : a.q + (k % N)) & 0xffffu) |
                  ((uint32_t)(__ldg(a.cexp + k) & 0xffff) << 16);
-    // spin bits: word (i, warp) holds bit (row & 31) = s_i of that row's chain
-    for (int i = 0; i < N; ++i) {
-        const uint32_t w = __ballot_sync(FULL, a.spins_in[c * N + i] != 0);
-        if (lane == 0) bits[i * 4 + warp] = w;
+    // spin bits: word (i, quadrant) holds bit (row & 31) = s_i of that row's chain
+    if (epi && h == 0) {
+        for (int i = 0; i < N; ++i) {
+            const uint32_t w = __ballot_sync(FULL, a.spins_in[c * N + i] != 0);
+            if (lane == 0) bits[i * 4 + q] = w;
+        }
     }
-    auto spin = [&](int i) -> int { return (int)((bits[i * 4 + warp] >> lane) & 1u); };
+    auto spin = [&](int i) -> int { return (int)((bits[i * 4 + q] >> lane) & 1u); };
     auto site_spin = [&](int k) -> int { return (int)(tab[k] & 0xffffu); };
     auto site_cexp = [&](int k) -> int { return (int)(int16_t)(tab[k] >> 16); };
+    const int iflip = (MODE == M_ROWS && j < N) ? (int)(__ldg(a.path ? a.path + j : a.q + j)) : -1;
+    // the slice this row takes at the site of cursor x (the flipped spin's
+    // slice is the other one); in the sweep the first site of a row also
+    // takes the kept slice, into the second accumulator
+    auto slice_of = [&](const Cursor &x) -> int {
+        const int sk = site_spin(x.k);
+        if (MODE == M_ROWS) return spin(sk) ^ (sk == iflip ? 1 : 0);
+        if (MODE == M_SWEEP && x.form == 0) return spin(sk) ^ (sk == site_spin(x.jj) ? 1 : 0);
+        return spin(sk);
+    };
+    // the halves of a row agree on its maximum and on its closing dot product
+    auto row_max = [&](float mx, int kind) -> float {
+        if (NH == 1) return mx;
+        xmax[(kind * NH + h) * NT + m] = mx;
+        bar_sync_n(1 + q, 32 * NH);
+        return fmaxf(mx, xmax[(kind * NH + (h ^ 1)) * NT + m]);
+    };
+    auto row_dot = [&](double s) -> double {
+        if (NH == 1) return s;
+        xdot[h * NT + m] = s;
+        bar_sync_n(1 + q, 32 * NH);
+        return xdot[m] + xdot[NT + m];
+    };
 
-    // start vector
-    float v[CHI];
+    // start row: written straight into the A operand (and, for the right
+    // environments, b_R as the stack's last entry)
     int64_t E = 0;      // exponent of the current row
     int64_t El = 0;     // sweep: exponent of l_{jj-1}
     int64_t Ekeep = 0, Eflip = 0;
     double pm = 0.0;
     int64_t pe = 0, acc_count = 0;
-    if (MODE == M_ROWS) {
-        if (j == 0) {
-            load_vec<CHI>(a.bl, v);
-        } else {
-            const size_t jm = (size_t)(j > 0 ? j - 1 : 0);
-            load_vec<CHI>(a.lstack + ((size_t)c * N + jm) * CHI, v);
-            E = a.lexp[(size_t)c * N + jm];
-        }
+    double fin_m = 0.0;  // rows / amplitude: the closing contraction
+    int64_t fin_E = 0;
+    const float *start = a.bl;
+    if (MODE == M_ROWS && j > 0) {
+        start = a.lstack + ((size_t)c * N + (j - 1)) * CHI;
+        E = a.lexp[(size_t)c * N + (j - 1)];
     } else if (MODE == M_RIGHT || MODE == M_SWEEP) {
-        load_vec<CHI>(a.br, v);
-        if (active) {
-            store_vec<CHI>(a.rstack + ((size_t)c * a.nr + (a.nr - 1)) * CHI, v);
-            a.rexp[(size_t)c * a.nr + (a.nr - 1)] = 0;
+        if (epi && active) {
+#pragma unroll 1
+            for (int ch = 0; ch < CPT; ++ch) {
+                const int o = 64 * (h * CPT + ch);
+                float y[64];
+                load_chunk(a.br + o, y);
+                store_chunk(a.rstack + ((size_t)c * a.nr + (a.nr - 1)) * CHI + o, y);
+            }
+            if (h == 0) a.rexp[(size_t)c * a.nr + (a.nr - 1)] = 0;
         }
+        start = (MODE == M_SWEEP && N == 1) ? a.bl : a.br;  // N = 1: no right-environment steps
         if (MODE == M_SWEEP) {
             pm = a.state[c].mant;
             pe = a.state[c].exp2;
-            if (N == 1) load_vec<CHI>(a.bl, v);  // no right-environment steps
         }
-    } else {
-        load_vec<CHI>(a.bl, v);
     }
     tc_before();
     __syncthreads();
     tc_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t tw = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's lanes
-    const uint32_t ta = tw + (uint32_t)C::A_COL;                // this warp's rows of A
-    if (total_steps > 0) write_A_tmem<CHI, F16>(ta, v);
+    const uint32_t tw = tmem + ((uint32_t)(q * 32) << 16);  // this warp's lanes
+    const uint32_t ta = tw + (uint32_t)C::A_COL;             // their rows of A
+    const uint32_t tm = tw + (uint32_t)C::META;              // their metadata
+    Cursor cc = cursor_start<MODE>(a, j);
+    // metadata of the next site (h = 0 warps): lane l carries the 16-bit slice
+    // patterns of rows (l & 16) | (l & 7) and that row + 8 of its quadrant
+    const int lane_a = (lane & 16) | (lane & 7), lane_b = lane_a | 8;
+    auto write_meta = [&](const Cursor &x) {
+        if (!epi || h != 0) return;
+        const int sl = slice_of(x);
+        const int s_a = __shfl_sync(FULL, sl, lane_a), s_b = __shfl_sync(FULL, sl, lane_b);
+        tmem_st_1(tm, (s_a ? C::HALF1 : C::HALF0) | ((s_b ? C::HALF1 : C::HALF0) << 16));
+        if (MODE == M_SWEEP && x.form == 0 && x.i == 0)  // the kept slice, second accumulator
+            tmem_st_1(tm + (uint32_t)(C::META2 - C::META),
+                      (s_a ? C::HALF0 : C::HALF1) | ((s_b ? C::HALF0 : C::HALF1) << 16));
+    };
+    // the exponent the renormalisation takes out of this row, held in the
+    // accumulator at column col (first pass over the thread's chunks; kind:
+    // exchange slot): max|v| brought into [1, 2), or 0 while every row of the
+    // quadrant has its max in [1, 2^8) -- its 16-bit split stays inside FP16's
+    // normal range with full precision relative to the max
+    auto row_exp = [&](uint32_t col, int kind) -> int {
+        float m8[8];
+#pragma unroll 1
+        for (int ch = 0; ch < CPT; ++ch) {
+            float y[64];
+            tmem_ld_64(tw + col + (uint32_t)(64 * (h * CPT + ch)), y);
+#pragma unroll
+            for (int i = 0; i < 64; ++i)
+                m8[i & 7] = (ch == 0 && i < 8) ? fabsf(y[i]) : fmaxf(m8[i & 7], fabsf(y[i]));
+        }
+        const float part = fmaxf(fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3])),
+                                 fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7])));
+        const float mx = row_max(part, kind);
+        const bool usable = (mx > 0.f) && isfinite(mx);
+        int e = usable ? rttd::exponent_of(mx) : 0;
+        if (__all_sync(FULL, !usable || (e >= 0 && e < 8)) || !usable) e = 0;
+        return e;
+    };
+    // chunk ch of this thread (row entries o .. o + 63), scaled by 2^-e
+    auto row_chunk = [&](uint32_t col, int e, int ch, float (&y)[64]) {
+        tmem_ld_64(tw + col + (uint32_t)(64 * (h * CPT + ch)), y);
+        scale_chunk(y, e);
+    };
+    // a row in global memory into the A operand
+    auto write_A_row = [&](const float *src) {
+#pragma unroll 1
+        for (int ch = 0; ch < CPT; ++ch) {
+            const int gc = h * CPT + ch;
+            float y[64];
+            load_chunk(src + 64 * gc, y);
+            write_A_chunk<CHI, F16>(ta, gc, y);
+        }
+    };
+    if (epi && total_steps > 0) {
+        write_A_row(start);
+        write_meta(cc);
+    }
     tc_before();
     __syncthreads();
     tc_after();
@@ -511,9 +655,9 @@ __global__ void __launch_bounds__(NT, 1)
     int p_at = 0;
     auto issue_next = [&]() {
         const long long g = g_issued;
-        const int st = (int)(g % NS);
-        const int y_hi = ((pc.form * 2 + 0) * a.L + pc.k) * 2 * CHI;
-        const int y_lo = ((pc.form * 2 + 1) * a.L + pc.k) * 2 * CHI;
+        const int st = (int)(g % NSG);
+        const int y_hi = ((pc.form * 2 + 0) * a.L + pc.k) * CHI;
+        const int y_lo = ((pc.form * 2 + 1) * a.L + pc.k) * CHI;
         const uint32_t dst = stage0 + (uint32_t)st * C::STAGE;
         mbar_expect_tx(full_bar(st), (uint32_t)C::STAGE);
         tma_load_2d(dst, &map, p_at * 64, y_hi, full_bar(st));
@@ -524,20 +668,22 @@ __global__ void __launch_bounds__(NT, 1)
             cursor_next<MODE>(pc, a, span);
         }
     };
-    if (tid == 0) {
-        while (g_issued < total_atoms && g_issued < NS) issue_next();
+    if (issuer) {
+        while (g_issued < total_atoms && g_issued < NSG) issue_next();
     }
 
-    Cursor cc = cursor_start<MODE>(a, j);
     bool aborted = false;
 
     for (long long t = 0; t < total_steps; ++t) {
-        // ---------------- MMA issue (thread 0)
-        if (tid == 0) {
+        const bool dbl = (MODE == M_SWEEP) && cc.form == 0 && cc.i == 0;
+        // ---------------- MMA issue, then the refill (producer)
+        if (issuer) {
+            const uint32_t a_hi = tmem + (uint32_t)C::A_COL, a_lo = a_hi + (uint32_t)(CHI / 2);
+            const uint32_t meta = tmem + (uint32_t)C::META;
             for (int at = 0; at < C::KA; ++at) {
                 const long long g = t * C::KA + at;
-                const int st = (int)(g % NS);
-                if (!mbar_wait(full_bar(st), (uint32_t)((g / NS) & 1), a.wait_limit)) {
+                const int st = (int)(g % NSG);
+                if (!mbar_wait(full_bar(st), (uint32_t)((g / NSG) & 1), a.wait_limit)) {
                     atomicOr(a.err, 1);
                     *abort_flag = 1;
                     break;
@@ -545,14 +691,22 @@ __global__ void __launch_bounds__(NT, 1)
                 g_waited = g + 1;
                 tc_after();
                 const uint32_t b_hi = stage0 + (uint32_t)st * C::STAGE, b_lo = b_hi + C::BOX;
-                const uint32_t a_hi = tmem + (uint32_t)C::A_COL, a_lo = a_hi + (uint32_t)(CHI / 2);
 #pragma unroll
-                for (int kb = 0; kb < 4; ++kb) {
-                    const uint32_t ao = (uint32_t)(at * 32 + kb * 8);
-                    const uint32_t bo = (uint32_t)(kb * 32);
-                    mma_f16_ts(tmem, a_hi + ao, sdesc(b_hi + bo), C::IDESC, (at | kb) != 0 ? 1u : 0u);
-                    mma_f16_ts(tmem, a_hi + ao, sdesc(b_lo + bo), C::IDESC, 1u);
-                    mma_f16_ts(tmem, a_lo + ao, sdesc(b_hi + bo), C::IDESC, 1u);
+                for (int kk = 0; kk < 2; ++kk) {
+                    // logical K [64 at + 32 kk, +32): row entries 32 at + 16 kk .. +16
+                    const uint32_t ao = (uint32_t)(at * 16 + kk * 8);
+                    const uint32_t bo = (uint32_t)(kk * 64);
+                    const uint32_t first = (at | kk) != 0 ? 1u : 0u;
+                    mma_sp_ts(tmem, a_hi + ao, sdesc(b_hi + bo), meta, C::IDESC, first);
+                    mma_sp_ts(tmem, a_hi + ao, sdesc(b_lo + bo), meta, C::IDESC, 1u);
+                    mma_sp_ts(tmem, a_lo + ao, sdesc(b_hi + bo), meta, C::IDESC, 1u);
+                    if (dbl) {
+                        const uint32_t d2 = tmem + (uint32_t)C::ACC2;
+                        const uint32_t meta2 = tmem + (uint32_t)C::META2;
+                        mma_sp_ts(d2, a_hi + ao, sdesc(b_hi + bo), meta2, C::IDESC, first);
+                        mma_sp_ts(d2, a_hi + ao, sdesc(b_lo + bo), meta2, C::IDESC, 1u);
+                        mma_sp_ts(d2, a_lo + ao, sdesc(b_hi + bo), meta2, C::IDESC, 1u);
+                    }
                 }
                 mma_commit(empty_bar(st));
             }
@@ -561,9 +715,9 @@ __global__ void __launch_bounds__(NT, 1)
             if (!*abort_flag) {
                 for (int at = 0; at < C::KA; ++at) {
                     const long long g = t * C::KA + at;
-                    if (g + NS >= total_atoms) break;
-                    const int st = (int)(g % NS);
-                    if (!mbar_wait(empty_bar(st), (uint32_t)((g / NS) & 1), a.wait_limit)) {
+                    if (g + NSG >= total_atoms) break;
+                    const int st = (int)(g % NSG);
+                    if (!mbar_wait(empty_bar(st), (uint32_t)((g / NSG) & 1), a.wait_limit)) {
                         atomicOr(a.err, 1);
                         *abort_flag = 1;
                         break;
@@ -572,120 +726,155 @@ __global__ void __launch_bounds__(NT, 1)
                 }
             }
         }
-        // ---------------- wait for the accumulator
-        if (!mbar_wait(done_bar, (uint32_t)(t & 1), a.wait_limit)) {
+        bool write_next = false;
+        const int k = cc.k;
+        const int ck = site_cexp(k);
+        const bool last = (t + 1 == total_steps);
+        // ---------------- wait for the accumulator (epilogue warps)
+        if (epi && !mbar_wait(done_bar, (uint32_t)(t & 1), a.wait_limit)) {
             atomicOr(a.err, 1);
             *abort_flag = 1;
         }
         tc_after();
         __syncwarp();
-        bool write_next = false;
-        const int k = cc.k;
-        const int sk = site_spin(k);
-        const int ck = site_cexp(k);
         // ---------------- epilogue
-        if (MODE == M_ROWS) {
-            const int iflip = (j < N) ? site_spin(j) : -1;
-            acc_select<CHI>(tw, spin(sk) ^ (sk == iflip ? 1 : 0), v);
-            E += renorm<CHI>(v) - ck;
-            write_next = (t + 1 < total_steps);
-        } else if (MODE == M_LEFT) {
-            acc_select<CHI>(tw, spin(sk), v);
-            E += renorm<CHI>(v) - ck;
-            if (active) {
-                store_vec<CHI>(a.lstack + ((size_t)c * N + k) * CHI, v);
-                a.lexp[(size_t)c * N + k] = (int32_t)E;
+        if (!epi) {
+            // the producer warp's other lanes only keep the cursor
+        } else if (MODE != M_SWEEP || cc.form == 1) {
+            // rows, amplitude, environments, and the sweep's right environment
+            const int e = row_exp(0u, 0);
+            E += e - ck;
+            float *dst = nullptr;
+            if (MODE == M_LEFT) {
+                dst = a.lstack + ((size_t)c * N + k) * CHI;
+                if (lead) a.lexp[(size_t)c * N + k] = (int32_t)E;
+            } else if (MODE == M_RIGHT || MODE == M_SWEEP) {
+                dst = a.rstack + ((size_t)c * a.nr + (k - rbase)) * CHI;
+                if (lead) a.rexp[(size_t)c * a.nr + (k - rbase)] = (int32_t)E;
             }
-            write_next = (t + 1 < total_steps);
-        } else if (MODE == M_RIGHT) {
-            acc_select<CHI>(tw, spin(sk), v);
-            E += renorm<CHI>(v) - ck;
-            if (active) {
-                store_vec<CHI>(a.rstack + ((size_t)c * a.nr + (k - rbase)) * CHI, v);
-                a.rexp[(size_t)c * a.nr + (k - rbase)] = (int32_t)E;
+            // the sweep's last right-environment step hands over to proposal 0 (from b_L)
+            const bool to_bl = (MODE == M_SWEEP) && cc.tt == N - 2;
+            write_next = (MODE == M_SWEEP) || !last;
+            const bool closing = last && (MODE == M_ROWS || MODE == M_INIT);
+            const float *rclose = a.br;
+            if (closing) {
+                fin_E = E;
+                if (MODE == M_ROWS) {
+                    const int rq = row_end(a, j) + 1 - a.kmin;  // r_{end+1}; b_R for j = N
+                    rclose = a.rstack + ((size_t)c * a.nr + rq) * CHI;
+                    fin_E = E + a.rexp[(size_t)c * a.nr + rq];
+                }
             }
-            write_next = (t + 1 < total_steps);
-        } else if (MODE == M_INIT) {
-            acc_select<CHI>(tw, spin(sk), v);
-            E += renorm<CHI>(v) - ck;
-            write_next = (t + 1 < total_steps);
-        } else {  // M_SWEEP
-            if (cc.form == 1) {  // right environment of the last block
-                acc_select<CHI>(tw, spin(sk), v);
-                E += renorm<CHI>(v) - ck;
-                if (active) {
-                    store_vec<CHI>(a.rstack + ((size_t)c * a.nr + (k - rbase)) * CHI, v);
-                    a.rexp[(size_t)c * a.nr + (k - rbase)] = (int32_t)E;
+            float acc8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+            for (int ch = 0; ch < CPT; ++ch) {
+                const int gc = h * CPT + ch;
+                float y[64];
+                row_chunk(0u, e, ch, y);
+                if (dst && active) store_chunk(dst + 64 * gc, y);
+                if (write_next && !to_bl) write_A_chunk<CHI, F16>(ta, gc, y);
+                if (closing) dot_chunk(y, rclose + 64 * gc, acc8);
+            }
+            if (closing) fin_m = row_dot(dot_finish(acc8));
+            if (to_bl) {
+                write_A_row(a.bl);
+                El = 0;
+            }
+        } else {  // M_SWEEP, a proposal row (form 0)
+            const int jj = cc.jj;
+            const int iq = site_spin(jj);
+            const bool row_end_here = (cc.i + 1 == span);
+            float acc8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const float *rr = a.rstack + ((size_t)c * a.nr + jj) * CHI;
+            if (cc.i == 0) {
+                // unflipped continuation: l_jj if the proposal is rejected
+                const int e2 = row_exp((uint32_t)C::ACC2, 1);
+                Ekeep = El + e2 - ck;
+#pragma unroll 1
+                for (int ch = 0; ch < CPT; ++ch) {
+                    const int gc = h * CPT + ch;
+                    float y[64];
+                    row_chunk((uint32_t)C::ACC2, e2, ch, y);
+                    if (active) store_chunk(a.lstack + ((size_t)c * N + jj) * CHI + 64 * gc, y);
                 }
-                if (cc.tt == N - 2) {  // next: proposal 0 starts from b_L
-                    load_vec<CHI>(a.bl, v);
-                    El = 0;
+                if (lead) a.lexp[(size_t)c * N + jj] = (int32_t)Ekeep;
+                // flipped start of the proposal row (kept for an acceptance)
+                const int e1 = row_exp(0u, 0);
+                Eflip = El + e1 - ck;
+                E = Eflip;
+#pragma unroll 1
+                for (int ch = 0; ch < CPT; ++ch) {
+                    const int gc = h * CPT + ch;
+                    float y[64];
+                    row_chunk(0u, e1, ch, y);
+                    if (active) store_chunk(a.tmp + (size_t)c * CHI + 64 * gc, y);
+                    if (!row_end_here) write_A_chunk<CHI, F16>(ta, gc, y);
+                    else dot_chunk(y, rr + 64 * gc, acc8);
                 }
+                if (lead) a.tmp_exp[c] = (int32_t)Eflip;
+            } else {
+                const int e = row_exp(0u, 0);
+                E += e - ck;
+#pragma unroll 1
+                for (int ch = 0; ch < CPT; ++ch) {
+                    const int gc = h * CPT + ch;
+                    float y[64];
+                    row_chunk(0u, e, ch, y);
+                    if (!row_end_here) write_A_chunk<CHI, F16>(ta, gc, y);
+                    else dot_chunk(y, rr + 64 * gc, acc8);
+                }
+            }
+            if (!row_end_here) {
                 write_next = true;
             } else {
-                const int jj = cc.jj;
-                const int iq = site_spin(jj);
-                if (cc.i == 0) {
-                    const int si = spin(iq);
-                    // unflipped continuation: l_jj if the proposal is rejected
-                    acc_select<CHI>(tw, si, v);
-                    Ekeep = El + renorm<CHI>(v) - ck;
-                    if (active) {
-                        store_vec<CHI>(a.lstack + ((size_t)c * N + jj) * CHI, v);
-                        a.lexp[(size_t)c * N + jj] = (int32_t)Ekeep;
-                    }
-                    // flipped start of the proposal row
-                    acc_select<CHI>(tw, si ^ 1, v);
-                    Eflip = El + renorm<CHI>(v) - ck;
-                    if (active) {
-                        store_vec<CHI>(a.tmp + (size_t)c * CHI, v);
-                        a.tmp_exp[c] = (int32_t)Eflip;
-                    }
-                    E = Eflip;
+                // Metropolis decision of proposal jj (spin iq): every thread of
+                // a row takes it from the same numbers
+                double mm = row_dot(dot_finish(acc8));
+                int64_t Ep = E + a.rexp[(size_t)c * a.nr + jj];
+                normalize_scalar(mm, Ep);
+                const double ratio = ldexp(mm / pm, (int)(Ep - pe));
+                const double x = rttd::mcmc_uniform(a.seed, (uint64_t)(a.chain0 + c),
+                                                    (uint64_t)(a.sweep0 + cc.sw), (uint64_t)jj);
+                const bool accept = active && (x < ratio * ratio);
+                if (accept) {
+                    pm = mm;
+                    pe = Ep;
+                    ++acc_count;
+                    El = Eflip;
                 } else {
-                    acc_select<CHI>(tw, spin(sk) ^ (sk == iq ? 1 : 0), v);
-                    E += renorm<CHI>(v) - ck;
+                    El = Ekeep;
                 }
-                if (cc.i + 1 < span) {
-                    write_next = true;
-                } else {
-                    // Metropolis decision of proposal jj (spin iq)
-                    const float *r = a.rstack + ((size_t)c * a.nr + jj) * CHI;
-                    int64_t Ep = E + a.rexp[(size_t)c * a.nr + jj];
-                    double m = dot<CHI>(v, r);
-                    normalize_scalar(m, Ep);
-                    const double ratio = ldexp(m / pm, (int)(Ep - pe));
-                    const double x = rttd::mcmc_uniform(a.seed, (uint64_t)(a.chain0 + c),
-                                                        (uint64_t)(a.sweep0 + cc.sw), (uint64_t)jj);
-                    const bool accept = active && (x < ratio * ratio);
-                    if (accept) {
-                        pm = m;
-                        pe = Ep;
-                        ++acc_count;
-                        load_vec<CHI>(a.tmp + (size_t)c * CHI, v);
-                        store_vec<CHI>(a.lstack + ((size_t)c * N + jj) * CHI, v);
-                        a.lexp[(size_t)c * N + jj] = (int32_t)Eflip;
-                        El = Eflip;
-                    } else {
-                        El = Ekeep;
-                    }
+                if (h == 0) {
                     const uint32_t flips = __ballot_sync(FULL, accept);
-                    if (lane == 0) bits[iq * 4 + warp] ^= flips;
+                    if (lane == 0) bits[iq * 4 + q] ^= flips;
                     __syncwarp();
-                    if (jj + 1 < N) {  // next proposal starts from l_jj
-                        load_vec<CHI>(a.lstack + ((size_t)c * N + jj) * CHI, v);
-                        write_next = true;
-                    } else if (cc.sw + 1 < a.n_sweeps) {  // next sweep
-                        load_vec<CHI>(N > 1 ? a.br : a.bl, v);
-                        E = 0;
-                        El = 0;
-                        write_next = true;
-                    }
+                }
+                const bool next_prop = jj + 1 < N;
+                const bool next_sweep = !next_prop && cc.sw + 1 < a.n_sweeps;
+                // l_jj: the flipped start on acceptance (copied over the kept
+                // row), else the kept row; the next proposal starts from it
+                float *lj = a.lstack + ((size_t)c * N + jj) * CHI;
+#pragma unroll 1
+                for (int ch = 0; ch < CPT; ++ch) {
+                    const int gc = h * CPT + ch;
+                    float y[64];
+                    load_chunk((accept ? a.tmp + (size_t)c * CHI : lj) + 64 * gc, y);
+                    if (accept) store_chunk(lj + 64 * gc, y);
+                    if (next_prop) write_A_chunk<CHI, F16>(ta, gc, y);
+                }
+                if (accept && h == 0) a.lexp[(size_t)c * N + jj] = (int32_t)Eflip;
+                if (next_prop) {
+                    write_next = true;
+                } else if (next_sweep) {  // next sweep
+                    write_A_row(N > 1 ? a.br : a.bl);
+                    E = 0;
+                    El = 0;
+                    write_next = true;
                 }
             }
         }
-        if (write_next) write_A_tmem<CHI, F16>(ta, v);
         cursor_next<MODE>(cc, a, span);
+        if (write_next) write_meta(cc);
         tc_before();
         __syncthreads();
         tc_after();
@@ -695,48 +884,66 @@ __global__ void __launch_bounds__(NT, 1)
         }
     }
 
-    // ---------------- final contraction / outputs
-    if (!aborted) {
+    // ---------------- outputs
+    if (!aborted && lead) {
         if (MODE == M_ROWS) {
-            const int rq = row_end(a, j) + 1 - a.kmin;  // r_{end+1}; b_R for j = N
-            int64_t Ep = E + a.rexp[(size_t)c * a.nr + rq];
-            double m = dot<CHI>(v, a.rstack + ((size_t)c * a.nr + rq) * CHI);
-            normalize_scalar(m, Ep);
-            if (active) {
-                a.rows_mant[c * (N + 1) + j] = m;
-                a.rows_exp[c * (N + 1) + j] = Ep;
-            }
+            double mm = fin_m;
+            int64_t Ep = fin_E;
+            normalize_scalar(mm, Ep);
+            a.rows_mant[c * (N + 1) + j] = mm;
+            a.rows_exp[c * (N + 1) + j] = Ep;
         } else if (MODE == M_INIT) {
-            double m = dot<CHI>(v, a.br);
-            int64_t Ep = E;
-            normalize_scalar(m, Ep);
-            if (active) {
-                if (a.state) {
-                    a.state[c].mant = m;
-                    a.state[c].exp2 = Ep;
-                }
-                if (a.log_abs)
-                    a.log_abs[c] = (m == 0.0) ? -INFINITY : (double)Ep * 0.6931471805599453 + log(fabs(m));
-                if (a.sign) a.sign[c] = (m > 0.0) ? 1 : ((m < 0.0) ? -1 : 0);
+            double mm = fin_m;
+            int64_t Ep = fin_E;
+            normalize_scalar(mm, Ep);
+            if (a.state) {
+                a.state[c].mant = mm;
+                a.state[c].exp2 = Ep;
             }
+            if (a.log_abs)
+                a.log_abs[c] = (mm == 0.0) ? -INFINITY : (double)Ep * 0.6931471805599453 + log(fabs(mm));
+            if (a.sign) a.sign[c] = (mm > 0.0) ? 1 : ((mm < 0.0) ? -1 : 0);
         } else if (MODE == M_SWEEP) {
-            if (active) {
-                for (int i = 0; i < N; ++i) a.spins_out[c * N + i] = (uint8_t)spin(i);
-                a.state[c].mant = pm;
-                a.state[c].exp2 = pe;
-                if (a.n_accept) a.n_accept[c] += acc_count;
-            }
+            for (int i = 0; i < N; ++i) a.spins_out[c * N + i] = (uint8_t)spin(i);
+            a.state[c].mant = pm;
+            a.state[c].exp2 = pe;
+            if (a.n_accept) a.n_accept[c] += acc_count;
         }
     }
     // ---------------- teardown: drain own copies (bounded), free TMEM
-    if (tid == 0 && aborted) {
+    if (issuer && aborted) {
         for (long long g = g_waited; g < g_issued; ++g)
-            mbar_wait(full_bar((int)(g % NS)), (uint32_t)((g / NS) & 1), a.wait_limit);
+            mbar_wait(full_bar((int)(g % NSG)), (uint32_t)((g / NSG) & 1), a.wait_limit);
     }
     tc_before();
     __syncthreads();
     tc_after();
-    if (warp == 0) tmem_dealloc(tmem, C::TALLOC);
+    if (warp == 0) tmem_dealloc(tmem, TALLOC);
+}
+
+// ------------------------------------------------------------------ failure-detection self-test
+// A bounded wait that nothing completes: one warp allocates tensor memory,
+// arms an mbarrier that no copy and no MMA will ever arrive on, waits on it
+// with the given clock budget, records bit 0 in the error word when the
+// budget runs out (as every wait of the sampler's kernels does), frees its
+// tensor memory and returns.  Nothing asynchronous is in flight at any time.
+__global__ void __launch_bounds__(32, 1) k_wait_selftest(int *err, long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t slot;
+    tmem_alloc(sa(&slot), 32);
+    if (threadIdx.x == 0) {
+        mbar_init(sa(&bar), 1);
+        fence_barrier_init();
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = slot;
+    if (threadIdx.x == 0 && !mbar_wait(sa(&bar), 0u, limit)) atomicOr(err, 1);
+    tc_before();
+    __syncthreads();
+    tc_after();
+    tmem_dealloc(tmem, 32);
 }
 
 // ------------------------------------------------------------------ split-row sweep (chi = 64)
@@ -1442,11 +1649,11 @@ tcd::Args make_args(rtt_s *h, int64_t B) {
 
 template <int CHI, int MODE, bool F16>
 cudaError_t launch(const TcPlan *p, const tcd::Args &a, dim3 grid, cudaStream_t st) {
-    const size_t smem = tcd::Cfg<CHI, F16>::smem_bytes(a.N, a.L);
+    const size_t smem = tcd::SCfg<CHI, F16>::smem_bytes(a.N, a.L);
     cudaError_t e = cudaFuncSetAttribute(tcd::k_tc<CHI, MODE, F16>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    tcd::k_tc<CHI, MODE, F16><<<grid, tcd::NT, smem, st>>>(p->map, a);
+    tcd::k_tc<CHI, MODE, F16><<<grid, tcd::NT * tcd::SCfg<CHI, F16>::NH + 32, smem, st>>>(p->map_sp, a);
     return cudaGetLastError();
 }
 
@@ -1492,30 +1699,85 @@ rtt_status tc_plan_create(rtt_s *h, const double *tensors, const double *bl, con
             mx = std::max(mx, std::fabs(tensors[(size_t)k * 2 * chi * chi + i]));
         cexp[k] = (mx > 0.0) ? -std::ilogb(mx) : 0;
     }
-    const size_t rows = (size_t)4 * L * 2 * chi;
-    std::vector<uint16_t> Bh(rows * chi);
-    for (int k = 0; k < L; ++k)
-        for (int s = 0; s < 2; ++s)
-            for (int n = 0; n < chi; ++n)
-                for (int kk = 0; kk < chi; ++kk) {
-                    const double *A = tensors + ((size_t)k * 2 + s) * chi * chi;
-                    // left-to-right operand: row n = output column b, K index = a
-                    const double xt = std::ldexp(A[(size_t)kk * chi + n], cexp[k]);
-                    // right-to-left operand: row n = output index a, K index = b
-                    const double xb = std::ldexp(A[(size_t)n * chi + kk], cexp[k]);
-                    const size_t r0 = ((size_t)(0 * L + k) * 2 * chi + s * chi + n) * chi + kk;
-                    const size_t r1 = ((size_t)(1 * L + k) * 2 * chi + s * chi + n) * chi + kk;
-                    const size_t r2 = ((size_t)(2 * L + k) * 2 * chi + s * chi + n) * chi + kk;
-                    const size_t r3 = ((size_t)(3 * L + k) * 2 * chi + s * chi + n) * chi + kk;
-                    split16(xt, p->f16, Bh[r0], Bh[r1]);
-                    split16(xb, p->f16, Bh[r2], Bh[r3]);
-                }
     cudaError_t e;
-    if ((e = cudaMalloc((void **)&p->d_B, Bh.size() * sizeof(uint16_t))) != cudaSuccess)
-        return status_of(e, "tc plan: tensors");
-    if ((e = cudaMemcpy(p->d_B, Bh.data(), Bh.size() * sizeof(uint16_t),
-                        cudaMemcpyHostToDevice)) != cudaSuccess)
-        return status_of(e, "tc plan: tensors copy");
+    // sparse operand of the generic tile kernel: row n, K index 2x + s
+    {
+        const size_t rows = (size_t)4 * L * chi, K = (size_t)2 * chi;
+        std::vector<uint16_t> Bs(rows * K);
+        for (int k = 0; k < L; ++k)
+            for (int s = 0; s < 2; ++s) {
+                const double *A = tensors + ((size_t)k * 2 + s) * chi * chi;
+                for (int n = 0; n < chi; ++n)
+                    for (int x = 0; x < chi; ++x) {
+                        // left to right: output b = n, contracted a = x
+                        const double xt = std::ldexp(A[(size_t)x * chi + n], cexp[k]);
+                        // right to left: output a = n, contracted b = x
+                        const double xb = std::ldexp(A[(size_t)n * chi + x], cexp[k]);
+                        const size_t col = (size_t)2 * x + s;
+                        split16(xt, p->f16, Bs[((size_t)(0 * L + k) * chi + n) * K + col],
+                                Bs[((size_t)(1 * L + k) * chi + n) * K + col]);
+                        split16(xb, p->f16, Bs[((size_t)(2 * L + k) * chi + n) * K + col],
+                                Bs[((size_t)(3 * L + k) * chi + n) * K + col]);
+                    }
+            }
+        if ((e = cudaMalloc((void **)&p->d_Bs, Bs.size() * sizeof(uint16_t))) != cudaSuccess)
+            return status_of(e, "tc plan: tensors");
+        if ((e = cudaMemcpy(p->d_Bs, Bs.data(), Bs.size() * sizeof(uint16_t),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return status_of(e, "tc plan: tensors copy");
+        const cuuint64_t gdim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+        const cuuint64_t gstride[1] = {(cuuint64_t)K * sizeof(uint16_t)};
+        const cuuint32_t box[2] = {64u, (cuuint32_t)chi};
+        const cuuint32_t estride[2] = {1u, 1u};
+        CUresult r = enc(&p->map_sp,
+                         p->f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                         2, p->d_Bs, gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            rtt_set_error("cuTensorMapEncodeTiled failed (sparse operand)");
+            return RTT_ERR_CUDA;
+        }
+    }
+    // dense operand of the chi = 64 split-row sweep
+    if (chi == 64) {
+        const size_t rows = (size_t)4 * L * 2 * chi;
+        std::vector<uint16_t> Bh(rows * chi);
+        for (int k = 0; k < L; ++k)
+            for (int s = 0; s < 2; ++s)
+                for (int n = 0; n < chi; ++n)
+                    for (int kk = 0; kk < chi; ++kk) {
+                        const double *A = tensors + ((size_t)k * 2 + s) * chi * chi;
+                        // left-to-right operand: row n = output column b, K index = a
+                        const double xt = std::ldexp(A[(size_t)kk * chi + n], cexp[k]);
+                        // right-to-left operand: row n = output index a, K index = b
+                        const double xb = std::ldexp(A[(size_t)n * chi + kk], cexp[k]);
+                        const size_t r0 = ((size_t)(0 * L + k) * 2 * chi + s * chi + n) * chi + kk;
+                        const size_t r1 = ((size_t)(1 * L + k) * 2 * chi + s * chi + n) * chi + kk;
+                        const size_t r2 = ((size_t)(2 * L + k) * 2 * chi + s * chi + n) * chi + kk;
+                        const size_t r3 = ((size_t)(3 * L + k) * 2 * chi + s * chi + n) * chi + kk;
+                        split16(xt, p->f16, Bh[r0], Bh[r1]);
+                        split16(xb, p->f16, Bh[r2], Bh[r3]);
+                    }
+        if ((e = cudaMalloc((void **)&p->d_B, Bh.size() * sizeof(uint16_t))) != cudaSuccess)
+            return status_of(e, "tc plan: tensors");
+        if ((e = cudaMemcpy(p->d_B, Bh.data(), Bh.size() * sizeof(uint16_t),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return status_of(e, "tc plan: tensors copy");
+        const cuuint64_t gdim[2] = {(cuuint64_t)chi, (cuuint64_t)rows};
+        const cuuint64_t gstride[1] = {(cuuint64_t)chi * sizeof(uint16_t)};
+        const cuuint32_t box[2] = {64u, (cuuint32_t)(2 * chi)};
+        const cuuint32_t estride[2] = {1u, 1u};
+        CUresult r = enc(&p->map,
+                         p->f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                         2, p->d_B, gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            rtt_set_error("cuTensorMapEncodeTiled failed");
+            return RTT_ERR_CUDA;
+        }
+    }
     if ((e = cudaMalloc((void **)&p->d_cexp, (size_t)L * sizeof(int32_t))) != cudaSuccess)
         return status_of(e, "tc plan: prescale");
     cudaMemcpy(p->d_cexp, cexp.data(), (size_t)L * sizeof(int32_t), cudaMemcpyHostToDevice);
@@ -1530,19 +1792,6 @@ rtt_status tc_plan_create(rtt_s *h, const double *tensors, const double *bl, con
     cudaMemcpy(p->d_br, brf.data(), chi * 4, cudaMemcpyHostToDevice);
     if ((e = cudaMalloc((void **)&p->d_err, sizeof(int))) != cudaSuccess) return status_of(e, "tc plan");
     cudaMemset(p->d_err, 0, sizeof(int));
-    const cuuint64_t gdim[2] = {(cuuint64_t)chi, (cuuint64_t)rows};
-    const cuuint64_t gstride[1] = {(cuuint64_t)chi * sizeof(uint16_t)};
-    const cuuint32_t box[2] = {64u, (cuuint32_t)(2 * chi)};
-    const cuuint32_t estride[2] = {1u, 1u};
-    CUresult r = enc(&p->map,
-                     p->f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                     p->d_B, gdim, gstride, box, estride,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        rtt_set_error("cuTensorMapEncodeTiled failed");
-        return RTT_ERR_CUDA;
-    }
     return RTT_OK;
 }
 
@@ -1550,6 +1799,7 @@ void tc_plan_destroy(rtt_s *h) {
     TcPlan *p = h->tc;
     if (!p) return;
     cudaFree(p->d_B);
+    cudaFree(p->d_Bs);
     cudaFree(p->d_cexp);
     cudaFree(p->d_bl);
     cudaFree(p->d_br);
@@ -1666,3 +1916,8 @@ rtt_status tc_sweep(rtt_s *h, uint8_t *spins, rtt_chain_state *state, int64_t B,
 }
 
 int *tc_error_word(rtt_s *h) { return h->tc ? h->tc->d_err : nullptr; }
+
+rtt_status tc_wait_selftest(rtt_s *h, long long budget_cycles, cudaStream_t st) {
+    tcd::k_wait_selftest<<<1, 32, 0, st>>>(h->tc->d_err, budget_cycles);
+    return status_of(cudaGetLastError(), "wait self-test");
+}

@@ -77,6 +77,8 @@ def lib():
         L.rtt_mcmc_sweep.argtypes = [P, P, P, I64, I64, I64, I32, I32, P, P, P]
         L.rtt_observables.argtypes = [P, P, I32, I64, P, I64, ctypes.POINTER(_Stats), P]
         L.rtt_mcmc_uniforms.argtypes = [U64, I64, P, P, P]
+        L.rtt_wait_selftest.argtypes = [P, I64, P]
+        L.rtt_device_status.argtypes = [P, ctypes.POINTER(I32)]
         L.rtt_profile.argtypes = [P, I32]
         L.rtt_profile_read.argtypes = [P, ctypes.POINTER(_KTime), I32, ctypes.POINTER(I32)]
         L.rtt_batch_create.argtypes = [P, I32, P, ctypes.POINTER(P)]
@@ -122,7 +124,8 @@ def lib():
         L.rtt_last_error.restype = ctypes.c_char_p
         for name in ("rtt_create", "rtt_destroy", "rtt_reserve", "rtt_scratch_bytes",
                      "rtt_log_amplitudes", "rtt_local_energy", "rtt_mcmc_sweep",
-                     "rtt_observables", "rtt_mcmc_uniforms", "rtt_profile", "rtt_profile_read"):
+                     "rtt_observables", "rtt_mcmc_uniforms", "rtt_profile", "rtt_profile_read",
+                     "rtt_wait_selftest", "rtt_device_status"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -323,6 +326,18 @@ class RTT:
         _check(lib().rtt_profile_read(self._h, buf, 32, ctypes.byref(n)), "rtt_profile_read")
         return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].ms))
                 for i in range(min(n.value, 32))}
+
+    def device_status(self):
+        """(status, flags) of rtt_device_status: the handle's device error flags
+        since the last call (bit 0: a bounded wait ran out), then cleared."""
+        f = ctypes.c_int32()
+        st = lib().rtt_device_status(self._h, ctypes.byref(f))
+        return int(st), int(f.value)
+
+    def wait_selftest(self, budget_cycles: int, stream=None):
+        """rtt_wait_selftest: one bounded wait that nothing completes."""
+        _check(lib().rtt_wait_selftest(self._h, int(budget_cycles), _stream(stream)),
+               "rtt_wait_selftest")
 
     def log_amplitudes(self, spins: torch.Tensor, stream=None):
         B = spins.shape[0]

@@ -197,3 +197,13 @@ def test_training_loop_rejects_bad_arguments(lib):
     assert lib.rtt_made_permutation(0, 1, 0, out.ctypes.data) == 1
     with pytest.raises(rtt.RTTError, match="INVALID_ARG"):
         rtt.made_permutation(0, 1, 0)
+
+
+def test_wait_selftest_rejects_a_null_handle(lib):
+    assert lib.rtt_wait_selftest(None, 2000000, None) == 1
+
+
+def test_noalloc_energy_rejects_a_null_handle(lib):
+    e = np.zeros(4)
+    assert lib.rtt_local_energy_noalloc(None, None, 4, e.ctypes.data, None, None) == 1
+    assert np.all(e == 0)

@@ -125,3 +125,16 @@ def test_gram_schmidt_and_back_transform_host_calls(rtt):
     v = np.ones(4)
     assert lib.rtt_dual_back_transform(4, buf.ctypes.data, v.ctypes.data, v.ctypes.data) == 1
     assert lib.rtt_dual_back_transform(4, None, v.ctypes.data, buf.ctypes.data) == 1
+
+
+def test_gram_schmidt_error_leaves_the_output_untouched(rtt):
+    """A non-finite S~ entry that T uses (here S~[1][2], found after row 0 has
+    been read) is reported as RTT_ERR_NUMERIC before any entry of the
+    caller's T is written."""
+    _, St = dual.exact_tilde_matrices(_states(4))
+    bad = St.copy()
+    bad[1, 2] = np.nan
+    T = np.full((4, 4), 7.25)
+    st = rtt.lib().rtt_dual_gram_schmidt(4, np.ascontiguousarray(bad).ctypes.data, 0, T.ctypes.data)
+    assert st == 4
+    assert np.all(T == 7.25)

@@ -10,6 +10,7 @@ import torch
 
 from paper_2604_22718_gb300 import inputs
 from oracle import oracle as orc
+from parity_util import check_sweep_divergences, eps_site, local_energy_bound
 
 pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
@@ -50,16 +51,13 @@ def test_simt_largest_bond_dimension(chi):
 
 @pytest.mark.parametrize("chi,B", [(64, 300), (128, 200)])
 def test_tc_sweep_ragged_tiles_follow_oracle(chi, B):
-    """Several 128-row tiles and a ragged last one: one FP16X3 sweep takes the
-    oracle's decisions on at least 90 % of the chains (the rest are near ties),
-    every chain's amplitude stays consistent with its spins."""
+    """Several 128-row tiles and a ragged last one: every decision of one
+    FP16X3 sweep is the FP64 rule's at the same state except at explained near
+    ties; every chain's amplitude stays consistent with its spins."""
     rtt = _rtt()
     inst = inputs.make_instance(4, 4, 2, chi, 3.0, seed=50 + chi)
     o = orc.Oracle(inst)
     s0 = inputs.initial_spins(51, B, 16)
-    so = s0.copy()
-    mo, eo = o.init_chains(so)
-    o.mcmc(13, so, mo, eo, 0, 1, record=False, threads=16)
     with rtt.RTT(inst, "fp16x3", seed=13) as m:
         sg = torch.from_numpy(s0.copy()).cuda()
         _, _, st = m.log_amplitudes(sg)
@@ -70,19 +68,23 @@ def test_tc_sweep_ragged_tiles_follow_oracle(chi, B):
         la_now = m.log_amplitudes(sg)[0].cpu().numpy()
         torch.cuda.synchronize()
         assert _status_ok(rtt, m)
-    same = np.all(sg.cpu().numpy() == so, axis=1)
-    assert same.mean() >= 0.9, same.mean()
+    s1 = sg.cpu().numpy()
+    n, nd, worst = check_sweep_divergences(o, 13, s0, s1, 0, eps_site(chi, "fp16x3"),
+                                           slack=2.0 ** -23)
+    print(f"chi {chi}: {nd} of {n} decisions differ, worst gap/tolerance {worst:.3f}")
     # the tracked amplitude of every chain (last tile included) is its spins' amplitude
     d = np.abs(la_track - la_now)
-    assert np.median(d) < 1e-5 and np.mean(d <= 1e-3) >= 0.99, np.sort(d)[-5:]
-    assert np.all(acc.cpu().numpy() <= 16)
+    K = o.amplitude_cond(s1)
+    assert np.all(d <= 2 * eps_site(chi, "fp16x3") * (K[:, 0] + K[:, 2])), np.sort(d)[-5:]
+    assert np.all(acc.cpu().numpy() == np.sum(s1 != s0, axis=1))
 
 
 def test_plain_6x6_fp16x3_full_batch_sampled():
-    """The bench configuration: 4096 chains, FP16X3, two measured sweeps; sampled
-    chains' measured energies (entering configurations) against the oracle on
-    the seeded start, and the final local energies against the oracle's own
-    chains where the two took the same steps."""
+    """The 6x6 configuration: 4096 chains, FP16X3, two measured sweeps (two
+    calls); for picked chains the measured energies of the entering
+    configurations and the final local energies against the oracle on the
+    same configurations, each within its own split bound, and both sweeps'
+    decisions replayed by the oracle, every divergence an explained near tie."""
     rtt = _rtt()
     w = inputs.WORKLOADS["plain_6x6"]
     inst = inputs.workload("plain_6x6")
@@ -94,23 +96,20 @@ def test_plain_6x6_fp16x3_full_batch_sampled():
         sg = torch.from_numpy(s0.copy()).cuda()
         _, _, st = m.log_amplitudes(sg)
         tr = torch.empty((2, B), dtype=torch.float64, device="cuda")
-        m.mcmc_sweep(sg, st, 0, 2, 1, tr)
-        e_end = m.local_energy(sg)
+        m.mcmc_sweep(sg, st, 0, 1, 1, tr[0:1])
+        s1 = sg.cpu().numpy()
+        m.mcmc_sweep(sg, st, 1, 1, 1, tr[1:2])
+        e_end, r_end = m.local_energy(sg, with_ratios=True)
         torch.cuda.synchronize()
         assert _status_ok(rtt, m)
-        s_end = sg.cpu().numpy()
+        s2 = sg.cpu().numpy()
     tr, e_end = tr.cpu().numpy(), e_end.cpu().numpy()
-    scale = inst.bonds.shape[0] + inst.h * 36
-    e0_o = o.local_energies(s0[pick], threads=7)
-    assert np.all(np.abs(tr[0][pick] - e0_o) <= 1e-3 * scale), (tr[0][pick], e0_o)
-    # the final energies on the oracle's own chains (each picked chain run alone
-    # under its own chain index), where the FP16X3 chains took the same steps
-    so = s0[pick].copy()
-    for k, c in enumerate(pick):
-        sc = s0[c:c + 1].copy()
-        mc, ec = o.init_chains(sc)
-        o.mcmc(w["seed"], sc, mc, ec, 0, 2, chain0=int(c), record=False)
-        so[k] = sc[0]
-    same = np.all(s_end[pick] == so, axis=1)
-    e_o = o.local_energies(so, threads=7)
-    assert np.all((np.abs(e_end[pick] - e_o) <= 1e-3 * scale)[same]), (e_end[pick], e_o, same)
+    eps = eps_site(64, "fp16x3")
+    for a, b, sweep in ((s0, s1, 0), (s1, s2, 1)):
+        for c in pick:
+            check_sweep_divergences(o, w["seed"], a[c:c + 1], b[c:c + 1], sweep, eps,
+                                    chain0=int(c), slack=2.0 ** -23)
+    for conf, e_gpu in ((s0, tr[0]), (s1, tr[1]), (s2, e_end)):
+        e_o, r_o = o.local_energies(conf[pick], with_ratios=True, threads=7)
+        bound = local_energy_bound(o, conf[pick], r_o, eps, inst.J, inst.h, inst.bonds.shape[0])
+        assert np.all(np.abs(e_gpu[pick] - e_o) <= bound), (e_gpu[pick], e_o, bound)

@@ -8,6 +8,7 @@ import pytest
 import torch
 
 from paper_2604_22718_gb300 import inputs
+from parity_util import check_sweep_divergences, eps_site
 from oracle import oracle as orc
 from oracle import dual
 
@@ -161,17 +162,15 @@ def test_fp16x3_general_path_amplitudes_and_energies(lx, ly, names, chi, B):
 
 def test_fp16x3_general_path_sweep_follows_oracle():
     """The general split-row sweep (chi = 64, sigma^V + sigma^H + sigma^D +
-    sigma^D'): one sweep over three row tiles takes the oracle's decisions on at
-    least 90 % of the chains; tracked amplitudes stay those of the spins; the
-    measured trace is the standalone energy of the entering configurations."""
+    sigma^D'): every decision of one sweep over three row tiles is the FP64
+    rule's at the same state except at explained near ties; tracked amplitudes
+    stay those of the spins; the measured trace is the standalone energy of the
+    entering configurations."""
     rtt = _rtt()
     inst = inputs.workload("vhdd_6x6")
     o = orc.Oracle(inst)
     B = 300
     s0 = inputs.initial_spins(63, B, 36)
-    so = s0.copy()
-    mo, eo = o.init_chains(so)
-    o.mcmc(17, so, mo, eo, 0, 1, record=False, threads=16)
     with rtt.RTT(inst, "fp16x3", seed=17) as m:
         sg = torch.from_numpy(s0.copy()).cuda()
         _, _, st = m.log_amplitudes(sg)
@@ -182,8 +181,11 @@ def test_fp16x3_general_path_sweep_follows_oracle():
                     torch.log(rtt.state_mant(st).abs())).cpu().numpy()
         la_now = m.log_amplitudes(sg)[0].cpu().numpy()
         torch.cuda.synchronize()
-    same = np.all(sg.cpu().numpy() == so, axis=1)
-    assert same.mean() >= 0.9, same.mean()
+    s1 = sg.cpu().numpy()
+    eps = eps_site(64, "fp16x3")
+    n, nd, worst = check_sweep_divergences(o, 17, s0, s1, 0, eps, slack=2.0 ** -23)
+    print(f"general path sweep: {nd} of {n} decisions differ, worst gap/tolerance {worst:.3f}")
     d = np.abs(la_track - la_now)
-    assert np.median(d) < 1e-5 and np.mean(d <= 1e-3) >= 0.99
+    K = o.amplitude_cond(s1)
+    assert np.all(d <= 2 * eps * (K[:, 0] + K[:, 2]))
     assert torch.equal(tr[0], e0)

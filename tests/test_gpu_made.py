@@ -104,8 +104,7 @@ def test_sampler_matches_oracle_and_reports_its_own_log_prob():
     # the density the proposal was drawn from is exactly the one evaluated later
     assert np.array_equal(lq, lq_fwd)
     so, lqo = made.sample(p, order, B, seed=77, chain0=100, rnd=9, N=N)
-    same = np.all(sp == so, axis=1)
-    assert same.mean() >= 0.99
+    same = check_sample_divergences(p, order, sp, so, 77, 100, 9)
     np.testing.assert_allclose(lq[same], lqo[same], rtol=1e-5, atol=1e-5)
 
 
@@ -288,3 +287,94 @@ def test_training_loop_equals_train_steps_on_its_row_order():
     assert np.array_equal(pa, pb)
     np.testing.assert_allclose(hist, ref, rtol=1e-12)
     assert hist[-1] < hist[0]
+
+
+# ---------------------------------------------------------------- FP32 bounds
+U32 = 2.0 ** -24
+
+
+def fp32_logit_bound(p, x):
+    """Per row and position, a bound on |logit_FP32 - logit| of the forward
+    pass on inputs x (+-1): every layer's output adds at most (K + 1) u_32 of
+    its absolute sum (K terms accumulated by fma from the bias), ReLU is
+    1-Lipschitz, and each layer propagates the error of its input through
+    |W|."""
+    a1 = np.abs(x) @ np.abs(p["W1"]).T + np.abs(p["b1"])
+    d1 = (x.shape[1] + 1) * U32 * a1
+    _, h1, _, h2, _ = made.forward(p, x)
+    d2 = d1 @ np.abs(p["W2"]).T + (h1.shape[1] + 1) * U32 * (np.abs(h1) @ np.abs(p["W2"]).T + np.abs(p["b2"]))
+    return d2 @ np.abs(p["W3"]).T + (h2.shape[1] + 1) * U32 * (np.abs(h2) @ np.abs(p["W3"]).T + np.abs(p["b3"]))
+
+
+def check_sample_divergences(p, order, sp_gpu, sp_oracle, seed, chain0, rnd):
+    """Ancestral samples drawn from the same Philox stream: where a GPU sample
+    differs from the oracle's, the first position d at which they differ must
+    be a near tie, |u_d - q_d| within the FP32 bound of q_d = sigmoid(logit_d)
+    at the common prefix (sigmoid' <= 1/4).  Returns the rows that agree."""
+    N = sp_gpu.shape[1]
+    same = np.all(sp_gpu == sp_oracle, axis=1)
+    for c in np.flatnonzero(~same):
+        d = int(np.argmax(sp_gpu[c, order] != sp_oracle[c, order]))
+        x = np.zeros((1, N))
+        x[0, :d] = 1.0 - 2.0 * sp_oracle[c, order[:d]]
+        logit = made.forward(p, x)[4][0, d]
+        q = 1.0 / (1.0 + np.exp(-logit))
+        u = orc.uniform_keyed(seed, made.MADE_STREAM, chain0 + c, rnd, d)
+        tol = fp32_logit_bound(p, x)[0, d] / 4.0 + 1e-12
+        assert abs(u - q) <= tol, (c, d, u, q, tol)
+    return same
+
+
+def test_independence_step_matches_oracle_chain_by_chain():
+    """rtt_indep_mh on an FP64 handle with FP32 inference against the oracle's
+    independence step (Sec. 3.3, Metropolis-Hastings on |psi|^2 with a
+    proposal q): the same Philox proposals (divergent samples explained), and
+    for every chain whose proposal agrees the same accept/reject decision,
+    except where log u lies within the FP32 bound of the log acceptance ratio;
+    accepted chains carry the FP64 amplitude of their new spins bit for bit."""
+    rtt = _rtt()
+    inst = inputs.make_instance(2, 5, 2, 8, 1.5, seed=61, mixing=True)
+    N, H, B = inst.n_spins, 64, 2000
+    o = orc.Oracle(inst)
+    order = inst.path[:N].astype(np.int32)
+    w = inputs.made_init_weights(62, N, H)
+    p = made.masked_params(w, N, H)
+    s_cur = inputs.initial_spins(63, B, N)
+    chain0, rnd, seed = 5, 3, 64
+    with rtt.RTT(inst, "fp64") as m, rtt.MADE(N, H, order, w, seed=seed) as mm:
+        mm.set_inference(False)
+        sg = torch.from_numpy(s_cur.copy()).cuda()
+        _, _, st = m.log_amplitudes(sg)
+        prop, lq_new = mm.sample(B, chain0=chain0, round=rnd)      # the proposals it draws
+        lq_cur = mm.log_prob(sg)
+        acc = torch.zeros(B, dtype=torch.int64, device="cuda")
+        rtt.indep_mh(m, mm, sg, st, rnd, acc, chain0=chain0)
+        torch.cuda.synchronize()
+        prop, lq_new, lq_cur = prop.cpu().numpy(), lq_new.cpu().numpy(), lq_cur.cpu().numpy()
+        s_after, st_after, acc = sg.cpu().numpy(), st.cpu().numpy(), acc.cpu().numpy()
+    so, lqo_new = made.sample(p, order, B, seed, chain0, rnd, N)
+    same = check_sample_divergences(p, order, prop, so, seed, chain0, rnd)
+    lqo_cur = made.log_prob(p, s_cur, order)
+    la_cur, _, _, _ = o.log_amplitudes(s_cur)
+    la_new, _, m_new, e_new = o.log_amplitudes(so)
+    x_cur, _ = made.inputs_of(s_cur, order)
+    x_new, _ = made.inputs_of(so, order)
+    # log q carries at most the sum over positions of the logit bound
+    tol = fp32_logit_bound(p, x_cur).sum(axis=1) + fp32_logit_bound(p, x_new).sum(axis=1) + 1e-9
+    accepted_gpu = acc == 1
+    assert np.array_equal(accepted_gpu, np.all(s_after == prop, axis=1) & np.any(prop != s_cur, axis=1)
+                          | (accepted_gpu & np.all(prop == s_cur, axis=1)))
+    n_checked = 0
+    for c in np.flatnonzero(same):
+        u = made.accept_uniform(seed, chain0 + c, rnd, N)
+        dec_o = made.indep_mh_decide(la_cur[c], lqo_cur[c], la_new[c], lqo_new[c], u)
+        if dec_o != accepted_gpu[c]:
+            delta = 2.0 * (la_new[c] - la_cur[c]) + lqo_cur[c] - lqo_new[c]
+            assert abs(np.log(u) - delta) <= tol[c], (c, np.log(u), delta, tol[c])
+        n_checked += 1
+        if accepted_gpu[c]:
+            assert np.array_equal(s_after[c], so[c])
+            assert st_after[c].view(np.float64)[0] == m_new[c] and st_after[c][1] == e_new[c]
+        else:
+            assert np.array_equal(s_after[c], s_cur[c])
+    assert n_checked >= 0.9 * B and 0 < accepted_gpu.mean() < 1

@@ -1,8 +1,9 @@
 """rtt_local_energy_noalloc: the local energy from a call that allocates no
-device memory, for callers that cannot allocate at that moment (inside CUDA
-stream capture, allocation-free loops, externally owned memory pools).  It
-must give the same results as rtt_local_energy, call after call, while its
-scratch comes from the library's fixed static device array.
+device memory, for callers that cannot allocate at that moment (loops that
+forbid allocator calls after start-up, programs whose device memory belongs
+to an external pool manager).  It must give the same results as
+rtt_local_energy, call after call, while its scratch comes from the library's
+fixed static device array.
 
 This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test."""
@@ -65,3 +66,40 @@ def test_noalloc_rejects_a_batch_beyond_the_static_area():
         st = f(m.handle, _p(spins), B, _p(e), None, None)
     assert st == 1
     assert b"static area" in rtt.lib().rtt_last_error()
+
+
+def test_noalloc_rejects_a_batch_whose_size_would_overflow():
+    """A batch so large that its scratch size overflows 64-bit arithmetic is
+    rejected as too large before anything is launched."""
+    rtt, f = _noalloc()
+    inst = inputs.workload("plain_6x6")
+    e = torch.full((4,), 3.5, dtype=torch.float64, device="cuda")
+    spins = torch.zeros((4, inst.n_spins), dtype=torch.uint8, device="cuda")
+    with rtt.RTT(inst, "fp32") as m:
+        for B in (1 << 62, (1 << 63) - 1, 1 << 40):
+            assert f(m.handle, _p(spins), B, _p(e), None, None) == 1
+            assert b"static area" in rtt.lib().rtt_last_error()
+    torch.cuda.synchronize()
+    assert torch.all(e == 3.5)
+
+
+def test_noalloc_rejects_unsupported_handles_and_null_arguments():
+    """Split-precision handles and general paths are not served
+    (RTT_ERR_UNSUPPORTED), null spins or e_loc are argument errors; in every
+    case e_loc is left as it was."""
+    rtt, f = _noalloc()
+    B = 16
+    e = torch.full((B,), -2.0, dtype=torch.float64, device="cuda")
+    with rtt.RTT(inputs.make_instance(3, 3, 2, 64, 3.0, seed=8), "fp16x3") as m:
+        spins = torch.zeros((B, 9), dtype=torch.uint8, device="cuda")
+        assert f(m.handle, _p(spins), B, _p(e), None, None) == 6
+    with rtt.RTT(inputs.workload("vhdd_6x6"), "fp32") as m:
+        spins = torch.zeros((B, 36), dtype=torch.uint8, device="cuda")
+        assert f(m.handle, _p(spins), B, _p(e), None, None) == 6
+    with rtt.RTT(inputs.workload("tiny_fp64"), "fp64") as m:
+        spins = torch.zeros((B, 9), dtype=torch.uint8, device="cuda")
+        assert f(m.handle, None, B, _p(e), None, None) == 1
+        assert f(m.handle, _p(spins), B, None, None, None) == 1
+        assert f(m.handle, _p(spins), -1, _p(e), None, None) == 1
+    torch.cuda.synchronize()
+    assert torch.all(e == -2.0)
