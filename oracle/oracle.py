@@ -293,6 +293,47 @@ class Oracle:
         return r2, u, taken, u < r2, states
 
 
+def mps_energy(inst) -> float:
+    """<psi|H|psi> / <psi|psi> of an R = 1 RTT -- a matrix product state in the
+    order of its path (Sec. 2.1, MPS = TT with Omega = N) -- by double-layer
+    transfer matrices, polynomial in N and chi: E <- sum_{s,t} O(s,t)
+    A_k[s]^T E A_k[t] site by site from b_L b_L^T, closed with b_R, each
+    contraction rescaled by its largest entry (the scales summed as logs); one
+    pass per Hamiltonian term, divided by the pass without operators."""
+    n, path, A = inst.n_spins, np.asarray(inst.path), np.asarray(inst.tensors)
+    if path.shape[0] != n:
+        raise ValueError("mps_energy needs R = 1 (each spin on one site)")
+    pos = {int(path[k]): k for k in range(path.shape[0])}
+    Zd = np.array([[1.0, 0.0], [0.0, -1.0]])
+    Xo = np.array([[0.0, 1.0], [1.0, 0.0]])
+
+    def expval(ops_at_sites):
+        E = np.outer(inst.b_left, inst.b_left)
+        logs = 0.0
+        for k in range(path.shape[0]):
+            O = ops_at_sites.get(k)
+            En = np.zeros_like(E)
+            for s in (0, 1):
+                for t in (0, 1):
+                    w = (1.0 if s == t else 0.0) if O is None else O[s, t]
+                    if w != 0.0:
+                        En += w * (A[k, s].T @ E @ A[k, t])
+            mx = np.abs(En).max()
+            E = En / mx
+            logs += math.log(mx)
+        return float(inst.b_right @ E @ inst.b_right), logs
+
+    den, ld = expval({})
+    e = 0.0
+    for i, j in np.asarray(inst.bonds).reshape(-1, 2):
+        num, ln = expval({pos[int(i)]: Zd, pos[int(j)]: Zd})
+        e += inst.J * num / den * math.exp(ln - ld)
+    for i in range(n):
+        num, ln = expval({pos[i]: Xo})
+        e -= inst.h * num / den * math.exp(ln - ld)
+    return e
+
+
 def philox4x64(counter, key):
     lib = _load()
     c = np.ascontiguousarray(counter, dtype=np.uint64)

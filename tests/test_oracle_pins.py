@@ -249,51 +249,11 @@ def test_local_energy_matches_dense_hamiltonian():
     assert o.exact_energy() == pytest.approx(e_exact, rel=1e-12)
 
 
-def _mps_energy(inst):
-    """<H> of an R = 1 RTT (an MPS in the order of its path) by double-layer
-    transfer matrices: E <- sum_{s,s'} O(s,s') A[s]^T E A[s'] site by site."""
-    n, path, A = inst.n_spins, inst.path, inst.tensors
-    pos = {int(path[k]): k for k in range(path.shape[0])}
-    Zd = np.array([[1.0, 0.0], [0.0, -1.0]])
-    Xo = np.array([[0.0, 1.0], [1.0, 0.0]])
-    Id = np.eye(2)
-
-    def expval(ops_at_sites):
-        E = np.outer(inst.b_left, inst.b_left)
-        for k in range(path.shape[0]):
-            O = ops_at_sites.get(k, Id)
-            En = np.zeros_like(E)
-            for s in (0, 1):
-                for t in (0, 1):
-                    if O[s, t] != 0.0:
-                        En += O[s, t] * (A[k, s].T @ E @ A[k, t])
-            mx = np.abs(En).max()
-            E = En / mx
-            scale_log = math.log(mx)
-            expval.logs.append(scale_log)
-        return float(inst.b_right @ E @ inst.b_right)
-
-    def ratio(ops):
-        expval.logs = []
-        num = expval(ops)
-        ln = sum(expval.logs)
-        expval.logs = []
-        den = expval({})
-        ld = sum(expval.logs)
-        return num / den * math.exp(ln - ld)
-    e = 0.0
-    for i, j in inst.bonds:
-        e += inst.J * ratio({pos[int(i)]: Zd, pos[int(j)]: Zd})
-    for i in range(n):
-        e -= inst.h * ratio({pos[i]: Xo})
-    return e
-
-
 def test_R1_transfer_matrix_energy_matches_enumeration():
     """R = 1: the RTT is an MPS (Sec. 2.1); its energy by transfer matrices."""
     inst = inputs.make_instance(4, 3, 1, 5, 2.5, seed=14, mixing=True)
     o = orc.Oracle(inst)
-    assert o.exact_energy() == pytest.approx(_mps_energy(inst), rel=1e-10)
+    assert o.exact_energy() == pytest.approx(orc.mps_energy(inst), rel=1e-10)
 
 
 def _chi1_instance(R, lx, ly, seed):
