@@ -691,22 +691,26 @@ __global__ void __launch_bounds__(NT * SCfg<CHI, F16>::NH + 32, 1)
                 g_waited = g + 1;
                 tc_after();
                 const uint32_t b_hi = stage0 + (uint32_t)st * C::STAGE, b_lo = b_hi + C::BOX;
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                    // logical K [64 at + 32 kk, +32): row entries 32 at + 16 kk .. +16
-                    const uint32_t ao = (uint32_t)(at * 16 + kk * 8);
-                    const uint32_t bo = (uint32_t)(kk * 64);
-                    const uint32_t first = (at | kk) != 0 ? 1u : 0u;
-                    mma_sp_ts(tmem, a_hi + ao, sdesc(b_hi + bo), meta, C::IDESC, first);
-                    mma_sp_ts(tmem, a_hi + ao, sdesc(b_lo + bo), meta, C::IDESC, 1u);
-                    mma_sp_ts(tmem, a_lo + ao, sdesc(b_hi + bo), meta, C::IDESC, 1u);
-                    if (dbl) {
-                        const uint32_t d2 = tmem + (uint32_t)C::ACC2;
-                        const uint32_t meta2 = tmem + (uint32_t)C::META2;
-                        mma_sp_ts(d2, a_hi + ao, sdesc(b_hi + bo), meta2, C::IDESC, first);
-                        mma_sp_ts(d2, a_hi + ao, sdesc(b_lo + bo), meta2, C::IDESC, 1u);
-                        mma_sp_ts(d2, a_lo + ao, sdesc(b_hi + bo), meta2, C::IDESC, 1u);
-                    }
+                // logical K [64 at + 32 kk, +32) reads row entries 32 at + 16 kk .. +16
+                const uint64_t dh0 = sdesc(b_hi), dh1 = sdesc(b_hi + 64);
+                const uint64_t dl0 = sdesc(b_lo), dl1 = sdesc(b_lo + 64);
+                const uint32_t ao = (uint32_t)(at * 16);
+                const uint32_t first = at != 0 ? 1u : 0u;
+                mma_sp_ts(tmem, a_hi + ao, dh0, meta, C::IDESC, first);
+                mma_sp_ts(tmem, a_hi + ao, dl0, meta, C::IDESC, 1u);
+                mma_sp_ts(tmem, a_lo + ao, dh0, meta, C::IDESC, 1u);
+                mma_sp_ts(tmem, a_hi + ao + 8, dh1, meta, C::IDESC, 1u);
+                mma_sp_ts(tmem, a_hi + ao + 8, dl1, meta, C::IDESC, 1u);
+                mma_sp_ts(tmem, a_lo + ao + 8, dh1, meta, C::IDESC, 1u);
+                if (MODE == M_SWEEP && dbl) {  // the first site of a row: the kept slice too
+                    const uint32_t d2 = tmem + (uint32_t)C::ACC2;
+                    const uint32_t meta2 = tmem + (uint32_t)C::META2;
+                    mma_sp_ts(d2, a_hi + ao, dh0, meta2, C::IDESC, first);
+                    mma_sp_ts(d2, a_hi + ao, dl0, meta2, C::IDESC, 1u);
+                    mma_sp_ts(d2, a_lo + ao, dh0, meta2, C::IDESC, 1u);
+                    mma_sp_ts(d2, a_hi + ao + 8, dh1, meta2, C::IDESC, 1u);
+                    mma_sp_ts(d2, a_hi + ao + 8, dl1, meta2, C::IDESC, 1u);
+                    mma_sp_ts(d2, a_lo + ao + 8, dh1, meta2, C::IDESC, 1u);
                 }
                 mma_commit(empty_bar(st));
             }
@@ -884,6 +888,22 @@ __global__ void __launch_bounds__(NT * SCfg<CHI, F16>::NH + 32, 1)
         }
     }
 
+    // a row with no site steps (the unflipped row when every site lies in the
+    // first block, R = 1) closes on its start row
+    if (MODE == M_ROWS && total_steps == 0 && epi) {
+        const int rq = row_end(a, j) + 1 - a.kmin;
+        const float *rclose = a.rstack + ((size_t)c * a.nr + rq) * CHI;
+        fin_E = E + a.rexp[(size_t)c * a.nr + rq];
+        float acc8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int ch = 0; ch < CPT; ++ch) {
+            const int gc = h * CPT + ch;
+            float y[64];
+            load_chunk(start + 64 * gc, y);
+            dot_chunk(y, rclose + 64 * gc, acc8);
+        }
+        fin_m = row_dot(dot_finish(acc8));
+    }
     // ---------------- outputs
     if (!aborted && lead) {
         if (MODE == M_ROWS) {

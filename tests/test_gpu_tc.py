@@ -99,14 +99,16 @@ def test_split_log_amplitudes_within_bound(name, make, B, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("name,make,B", CASES[:3], ids=[c[0] for c in CASES[:3]])
+@pytest.mark.parametrize("name,make,B", CASES, ids=[c[0] for c in CASES])
 def test_split_local_energy_teacher_forced(name, make, B, prec):
     """Same configurations through the FP64 oracle and the split path.  Every
     ratio psi(s^(i))/psi(s) obeys the split bound of its two amplitudes,
     |dr| <= |r| eps_site (K(s) + K(s^(i))), K = sum_k kappa_k + kappa_fin from
-    the oracle; FP16X3 also meets the precision gate of the metric: the mean
-    local energy within 1e-4 relative (of the mean |E_loc| when the mean is
-    near zero)."""
+    the oracle, and so every local energy the bound that follows from them.
+    FP16X3 also meets the precision gate of the metric (the mean local energy
+    within 1e-4 relative, of the mean |E_loc| when the mean is near zero)
+    wherever that bound itself lies within the gate: the R = 1 case with
+    random chi = 128 cores has ratios large enough that it does not."""
     rtt = _rtt()
     inst = make()
     o = orc.Oracle(inst)
@@ -134,7 +136,13 @@ def test_split_local_energy_teacher_forced(name, make, B, prec):
     print(f"[{name}] {prec} E_loc: mean rel err {rel_mean:.2e} (|dE| {de:.2e}), "
           f"max |dr|/bound {np.max(dr / bound):.3f}, median |dr|/|r| {np.median(dr / np.abs(r_o[:nc])):.2e}")
     assert np.all(dr <= bound)
-    if prec == "fp16x3":
+    ebound = local_energy_bound(o, spins, r_o, eps, inst.J, inst.h, inst.bonds.shape[0])
+    scale = max(abs(e_o.mean()), np.mean(np.abs(e_o)))
+    print(f"[{name}] {prec} E_loc: max |dE|/bound {np.max(np.abs(e - e_o) / ebound):.3f}, "
+          f"mean bound / scale {ebound.mean() / scale:.2e}")
+    assert np.all(np.abs(e - e_o) <= ebound)
+    assert de <= ebound.mean()
+    if prec == "fp16x3" and ebound.mean() <= 1e-4 * scale:
         assert rel_mean <= 1e-4
 
 
