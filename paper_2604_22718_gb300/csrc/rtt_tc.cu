@@ -1598,6 +1598,544 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, tcols);
 }
 
+
+// ------------------------------------------------------------------ split-row sweep (chi = 128)
+// The chi = 128 sweep on a CTA pair, with the sparse site products of k_tc:
+// each proposal row is split between a left tile (sites j..j+nL-1 from
+// l_{j-1}, rank 0) and a right tile (the rest, backwards from the cached
+// right environment, rank 1), each on its own SM with its own tensor pipe and
+// tensor memory, so a proposal costs about half the sequential site steps of
+// the single-tile sweep and a batch holds twice the SMs.  Per CTA: four
+// epilogue warps (one row per thread, 64-column chunks) and one producer warp
+// whose lane 0 streams the site tensors by TMA and issues the MMAs.
+//   left : first site of a row into two accumulators (flipped slice, the kept
+//          slice = l_j if rejected); at its last site it waits for the right
+//          half-row, forms psi(s') by one dot product, decides (R8: FP64
+//          ratio, 53-bit uniform), keeps the flip bits and stores them into
+//          the right CTA's spin words, then arrives on the right's decision
+//          barrier (release / acquire at cluster scope).
+//   right: per sweep the right environment r_k (last block), then per
+//          proposal its half-row; the finished half-row (FP32, 128 x 128,
+//          float4 chunks swizzled by row) and its exponents go to the left
+//          CTA's shared memory in one bulk copy completing on the left's
+//          mbarrier.  It waits for the left's decision on spin p(j) only
+//          before the metadata of a site that carries that spin, and before
+//          it rewrites its hand-off buffer.
+// TMEM (512 columns in both): accumulator [0,128), kept accumulator
+// [128,256) (left), A hi/lo [256,384), metadata at 384 and 448.  Every wait is
+// bounded; both CTAs meet in a cluster barrier before they exit.
+constexpr int SPP_THREADS = NT + 32;
+constexpr int SPP_HAND = NT * 128 * 4;        // one right half-row hand-off, [128][128] floats
+constexpr int kPairLeftLess128 = -1;          // sites the left tile takes below half a row
+
+inline size_t spp_smem(int N, int L) {
+    return 1024 + (size_t)SCfg<128>::NSTG * SCfg<128>::STAGE + SPP_HAND + 4 * NT + 128 +
+           (size_t)16 * N + (size_t)4 * L;
+}
+
+// Chunk ch (entries 64 ch .. 64 ch + 63) of the closing contraction against
+// the hand-off buffer (row m, float4 chunk x at ((x ^ (m & 7)) << 2)), in the
+// partial sums dot_chunk uses.
+__device__ __forceinline__ void dot_hand(const float (&y)[64], const float *__restrict__ hrow, int m,
+                                         int ch, float (&acc)[8]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float4 x = *reinterpret_cast<const float4 *>(hrow + (((16 * ch + i) ^ (m & 7)) << 2));
+        const int p = (2 * i) & 7;
+        acc[p] = fmaf(y[4 * i], x.x, acc[p]);
+        acc[p + 1] = fmaf(y[4 * i + 1], x.y, acc[p + 1]);
+        acc[(p + 2) & 7] = fmaf(y[4 * i + 2], x.z, acc[(p + 2) & 7]);
+        acc[(p + 3) & 7] = fmaf(y[4 * i + 3], x.w, acc[(p + 3) & 7]);
+    }
+}
+__device__ __forceinline__ void put_hand(const float (&y)[64], float *__restrict__ hrow, int m, int ch) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        *reinterpret_cast<float4 *>(hrow + (((16 * ch + i) ^ (m & 7)) << 2)) =
+            make_float4(y[4 * i], y[4 * i + 1], y[4 * i + 2], y[4 * i + 3]);
+}
+
+// Position of a CTA in its sequence of site steps: sweep, proposal, step of
+// the half-row (or of the right environment when env is set).
+struct PairCur {
+    int sw, j, t, env;
+};
+
+template <bool F16, bool GEN>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPP_THREADS, 1)
+    k_sp_pair(const __grid_constant__ CUtensorMap map, const Args a) {
+    constexpr int CHI = 128;
+    using C = SCfg<CHI, F16>;
+    static_assert(C::NH == 1 && C::CPT == 2, "one epilogue thread per row");
+    constexpr int NSG = C::NSTG;
+    constexpr int CPT = C::CPT;
+    constexpr uint32_t HAND_BYTES = (uint32_t)SPP_HAND + 4u * NT;
+    extern __shared__ uint8_t smem_raw[];
+    // the dynamic shared memory starts at the same offset in both CTAs, so the
+    // 1024-byte alignment gives the same layout in both
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t stage0 = sa(base);
+    float *hand = (float *)(base + NSG * C::STAGE);      // [128][128] (+ exponents below)
+    int32_t *hexp = (int32_t *)(hand + NT * CHI);        // [128]
+    uint64_t *bars = (uint64_t *)(hexp + NT);
+    const uint32_t bar0 = sa(bars);
+    // bars: full[NSG], empty[NSG], done, hand (left), decision (right)
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (NSG + s); };
+    const uint32_t done_bar = bar0 + 8u * (2 * NSG);
+    const uint32_t hand_bar = bar0 + 8u * (2 * NSG + 1);
+    const uint32_t dec_bar = bar0 + 8u * (2 * NSG + 2);
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NSG + 3);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    uint32_t *bits = (uint32_t *)((uint8_t *)bars + 128);
+    uint32_t *tab = bits + 4 * a.N;
+
+    const int X = (int)cluster_rank();  // 0 left, 1 right
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool epi = warp < 4;
+    const bool issuer = warp == 4 && lane == 0;
+    const int q = warp & 3;
+    const int m = 32 * q + lane;
+    const int64_t c_raw = (int64_t)(blockIdx.x >> 1) * NT + m;
+    const bool active = epi && c_raw < a.B;
+    const int64_t c = c_raw < a.B ? c_raw : a.B - 1;
+    const int N = a.N, L = a.L;
+    const int span = (a.R - 1) * N + 1;
+    const int rbase = a.kmin;
+    auto nL_of = [&](int j) -> int {
+        const int T = GEN ? L - j : span;
+        return min(T - 1, max(1, T / 2 - kPairLeftLess128));
+    };
+    auto nR_of = [&](int j) -> int { return (GEN ? L - j : span) - nL_of(j); };
+    const bool has_env = X == 1 && !GEN && N > 1;  // the right tile rebuilds r per sweep (N - 1 steps)
+    auto site_of = [&](const PairCur &x) -> int {
+        if (x.env) return L - 1 - x.t;
+        if (X == 0) return x.j + x.t;
+        return GEN ? L - 1 - x.t : (a.R - 1) * N + x.j - x.t;
+    };
+    auto cur_start = [&]() -> PairCur { return PairCur{0, 0, 0, has_env ? 1 : 0}; };
+    auto cur_next = [&](PairCur &x) {
+        if (x.env) {
+            if (++x.t == N - 1) {
+                x.env = 0;
+                x.t = 0;
+                x.j = 0;
+            }
+            return;
+        }
+        if (++x.t == (X == 0 ? nL_of(x.j) : nR_of(x.j))) {
+            x.t = 0;
+            if (++x.j == N) {
+                x.j = 0;
+                ++x.sw;
+                x.env = has_env ? 1 : 0;
+            }
+        }
+    };
+    long long per_sweep = has_env ? N - 1 : 0;
+    for (int j = 0; j < N; ++j) per_sweep += X == 0 ? nL_of(j) : nR_of(j);
+    const long long total_steps = per_sweep * a.n_sweeps;
+    const long long total_atoms = total_steps * C::KA;
+
+    if (warp == 0) tmem_alloc(sa(tmem_slot), 512u);
+    if (issuer) {
+        for (int s = 0; s < NSG; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        mbar_init(done_bar, 1);
+        mbar_init(hand_bar, 1);  // armed by the left with the bytes of one hand-off
+        mbar_init(dec_bar, 4);   // one arrival per left epilogue warp
+        *abort_flag = 0;
+        fence_barrier_init();
+        if (X == 0 && total_steps > 0) mbar_expect_tx(hand_bar, HAND_BYTES);  // the first hand-off
+    }
+    for (int k = tid; k < L; k += SPP_THREADS)
+        tab[k] = ((uint32_t)__ldg(GEN ? a.path + k : a.q + (k % N)) & 0xffffu) |
+                 ((uint32_t)(__ldg(a.cexp + k) & 0xffff) << 16);
+    if (epi) {
+        for (int i = 0; i < N; ++i) {
+            const uint32_t w = __ballot_sync(FULL, a.spins_in[c * N + i] != 0);
+            if (lane == 0) bits[i * 4 + q] = w;
+        }
+    }
+    auto spin = [&](int i) -> int { return (int)((bits[i * 4 + q] >> lane) & 1u); };
+    auto site_spin = [&](int k) -> int { return (int)(tab[k] & 0xffffu); };
+    auto site_cexp = [&](int k) -> int { return (int)(int16_t)(tab[k] >> 16); };
+    auto fail_now = [&]() {
+        atomicOr(a.err, 1);
+        *abort_flag = 1;
+    };
+    auto bwait_cluster = [&](uint32_t bar, uint32_t parity) -> bool {
+        if (*abort_flag) return false;
+        if (!mbar_wait_cluster(bar, parity, a.wait_limit)) {
+            fail_now();
+            return false;
+        }
+        return true;
+    };
+    // the slice a row takes at the site of x: the proposal's spin flipped
+    auto slice_of = [&](const PairCur &x) -> int {
+        const int sk = site_spin(site_of(x));
+        if (x.env) return spin(sk);
+        return spin(sk) ^ (sk == site_spin(x.j) ? 1 : 0);
+    };
+
+    // start rows
+    int64_t E = 0, El = 0, Ekeep = 0, Eflip = 0;
+    double pm = 0.0;
+    int64_t pe = 0, acc_count = 0;
+    const float *start = X == 0 ? a.bl : a.br;
+    if (X == 0) {
+        pm = a.state[c].mant;
+        pe = a.state[c].exp2;
+    } else if (!GEN && active) {
+#pragma unroll 1
+        for (int ch = 0; ch < CPT; ++ch) {
+            float y[64];
+            load_chunk(a.br + 64 * ch, y);
+            store_chunk(a.rstack + ((size_t)c * a.nr + (a.nr - 1)) * CHI + 64 * ch, y);
+        }
+        a.rexp[(size_t)c * a.nr + (a.nr - 1)] = 0;
+    }
+    tc_before();
+    cluster_sync_all();  // barriers initialised in both CTAs before any remote arrive
+    tc_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t tw = tmem + ((uint32_t)(q * 32) << 16);
+    const uint32_t ta = tw + (uint32_t)C::A_COL;
+    const uint32_t tm = tw + (uint32_t)C::META;
+    const int lane_a = (lane & 16) | (lane & 7), lane_b = lane_a | 8;
+    auto write_meta = [&](const PairCur &x) {
+        const int sl = slice_of(x);
+        const int s_a = __shfl_sync(FULL, sl, lane_a), s_b = __shfl_sync(FULL, sl, lane_b);
+        tmem_st_1(tm, (s_a ? C::HALF1 : C::HALF0) | ((s_b ? C::HALF1 : C::HALF0) << 16));
+        if (X == 0 && x.t == 0)  // the first site of a left half-row: the kept slice too
+            tmem_st_1(tm + (uint32_t)(C::META2 - C::META),
+                      (s_a ? C::HALF0 : C::HALF1) | ((s_b ? C::HALF0 : C::HALF1) << 16));
+    };
+    auto row_exp = [&](uint32_t col) -> int {
+        float m8[8];
+#pragma unroll 1
+        for (int ch = 0; ch < CPT; ++ch) {
+            float y[64];
+            tmem_ld_64(tw + col + (uint32_t)(64 * ch), y);
+#pragma unroll
+            for (int i = 0; i < 64; ++i)
+                m8[i & 7] = (ch == 0 && i < 8) ? fabsf(y[i]) : fmaxf(m8[i & 7], fabsf(y[i]));
+        }
+        const float mx = fmaxf(fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3])),
+                               fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7])));
+        const bool usable = (mx > 0.f) && isfinite(mx);
+        int e = usable ? rttd::exponent_of(mx) : 0;
+        if (__all_sync(FULL, !usable || (e >= 0 && e < 8)) || !usable) e = 0;
+        return e;
+    };
+    auto row_chunk = [&](uint32_t col, int e, int ch, float (&y)[64]) {
+        tmem_ld_64(tw + col + (uint32_t)(64 * ch), y);
+        scale_chunk(y, e);
+    };
+    auto write_A_row = [&](const float *src) {
+#pragma unroll 1
+        for (int ch = 0; ch < CPT; ++ch) {
+            float y[64];
+            load_chunk(src + 64 * ch, y);
+            write_A_chunk<CHI, F16>(ta, ch, y);
+        }
+    };
+    PairCur cur = cur_start();
+    if (epi && total_steps > 0) {
+        write_A_row(start);
+        write_meta(cur);
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+
+    // producer: atom g = step * KA + at, its own cursor ahead of the steps
+    long long g_issued = 0, g_waited = 0;
+    PairCur pc = cur_start();
+    int p_at = 0;
+    auto issue_next = [&]() {
+        const long long g = g_issued;
+        const int st = (int)(g % NSG);
+        const int k = site_of(pc);
+        const int y_hi = ((X * 2 + 0) * L + k) * CHI;
+        const int y_lo = ((X * 2 + 1) * L + k) * CHI;
+        const uint32_t dst = stage0 + (uint32_t)st * C::STAGE;
+        mbar_expect_tx(full_bar(st), (uint32_t)C::STAGE);
+        tma_load_2d(dst, &map, p_at * 64, y_hi, full_bar(st));
+        tma_load_2d(dst + C::BOX, &map, p_at * 64, y_lo, full_bar(st));
+        ++g_issued;
+        if (++p_at == C::KA) {
+            p_at = 0;
+            cur_next(pc);
+        }
+    };
+    if (issuer)
+        while (g_issued < total_atoms && g_issued < NSG) issue_next();
+
+    const uint32_t peer_dec = peer_addr(dec_bar, 1u);
+    const uint32_t peer_hand = peer_addr(hand_bar, 0u);
+    const uint32_t peer_buf = peer_addr(sa(hand), 0u);
+    long long nhand = 0, ndec = 0;
+    int pend = -1;  // right: the spin whose decision is outstanding
+    auto settle = [&]() {
+        if (pend >= 0) {
+            bwait_cluster(dec_bar, (uint32_t)(ndec++ & 1));
+            pend = -1;
+        }
+    };
+    bool aborted = false;
+
+    for (long long t = 0; t < total_steps; ++t) {
+        const bool dbl = X == 0 && cur.t == 0;
+        // ---------------- MMA issue, then the refill (producer)
+        if (issuer) {
+            const uint32_t a_hi = tmem + (uint32_t)C::A_COL, a_lo = a_hi + (uint32_t)(CHI / 2);
+            const uint32_t meta = tmem + (uint32_t)C::META;
+            for (int at = 0; at < C::KA; ++at) {
+                const long long g = t * C::KA + at;
+                const int st = (int)(g % NSG);
+                if (!mbar_wait(full_bar(st), (uint32_t)((g / NSG) & 1), a.wait_limit)) {
+                    fail_now();
+                    break;
+                }
+                g_waited = g + 1;
+                tc_after();
+                const uint32_t b_hi = stage0 + (uint32_t)st * C::STAGE, b_lo = b_hi + C::BOX;
+                const uint64_t dh0 = sdesc(b_hi), dh1 = sdesc(b_hi + 64);
+                const uint64_t dl0 = sdesc(b_lo), dl1 = sdesc(b_lo + 64);
+                const uint32_t ao = (uint32_t)(at * 16);
+                const uint32_t first = at != 0 ? 1u : 0u;
+                mma_sp_ts(tmem, a_hi + ao, dh0, meta, C::IDESC, first);
+                mma_sp_ts(tmem, a_hi + ao, dl0, meta, C::IDESC, 1u);
+                mma_sp_ts(tmem, a_lo + ao, dh0, meta, C::IDESC, 1u);
+                mma_sp_ts(tmem, a_hi + ao + 8, dh1, meta, C::IDESC, 1u);
+                mma_sp_ts(tmem, a_hi + ao + 8, dl1, meta, C::IDESC, 1u);
+                mma_sp_ts(tmem, a_lo + ao + 8, dh1, meta, C::IDESC, 1u);
+                if (dbl) {
+                    const uint32_t d2 = tmem + (uint32_t)C::ACC2;
+                    const uint32_t meta2 = tmem + (uint32_t)C::META2;
+                    mma_sp_ts(d2, a_hi + ao, dh0, meta2, C::IDESC, first);
+                    mma_sp_ts(d2, a_hi + ao, dl0, meta2, C::IDESC, 1u);
+                    mma_sp_ts(d2, a_lo + ao, dh0, meta2, C::IDESC, 1u);
+                    mma_sp_ts(d2, a_hi + ao + 8, dh1, meta2, C::IDESC, 1u);
+                    mma_sp_ts(d2, a_hi + ao + 8, dl1, meta2, C::IDESC, 1u);
+                    mma_sp_ts(d2, a_lo + ao + 8, dh1, meta2, C::IDESC, 1u);
+                }
+                mma_commit(empty_bar(st));
+            }
+            mma_commit(done_bar);
+            if (!*abort_flag) {
+                for (int at = 0; at < C::KA; ++at) {
+                    const long long g = t * C::KA + at;
+                    if (g + NSG >= total_atoms) break;
+                    const int st = (int)(g % NSG);
+                    if (!mbar_wait(empty_bar(st), (uint32_t)((g / NSG) & 1), a.wait_limit)) {
+                        fail_now();
+                        break;
+                    }
+                    issue_next();
+                }
+            }
+        }
+        bool write_next = false;
+        const int k = site_of(cur);
+        const int ck = site_cexp(k);
+        if (epi && !mbar_wait(done_bar, (uint32_t)(t & 1), a.wait_limit)) fail_now();
+        tc_after();
+        __syncwarp();
+        if (!epi) {
+            // the producer warp's other lanes only keep the cursor
+        } else if (cur.env) {
+            // ---------------- right environment r_k = A_k r_{k+1}
+            const int e = row_exp(0u);
+            E += e - ck;
+            float *dst = a.rstack + ((size_t)c * a.nr + (k - rbase)) * CHI;
+            if (active) a.rexp[(size_t)c * a.nr + (k - rbase)] = (int32_t)E;
+#pragma unroll 1
+            for (int ch = 0; ch < CPT; ++ch) {
+                float y[64];
+                row_chunk(0u, e, ch, y);
+                if (active) store_chunk(dst + 64 * ch, y);
+                write_A_chunk<CHI, F16>(ta, ch, y);  // the last one starts proposal 0's half-row
+            }
+            write_next = true;
+        } else if (X == 0) {
+            // ---------------- left half-row of proposal j
+            const int j = cur.j;
+            const bool lastl = cur.t + 1 == nL_of(j);
+            int efin;
+            if (cur.t == 0) {
+                // the kept slice: l_j if the proposal is rejected
+                const int e2 = row_exp((uint32_t)C::ACC2);
+                Ekeep = El + e2 - ck;
+#pragma unroll 1
+                for (int ch = 0; ch < CPT; ++ch) {
+                    float y[64];
+                    row_chunk((uint32_t)C::ACC2, e2, ch, y);
+                    if (active) store_chunk(a.lstack + ((size_t)c * N + j) * CHI + 64 * ch, y);
+                }
+                // the flipped start of the row (l_j if accepted)
+                const int e1 = row_exp(0u);
+                Eflip = El + e1 - ck;
+                E = Eflip;
+#pragma unroll 1
+                for (int ch = 0; ch < CPT; ++ch) {
+                    float y[64];
+                    row_chunk(0u, e1, ch, y);
+                    if (active) store_chunk(a.tmp + (size_t)c * CHI + 64 * ch, y);
+                    if (!lastl) write_A_chunk<CHI, F16>(ta, ch, y);
+                }
+                efin = e1;
+            } else {
+                const int e = row_exp(0u);
+                E += e - ck;
+                if (!lastl) {
+#pragma unroll 1
+                    for (int ch = 0; ch < CPT; ++ch) {
+                        float y[64];
+                        row_chunk(0u, e, ch, y);
+                        write_A_chunk<CHI, F16>(ta, ch, y);
+                    }
+                }
+                efin = e;
+            }
+            if (!lastl) {
+                write_next = true;
+            } else {
+                // the right half-row, from the peer CTA; then arm the next hand-off
+                bwait_cluster(hand_bar, (uint32_t)(nhand++ & 1));
+                const bool next_prop = j + 1 < N;
+                const bool next_sweep = !next_prop && cur.sw + 1 < a.n_sweeps;
+                if (tid == 0 && (next_prop || next_sweep)) mbar_expect_tx(hand_bar, HAND_BYTES);
+                float acc8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+                for (int ch = 0; ch < CPT; ++ch) {
+                    float y[64];
+                    row_chunk(0u, efin, ch, y);
+                    dot_hand(y, hand + m * CHI, m, ch, acc8);
+                }
+                double mm = dot_finish(acc8);
+                int64_t Ep = E + hexp[m];
+                normalize_scalar(mm, Ep);
+                const double ratio = ldexp(mm / pm, (int)(Ep - pe));
+                const double x = rttd::mcmc_uniform(a.seed, (uint64_t)(a.chain0 + c),
+                                                    (uint64_t)(a.sweep0 + cur.sw), (uint64_t)j);
+                const bool accept = active && !*abort_flag && (x < ratio * ratio);
+                if (accept) {
+                    pm = mm;
+                    pe = Ep;
+                    ++acc_count;
+                    El = Eflip;
+                } else {
+                    El = Ekeep;
+                }
+                const int iq = site_spin(j);
+                const uint32_t flips = __ballot_sync(FULL, accept);
+                if (lane == 0) {
+                    const uint32_t w = bits[iq * 4 + q] ^ flips;
+                    bits[iq * 4 + q] = w;
+                    st_cluster_u32(peer_addr(sa(bits + iq * 4 + q), 1u), w);
+                    mbar_arrive_remote(peer_dec);  // the decision is with the right CTA
+                }
+                __syncwarp();
+                // l_j: the flipped start on acceptance (copied over the kept row)
+                float *lj = a.lstack + ((size_t)c * N + j) * CHI;
+#pragma unroll 1
+                for (int ch = 0; ch < CPT; ++ch) {
+                    float y[64];
+                    load_chunk((accept ? a.tmp + (size_t)c * CHI : lj) + 64 * ch, y);
+                    if (accept) store_chunk(lj + 64 * ch, y);
+                    if (next_prop) write_A_chunk<CHI, F16>(ta, ch, y);
+                }
+                if (next_prop) {
+                    write_next = true;
+                } else if (next_sweep) {
+                    write_A_row(a.bl);
+                    El = 0;
+                    write_next = true;
+                }
+            }
+        } else {
+            // ---------------- right half-row of proposal j
+            const int j = cur.j;
+            const bool lastr = cur.t + 1 == nR_of(j);
+            const int e = row_exp(0u);
+            E += e - ck;
+            if (!lastr) {
+#pragma unroll 1
+                for (int ch = 0; ch < CPT; ++ch) {
+                    float y[64];
+                    row_chunk(0u, e, ch, y);
+                    write_A_chunk<CHI, F16>(ta, ch, y);
+                }
+                write_next = true;
+            } else {
+                settle();  // the previous hand-off has been read
+#pragma unroll 1
+                for (int ch = 0; ch < CPT; ++ch) {
+                    float y[64];
+                    row_chunk(0u, e, ch, y);
+                    put_hand(y, hand + m * CHI, m, ch);
+                }
+                hexp[m] = (int32_t)E;
+                fence_async_smem();
+                bar_sync_n(1, NT);  // the four epilogue warps have written
+                if (tid == 0 && !*abort_flag) bulk_copy_to_peer(peer_buf, sa(hand), HAND_BYTES, peer_hand);
+                const bool next_prop = j + 1 < N;
+                const bool next_sweep = !next_prop && cur.sw + 1 < a.n_sweeps;
+                if (next_prop) {  // the next half-row's first MMA does not depend on this decision
+                    if (GEN) {
+                        write_A_row(a.br);
+                        E = 0;
+                    } else {
+                        write_A_row(a.rstack + ((size_t)c * a.nr + (j + 1)) * CHI);
+                        E = a.rexp[(size_t)c * a.nr + (j + 1)];
+                    }
+                    write_next = true;
+                } else if (next_sweep) {
+                    write_A_row(a.br);
+                    E = 0;
+                    write_next = true;
+                }
+                pend = site_spin(j);  // this proposal's decision is now outstanding
+            }
+        }
+        cur_next(cur);
+        if (write_next && epi) {
+            if (X == 1 && pend >= 0 && site_spin(site_of(cur)) == pend) settle();
+            write_meta(cur);
+        }
+        tc_before();
+        __syncthreads();
+        tc_after();
+        if (*abort_flag) {
+            aborted = true;
+            break;
+        }
+    }
+    if (X == 1 && epi) settle();
+    // after an expired wait: let a hand-off that is still in flight land
+    if (X == 0 && tid == 0 && aborted && total_steps > 0)
+        mbar_wait_cluster(hand_bar, (uint32_t)(nhand & 1), a.wait_limit);
+    if (X == 0 && !aborted && active) {
+        for (int i = 0; i < N; ++i) a.spins_out[c * N + i] = (uint8_t)spin(i);
+        a.state[c].mant = pm;
+        a.state[c].exp2 = pe;
+        if (a.n_accept) a.n_accept[c] += acc_count;
+    }
+    if (issuer && aborted) {
+        for (long long g = g_waited; g < g_issued; ++g)
+            mbar_wait(full_bar((int)(g % NSG)), (uint32_t)((g / NSG) & 1), a.wait_limit);
+    }
+    tc_before();
+    cluster_sync_all();  // no CTA leaves while its peer may still store into it
+    tc_after();
+    if (warp == 0) tmem_dealloc(tmem, 512u);
+}
+
 }  // namespace tcd
 
 // ====================================================================== host side
@@ -1911,7 +2449,19 @@ rtt_status tc_sweep(rtt_s *h, uint8_t *spins, rtt_chain_state *state, int64_t B,
                       "at least two replicas");
         return RTT_ERR_UNSUPPORTED;
     }
-    if (p->chi == 64 && h->R >= 2 && h->N >= 2) {
+    const size_t smem_pair128 = std::max(tcd::spp_smem(h->N, h->L), (size_t)164 * 1024);
+    if (p->chi == 128 && h->periodic && h->R >= 2 && h->N >= 2 && smem_pair128 <= (size_t)227 * 1024) {
+        // split-row sweep on CTA pairs with the sparse site products; the same
+        // shared-memory floor keeps every other TMEM-allocating CTA off its SMs
+        auto go = [&](auto kern) {
+            cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem_pair128);
+            if (err == cudaSuccess) kern<<<2 * tiles(B), tcd::SPP_THREADS, smem_pair128, st>>>(p->map_sp, a);
+            return err;
+        };
+        e = p->f16 ? go(tcd::k_sp_pair<true, false>) : go(tcd::k_sp_pair<false, false>);
+        if (e == cudaSuccess) e = cudaGetLastError();
+    } else if (p->chi == 64 && h->R >= 2 && h->N >= 2) {
         // split-row sweep on CTA pairs.  At least 164 KB of shared memory: no
         // other CTA that allocates TMEM (a second pair CTA, a 66 KB tile kernel
         // of the energy) fits beside a pair CTA on one SM, so no tcgen05.alloc

@@ -167,13 +167,14 @@ def test_split_sampler_energy_matches_exact(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("chi", [64, 128])
-def test_split_sweep_follows_oracle_decisions(prec, chi):
+@pytest.mark.parametrize("R,chi", [(2, 64), (2, 128), (1, 128)])
+def test_split_sweep_follows_oracle_decisions(prec, R, chi):
     """One sweep from the same start: every decision the split-precision sweep
     takes is the FP64 rule's at the same state, except at near ties |u - r^2|
-    within the ratio bound; none is left unexplained."""
+    within the ratio bound; none is left unexplained.  R = 2 runs the
+    split-row sweeps on CTA pairs, R = 1 the single-tile sweep."""
     rtt = _rtt()
-    inst = inputs.make_instance(6, 6, 2, chi, 3.0, seed=5)
+    inst = inputs.make_instance(6, 6, R, chi, 3.0, seed=5)
     o = orc.Oracle(inst)
     B = 64
     s0 = inputs.initial_spins(44, B, 36)
@@ -191,6 +192,38 @@ def test_split_sweep_follows_oracle_decisions(prec, chi):
                      f"(largest gap / tolerance {worst:.3f})")
     assert np.array_equal(acc.cpu().numpy(),
                           np.sum(s1[:, inst.path[:36]] != s0[:, inst.path[:36]], axis=1))
+
+
+@pytest.mark.parametrize("chi", [64, 128])
+def test_split_two_sweeps_in_one_call_equal_two_calls(chi):
+    """Two sweeps in one call (the sweep boundary inside the kernel: the right
+    environment rebuilt from the new spins, the left row restarted from b_L)
+    give the same spins, amplitudes and acceptance counts, bit for bit, as two
+    calls of one sweep each; each of those sweeps follows the FP64 rule except
+    at explained near ties.  Two tiles, the second ragged."""
+    rtt = _rtt()
+    inst = inputs.make_instance(6, 6, 2, chi, 3.0, seed=5)
+    o = orc.Oracle(inst)
+    B = 200
+    s0 = inputs.initial_spins(46, B, 36)
+    with rtt.RTT(inst, "fp16x3", seed=13) as m:
+        sa_ = torch.from_numpy(s0.copy()).cuda()
+        _, _, sta = m.log_amplitudes(sa_)
+        sb = sa_.clone()
+        stb = sta.clone()
+        acca = torch.zeros(B, dtype=torch.int64, device="cuda")
+        accb = torch.zeros(B, dtype=torch.int64, device="cuda")
+        m.mcmc_sweep(sa_, sta, 0, 2, 1, None, acca)
+        m.mcmc_sweep(sb, stb, 0, 1, 1, None, accb)
+        s_mid = sb.cpu().numpy()
+        m.mcmc_sweep(sb, stb, 1, 1, 1, None, accb)
+        torch.cuda.synchronize()
+        assert _status_ok(m)
+    assert torch.equal(sa_, sb) and torch.equal(sta, stb) and torch.equal(acca, accb)
+    eps = eps_site(chi, "fp16x3")
+    for sw, (x0, x1) in enumerate([(s0, s_mid), (s_mid, sb.cpu().numpy())]):
+        n, nd, worst = check_sweep_divergences(o, 13, x0, x1, sw, eps, slack=2.0 ** -23)
+        print(chi, f"sweep {sw}: {nd} of {n} decisions differ from FP64 (worst {worst:.3f})")
 
 
 @pytest.mark.parametrize("prec", PRECS)
