@@ -70,7 +70,7 @@ def parse():
 
 
 # timed steps when --steps is not given: each runs for seconds
-DEFAULT_STEPS = {"learned_16x16": 20, "plain_6x6": 1000, "vhdd_6x6": 500, "prec_10x10": 50,
+DEFAULT_STEPS = {"learned_16x16": 20, "plain_16x16": 20, "plain_6x6": 1000, "vhdd_6x6": 500, "prec_10x10": 50,
                  "tiny_fp64": 1000, "batched64": 3, "dual_6x6": 500, "physical_6x6": 3,
                  "physical_10x10": 2}
 

@@ -192,6 +192,9 @@ WORKLOADS = {
     "plain_6x6":     dict(lx=6, ly=6, R=2, chi=64, h=3.0, mixing=True, chains=4096, sweeps=2000, seed=22720),
     "prec_10x10":    dict(lx=10, ly=10, R=3, chi=128, h=3.04, mixing=True, chains=16384, sweeps=1000, seed=22721),
     "learned_16x16": dict(lx=16, ly=16, R=2, chi=128, h=3.044, mixing=True, chains=8192, sweeps=128, seed=22723),
+    # the same state and chains with local flips only (the plain sampler the
+    # learned proposal is compared with)
+    "plain_16x16":   dict(lx=16, ly=16, R=2, chi=128, h=3.044, mixing=True, chains=8192, sweeps=128, seed=22723),
     # the path sigma^V + sigma^H + sigma^D + sigma^D' of Sec. 4 (four replicas), FP32/FP64 sampler
     "vhdd_6x6":      dict(lx=6, ly=6, R=4, chi=64, h=3.0, mixing=True, chains=4096, sweeps=100, seed=22729,
                           orderings=("V", "H", "D", "Dp")),
