@@ -1,25 +1,27 @@
 // rtt_tc.cu -- tensor-core form of the RTT site chain (sm_103a, tcgen05).
 //
-// Per site k the rows of a 128-chain tile are contracted with both spin
-// slices at once, D[128 x 2chi] = V[128 x chi] . [A_k[0] | A_k[1]] (Eq. RTT
-// evaluated left to right; right-to-left steps use the transposed slices),
-// on the 5th-generation tensor cores:
+// Per site k the rows of a 128-chain tile are multiplied by the slice of
+// their own spin, v <- v A_k[s] (Eq. RTT evaluated left to right; right-to-
+// left steps use the transposed slices), on the 5th-generation tensor cores:
 //   - operands in 16-bit hi/lo split form, x = hi + lo + O(u^2 |x|) with u
 //     the unit roundoff of the 16-bit type (BF16: 2^-8, FP16: 2^-11); three
 //     products hi.hi + hi.lo + lo.hi accumulate in FP32 in TMEM.  Each site
 //     tensor is prescaled by an exact power of two 2^c_k (max entry in [1,2))
 //     so that FP16 stays in its normal range; c_k is taken back out of the
 //     integer exponent sum;
+//   - the two slices are interleaved along K, so a row's operand is 2:4
+//     sparse and one tcgen05.mma.sp with a per-row metadata word computes
+//     exactly the row's own slice (SCfg); the chi = 64 split-row sweep keeps
+//     the dense form, both slices at once (N = 2 chi) and a per-row select;
 //   - the site tensors are streamed by TMA (128-byte swizzle, K-major) into a
-//     two-stage shared-memory ring; the rows live in shared memory in the
-//     same swizzled K-major layout, written by the epilogue;
-//   - epilogue (one thread per row = TMEM lane): load both accumulator
-//     halves, keep the half of the row's spin at site k, rescale by an exact
-//     power of two (exponent summed in an integer), split to hi/lo BF16 and
-//     store the row back as the next site's A operand.
-// Thread 0 issues TMA and MMA; every wait is bounded by a clock budget after
-// which the CTA records an error flag, drains its own copies, frees its TMEM
-// and returns.
+//     ring of shared-memory stages; the rows live in tensor memory as the A
+//     operand, written by the epilogue;
+//   - epilogue: load the accumulator, rescale by an exact power of two
+//     (exponent summed in an integer), split to hi/lo and store the row back
+//     as the next site's A operand, with the next site's metadata.
+// A producer warp issues TMA and MMA; every wait is bounded by a clock budget
+// after which the CTA records an error flag, drains its own copies, frees
+// its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -2136,6 +2138,333 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPP_THREADS, 1)
     if (warp == 0) tmem_dealloc(tmem, 512u);
 }
 
+
+// ------------------------------------------------------------------ flip rows, two tiles per CTA (chi = 128)
+// The rows of the local energy with two 128-chain tiles of the same flip row
+// j per CTA, so that the epilogue of one tile runs while the tensor pipe
+// works on the other (each tile's chain of sites is serial).  Tensor memory
+// holds both tiles -- tile u from column 256 u: accumulator [0,128), the hi
+// half of the row operand [128,192), metadata at 192 -- because the lo half
+// of each row operand lives in shared memory, in 128-byte-swizzled K-major
+// atoms that the MMA reads through a descriptor.  Both tiles read the same
+// site tensors, streamed once per site by a TMA warp into the ring; a stage
+// is released when the second tile's MMAs on it complete.  Warps 0-3:
+// epilogue (row m of both tiles), warp 4: MMA issue, warp 5: TMA.  The
+// epilogue hands each tile's next operand to the MMA warp through a named
+// barrier per tile.
+constexpr int R2_THREADS = NT + 64;
+
+inline size_t rows2_smem(int N, int L) {
+    return 1024 + (size_t)SCfg<128>::NSTG * SCfg<128>::STAGE + (size_t)2 * NT * 128 * 2 + 128 +
+           (size_t)32 * N + (size_t)4 * L;
+}
+
+// D (+)= A . B with A 2:4 sparse, its compressed entries read from shared
+// memory through a descriptor.
+__device__ __forceinline__ void mma_sp_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t meta,
+                                          uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %5, 0;\n\t"
+        "tcgen05.mma.sp.cta_group::1.kind::f16 [%0], %1, %2, [%3], %4, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(meta), "r"(idesc), "r"(accum)
+        : "memory");
+}
+// 32 columns of this warp's 32 TMEM lanes, then wait.
+__device__ __forceinline__ void tmem_st_x32(uint32_t t, const uint32_t (&x)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(t), "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(x[7]), "r"(x[8]), "r"(x[9]), "r"(x[10]), "r"(x[11]), "r"(x[12]), "r"(x[13]), "r"(x[14]), "r"(x[15]), "r"(x[16]), "r"(x[17]), "r"(x[18]), "r"(x[19]), "r"(x[20]), "r"(x[21]), "r"(x[22]), "r"(x[23]), "r"(x[24]), "r"(x[25]), "r"(x[26]), "r"(x[27]), "r"(x[28]), "r"(x[29]), "r"(x[30]), "r"(x[31])
+        : "memory");
+}
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+template <bool F16>
+__global__ void __launch_bounds__(R2_THREADS, 1)
+    k_rows2(const __grid_constant__ CUtensorMap map, const Args a) {
+    constexpr int CHI = 128;
+    using C = SCfg<CHI, F16>;
+    constexpr int NSG = C::NSTG;
+    constexpr int CPT = 2;
+    constexpr uint32_t ATOM = (uint32_t)NT * 128;  // one 64-entry K atom of 128 rows
+    constexpr uint32_t ALO = 2 * ATOM;             // one tile's lo operand
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t stage0 = sa(base);
+    const uint32_t alo0 = stage0 + (uint32_t)(NSG * C::STAGE);
+    uint64_t *bars = (uint64_t *)(base + NSG * C::STAGE + 2 * ALO);
+    const uint32_t bar0 = sa(bars);
+    // bars: full[NSG], empty[NSG], done[2]
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (NSG + s); };
+    auto done_bar = [&](int u) { return bar0 + 8u * (2 * NSG + u); };
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NSG + 2);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    long long *issued = (long long *)(bars + 2 * NSG + 3);
+    uint32_t *bits = (uint32_t *)((uint8_t *)bars + 128);  // [tile][spin][quadrant]
+    uint32_t *tab = bits + 8 * a.N;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool epi = warp < 4;
+    const int q = warp & 3;
+    const int m = 32 * q + lane;
+    const int N = a.N;
+    const int j = (int)blockIdx.y;
+    int64_t cu[2];
+    bool act[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int64_t cr = ((int64_t)blockIdx.x * 2 + u) * NT + m;
+        act[u] = epi && cr < a.B;
+        cu[u] = cr < a.B ? cr : a.B - 1;
+    }
+    const long long total_steps = n_steps_of<M_ROWS>(a, j);
+    const long long total_atoms = total_steps * C::KA;
+
+    if (warp == 0) tmem_alloc(sa(tmem_slot), 512u);
+    if (tid == 0) {
+        for (int s = 0; s < NSG; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        mbar_init(done_bar(0), 1);
+        mbar_init(done_bar(1), 1);
+        *abort_flag = 0;
+        issued[0] = 0;
+        fence_barrier_init();
+    }
+    for (int k = tid; k < a.L; k += R2_THREADS)
+        tab[k] = ((uint32_t)__ldg(a.path ? a.path + k : a.q + (k % N)) & 0xffffu) |
+                 ((uint32_t)(__ldg(a.cexp + k) & 0xffff) << 16);
+    if (epi) {
+#pragma unroll 1
+        for (int u = 0; u < 2; ++u)
+            for (int i = 0; i < N; ++i) {
+                const uint32_t w = __ballot_sync(FULL, a.spins_in[cu[u] * N + i] != 0);
+                if (lane == 0) bits[(u * N + i) * 4 + q] = w;
+            }
+    }
+    auto spin = [&](int u, int i) -> int { return (int)((bits[(u * N + i) * 4 + q] >> lane) & 1u); };
+    auto site_spin = [&](int k) -> int { return (int)(tab[k] & 0xffffu); };
+    auto site_cexp = [&](int k) -> int { return (int)(int16_t)(tab[k] >> 16); };
+    const int iflip = j < N ? (int)(__ldg(a.path ? a.path + j : a.q + j)) : -1;
+    auto bwait = [&](uint32_t bar, uint32_t parity) -> bool {
+        if (*abort_flag) return false;
+        if (!mbar_wait(bar, parity, a.wait_limit)) {
+            atomicOr(a.err, 1);
+            *abort_flag = 1;
+            return false;
+        }
+        return true;
+    };
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 4) {
+        // ---------------------------------------------------------- MMA issue
+        for (long long t = 0; t < total_steps; ++t) {
+#pragma unroll 1
+            for (int u = 0; u < 2; ++u) {
+                named_sync(1 + u, NT + 32);  // tile u's operand for this site is written
+                if (lane == 0) {
+                    tc_after();
+                    const uint32_t d = tmem + 256u * (uint32_t)u;
+                    const uint32_t a_hi = d + 128u, meta = d + 192u;
+                    const uint32_t a_lo = alo0 + (uint32_t)u * ALO;
+                    for (int at = 0; at < C::KA; ++at) {
+                        const long long g = t * C::KA + at;
+                        const int st = (int)(g % NSG);
+                        if (u == 0) bwait(full_bar(st), (uint32_t)((g / NSG) & 1));
+                        if (!*abort_flag) {
+                            const uint32_t b_hi = stage0 + (uint32_t)st * C::STAGE, b_lo = b_hi + C::BOX;
+                            const uint64_t dh0 = sdesc(b_hi), dh1 = sdesc(b_hi + 64);
+                            const uint64_t dl0 = sdesc(b_lo), dl1 = sdesc(b_lo + 64);
+                            // row entries 32 at .. 32 at + 31: K-steps 2 at and 2 at + 1
+                            const uint32_t ao = (uint32_t)(at * 16);
+                            const uint64_t al0 = sdesc(a_lo + (uint32_t)(at >> 1) * ATOM + (uint32_t)(at & 1) * 64u);
+                            const uint64_t al1 = sdesc(a_lo + (uint32_t)(at >> 1) * ATOM + (uint32_t)(at & 1) * 64u + 32u);
+                            const uint32_t first = at != 0 ? 1u : 0u;
+                            mma_sp_ts(d, a_hi + ao, dh0, meta, C::IDESC, first);
+                            mma_sp_ts(d, a_hi + ao, dl0, meta, C::IDESC, 1u);
+                            mma_sp_ss(d, al0, dh0, meta, C::IDESC, 1u);
+                            mma_sp_ts(d, a_hi + ao + 8, dh1, meta, C::IDESC, 1u);
+                            mma_sp_ts(d, a_hi + ao + 8, dl1, meta, C::IDESC, 1u);
+                            mma_sp_ss(d, al1, dh1, meta, C::IDESC, 1u);
+                        }
+                        if (u == 1) mma_commit(empty_bar(st));  // both tiles have read the stage
+                    }
+                    mma_commit(done_bar(u));
+                }
+                __syncwarp();
+            }
+        }
+    } else if (warp == 5) {
+        // ---------------------------------------------------------- TMA
+        if (lane == 0) {
+            for (long long g = 0; g < total_atoms; ++g) {
+                const int st = (int)(g % NSG);
+                if (g >= NSG && !bwait(empty_bar(st), (uint32_t)(((g / NSG) - 1) & 1))) break;
+                if (*abort_flag) break;
+                const int k = j + (int)(g / C::KA), at = (int)(g % C::KA);
+                const uint32_t dst = stage0 + (uint32_t)st * C::STAGE;
+                mbar_expect_tx(full_bar(st), (uint32_t)C::STAGE);
+                tma_load_2d(dst, &map, at * 64, (0 * a.L + k) * CHI, full_bar(st));
+                tma_load_2d(dst + C::BOX, &map, at * 64, (1 * a.L + k) * CHI, full_bar(st));
+                issued[0] = g + 1;
+            }
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue (rows m of both tiles)
+        const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
+        const int lane_a = (lane & 16) | (lane & 7), lane_b = lane_a | 8;
+        auto write_meta = [&](int u, int k) {
+            const int sk = site_spin(k);
+            const int sl = spin(u, sk) ^ (sk == iflip ? 1 : 0);
+            const int s_a = __shfl_sync(FULL, sl, lane_a), s_b = __shfl_sync(FULL, sl, lane_b);
+            tmem_st_1(tq + 256u * (uint32_t)u + 192u,
+                      (s_a ? C::HALF1 : C::HALF0) | ((s_b ? C::HALF1 : C::HALF0) << 16));
+        };
+        // entries 64 ch .. 64 ch + 63 of row m as tile u's operand: hi into
+        // TMEM, lo into the swizzled shared-memory atom ch
+        auto write_op = [&](int u, int ch, const float (&y)[64]) {
+            uint32_t hh[32], ll[32];
+#pragma unroll
+            for (int p = 0; p < 32; ++p) split2<F16>(y[2 * p], y[2 * p + 1], hh[p], ll[p]);
+            tmem_st_x32(tq + 256u * (uint32_t)u + 128u + (uint32_t)(32 * ch), hh);
+            const uint32_t row = alo0 + (uint32_t)u * ALO + (uint32_t)ch * ATOM + (uint32_t)m * 128u;
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8)
+                st_shared_v4(row + ((uint32_t)(c8 ^ (m & 7)) << 4), ll[4 * c8], ll[4 * c8 + 1],
+                             ll[4 * c8 + 2], ll[4 * c8 + 3]);
+        };
+        auto publish = [&](int u) {
+            fence_async_smem();
+            tc_before();
+            named_arrive(1 + u, NT + 32);
+        };
+        auto row_exp = [&](int u) -> int {
+            float m8[8];
+#pragma unroll 1
+            for (int ch = 0; ch < CPT; ++ch) {
+                float y[64];
+                tmem_ld_64(tq + 256u * (uint32_t)u + (uint32_t)(64 * ch), y);
+#pragma unroll
+                for (int i = 0; i < 64; ++i)
+                    m8[i & 7] = (ch == 0 && i < 8) ? fabsf(y[i]) : fmaxf(m8[i & 7], fabsf(y[i]));
+            }
+            const float mx = fmaxf(fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3])),
+                                   fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7])));
+            const bool usable = (mx > 0.f) && isfinite(mx);
+            int e = usable ? rttd::exponent_of(mx) : 0;
+            if (__all_sync(FULL, !usable || (e >= 0 && e < 8)) || !usable) e = 0;
+            return e;
+        };
+        int64_t E[2] = {0, 0}, fin_E[2] = {0, 0};
+        double fin_m[2] = {0.0, 0.0};
+        const float *start[2] = {a.bl, a.bl};
+        if (j > 0) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                start[u] = a.lstack + ((size_t)cu[u] * N + (j - 1)) * CHI;
+                E[u] = a.lexp[(size_t)cu[u] * N + (j - 1)];
+            }
+        }
+        const int rq = row_end(a, j) + 1 - a.kmin;  // r_{end+1}; b_R for j = N
+        if (total_steps > 0) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+#pragma unroll 1
+                for (int ch = 0; ch < CPT; ++ch) {
+                    float y[64];
+                    load_chunk(start[u] + 64 * ch, y);
+                    write_op(u, ch, y);
+                }
+                write_meta(u, j);
+                publish(u);
+            }
+        }
+        for (long long t = 0; t < total_steps; ++t) {
+            const int k = j + (int)t;
+            const int ck = site_cexp(k);
+            const bool last = t + 1 == total_steps;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                bwait(done_bar(u), (uint32_t)(t & 1));
+                tc_after();
+                __syncwarp();
+                const int e = row_exp(u);
+                E[u] += e - ck;
+                if (!last) {
+#pragma unroll 1
+                    for (int ch = 0; ch < CPT; ++ch) {
+                        float y[64];
+                        tmem_ld_64(tq + 256u * (uint32_t)u + (uint32_t)(64 * ch), y);
+                        scale_chunk(y, e);
+                        write_op(u, ch, y);
+                    }
+                    write_meta(u, k + 1);
+                    publish(u);
+                } else {
+                    const float *rclose = a.rstack + ((size_t)cu[u] * a.nr + rq) * CHI;
+                    float acc8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+                    for (int ch = 0; ch < CPT; ++ch) {
+                        float y[64];
+                        tmem_ld_64(tq + 256u * (uint32_t)u + (uint32_t)(64 * ch), y);
+                        scale_chunk(y, e);
+                        dot_chunk(y, rclose + 64 * ch, acc8);
+                    }
+                    fin_m[u] = dot_finish(acc8);
+                    fin_E[u] = E[u] + a.rexp[(size_t)cu[u] * a.nr + rq];
+                }
+            }
+        }
+        if (total_steps == 0) {
+            // no site steps (R = 1 and the unflipped row in the first block):
+            // the start row closes on r_{end+1}
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float *rclose = a.rstack + ((size_t)cu[u] * a.nr + rq) * CHI;
+                float acc8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+                for (int ch = 0; ch < CPT; ++ch) {
+                    float y[64];
+                    load_chunk(start[u] + 64 * ch, y);
+                    dot_chunk(y, rclose + 64 * ch, acc8);
+                }
+                fin_m[u] = dot_finish(acc8);
+                fin_E[u] = E[u] + a.rexp[(size_t)cu[u] * a.nr + rq];
+            }
+        }
+        if (!*abort_flag) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (act[u]) {
+                    double mm = fin_m[u];
+                    int64_t Ep = fin_E[u];
+                    normalize_scalar(mm, Ep);
+                    a.rows_mant[cu[u] * (N + 1) + j] = mm;
+                    a.rows_exp[cu[u] * (N + 1) + j] = Ep;
+                }
+        }
+    }
+    // ---------------- teardown: drain own copies (bounded), free TMEM
+    tc_before();
+    __syncthreads();
+    tc_after();
+    if (tid == 5 * 32 && *abort_flag) {
+        const long long n = issued[0];
+        for (long long g = (n > NSG ? n - NSG : 0); g < n; ++g)
+            mbar_wait(full_bar((int)(g % NSG)), (uint32_t)((g / NSG) & 1), a.wait_limit);
+    }
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512u);
+}
+
 }  // namespace tcd
 
 // ====================================================================== host side
@@ -2390,7 +2719,21 @@ rtt_status tc_rows(rtt_s *h, const uint8_t *spins, int64_t B, cudaStream_t st) {
     tcd::Args a = make_args(h, B);
     a.spins_in = spins;
     prof_begin(h, KID_TC_ROWS, st);
-    cudaError_t e = launch_chi<tcd::M_ROWS>(h->tc, a, dim3(tiles(B), h->N + 1), st);
+    cudaError_t e;
+    const size_t smem2 = tcd::rows2_smem(h->N, h->L);
+    if (h->tc->chi == 128 && smem2 <= (size_t)227 * 1024) {
+        // two tiles per CTA (one tile's epilogue beside the other's MMAs)
+        auto go = [&](auto kern) {
+            cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+            if (err == cudaSuccess)
+                kern<<<dim3((tiles(B) + 1) / 2, h->N + 1), tcd::R2_THREADS, smem2, st>>>(h->tc->map_sp, a);
+            return err;
+        };
+        e = h->tc->f16 ? go(tcd::k_rows2<true>) : go(tcd::k_rows2<false>);
+        if (e == cudaSuccess) e = cudaGetLastError();
+    } else {
+        e = launch_chi<tcd::M_ROWS>(h->tc, a, dim3(tiles(B), h->N + 1), st);
+    }
     prof_end(h, KID_TC_ROWS, st);
     return status_of(e, "tc flip rows");
 }
