@@ -169,7 +169,16 @@ class L2Flush:
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of a kernel, from
 # an ncu capture of that kernel as it is built now, keyed by (workload,
 # precision, kernel, chains); a kernel with no current capture reports None.
-MEASURED_TRAFFIC = {}
+# The 16x16 rows kernel was captured at 1024 chains (397.6 MB read + 9.7 MB
+# written): the environment rows and spins every (tile, row) CTA reads, 337 MB,
+# grow with the chains and the site tensors' 67 MB do not, so 8192 chains
+# move 8 x 340.7 MB + 67 MB.
+_ROWS16_TRAFFIC_8192 = 8 * (397.6e6 + 9.7e6 - 67.1e6) + 67.1e6
+MEASURED_TRAFFIC = {
+    ("learned_16x16", "fp16x3", "tc_rows", 8192): _ROWS16_TRAFFIC_8192,
+    ("plain_16x16", "fp16x3", "tc_rows", 8192): _ROWS16_TRAFFIC_8192,
+    ("plain_16x16", "fp16x3", "tc_rows", 1024): 397.6e6 + 9.7e6,
+}
 
 
 def measured_traffic(args, kernel, B):
