@@ -382,9 +382,20 @@ rtt_status rtt_made_permutation(int64_t n, uint64_t seed, int64_t epoch, int64_t
  * masked W2 rounded to BF16, FP32 accumulation, the same kernel for sampling
  * and for evaluation, so the density a proposal is drawn from is exactly the
  * one the acceptance test evaluates; bf16 = 0 runs it in FP32 on the CUDA
- * cores.  Training is FP32 either way.  BF16 needs H in {64, 128, 192, 256,
+ * cores.  Training is set apart (rtt_made_set_training).  BF16 needs H in {64, 128, 192, 256,
  * 512} (RTT_ERR_UNSUPPORTED otherwise) and is the default for those. */
 rtt_status rtt_made_set_inference(rtt_made m, int32_t bf16);
+/* Arithmetic of the training GEMMs (forward and backward of rtt_made_gradients,
+ * rtt_made_train_step and rtt_made_fit): tc = 1 runs them on the tensor
+ * cores, each FP32 operand split into BF16 hi + lo and three products hi.hi +
+ * hi.lo + lo.hi accumulated in FP32 (relative error O(2^-16) per product);
+ * tc = 0 (the default: faster at the model sizes the sampler trains, whose
+ * 128 x 128 output tiles leave most SMs idle) runs them in FP32 on the CUDA
+ * cores (FMA in increasing k).
+ * Host only, no device work; RTT_ERR_INVALID_ARG for a null model.  A bounded
+ * wait that runs out in the tensor-core GEMM sets bit 0 of the flags that
+ * rtt_made_device_status reports. */
+rtt_status rtt_made_set_training(rtt_made m, int32_t tc);
 /* Device-side error flags of the model's tensor-core layer since the last
  * call (bit 0: a bounded wait ran out of its clock budget; that CTA recorded
  * the flag, drained its own copies, freed its tensor memory and returned

@@ -58,6 +58,7 @@ struct rtt_made_s {
     size_t off_W1 = 0, off_b1 = 0, off_W2 = 0, off_b2 = 0, off_W3 = 0, off_b3 = 0;
     // BF16 tensor-core inference of the H x H layer (when H allows it)
     int infer_bf16 = 0;
+    int train_tc = 0;                  // training GEMMs on the tensor cores (BF16 hi/lo)
     __nv_bfloat16 *d_w2b = nullptr;    // [H][H] masked W2, row n = output unit, K-major
     __nv_bfloat16 *d_h1b = nullptr;    // [cap][H] ReLU(first layer) in BF16
     int *d_err = nullptr;              // bit 0: a bounded wait of the layer kernel expired
@@ -167,13 +168,46 @@ __global__ void k_loss(const float *__restrict__ lg, const uint8_t *__restrict__
     logq[b] = acc;
 }
 
-// out[n] = sum_b D[b][n] (increasing b); one thread per column
-__global__ void k_colsum(const float *__restrict__ D, int64_t B, int N, float *__restrict__ out) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+// The training loss: one warp per row b, lane l taking d = l, l + 32, ...;
+// d3 as in k_loss (the same FP64 expression per entry), and log q(s_b) summed
+// in the lanes' order then across the warp (only the minibatch NLL uses it).
+__global__ void k_loss_train(const float *__restrict__ lg, const uint8_t *__restrict__ s, int64_t B,
+                             int N, const int32_t *__restrict__ order, double *__restrict__ logq,
+                             float *__restrict__ d3) {
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= B) return;
+    double acc = 0.0;
+    for (int d = lane; d < N; d += 32) {
+        const double y = (double)lg[b * N + d];
+        const int t = s[b * N + order[d]];
+        acc += log_sigmoid(t ? y : -y);
+        const double sg = 1.0 / (1.0 + exp(-y));
+        d3[b * N + d] = (float)((sg - (double)t) / (double)B);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) logq[b] = acc;
+}
+
+// out[n] = sum_b D[b][n]: block (32 columns) x (32 row groups); thread (x, y)
+// sums rows y, y + 32, ... of column x in increasing order, then the 32 partial
+// sums of a column are added in increasing y
+__global__ void __launch_bounds__(1024) k_colsum_par(const float *__restrict__ D, int64_t B, int N,
+                                                     float *__restrict__ out) {
+    __shared__ float part[32][33];
+    const int x = threadIdx.x, y = threadIdx.y;
+    const int n = blockIdx.x * 32 + x;
     float acc = 0.f;
-    for (int64_t b = 0; b < B; ++b) acc += D[b * N + n];
-    out[n] = acc;
+    if (n < N)
+        for (int64_t b = y; b < B; b += 32) acc += D[b * N + n];
+    part[y][x] = acc;
+    __syncthreads();
+    if (y == 0 && n < N) {
+        float t = 0.f;
+        for (int i = 0; i < 32; ++i) t += part[i][x];
+        out[n] = t;
+    }
 }
 
 __global__ void k_sum_neg(const double *__restrict__ x, int64_t n, double *__restrict__ out) {
@@ -582,6 +616,175 @@ __global__ void k_accumulate(double *__restrict__ acc, const double *__restrict_
     if (blockIdx.x == 0 && threadIdx.x == 0) *acc += *x;
 }
 
+// ---------------------------------------------------------------- tensor-core training GEMM
+// The same C = epi(bias + opA . opB) as k_gemm on the 5th-generation tensor
+// cores, for training: each FP32 operand is split into BF16 hi + lo (x = hi +
+// lo + O(2^-18 |x|)), and three products hi.hi + hi.lo + lo.hi accumulate in
+// FP32 in tensor memory (the dropped lo.lo is O(2^-18) too).  One 128 x 128
+// tile of C per CTA of 128 threads (thread = row of the tile in the
+// epilogue); K in blocks of 64: all threads read a block of both operands in
+// FP32 (either orientation, zero past the edges), split it and store it into
+// a two-stage shared-memory ring in the 128-byte-swizzled K-major layout;
+// thread 0 issues the block's 12 MMAs (M = N = 128, K = 16) and commits them
+// to the stage's mbarrier, which the threads wait on before they refill the
+// stage.  Every wait is bounded; on expiry the CTA records bit 0 in err,
+// skips the rest and writes nothing.
+constexpr int GT_THREADS = 128;
+constexpr uint32_t GT_TILE = 128u * 128u;              // bytes of one 128 x 64 BF16 tile
+constexpr uint32_t GT_STAGE = 4u * GT_TILE;            // A hi, A lo, B hi, B lo
+constexpr uint32_t GT_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);  // BF16 x BF16 -> FP32, K-major, 128 x 128
+constexpr size_t GT_SMEM = 1024 + 2 * (size_t)GT_STAGE + 64;
+
+__device__ __forceinline__ void gt_split8(const float (&v)[8], uint4 &hi, uint4 &lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * p], v[2 * p + 1]);
+        const float2 hf = __bfloat1622float2(hb);
+        const __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * p] - hf.x, v[2 * p + 1] - hf.y);
+        h[p] = *reinterpret_cast<const uint32_t *>(&hb);
+        l[p] = *reinterpret_cast<const uint32_t *>(&lb);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+__device__ __forceinline__ void gt_st16(uint32_t addr, const uint4 &v) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(GT_THREADS, 1)
+    k_gemm_tc(int M, int N, int K, const float *__restrict__ A, int lda, const float *__restrict__ B,
+              int ldb, float *__restrict__ C, int ldc, const float *__restrict__ bias, int relu,
+              const float *__restrict__ gate, const float *__restrict__ mask, int *err,
+              long long limit) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t ring = tcd::sa(base);
+    uint64_t *bars = (uint64_t *)(base + 2 * GT_STAGE);
+    const uint32_t bar0 = tcd::sa(bars);
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m0 = blockIdx.y * 128, n0 = blockIdx.x * 128;
+    if (warp == 0) tcd::tmem_alloc(tcd::sa(tmem_slot), 128u);
+    if (tid == 0) {
+        tcd::mbar_init(bar0, 1);
+        tcd::mbar_init(bar0 + 8u, 1);
+        *abort_flag = 0;
+        tcd::fence_barrier_init();
+    }
+    tcd::tc_before();
+    __syncthreads();
+    tcd::tc_after();
+    const uint32_t tmem = *tmem_slot;
+    const int nkb = (K + 63) / 64;
+    // element (r, k) of a 128 x 64 operand tile: opA[m0 + r][k] or opB[k][n0 + r]
+    auto elem_a = [&](int r, int k) -> float {
+        const int m = m0 + r;
+        if (m >= M || k >= K) return 0.f;
+        return TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
+    };
+    auto elem_b = [&](int r, int k) -> float {
+        const int n = n0 + r;
+        if (n >= N || k >= K) return 0.f;
+        return TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
+    };
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb & 1;
+        if (kb >= 2 && !*abort_flag) {
+            // the MMAs of block kb - 2 have read this stage
+            if (!tcd::mbar_wait(bar0 + 8u * s, (uint32_t)(((kb - 2) >> 1) & 1), limit)) {
+                atomicOr(err, 1);
+                *abort_flag = 1;
+            }
+        }
+        __syncthreads();
+        if (*abort_flag) break;
+        const uint32_t st = ring + (uint32_t)s * GT_STAGE;
+        // thread tid fills row tid of the four tiles, 8 K-entries at a time
+        const int k0 = kb * 64;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float va[8], vb[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                va[i] = elem_a(tid, k0 + 8 * c + i);
+                vb[i] = elem_b(tid, k0 + 8 * c + i);
+            }
+            uint4 ah, al, bh, bl;
+            gt_split8(va, ah, al);
+            gt_split8(vb, bh, bl);
+            const uint32_t off = (uint32_t)tid * 128u + ((uint32_t)(c ^ (tid & 7)) << 4);
+            gt_st16(st + off, ah);
+            gt_st16(st + GT_TILE + off, al);
+            gt_st16(st + 2 * GT_TILE + off, bh);
+            gt_st16(st + 3 * GT_TILE + off, bl);
+        }
+        tcd::fence_async_smem();
+        tcd::tc_before();
+        __syncthreads();
+        if (tid == 0) {
+            tcd::tc_after();
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t o = (uint32_t)(kk * 32);
+                const uint64_t ah = tcd::sdesc(st + o), al = tcd::sdesc(st + GT_TILE + o);
+                const uint64_t bh = tcd::sdesc(st + 2 * GT_TILE + o), bl = tcd::sdesc(st + 3 * GT_TILE + o);
+                tcd::mma_bf16(tmem, ah, bh, GT_IDESC, (kb | kk) ? 1u : 0u);
+                tcd::mma_bf16(tmem, ah, bl, GT_IDESC, 1u);
+                tcd::mma_bf16(tmem, al, bh, GT_IDESC, 1u);
+            }
+            tcd::mma_commit(bar0 + 8u * s);
+        }
+    }
+    // the last block's MMAs complete after every earlier one
+    if (nkb > 0 && !*abort_flag) {
+        const int kl = nkb - 1;
+        if (!tcd::mbar_wait(bar0 + 8u * (kl & 1), (uint32_t)((kl >> 1) & 1), limit)) {
+            atomicOr(err, 1);
+            *abort_flag = 1;
+        }
+    }
+    tcd::tc_after();
+    __syncthreads();
+    if (!*abort_flag) {
+        const int m = m0 + tid;
+        const uint32_t tq = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int cb = 0; cb < 128; cb += 64) {
+            uint32_t x0[32], x1[32];
+            if (nkb > 0) {
+                tcd::tmem_ld_2x32(tq + (uint32_t)cb, tq + (uint32_t)cb + 32u, x0, x1);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) x0[i] = x1[i] = 0u;
+            }
+            if (m < M) {
+#pragma unroll
+                for (int i = 0; i < 64; ++i) {
+                    const int n = n0 + cb + i;
+                    if (n < N) {
+                        float c = __uint_as_float(i < 32 ? x0[i] : x1[i - 32]);
+                        if (bias) c += bias[n];
+                        if (relu) c = fmaxf(c, 0.f);
+                        if (gate && !(gate[(size_t)m * ldc + n] > 0.f)) c = 0.f;
+                        if (mask) c *= mask[(size_t)m * ldc + n];
+                        C[(size_t)m * ldc + n] = c;
+                    }
+                }
+            }
+        }
+    }
+    tcd::tc_before();
+    __syncthreads();
+    tcd::tc_after();
+    if (warp == 0) tcd::tmem_dealloc(tmem, 128u);
+}
+
 inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 template <bool TA, bool TB>
@@ -590,6 +793,20 @@ cudaError_t gemm(int M, int N, int K, const float *A, int lda, const float *B, i
                  cudaStream_t st) {
     dim3 grid(nb(N, 64), nb(M, 64));
     k_gemm<TA, TB><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, gate, mask);
+    return cudaGetLastError();
+}
+// the training GEMM: tensor cores (BF16 hi/lo, three products) or k_gemm
+template <bool TA, bool TB>
+cudaError_t gemm_train(bool tc, int *err, int M, int N, int K, const float *A, int lda,
+                       const float *B, int ldb, float *C, int ldc, const float *bias, int relu,
+                       const float *gate, const float *mask, cudaStream_t st) {
+    if (!tc) return gemm<TA, TB>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, gate, mask, st);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)GT_SMEM);
+    if (e != cudaSuccess) return e;
+    dim3 grid(nb(N, 128), nb(M, 128));
+    k_gemm_tc<TA, TB><<<grid, GT_THREADS, GT_SMEM, st>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu,
+                                                          gate, mask, err, 4000000000LL);
     return cudaGetLastError();
 }
 
@@ -658,17 +875,19 @@ rtt_status ensure_ws(rtt_made_s *m, int64_t B) {
 }
 
 // forward pass for rows of spins -> m->d_h1, d_h2, d_lg (and x)
-rtt_status forward(rtt_made_s *m, const uint8_t *spins, int64_t B, cudaStream_t st) {
+// (train: the training GEMMs, tensor cores when m->train_tc; else FP32 k_gemm)
+rtt_status forward(rtt_made_s *m, const uint8_t *spins, int64_t B, cudaStream_t st, bool train = false) {
     const int N = m->N, H = m->H;
     const float *p = m->d_p;
+    const bool tc = train && m->train_tc;
     mk::k_inputs<<<mk::nb(B * N, 256), 256, 0, st>>>(spins, B, N, m->d_order, m->d_x);
     MC(cudaGetLastError(), "made inputs");
-    MC((mk::gemm<false, true>((int)B, H, N, m->d_x, N, p + m->off_W1, N, m->d_h1, H,
-                              p + m->off_b1, 1, nullptr, nullptr, st)), "made layer 1");
-    MC((mk::gemm<false, true>((int)B, H, H, m->d_h1, H, p + m->off_W2, H, m->d_h2, H,
-                              p + m->off_b2, 1, nullptr, nullptr, st)), "made layer 2");
-    MC((mk::gemm<false, true>((int)B, N, H, m->d_h2, H, p + m->off_W3, H, m->d_lg, N,
-                              p + m->off_b3, 0, nullptr, nullptr, st)), "made output");
+    MC((mk::gemm_train<false, true>(tc, m->d_err, (int)B, H, N, m->d_x, N, p + m->off_W1, N, m->d_h1,
+                                    H, p + m->off_b1, 1, nullptr, nullptr, st)), "made layer 1");
+    MC((mk::gemm_train<false, true>(tc, m->d_err, (int)B, H, H, m->d_h1, H, p + m->off_W2, H, m->d_h2,
+                                    H, p + m->off_b2, 1, nullptr, nullptr, st)), "made layer 2");
+    MC((mk::gemm_train<false, true>(tc, m->d_err, (int)B, N, H, m->d_h2, H, p + m->off_W3, H, m->d_lg,
+                                    N, p + m->off_b3, 0, nullptr, nullptr, st)), "made output");
     return RTT_OK;
 }
 
@@ -762,9 +981,11 @@ rtt_status gradients(rtt_made_s *m, const uint8_t *spins, int64_t B, double *nll
     const int N = m->N, H = m->H;
     const float *p = m->d_p;
     float *g = m->d_g;
-    rtt_status s = forward(m, spins, B, st);
+    rtt_status s = forward(m, spins, B, st, true);
+    const bool tc = m->train_tc != 0;
     if (s != RTT_OK) return s;
-    mk::k_loss<<<mk::nb(B, 128), 128, 0, st>>>(m->d_lg, spins, B, N, m->d_order, m->d_logq, m->d_d3);
+    mk::k_loss_train<<<mk::nb(B * 32, 256), 256, 0, st>>>(m->d_lg, spins, B, N, m->d_order, m->d_logq,
+                                                          m->d_d3);
     MC(cudaGetLastError(), "made loss");
     if (nll_dev) {
         mk::k_sum_neg<<<1, 1, 0, st>>>(m->d_logq, B, nll_dev);
@@ -772,21 +993,21 @@ rtt_status gradients(rtt_made_s *m, const uint8_t *spins, int64_t B, double *nll
     }
     const float *mask = m->d_mask;
     // output layer: dW3 = d3^T h2 (masked), db3 = colsum d3
-    MC((mk::gemm<true, false>(N, H, (int)B, m->d_d3, N, m->d_h2, H, g + m->off_W3, H, nullptr, 0,
+    MC((mk::gemm_train<true, false>(tc, m->d_err, N, H, (int)B, m->d_d3, N, m->d_h2, H, g + m->off_W3, H, nullptr, 0,
                               nullptr, mask + m->off_W3, st)), "made dW3");
-    mk::k_colsum<<<mk::nb(N, 128), 128, 0, st>>>(m->d_d3, B, N, g + m->off_b3);
+    mk::k_colsum_par<<<mk::nb(N, 32), dim3(32, 32), 0, st>>>(m->d_d3, B, N, g + m->off_b3);
     // dh2 = (d3 W3) * [h2 > 0]
-    MC((mk::gemm<false, false>((int)B, H, N, m->d_d3, N, p + m->off_W3, H, m->d_dh2, H, nullptr, 0,
+    MC((mk::gemm_train<false, false>(tc, m->d_err, (int)B, H, N, m->d_d3, N, p + m->off_W3, H, m->d_dh2, H, nullptr, 0,
                                m->d_h2, nullptr, st)), "made dh2");
-    MC((mk::gemm<true, false>(H, H, (int)B, m->d_dh2, H, m->d_h1, H, g + m->off_W2, H, nullptr, 0,
+    MC((mk::gemm_train<true, false>(tc, m->d_err, H, H, (int)B, m->d_dh2, H, m->d_h1, H, g + m->off_W2, H, nullptr, 0,
                               nullptr, mask + m->off_W2, st)), "made dW2");
-    mk::k_colsum<<<mk::nb(H, 128), 128, 0, st>>>(m->d_dh2, B, H, g + m->off_b2);
+    mk::k_colsum_par<<<mk::nb(H, 32), dim3(32, 32), 0, st>>>(m->d_dh2, B, H, g + m->off_b2);
     // dh1 = (dh2 W2) * [h1 > 0]
-    MC((mk::gemm<false, false>((int)B, H, H, m->d_dh2, H, p + m->off_W2, H, m->d_dh1, H, nullptr, 0,
+    MC((mk::gemm_train<false, false>(tc, m->d_err, (int)B, H, H, m->d_dh2, H, p + m->off_W2, H, m->d_dh1, H, nullptr, 0,
                                m->d_h1, nullptr, st)), "made dh1");
-    MC((mk::gemm<true, false>(H, N, (int)B, m->d_dh1, H, m->d_x, N, g + m->off_W1, N, nullptr, 0,
+    MC((mk::gemm_train<true, false>(tc, m->d_err, H, N, (int)B, m->d_dh1, H, m->d_x, N, g + m->off_W1, N, nullptr, 0,
                               nullptr, mask + m->off_W1, st)), "made dW1");
-    mk::k_colsum<<<mk::nb(H, 128), 128, 0, st>>>(m->d_dh1, B, H, g + m->off_b1);
+    mk::k_colsum_par<<<mk::nb(H, 32), dim3(32, 32), 0, st>>>(m->d_dh1, B, H, g + m->off_b1);
     MC(cudaGetLastError(), "made gradients");
     return RTT_OK;
 }
@@ -884,6 +1105,12 @@ rtt_status rtt_made_set_inference(rtt_made m, int32_t bf16) {
     return RTT_OK;
 }
 
+rtt_status rtt_made_set_training(rtt_made m, int32_t tc) {
+    if (!m) return mfail(RTT_ERR_INVALID_ARG, "rtt_made_set_training: null model");
+    m->train_tc = tc ? 1 : 0;
+    return RTT_OK;
+}
+
 rtt_status rtt_made_device_status(rtt_made m, int32_t *flags) {
     if (!m) return mfail(RTT_ERR_INVALID_ARG, "rtt_made_device_status: null model");
     MGuard guard(m->device);
@@ -892,7 +1119,7 @@ rtt_status rtt_made_device_status(rtt_made m, int32_t *flags) {
     MC(cudaMemcpy(&v, m->d_err, sizeof(int), cudaMemcpyDeviceToHost), "rtt_made_device_status");
     MC(cudaMemset(m->d_err, 0, sizeof(int)), "rtt_made_device_status");
     if (flags) *flags = v;
-    if (v & 1) return mfail(RTT_ERR_TIMEOUT, "a bounded wait in the BF16 layer kernel expired");
+    if (v & 1) return mfail(RTT_ERR_TIMEOUT, "a bounded wait in a tensor-core kernel of the model expired");
     return RTT_OK;
 }
 

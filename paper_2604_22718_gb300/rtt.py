@@ -101,6 +101,8 @@ def lib():
         L.rtt_indep_mh.argtypes = [P, P, P, P, I64, I64, I64, P, P]
         L.rtt_made_fit.argtypes = [P, P, I64, I32, I32, ctypes.c_float, U64, P, P]
         L.rtt_made_permutation.argtypes = [I64, U64, I64, P]
+        L.rtt_made_set_training.argtypes = [P, I32]
+        L.rtt_made_set_training.restype = ctypes.c_int
         L.rtt_made_set_inference.argtypes = [P, I32]
         L.rtt_made_device_status.argtypes = [P, ctypes.POINTER(I32)]
         L.rtt_made_set_inference.restype = ctypes.c_int
@@ -531,8 +533,13 @@ class MADE:
         of sampling and evaluation (rtt_made_set_inference)."""
         _check(lib().rtt_made_set_inference(self._m, 1 if bf16 else 0), "rtt_made_set_inference")
 
+    def set_training(self, tc: bool):
+        """Tensor-core BF16 hi/lo (True) or FP32 CUDA-core (False, the default)
+        arithmetic for the training GEMMs (rtt_made_set_training)."""
+        _check(lib().rtt_made_set_training(self._m, 1 if tc else 0), "rtt_made_set_training")
+
     def device_status(self) -> int:
-        """Error flags of the tensor-core layer since the last call (0 = none)."""
+        """Error flags of the model's tensor-core kernels since the last call (0 = none)."""
         f = ctypes.c_int32()
         st = lib().rtt_made_device_status(self._m, ctypes.byref(f))
         if st not in (0, 5):

@@ -156,6 +156,7 @@ def test_made_and_batch_calls_reject_bad_arguments_before_any_cuda_call(lib):
     assert lib.rtt_made_sample(None, 4, 0, 0, None, None, None) == 1
     assert lib.rtt_made_train_step(None, None, 4, 1e-3, None, None) == 1
     assert lib.rtt_made_set_inference(None, 1) == 1
+    assert lib.rtt_made_set_training(None, 1) == 1
     assert lib.rtt_indep_mh(None, None, None, None, 4, 0, 0, None, None) == 1
     assert lib.rtt_made_destroy(None) == 0
     chains = np.array([16], dtype=np.int64)
