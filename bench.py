@@ -326,6 +326,47 @@ def cpu_baseline(inst, w, seed):
                       f"{dt:.1f} s wall)"}
 
 
+def batched_sample_flops(inst) -> float:
+    """Algorithmic flops of one sample (sweep + right environment + rows) of an instance."""
+    N, R, chi = inst.n_spins, inst.path.shape[0] // inst.n_spins, inst.chi
+    steps = site_steps(N, R, "simt_sweep") + site_steps(N, R, "simt_right_env") + \
+        site_steps(N, R, "simt_rows")
+    return steps * 2.0 * chi * chi
+
+
+def cpu_baseline_batched(insts, per, seed):
+    """The FP64 oracle on this host's cores for the batched workload, bounded:
+    for each chi of the workload its instance with the fewest site steps runs
+    one sweep + E_loc on one chain per host thread; the flop rate of those runs,
+    divided by the workload's mean algorithmic flops per sample, is the oracle's
+    samples/s on the whole workload."""
+    from oracle import oracle as orc
+    from paper_2604_22718_gb300 import inputs
+    cores = os.cpu_count() or 1
+    picks = {}
+    for inst in insts:
+        if inst.chi not in picks or batched_sample_flops(inst) < batched_sample_flops(picks[inst.chi]):
+            picks[inst.chi] = inst
+    done_flops, wall = 0.0, 0.0
+    for chi, inst in sorted(picks.items()):
+        o = orc.Oracle(inst)
+        warm = inputs.initial_spins(seed + 3, 1, inst.n_spins)
+        wm, we = o.init_chains(warm)
+        o.mcmc(seed, warm, wm, we, 0, 1, measure_every=1, threads=1)
+        spins = inputs.initial_spins(seed + chi, cores, inst.n_spins)
+        mant, ex = o.init_chains(spins)
+        t0 = time.perf_counter()
+        o.mcmc(seed, spins, mant, ex, 0, 1, measure_every=1, threads=cores)
+        wall += time.perf_counter() - t0
+        done_flops += cores * batched_sample_flops(inst)
+    mean_flops = sum(batched_sample_flops(i) for i in insts) / len(insts)
+    return {"value": done_flops / wall / mean_flops, "unit": "samples/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"one chain per thread x 1 sweep + E_loc of the smallest instance of each chi "
+                      f"({sorted(picks)}), {wall:.1f} s wall; its flop rate over the workload's mean "
+                      f"{mean_flops:.3g} algorithmic flops per sample"}
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -554,12 +595,31 @@ def run_batched(args):
     e1.record(stream)
     torch.cuda.synchronize()
     sep_ms = e0.elapsed_time(e1)
-    flops = 0.0
-    for inst in insts:
-        N, R, chi = inst.n_spins, inst.path.shape[0] // inst.n_spins, inst.chi
-        steps = site_steps(N, R, "simt_sweep") + site_steps(N, R, "simt_right_env") + \
-            site_steps(N, R, "simt_rows")
-        flops += per * steps * 2.0 * chi * chi
+    flops = sum(per * batched_sample_flops(inst) for inst in insts)
+    # end to end: each step's spins and chain states from pinned host buffers,
+    # its energies, spins and states back to them
+    e2e = None
+    if not args.no_e2e:
+        sp_h = spins.cpu().pin_memory()
+        st_h = st.cpu().pin_memory()
+        e_h = torch.empty(b.total_chains, dtype=torch.float64).pin_memory()
+        sp_d, st_d = torch.empty_like(spins), torch.empty_like(st)
+        ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        for t in range(K):
+            ee[t][0].record(stream)
+            sp_d.copy_(sp_h, non_blocking=True)
+            st_d.copy_(st_h, non_blocking=True)
+            b.step(sp_d, st_d, W + K + t, e)
+            e_h.copy_(e, non_blocking=True)
+            sp_h.copy_(sp_d, non_blocking=True)
+            st_h.copy_(st_d, non_blocking=True)
+            ee[t][1].record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = sum(a.elapsed_time(z) for a, z in ee)
+        nbytes = spins.numel() + st.numel() * st.element_size()
+        e2e = {"value": b.total_chains * K / (e2e_ms / 1e3), "unit": "samples/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8 * b.total_chains}
     achieved = flops / (ms / K / 1e3) / 1e12
     peaks, kind = measured_peaks()
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -575,8 +635,10 @@ def run_batched(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "k_batch",
                      "peak_source": "fp32 CUDA-core fma peak"},
-        "gpu_launches": K, "clocks": clk,
+        "gpu_launches": K, "clocks": clk, "e2e": e2e,
     }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_batched(insts, per, 22722)
     print(json.dumps(line), flush=True)
     for m in handles:
         m.close()

@@ -12,6 +12,7 @@ import torch
 
 from oracle import oracle as orc
 from paper_2604_22718_gb300 import inputs
+from parity_util import eps_site, local_energy_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -99,8 +100,52 @@ def test_batch_sampled_chains_against_oracle():
         # the step measures the configuration it starts from
         s_in = spins0[so:so + chains[i] * N].reshape(chains[i], N)[pick]
         e_o = o.local_energies(s_in, threads=2)
-        scale = inst.bonds.shape[0] + inst.h * N
-        assert np.all(np.abs(e[co + np.array(pick)] - e_o) <= 1e-4 * scale), (i, e[co + np.array(pick)], e_o)
+        # FP32 rows: every ratio within |r| (chi + 1) u_32 (K(s) + K(s^(i)))
+        _, r_o = o.local_energies(s_in, with_ratios=True, threads=2)
+        bound = local_energy_bound(o, s_in, r_o, eps_site(inst.chi, "fp32"), inst.J, inst.h,
+                                   inst.bonds.shape[0])
+        assert np.all(np.abs(e[co + np.array(pick)] - e_o) <= bound), (i, e[co + np.array(pick)], e_o, bound)
+
+
+def test_batch_chi256_and_12x12_r4_instances():
+    """The batched workload's extremes in one launch: a chi = 256 instance (4x4,
+    R = 2) and the largest lattice with the most replicas (12x12, R = 4, L =
+    576, chi = 32).  Each reproduces a single FP32 handle bit for bit over two
+    steps, and picked chains' measured energies lie within their FP32 bound of
+    the FP64 oracle."""
+    from paper_2604_22718_gb300 import rtt
+    insts = [inputs.make_instance(4, 4, 2, 256, 3.1, seed=81), inputs.make_instance(12, 12, 4, 32, 2.7, seed=82)]
+    chains = [40, 33]
+    seeds = [11, 12]
+    with rtt.RTTBatch(insts, chains, seeds=seeds) as b:
+        spins0 = np.concatenate([inputs.initial_spins(83 + i, c, inst.n_spins).ravel()
+                                 for i, (inst, c) in enumerate(zip(insts, chains))])
+        sp = torch.from_numpy(spins0.copy()).cuda()
+        st = b.init(sp)
+        e = torch.empty(b.total_chains, dtype=torch.float64, device="cuda")
+        acc = torch.zeros(b.total_chains, dtype=torch.int64, device="cuda")
+        traces = []
+        for t in range(2):
+            b.step(sp, st, t, e, acc)
+            traces.append(e.clone())
+        torch.cuda.synchronize()
+        tr = torch.stack(traces).cpu().numpy()
+        sp, st, acc = sp.cpu().numpy(), st.cpu().numpy(), acc.cpu().numpy()
+    for i, inst in enumerate(insts):
+        co, so, B, N = int(b.chain_off[i]), int(b.spin_off[i]), chains[i], inst.n_spins
+        s_in = spins0[so:so + B * N].reshape(B, N)
+        s_ref, st_ref, tr_ref, acc_ref = _single_reference(rtt, inst, seeds[i], s_in, 2, 0)
+        assert np.array_equal(sp[so:so + B * N].reshape(B, N), s_ref), i
+        assert np.array_equal(st[co:co + B], st_ref), i
+        assert np.array_equal(acc[co:co + B], acc_ref), i
+        assert np.array_equal(tr[:, co:co + B], tr_ref), i
+        o = orc.Oracle(inst)
+        pick = [0, B - 1]
+        e_o, r_o = o.local_energies(s_in[pick], with_ratios=True, threads=2)
+        bound = local_energy_bound(o, s_in[pick], r_o, eps_site(inst.chi, "fp32"), inst.J, inst.h,
+                                   inst.bonds.shape[0])
+        print(inst.chi, inst.n_spins, "E_loc", tr[0, co + np.array(pick)], e_o, "bound", bound)
+        assert np.all(np.abs(tr[0, co + np.array(pick)] - e_o) <= bound), i
 
 
 def test_batch_rejects_non_fp32_and_small_chi():
