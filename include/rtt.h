@@ -32,8 +32,10 @@
  *     run everywhere.  General paths (the replicas visit the spins in
  *     different orders, e.g. sigma^V + sigma^H + sigma^D + sigma^D' -- the
  *     path sums of Sec. 2.2.1) run on FP64/FP32 handles, and on BF16X3/FP16X3
- *     handles for amplitudes and local energies and, with chi = 64 and R >= 2,
- *     for sweeps; the batched form and rtt_local_energy_noalloc need periodic
+ *     handles for amplitudes and local energies and, with R >= 2, for sweeps
+ *     (at chi = 128 when the batch's CTA pairs, two SMs per 128 chains, fit on
+ *     the GPU at once; RTT_ERR_UNSUPPORTED otherwise); the batched form and
+ *     rtt_local_energy_noalloc need periodic
  *     paths.  Each flip row of a general path spans its spin's first to last
  *     site, and a sweep rebuilds the part after the last site per proposal.
  *   - Errors: argument errors are detected before anything is launched and

@@ -2786,18 +2786,19 @@ rtt_status tc_sweep(rtt_s *h, uint8_t *spins, rtt_chain_state *state, int64_t B,
     a.n_accept = n_accept;
     cudaError_t e;
     prof_begin(h, KID_TC_SWEEP, st);
-    if (!h->periodic && !(p->chi == 64 && h->R >= 2 && h->N >= 2)) {
-        prof_end(h, KID_TC_SWEEP, st);
-        rtt_set_error("rtt_mcmc_sweep: tensor-core sweeps on a general path need chi = 64 and "
-                      "at least two replicas");
-        return RTT_ERR_UNSUPPORTED;
-    }
     const size_t smem_pair128 = std::max(tcd::spp_smem(h->N, h->L), (size_t)164 * 1024);
     int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (p->chi == 128 && h->periodic && h->R >= 2 && h->N >= 2 && smem_pair128 <= (size_t)227 * 1024 &&
-        2 * (int64_t)tiles(B) <= (int64_t)n_sm) {
+    const bool pair128 = p->chi == 128 && h->R >= 2 && h->N >= 2 && smem_pair128 <= (size_t)227 * 1024 &&
+                         2 * (int64_t)tiles(B) <= (int64_t)n_sm;
+    if (!h->periodic && !(p->chi == 64 && h->R >= 2 && h->N >= 2) && !pair128) {
+        prof_end(h, KID_TC_SWEEP, st);
+        rtt_set_error("rtt_mcmc_sweep: tensor-core sweeps on a general path need at least two "
+                      "replicas, and at chi = 128 a batch whose CTA pairs fit on the GPU at once");
+        return RTT_ERR_UNSUPPORTED;
+    }
+    if (pair128) {
         // split-row sweep on CTA pairs with the sparse site products, while the
         // pairs fit on the GPU at once (measured: 64 tiles of 16x16 chains run
         // 1.8x faster than on single tiles; 128 tiles of 10x10 chains, two
@@ -2809,7 +2810,10 @@ rtt_status tc_sweep(rtt_s *h, uint8_t *spins, rtt_chain_state *state, int64_t B,
             if (err == cudaSuccess) kern<<<2 * tiles(B), tcd::SPP_THREADS, smem_pair128, st>>>(p->map_sp, a);
             return err;
         };
-        e = p->f16 ? go(tcd::k_sp_pair<true, false>) : go(tcd::k_sp_pair<false, false>);
+        if (h->periodic)
+            e = p->f16 ? go(tcd::k_sp_pair<true, false>) : go(tcd::k_sp_pair<false, false>);
+        else
+            e = p->f16 ? go(tcd::k_sp_pair<true, true>) : go(tcd::k_sp_pair<false, true>);
         if (e == cudaSuccess) e = cudaGetLastError();
     } else if (p->chi == 64 && h->R >= 2 && h->N >= 2) {
         // split-row sweep on CTA pairs.  At least 164 KB of shared memory: no

@@ -108,12 +108,6 @@ def test_mixed_energy_between_periodic_and_general_paths_bit_exact():
 
 def test_general_path_rejected_where_unsupported():
     rtt = _rtt()
-    inst = inputs.make_path_instance(4, 4, ("V", "H"), 128, 3.0, seed=38)
-    with rtt.RTT(inst, "fp16x3") as m:          # chi = 128: no split-row sweep
-        sg = torch.from_numpy(inputs.initial_spins(1, 8, 16)).cuda()
-        _, _, st = m.log_amplitudes(sg)
-        with pytest.raises(rtt.RTTError):
-            m.mcmc_sweep(sg, st, 0, 1)
     with pytest.raises(rtt.RTTError):
         rtt.RTTBatch([inputs.make_path_instance(6, 6, ("V", "H"), 32, 3.0, seed=39)], [8])
 
@@ -160,17 +154,21 @@ def test_fp16x3_general_path_amplitudes_and_energies(lx, ly, names, chi, B):
     assert rel_mean <= 1e-4, rel_mean
 
 
-def test_fp16x3_general_path_sweep_follows_oracle():
-    """The general split-row sweep (chi = 64, sigma^V + sigma^H + sigma^D +
-    sigma^D'): every decision of one sweep over three row tiles is the FP64
-    rule's at the same state except at explained near ties; tracked amplitudes
-    stay those of the spins; the measured trace is the standalone energy of the
-    entering configurations."""
+@pytest.mark.parametrize("case", ["vhdd_6x6_chi64", "vh_4x4_chi128"])
+def test_fp16x3_general_path_sweep_follows_oracle(case):
+    """The general split-row sweeps on CTA pairs (chi = 64 dense, sigma^V +
+    sigma^H + sigma^D + sigma^D', three row tiles; chi = 128 sparse, sigma^V +
+    sigma^H, two row tiles): every decision of one sweep is the FP64 rule's at
+    the same state except at explained near ties; tracked amplitudes stay those
+    of the spins; the measured trace is the standalone energy of the entering
+    configurations."""
     rtt = _rtt()
-    inst = inputs.workload("vhdd_6x6")
+    if case == "vhdd_6x6_chi64":
+        inst, B = inputs.workload("vhdd_6x6"), 300
+    else:
+        inst, B = inputs.make_path_instance(4, 4, ("V", "H"), 128, 3.0, seed=38), 200
     o = orc.Oracle(inst)
-    B = 300
-    s0 = inputs.initial_spins(63, B, 36)
+    s0 = inputs.initial_spins(63, B, inst.n_spins)
     with rtt.RTT(inst, "fp16x3", seed=17) as m:
         sg = torch.from_numpy(s0.copy()).cuda()
         _, _, st = m.log_amplitudes(sg)
@@ -182,7 +180,7 @@ def test_fp16x3_general_path_sweep_follows_oracle():
         la_now = m.log_amplitudes(sg)[0].cpu().numpy()
         torch.cuda.synchronize()
     s1 = sg.cpu().numpy()
-    eps = eps_site(64, "fp16x3")
+    eps = eps_site(inst.chi, "fp16x3")
     n, nd, worst = check_sweep_divergences(o, 17, s0, s1, 0, eps, slack=2.0 ** -23)
     print(f"general path sweep: {nd} of {n} decisions differ, worst gap/tolerance {worst:.3f}")
     d = np.abs(la_track - la_now)
