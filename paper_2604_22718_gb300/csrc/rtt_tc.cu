@@ -186,28 +186,6 @@ __device__ __forceinline__ void tmem_ld_64(uint32_t t, float (&y)[64]) {
         y[32 + i] = __uint_as_float(x1[i]);
     }
 }
-// The exponent the per-site renormalisation takes out of the row held in the
-// accumulator at t: max|v| brought into [1, 2) by 2^-e, or 0 when every row of
-// the warp keeps its scale (max in [1, 2^8): its 16-bit split stays inside
-// FP16's normal range with full precision relative to the max, and the next
-// site's FP32 accumulator is looked at again).  Eight partial maxima.
-template <int CHI>
-__device__ __forceinline__ int acc_exponent(uint32_t t) {
-    float m[8];
-#pragma unroll
-    for (int c = 0; c < CHI / 64; ++c) {
-        float y[64];
-        tmem_ld_64(t + 64 * c, y);
-#pragma unroll
-        for (int i = 0; i < 64; ++i) m[i & 7] = (c == 0 && i < 8) ? fabsf(y[i]) : fmaxf(m[i & 7], fabsf(y[i]));
-    }
-    const float mx = fmaxf(fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3])),
-                           fmaxf(fmaxf(m[4], m[5]), fmaxf(m[6], m[7])));
-    const bool usable = (mx > 0.f) && isfinite(mx);
-    const int e = usable ? rttd::exponent_of(mx) : 0;
-    if (__all_sync(FULL, !usable || (e >= 0 && e < 8))) return 0;
-    return usable ? e : 0;
-}
 // y <- y 2^-e (exact; e = 0 leaves y)
 __device__ __forceinline__ void scale_chunk(float (&y)[64], int e) {
     if (e == 0) return;
@@ -329,16 +307,6 @@ __device__ __forceinline__ void write_A_chunk(uint32_t t_hi, int c, const float 
 #pragma unroll
     for (int p = 0; p < 32; ++p) split2<F16>(y[2 * p], y[2 * p + 1], h[p], l[p]);
     tmem_st_2x32(t_hi + (uint32_t)(32 * c), t_hi + (uint32_t)(CHI / 2 + 32 * c), h, l);
-}
-// The A operand from a row in global memory (chunk by chunk).
-template <int CHI, bool F16>
-__device__ __forceinline__ void write_A_from(uint32_t t_hi, const float *__restrict__ p) {
-#pragma unroll
-    for (int c = 0; c < CHI / 64; ++c) {
-        float y[64];
-        load_chunk(p + 64 * c, y);
-        write_A_chunk<CHI, F16>(t_hi, c, y);
-    }
 }
 
 // D (+)= A . B with A read from TMEM (K-major rows in TMEM lanes) and B from a
@@ -980,7 +948,6 @@ __global__ void __launch_bounds__(32, 1) k_wait_selftest(int *err, long long lim
 // with the current spins, so no right environment is kept.
 constexpr int SP_HAND = 64 * NT * 4;  // right half-rows, [64][128] floats
 
-__device__ __forceinline__ void named_sync_256() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ void named_arrive(int id, int n) {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
@@ -1119,11 +1086,6 @@ __device__ __forceinline__ uint32_t peer_addr(uint32_t addr, uint32_t rank) {
     uint32_t out;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(addr), "r"(rank));
     return out;
-}
-__device__ __forceinline__ void st_cluster_v4(uint32_t addr, float a, float b, float c, float d) {
-    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b),
-                 "f"(c), "f"(d)
-                 : "memory");
 }
 __device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
