@@ -2116,9 +2116,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPP_THREADS, 1)
 // barrier per tile.
 constexpr int R2_THREADS = NT + 64;
 
+// at least 164 KB, so that no other tensor-memory kernel shares the SM
+template <int CHI>
 inline size_t rows2_smem(int N, int L) {
-    return 1024 + (size_t)SCfg<128>::NSTG * SCfg<128>::STAGE + (size_t)2 * NT * 128 * 2 + 128 +
-           (size_t)32 * N + (size_t)4 * L;
+    return std::max(1024 + (size_t)SCfg<CHI>::NSTG * SCfg<CHI>::STAGE + (size_t)2 * NT * CHI * 2 + 128 +
+                        (size_t)32 * N + (size_t)4 * L,
+                    (size_t)164 * 1024);
 }
 
 // D (+)= A . B with A 2:4 sparse, its compressed entries read from shared
@@ -2143,15 +2146,14 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
                  : "memory");
 }
 
-template <bool F16>
+template <int CHI, bool F16>
 __global__ void __launch_bounds__(R2_THREADS, 1)
     k_rows2(const __grid_constant__ CUtensorMap map, const Args a) {
-    constexpr int CHI = 128;
     using C = SCfg<CHI, F16>;
     constexpr int NSG = C::NSTG;
-    constexpr int CPT = 2;
+    constexpr int CPT = CHI / 64;
     constexpr uint32_t ATOM = (uint32_t)NT * 128;  // one 64-entry K atom of 128 rows
-    constexpr uint32_t ALO = 2 * ATOM;             // one tile's lo operand
+    constexpr uint32_t ALO = CPT * ATOM;           // one tile's lo operand
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t stage0 = sa(base);
@@ -2682,8 +2684,8 @@ rtt_status tc_rows(rtt_s *h, const uint8_t *spins, int64_t B, cudaStream_t st) {
     a.spins_in = spins;
     prof_begin(h, KID_TC_ROWS, st);
     cudaError_t e;
-    const size_t smem2 = tcd::rows2_smem(h->N, h->L);
-    if (h->tc->chi == 128 && smem2 <= (size_t)227 * 1024) {
+    const size_t smem2 = h->tc->chi == 128 ? tcd::rows2_smem<128>(h->N, h->L) : tcd::rows2_smem<64>(h->N, h->L);
+    if (smem2 <= (size_t)227 * 1024) {
         // two tiles per CTA (one tile's epilogue beside the other's MMAs)
         auto go = [&](auto kern) {
             cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
@@ -2691,7 +2693,10 @@ rtt_status tc_rows(rtt_s *h, const uint8_t *spins, int64_t B, cudaStream_t st) {
                 kern<<<dim3((tiles(B) + 1) / 2, h->N + 1), tcd::R2_THREADS, smem2, st>>>(h->tc->map_sp, a);
             return err;
         };
-        e = h->tc->f16 ? go(tcd::k_rows2<true>) : go(tcd::k_rows2<false>);
+        if (h->tc->chi == 128)
+            e = h->tc->f16 ? go(tcd::k_rows2<128, true>) : go(tcd::k_rows2<128, false>);
+        else
+            e = h->tc->f16 ? go(tcd::k_rows2<64, true>) : go(tcd::k_rows2<64, false>);
         if (e == cudaSuccess) e = cudaGetLastError();
     } else {
         e = launch_chi<tcd::M_ROWS>(h->tc, a, dim3(tiles(B), h->N + 1), st);
