@@ -1590,7 +1590,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SPC_THREADS, 1)
 // bounded; both CTAs meet in a cluster barrier before they exit.
 constexpr int SPP_THREADS = NT + 32;
 constexpr int SPP_HAND = NT * 128 * 4;        // one right half-row hand-off, [128][128] floats
-constexpr int kPairLeftLess128 = -1;          // sites the left tile takes below half a row
+constexpr int kPairLeftLess128 = 1;           // sites the left tile takes below half a row
 
 inline size_t spp_smem(int N, int L) {
     return 1024 + (size_t)SCfg<128>::NSTG * SCfg<128>::STAGE + SPP_HAND + 4 * NT + 128 +
