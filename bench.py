@@ -544,8 +544,10 @@ def run_ours(args):
 
 def run_batched(args):
     """Batched form: the 64-instance workload (lattices {4,6,8,12}^2, R {2,3,4},
-    chi {32,64,128,256}, h ~ U[2.5,3.5], FP32), one persistent launch per step,
-    against the same instances run as separate per-instance launches."""
+    chi {32,64,128,256}, h ~ U[2.5,3.5]): the FP32 instances in one persistent
+    launch per step and, unless --precision fp32, the chi 64 / 128 instances in
+    the split precision on the tensor cores; against the same instances run as
+    separate per-instance launches."""
     import torch
     from paper_2604_22718_gb300 import inputs, rtt
     torch.cuda.set_device(0)
@@ -553,7 +555,10 @@ def run_batched(args):
     per = args.chains or 1024
     chains = [per] * len(insts)
     K, W = args.steps, args.warmup
-    b = rtt.RTTBatch(insts, chains)
+    tc_prec = args.precision if args.precision in ("fp16x3", "bf16x3") else None
+    precs = [tc_prec if (tc_prec and inst.chi in (64, 128)) else "fp32" for inst in insts]
+    n_tc = sum(p != "fp32" for p in precs)
+    b = rtt.RTTBatch(insts, chains, precisions=precs)
     cache = os.path.join(ROOT, "paper_2604_22718_gb300", "_build", "batch_tiles.json")
     os.makedirs(os.path.dirname(cache), exist_ok=True)
     t0 = time.perf_counter()
@@ -579,7 +584,7 @@ def run_batched(args):
     ms = sum(a.elapsed_time(z) for a, z in ev)
     value = b.total_chains * K / (ms / 1e3)
     # the same instances as separate launches (one rtt handle each, one sweep + E_loc)
-    handles = [rtt.RTT(inst, "fp32", seed=22722 + i) for i, inst in enumerate(insts)]
+    handles = [rtt.RTT(inst, precs[i], seed=22722 + i) for i, inst in enumerate(insts)]
     sps, sts, trs = [], [], []
     for i, (m, inst) in enumerate(zip(handles, insts)):
         sp = torch.from_numpy(inputs.initial_spins(3000 + i, per, inst.n_spins)).cuda()
@@ -626,16 +631,20 @@ def run_batched(args):
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": 1, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32" if not tc_prec else f"f32+{tc_prec}", "data": "synthetic",
         "config": {"workload": f"batched64: {len(insts)} instances x {per} chains, lattices "
-                               "{4,6,8,12}^2, R {2,3,4}, chi {32,64,128,256}, one persistent "
-                               "launch per step through a CUDA graph", "chains": b.total_chains},
+                               "{4,6,8,12}^2, R {2,3,4}, chi {32,64,128,256}; FP32 instances in one "
+                               "persistent launch per step through a CUDA graph"
+                               + (f", chi 64 and 128 instances ({n_tc}) in {tc_prec} on the tensor cores"
+                                  if tc_prec else ""), "chains": b.total_chains},
         "separate_launches_ms_per_step": sep_ms, "speedup_vs_separate": sep_ms / (ms / K),
         "tune_s": tune_s,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "k_batch",
-                     "peak_source": "fp32 CUDA-core fma peak"},
-        "gpu_launches": K, "clocks": clk, "e2e": e2e,
+                     "peak_source": "fp32 CUDA-core fma peak; achieved counts the whole step's "
+                                    "algorithmic flops, tensor-core instances included"},
+        # per tensor-core instance and step: sweep, left and right environments, rows, reduction
+        "gpu_launches": K * (1 + 5 * n_tc), "clocks": clk, "e2e": e2e,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_batched(insts, per, 22722)

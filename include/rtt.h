@@ -289,15 +289,17 @@ rtt_status rtt_profile_read(rtt_handle h, rtt_kernel_time *out, int32_t capacity
 
 /* ---------------------------------------------------------------------------
  * Batched form: many independent RTT instances of uneven N, R and chi sampled
- * together.  Each instance is an rtt_desc (FP32 precision, periodic path,
- * 17 <= chi <= 256, all on one device); each gets its own chains.  One call of
- * rtt_batch_step performs one Monte Carlo iteration of every chain of every
- * instance -- the local energy of the configuration it starts from
- * (Sec. 3.3 / Sec. 4 Eq. ising-model), then one systematic sweep (Sec. 3.3)
- * -- in ONE persistent kernel launch
- * (optionally through a CUDA graph).  Results of instance i equal, bit for
- * bit, those of an FP32 rtt_handle of the same description running
- * rtt_mcmc_sweep with chain0 = 0, sweep0 = sweep, measure_every = 1.
+ * together.  Each instance is an rtt_desc (periodic path, all on one device)
+ * and gets its own chains.  FP32 instances (17 <= chi <= 256) run on the CUDA
+ * cores in ONE persistent kernel launch per iteration (optionally through a
+ * CUDA graph); FP16X3 / BF16X3 instances (chi in {64, 128}) run on the tensor
+ * cores, each as one rtt_mcmc_sweep of its own handle on the same stream after
+ * that launch.  One call of rtt_batch_step performs one Monte Carlo iteration
+ * of every chain of every instance -- the local energy of the configuration
+ * it starts from (Sec. 3.3 / Sec. 4 Eq. ising-model), then one systematic
+ * sweep (Sec. 3.3).  Results of instance i equal, bit for bit, those of an
+ * rtt_handle of the same description running rtt_mcmc_sweep with chain0 = 0,
+ * sweep0 = sweep, measure_every = 1.
  *
  * Device buffers are packed instance after instance: spins [sum_i B_i N_i]
  * (instance i at spin offset so_i, chain c at so_i + c N_i), chain state and
@@ -317,8 +319,8 @@ rtt_status rtt_batch_init(rtt_batch b, const uint8_t *spins, rtt_chain_state *st
  * E_loc of the configuration the iteration starts from (measured before its
  * sweep, as rtt_mcmc_sweep measures); n_accept [sum B_i] (or NULL)
  * accumulates acceptances.
- * use_graph != 0 launches through a CUDA graph built on first use (its kernel
- * node is updated per call). */
+ * use_graph != 0 launches the persistent kernel through a CUDA graph built on
+ * first use (its kernel node is updated per call). */
 rtt_status rtt_batch_step(rtt_batch b, uint8_t *spins, rtt_chain_state *state, int64_t sweep,
                           double *e_loc, int64_t *n_accept, int32_t use_graph, void *stream);
 /* Autotuner: for every (chi, L) bucket (L <= 64, <= 256, > 256) time each tile

@@ -50,6 +50,7 @@ struct rtt_batch_s {
     int device = 0;
     int n = 0;
     std::vector<rtt_handle> h;
+    std::vector<char> tc;        // instance on the tensor cores (its own handle's sweep)
     std::vector<int64_t> B, chain_off, spin_off;
     int64_t total_chains = 0, total_spins = 0;
     std::vector<int> G, mult;    // per instance tile shape
@@ -439,8 +440,10 @@ rtt_status rtt_batch_create(const rtt_desc *descs, int32_t n, const int64_t *cha
         return bfail(RTT_ERR_INVALID_ARG, "rtt_batch_create: need descs, chains, out and n >= 1");
     *out = nullptr;
     for (int i = 0; i < n; ++i) {
-        if (descs[i].precision != RTT_FP32)
-            return bfail(RTT_ERR_UNSUPPORTED, "rtt_batch_create: the batched form runs FP32 instances");
+        if (descs[i].precision != RTT_FP32 && descs[i].precision != RTT_FP16X3 &&
+            descs[i].precision != RTT_BF16X3)
+            return bfail(RTT_ERR_UNSUPPORTED, "rtt_batch_create: instances are FP32 (persistent "
+                                              "kernel) or FP16X3 / BF16X3 (tensor cores)");
         if (descs[i].chi > 256 || chains[i] < 1)
             return bfail(RTT_ERR_INVALID_ARG, "rtt_batch_create: chi <= 256 and chains >= 1 required");
         if (descs[i].device != descs[0].device)
@@ -463,7 +466,8 @@ rtt_status rtt_batch_create(const rtt_desc *descs, int32_t n, const int64_t *cha
         rtt_status s = rtt_create(&d, &b->h[i]);
         if (s == RTT_OK && !b->h[i]->periodic)
             s = bfail(RTT_ERR_UNSUPPORTED, "rtt_batch_create: periodic paths only");
-        if (s == RTT_OK && b->h[i]->chip < 32) {
+        const bool on_tc = d.precision != RTT_FP32;
+        if (s == RTT_OK && !on_tc && b->h[i]->chip < 32) {
             rtt_destroy(b->h[i]);
             b->h[i] = nullptr;
             s = bfail(RTT_ERR_UNSUPPORTED, "rtt_batch_create: chi >= 17 required (32-lane rows)");
@@ -480,7 +484,8 @@ rtt_status rtt_batch_create(const rtt_desc *descs, int32_t n, const int64_t *cha
         b->total_spins += chains[i] * b->h[i]->N;
         b->G.push_back(32);
         b->mult.push_back(1);
-        nmax = std::max(nmax, b->h[i]->N);
+        b->tc.push_back(on_tc ? 1 : 0);
+        if (!on_tc) nmax = std::max(nmax, b->h[i]->N);
     }
     cudaError_t e = cudaMalloc((void **)&b->d_counter, sizeof(unsigned long long));
     if (e != cudaSuccess) {
@@ -496,8 +501,9 @@ rtt_status rtt_batch_create(const rtt_desc *descs, int32_t n, const int64_t *cha
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bt::k_batch, bt::NTB, b->smem);
     b->grid = std::max(1, sms * std::max(per, 1));
     rtt_status s = upload_insts(b);
-    std::vector<int> all(n);
-    for (int i = 0; i < n; ++i) all[i] = i;
+    std::vector<int> all;  // the persistent kernel's instances
+    for (int i = 0; i < n; ++i)
+        if (!b->tc[i]) all.push_back(i);
     if (s == RTT_OK) s = build_items(b, all, INT64_MAX);
     if (s != RTT_OK) {
         rtt_batch_destroy(b);
@@ -553,8 +559,24 @@ rtt_status rtt_batch_step(rtt_batch b, uint8_t *spins, rtt_chain_state *state, i
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bcuda(e, "rtt_batch_step: pending error");
+    // the tensor-core instances: one sweep of each on its own handle, measuring
+    // the configuration it starts from (as the persistent kernel does), into
+    // the instance's slices of the batch's arrays, after the persistent launch
+    auto tc_steps = [&]() -> rtt_status {
+        for (int i = 0; i < b->n; ++i) {
+            if (!b->tc[i]) continue;
+            rtt_status s = rtt_mcmc_sweep(b->h[i], spins + b->spin_off[i], state + b->chain_off[i],
+                                          b->B[i], 0, sweep, 1, 1, e_loc + b->chain_off[i],
+                                          n_accept ? n_accept + b->chain_off[i] : nullptr, stream);
+            if (s != RTT_OK) return s;
+        }
+        return RTT_OK;
+    };
     bt::StepArgs p = step_args(b, spins, state, sweep, e_loc, n_accept);
-    if (!use_graph || b->n_items == 0) return direct_launch(b, p, st);
+    if (!use_graph || b->n_items == 0) {
+        rtt_status s = direct_launch(b, p, st);
+        return s == RTT_OK ? tc_steps() : s;
+    }
     if (b->exec && (b->g_spins != spins || b->g_state != state || b->g_eloc != e_loc ||
                     b->g_acc != (void *)n_accept))
         drop_graph(b);
@@ -581,7 +603,7 @@ rtt_status rtt_batch_step(rtt_batch b, uint8_t *spins, rtt_chain_state *state, i
     }
     if ((e = cudaGraphLaunch(b->exec, st)) != cudaSuccess) return bcuda(e, "graph launch");
     b->base += (unsigned long long)b->n_items + (unsigned long long)b->grid;
-    return RTT_OK;
+    return tc_steps();
 }
 
 // Autotuner: per (chi, L) bucket, time each candidate tile shape (lanes per
@@ -595,7 +617,8 @@ rtt_status rtt_batch_tune(rtt_batch b, const char *cache_path, int32_t probe_cha
     DevGuard guard(b->device);
     cudaStream_t st = (cudaStream_t)stream;
     std::map<std::pair<int, int>, std::vector<int>> buckets;
-    for (int i = 0; i < b->n; ++i) buckets[{b->h[i]->chip, lbucket(b->h[i]->L)}].push_back(i);
+    for (int i = 0; i < b->n; ++i)
+        if (!b->tc[i]) buckets[{b->h[i]->chip, lbucket(b->h[i]->L)}].push_back(i);
     std::map<std::pair<int, int>, std::pair<int, int>> chosen;  // -> (G, mult)
     std::map<std::pair<int, int>, double> best_ms;
     if (cache_path) {
@@ -692,8 +715,9 @@ rtt_status rtt_batch_tune(rtt_batch b, const char *cache_path, int32_t probe_cha
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bcuda(e, "tune sync");
     drop_graph(b);
     if ((s = upload_insts(b)) != RTT_OK) return s;
-    std::vector<int> all(b->n);
-    for (int i = 0; i < b->n; ++i) all[i] = i;
+    std::vector<int> all;
+    for (int i = 0; i < b->n; ++i)
+        if (!b->tc[i]) all.push_back(i);
     if ((s = build_items(b, all, INT64_MAX)) != RTT_OK) return s;
     if (cache_path) {
         FILE *f = fopen(cache_path, "w");

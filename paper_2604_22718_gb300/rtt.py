@@ -408,9 +408,11 @@ def mcmc_uniforms(seed: int, counters: torch.Tensor, stream=None) -> torch.Tenso
 
 
 class RTTBatch:
-    """Many FP32 RTT instances sampled by one persistent kernel per iteration."""
+    """Many RTT instances sampled together: FP32 ones by one persistent kernel
+    per iteration, FP16X3 / BF16X3 ones (chi 64 or 128) on the tensor cores.
+    precisions: one name per instance ("fp32", "fp16x3", "bf16x3"), default FP32."""
 
-    def __init__(self, instances, chains, device: int | None = None, seeds=None):
+    def __init__(self, instances, chains, device: int | None = None, seeds=None, precisions=None):
         n = len(instances)
         chains = [int(c) for c in (chains if hasattr(chains, "__len__") else [chains] * n)]
         self.instances = list(instances)
@@ -429,7 +431,8 @@ class RTTBatch:
             descs[i] = _Desc(int(inst.n_spins), t.shape[0], t.shape[2], bonds.shape[0],
                              path.ctypes.data, t.ctypes.data, bl.ctypes.data, br.ctypes.data,
                              bonds.ctypes.data if bonds.size else None, float(inst.J),
-                             float(inst.h), RTT_FP32, self.device, seed)
+                             float(inst.h), PRECISIONS[precisions[i]] if precisions else RTT_FP32,
+                             self.device, seed)
         self._chains = np.asarray(chains, dtype=np.int64)
         b = ctypes.c_void_p()
         _check(lib().rtt_batch_create(descs, n, self._chains.ctypes.data, ctypes.byref(b)),

@@ -148,8 +148,70 @@ def test_batch_chi256_and_12x12_r4_instances():
         assert np.all(np.abs(tr[0, co + np.array(pick)] - e_o) <= bound), i
 
 
-def test_batch_rejects_non_fp32_and_small_chi():
+def test_batch_rejects_unsupported_instances():
     from paper_2604_22718_gb300 import rtt
     tiny = inputs.make_instance(3, 3, 2, 8, 3.0, seed=1, mixing=False)
     with pytest.raises(rtt.RTTError):
-        rtt.RTTBatch([tiny], [4])
+        rtt.RTTBatch([tiny], [4])                                   # chi < 17 on the CUDA cores
+    small = inputs.make_instance(3, 3, 2, 32, 3.0, seed=2)
+    with pytest.raises(rtt.RTTError):
+        rtt.RTTBatch([small], [4], precisions=["fp64"])             # FP64 is not batched
+    with pytest.raises(rtt.RTTError):
+        rtt.RTTBatch([small], [4], precisions=["fp16x3"])           # tensor cores need chi 64 or 128
+
+
+def _single_reference_prec(rtt, inst, prec, seed, spins, n_steps, sweep0):
+    B = spins.shape[0]
+    with rtt.RTT(inst, prec, seed=seed) as m:
+        sg = torch.from_numpy(spins.copy()).cuda()
+        _, _, st = m.log_amplitudes(sg)
+        tr = torch.empty((n_steps, B), dtype=torch.float64, device="cuda")
+        acc = torch.zeros(B, dtype=torch.int64, device="cuda")
+        for t in range(n_steps):
+            m.mcmc_sweep(sg, st, sweep0 + t, 1, 1, tr[t:t + 1], acc)
+        torch.cuda.synchronize()
+        return sg.cpu().numpy(), st.cpu().numpy(), tr.cpu().numpy(), acc.cpu().numpy()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_tensor_core_instances(use_graph):
+    """FP16X3 instances (chi 64 and 128) beside FP32 ones: every instance
+    reproduces a single handle of its own precision bit for bit over three
+    steps (ragged chain counts), and the tensor-core instances' measured
+    energies lie within their split bound of the FP64 oracle."""
+    from paper_2604_22718_gb300 import rtt
+    insts = [inputs.make_instance(4, 4, 2, 32, 3.0, seed=91), inputs.make_instance(4, 4, 3, 64, 2.9, seed=92),
+             inputs.make_instance(4, 4, 2, 128, 3.1, seed=93), inputs.make_instance(3, 4, 2, 128, 3.0, seed=94)]
+    precs = ["fp32", "fp16x3", "fp16x3", "fp32"]
+    chains = [45, 150, 70, 33]
+    seeds = [21, 22, 23, 24]
+    n_steps = 3
+    with rtt.RTTBatch(insts, chains, seeds=seeds, precisions=precs) as b:
+        spins0 = np.concatenate([inputs.initial_spins(95 + i, c, inst.n_spins).ravel()
+                                 for i, (inst, c) in enumerate(zip(insts, chains))])
+        sp = torch.from_numpy(spins0.copy()).cuda()
+        st = b.init(sp)
+        e = torch.empty(b.total_chains, dtype=torch.float64, device="cuda")
+        acc = torch.zeros(b.total_chains, dtype=torch.int64, device="cuda")
+        traces = []
+        for t in range(n_steps):
+            b.step(sp, st, 7 + t, e, acc, use_graph=use_graph)
+            traces.append(e.clone())
+        torch.cuda.synchronize()
+        tr = torch.stack(traces).cpu().numpy()
+        sp, st, acc = sp.cpu().numpy(), st.cpu().numpy(), acc.cpu().numpy()
+    for i, inst in enumerate(insts):
+        co, so, B, N = int(b.chain_off[i]), int(b.spin_off[i]), chains[i], inst.n_spins
+        s_in = spins0[so:so + B * N].reshape(B, N)
+        s_ref, st_ref, tr_ref, acc_ref = _single_reference_prec(rtt, inst, precs[i], seeds[i], s_in, n_steps, 7)
+        assert np.array_equal(sp[so:so + B * N].reshape(B, N), s_ref), i
+        assert np.array_equal(st[co:co + B], st_ref), i
+        assert np.array_equal(acc[co:co + B], acc_ref), i
+        assert np.array_equal(tr[:, co:co + B], tr_ref), i
+        if precs[i] == "fp16x3":
+            o = orc.Oracle(inst)
+            pick = [0, B - 1]
+            e_o, r_o = o.local_energies(s_in[pick], with_ratios=True, threads=2)
+            bound = local_energy_bound(o, s_in[pick], r_o, eps_site(inst.chi, "fp16x3"), inst.J, inst.h,
+                                       inst.bonds.shape[0])
+            assert np.all(np.abs(tr[0, co + np.array(pick)] - e_o) <= bound), i
